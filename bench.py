@@ -1,0 +1,391 @@
+"""Benchmark of the partition-method solver on one GB300 (or N replicas).
+
+Default workload: block tridiagonal A x = f with m = 16 blocks, N = 16384 block
+rows (n = 262144 unknowns) and 8 right-hand sides; D_j = 4I + G/4, B_j, C_j =
+G/4 (seeded synthetic data).  One step = the whole hot path on one system:
+factor (local block LU with spikes, reduced systems, recursion) + solve, for
+two paths: "fp64" (every step in FP64) and "fp32_ir" (FP32 local factors, FP64
+reduced systems, FP64-residual iterative refinement).  The headline value is
+the faster path whose normwise relative error against the FP64 oracle is
+<= 1e-10.  Metric: unknowns x right-hand sides solved per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload block16|babd8|scalar]
+
+--impl reference times the FP64 CPU oracle on the same workload (the
+baseline of this project).  With N > 1 (torchrun), every rank solves its own
+replica (replicas only, weak scaling); timings are max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "unknowns solved/s at rel err <=1e-10 vs plain FP64"
+UNIT = "unknowns*rhs/s"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+
+
+def _workload(name: str):
+    import gen
+    if name == "block16":
+        N, m, nr = 16384, 16, 8
+        s = gen.btri_random(N, m, nr, seed_rep=0)
+        return dict(kind="btri", N=N, m=m, nrhs=nr, sys=s, unknowns=N * m * nr,
+                    desc="block tridiagonal m=16, N=16384 block rows (n=262144), 8 RHS; D=4I+G/4, B,C=G/4")
+    if name == "babd8":
+        N, m, nr = 1 << 18, 8, 1
+        b = gen.babd_bvp(N, m, nr, seed_rep=0)
+        return dict(kind="babd", N=N, m=m, nrhs=nr, sys=b, unknowns=(N + 1) * m * nr,
+                    desc="BABD trapezoidal BVP m=8, N=2^18 steps (n=2097160), 1 RHS")
+    if name == "scalar":
+        n = 1 << 16
+        t = gen.tri_sdd(n, 1, seed_rep=0)
+        s = gen.BtriSystem(t.dl.reshape(n, 1, 1), t.d.reshape(n, 1, 1), t.du.reshape(n, 1, 1), t.f, t.xstar)
+        return dict(kind="btri", N=n, m=1, nrhs=1, sys=s, unknowns=n,
+                    desc="scalar tridiagonal n=2^16, d~U[4,6], dl,du~U[-1,1], 1 RHS")
+    raise SystemExit(f"unknown workload {name}")
+
+
+def _factor_flops_per_row(m: int) -> float:
+    # algorithmic count per local block row: block-Thomas factorization
+    # (2/3 + 2 + 2) m^3 plus the left spike 4 m^3
+    return (2.0 / 3.0 + 2.0 + 2.0 + 4.0) * m ** 3
+
+
+def _clock_sampler(stop_evt, out_rows):
+    cmd = ["nvidia-smi",
+           "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-lms", "100"]
+    try:
+        idx = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except Exception:
+        return
+    try:
+        while not stop_evt.is_set():
+            line = p.stdout.readline()
+            if not line:
+                break
+            out_rows.append(line.strip())
+    finally:
+        p.terminate()
+        try:
+            p.wait(timeout=2)
+        except Exception:
+            p.kill()
+
+
+def _clocks_summary(rows, local_rank=0):
+    vals, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in rows:
+        f = [x.strip() for x in r.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            if int(f[0]) != local_rank and len(rows) > 0:
+                pass
+            vals.append(float(f[1]))
+            mx = float(f[2])
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not vals:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+    return {"sm_mhz": statistics.median(vals), "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(vals)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    w = _workload(args.workload)
+    s = w["sys"]
+
+    def step():
+        if w["kind"] == "btri":
+            return oracle.btri_solve(s.B, s.D, s.C, s.F)
+        return oracle.babd_solve(s.S, s.R, s.B0, s.B1, s.RHS)
+
+    for _ in range(args.warmup):
+        step()
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        step()
+        t.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(t) / len(t)
+    val = w["unknowns"] / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "path": "sequential FP64 oracle (block Thomas / BABD GEPP), 1 core"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"the full workload, {args.steps} timed solves"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="block16", choices=["block16", "babd8", "scalar"])
+    ap.add_argument("--paths", default="fp64,fp32_ir")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    ws, rank, local = _dist()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+
+    from paper_0912_3678_gb300 import build as _build
+    if rank == 0 or ws == 1:
+        _build.build()
+    if dist is not None:
+        dist.barrier()
+    import paper_0912_3678_gb300 as bt
+
+    w = _workload(args.workload)
+    s = w["sys"]
+    N, m, nr = w["N"], w["m"], w["nrhs"]
+    stream = torch.cuda.current_stream(dev)
+
+    def dev_t(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    if w["kind"] == "btri":
+        mats_h = [s.B, s.D, s.C]
+        rhs_h = s.F
+        Plan = bt.BtPlan
+    else:
+        mats_h = [s.S, s.R, s.B0, s.B1]
+        rhs_h = s.RHS
+        Plan = bt.AbdPlan
+    mats = [dev_t(a) for a in mats_h]
+    F = dev_t(rhs_h)
+    X = torch.empty_like(F)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    results = {}
+    paths = [p for p in args.paths.split(",") if p]
+    for prec in paths:
+        plan = Plan(N, m, nrhs_max=nr, prec=prec)
+
+        def step():
+            plan.factor(*mats)
+            if prec == "fp64":
+                plan.solve(F, X)
+            else:
+                _, it, rc, code = plan.refine(F, X, tol=1e-12, maxit=30, raise_on_error=True)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        plan.trace(True)
+        l0 = plan.launches()
+        samples = []
+        stop_evt = threading.Event()
+        rows = []
+        th = None
+        if rank == 0 or ws == 1:
+            th = threading.Thread(target=_clock_sampler, args=(stop_evt, rows), daemon=True)
+            th.start()
+            time.sleep(0.3)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            samples.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        wall = time.perf_counter() - wall0
+        stop_evt.set()
+        if th is not None:
+            th.join(timeout=3)
+        launches = plan.launches() - l0
+        ms_steps = [a.elapsed_time(b) for a, b in samples]
+        ms = sum(ms_steps) / len(ms_steps)
+        kinds = {}
+        for k in bt.KERNEL_KINDS:
+            tot, n = plan.trace_query(k)
+            if n:
+                kinds[k] = (tot, n)
+        f0_ms, f0_n = plan.trace_query("factor", 0)
+        r_ms, r_n = plan.trace_query("residual", 0)
+        plan.trace(False)
+        ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        if dist is not None:
+            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        ms_max = float(ms_t.item())
+        Xh = X.cpu().numpy().copy()
+        results[prec] = dict(ms=ms_max, ms_steps=ms_steps, kinds=kinds, f0=(f0_ms, f0_n), resid=(r_ms, r_n),
+                             launches=launches / args.steps, X=Xh, clocks=_clocks_summary(rows, local),
+                             wall=wall, levels=plan.levels())
+        # end to end through the public API with pinned host buffers
+        mats_pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in mats_h]
+        F_pin = torch.from_numpy(np.ascontiguousarray(rhs_h)).pin_memory()
+        X_pin = torch.empty_like(F_pin).pin_memory()
+        e2e = []
+        for it in range(args.warmup + max(3, args.steps // 2)):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for d, h in zip(mats, mats_pin):
+                d.copy_(h, non_blocking=True)
+            F.copy_(F_pin, non_blocking=True)
+            step()
+            X_pin.copy_(X, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if it >= args.warmup:
+                e2e.append(e0.elapsed_time(e1))
+        e2e_ms = sum(e2e) / len(e2e)
+        e2t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        if dist is not None:
+            dist.all_reduce(e2t, op=dist.ReduceOp.MAX)
+        results[prec]["e2e_ms"] = float(e2t.item())
+        results[prec]["h2d"] = sum(int(a.nbytes) for a in mats_h) + int(rhs_h.nbytes)
+        results[prec]["d2h"] = int(rhs_h.nbytes)
+        plan.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- CPU baseline: the oracle on the host cores, bounded sample; its
+    # solution also gives each path's error against plain FP64.
+    cpu = None
+    ref = None
+    if not args.no_cpu_baseline:
+        import oracle
+        def oracle_solve():
+            if w["kind"] == "btri":
+                return oracle.btri_solve(s.B, s.D, s.C, s.F)
+            return oracle.babd_solve(s.S, s.R, s.B0, s.B1, s.RHS)
+        t0 = time.perf_counter()
+        ref = oracle_solve()
+        first = time.perf_counter() - t0
+        reps = max(1, min(50, int(10.0 / max(first, 1e-3))))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            oracle_solve()
+        per = (time.perf_counter() - t0) / reps
+        cpu = {"value": w["unknowns"] / per, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the full workload solved {reps + 1} times (about {per * (reps + 1):.1f} s), "
+                         "single-threaded C, FP64"}
+
+    import oracle as _o
+    for prec, r in results.items():
+        r["rel_err"] = _o.rel_err(r["X"], ref) if ref is not None else None
+    ok = {p: r for p, r in results.items() if r["rel_err"] is None or r["rel_err"] <= 1e-10}
+    head = min(ok, key=lambda p: ok[p]["ms"]) if ok else min(results, key=lambda p: results[p]["ms"])
+    r = results[head]
+    value = ws * w["unknowns"] / (r["ms"] / 1e3)
+    # roofline of the dominant kernel: the level-0 local factorization (FP64 or
+    # FP32 FMA pipe) or, for the refined path, whichever kernel kind took longest
+    kinds_sorted = sorted(r["kinds"].items(), key=lambda kv: -kv[1][0])
+    dom = kinds_sorted[0][0] if kinds_sorted else "factor"
+    if w["kind"] == "btri":
+        local_rows = N - (r["levels"][0][1] - 1)
+    else:
+        local_rows = N - r["levels"][0][1]
+    if dom == "factor" and r["f0"][1]:
+        flops = _factor_flops_per_row(m) * local_rows
+        t_launch = r["f0"][0] / r["f0"][1] / 1e3
+        unit_note = "level-0 local factorization"
+        peak = FP64_PEAK_TFLOPS if head == "fp64" else None
+    elif dom == "residual" and r["resid"][1]:
+        flops = 2.0 * 3 * m * m * nr * N
+        t_launch = r["resid"][0] / r["resid"][1] / 1e3
+        unit_note = "FP64 residual r = f - A x"
+        peak = FP64_PEAK_TFLOPS
+    else:
+        flops, t_launch, unit_note, peak = None, None, dom, None
+    if peak is None and flops is not None:
+        # an FP32 kernel: FP32 FMA peak from 128 lanes/SM
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    roof = None
+    if flops is not None:
+        ach = flops / t_launch / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": unit_note,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz" if peak < 5 else
+                               "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": w["desc"], "path": head, "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": f"replicas x{ws}", "levels": r["levels"]},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": ws * w["unknowns"] / (r["e2e_ms"] / 1e3), "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
+                "d2h_bytes_per_step": r["d2h"]},
+        "clocks": r["clocks"],
+        "gpu_launches": r["launches"],
+        "rel_err_vs_oracle": r["rel_err"],
+        "paths": {p: {"ms_per_step": q["ms"], "value": ws * w["unknowns"] / (q["ms"] / 1e3),
+                      "rel_err_vs_oracle": q["rel_err"], "e2e_ms": q["e2e_ms"],
+                      "kernel_ms_per_step": {k: v[0] / args.steps for k, v in q["kinds"].items()},
+                      "launches_per_step": q["launches"]} for p, q in results.items()},
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,178 @@
+/*
+ * bt.h -- C ABI of the GB300 partition-method solver for structured sparse
+ * systems A x = f (Amodio & Brugnano, "Parallel Factorizations in Numerical
+ * Analysis", Sec. 2, Eq. (syst)).
+ *
+ * The method: A is rearranged into local blocks A^(i) coupled through small
+ * separator blocks a^(i) (Sec. 2, Eq. (parpart); for BABD matrices Eq.
+ * (parpart1)), factored as A = F T G (Eqs. (parfact)-(parG)) with every
+ * partition factored independently (Eq. (parblock)), and solved by the
+ * F-solve and G-solve in parallel and the reduced system of Eq. (redmatr) /
+ * (redmatr1) on the separators (Sec. 2, "the solution of the system with the
+ * matrix T requires ... a reduced system").  Here each partition is a CTA (or
+ * a thread, for blocks of order m <= 4) of one GPU, and the reduced system is
+ * itself partitioned recursively on the device until one partition is left.
+ *
+ * Conventions for every entry point below:
+ *  - All array pointers are DEVICE pointers (cudaMalloc'ed or
+ *    torch-allocated memory on the plan's device), owned by the caller, in
+ *    row-major FP64.  Right-hand sides and solutions are [rows*m][nrhs].
+ *  - Calls are asynchronous on the plan's CUDA stream, except where stated.
+ *    The returned status covers argument checks and launch errors; numerical
+ *    failures (a zero or non-finite pivot) are recorded in a device status
+ *    word and returned by the next synchronising call (bt_sync/abd_sync,
+ *    bt_refine/abd_refine).
+ *  - Nothing throws across the ABI.  A plan is not thread-safe: one host
+ *    thread at a time may use it.
+ */
+#ifndef BT_H
+#define BT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BT_OK = 0,
+    BT_ERR_INVALID = 1,        /* bad argument or call order */
+    BT_ERR_NOMEM = 2,          /* device allocation failed */
+    BT_ERR_SINGULAR = 3,       /* zero pivot in a pivot block */
+    BT_ERR_NONFINITE = 4,      /* inf/nan pivot */
+    BT_ERR_NOT_CONVERGED = 5,  /* refinement hit maxit */
+    BT_ERR_TIMEOUT = 6,        /* a bounded device wait gave up */
+    BT_ERR_CUDA = 7            /* CUDA runtime error */
+} bt_status;
+
+typedef enum {
+    BT_FP64 = 0,     /* every factorization step in FP64 */
+    BT_FP32_IR = 1,  /* local factors in FP32, reduced system FP64; solve via FP64 refinement */
+    BT_BF16_IR = 2   /* local Schur-complement products with BF16 operands (FP32 accumulate),
+                        reduced system FP64; solve via FP64 refinement */
+} bt_prec;
+
+typedef struct bt_plan_s* bt_plan;
+typedef struct bt_plan_s* abd_plan;
+
+/* Human-readable name of a status code (static string). */
+const char* bt_status_string(bt_status s);
+
+/* ---------------------------------------------------------------------
+ * Block tridiagonal systems (Sec. 2: "(block) tridiagonal"; m = 1 is the
+ * scalar tridiagonal case).  Block row j (0 <= j < nblk):
+ *     B_j x_{j-1} + D_j x_j + C_j x_{j+1} = f_j,
+ * with B, D, C of shape [nblk][m][m]; B_0 and C_{nblk-1} are never read.
+ * ------------------------------------------------------------------- */
+
+/* Create a plan on the current CUDA device.
+ *   nblk     number of block rows N (>= 1);  m block order, one of 1,2,4,8,16,32.
+ *   nrhs_max largest nrhs later passed to bt_solve/bt_refine (1..32).
+ *   prec     precision of the local factors (bt_prec).
+ *   p        number of top-level partitions (Sec. 2, "p processors"); 0 picks
+ *            one from the device's SM count; must satisfy 1 <= p <= (nblk+1)/2.
+ *   stream   cudaStream_t for every later call (NULL = legacy default stream).
+ * Allocates all device workspace (factors of every recursion level).
+ * Returns BT_ERR_INVALID on bad sizes, BT_ERR_NOMEM if allocation fails. */
+bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int prec, int64_t p,
+                         void* stream);
+
+/* Factor A = F T G (Eqs. (parfact)-(parblock)): the local block LU of every
+ * partition with its fill-in spikes, the reduced matrix of Eq. (redmatr),
+ * and recursively its own factorization.  Reads B, D, C; does not modify
+ * them.  The plan keeps the three pointers for bt_residual/bt_refine: the
+ * caller keeps the arrays alive and unchanged until the next bt_factor or
+ * bt_plan_destroy.  Resets the device status word. */
+bt_status bt_factor(bt_plan plan, const double* B, const double* D, const double* C);
+
+/* Solve A X = F with the factors (the F-, T- and G-solves of Sec. 2):
+ * F, X: [nblk*m][nrhs], 1 <= nrhs <= nrhs_max; X may not alias F.
+ * With a BT_FP32_IR/BT_BF16_IR plan this is the low-precision solve only
+ * (use bt_refine for an FP64-accurate result). */
+bt_status bt_solve(bt_plan plan, const double* F, double* X, int nrhs);
+
+/* R = F - A X in FP64 with the matrices given to the last bt_factor. */
+bt_status bt_residual(bt_plan plan, const double* F, const double* X, double* R, int nrhs);
+
+/* Iterative refinement to FP64 accuracy: X = solve(F); repeat
+ * { R = F - A X (FP64); D = solve(R); X += D } until ||D||_F <= tol ||X||_F
+ * or maxit corrections.  SYNCHRONISES every iteration (two norms copied to
+ * the host).  iters_out (may be NULL): corrections applied;
+ * relcorr_out (may be NULL): last ||D||_F/||X||_F.
+ * Returns BT_ERR_NOT_CONVERGED after maxit, or a recorded numerical status. */
+bt_status bt_refine(bt_plan plan, const double* F, double* X, int nrhs, double tol, int maxit,
+                    int* iters_out, double* relcorr_out);
+
+/* Wait for the plan's stream; return the recorded numerical status. */
+bt_status bt_sync(bt_plan plan);
+
+/* Wait for the plan's stream and report where a numerical failure was seen:
+ * recursion level, partition index (-1 for the top-level direct solve) and
+ * block row of that level.  Any output pointer may be NULL. */
+bt_status bt_info(bt_plan plan, int* level, int64_t* partition, int64_t* row);
+
+/* Geometry of the recursion: number of levels with partitions (the last
+ * level is solved by one partition), and for level l (l < levels) its block
+ * rows and partition count.  Host call, no synchronisation. */
+bt_status bt_plan_levels(bt_plan plan, int* levels, int64_t* rows, int64_t* parts, int capacity);
+
+/* Device bytes held by the plan. */
+bt_status bt_plan_bytes(bt_plan plan, int64_t* bytes);
+
+/* Copy the top-level reduced matrix of Eq. (redmatr) out of the plan after
+ * bt_factor (device-to-device, asynchronous): for the p-1 separators s,
+ *   alpha[s] = T[s][s], beta[s] = T[s][s-1] (beta[0] = 0),
+ *   gamma[s] = T[s][s+1] (gamma[p-2] = 0), each [p-1][m][m] in FP64.
+ * For a BABD plan: alpha[i], beta[i] for the p+1 reduced rows of Eq.
+ * (redmatr1) (lower block bidiagonal; beta[0] = the corner block),
+ * gamma is not written. */
+bt_status bt_reduced_export(bt_plan plan, double* alpha, double* beta, double* gamma);
+
+/* Tracing.  bt_plan_trace(plan, 1) clears the records and brackets every
+ * later kernel launch of the plan with a pair of CUDA events on the plan's
+ * stream; bt_plan_trace(plan, 0) stops recording.  bt_plan_trace_query
+ * synchronises and returns, for kernel kind `kind` at recursion level
+ * `level` (levels >= 3 are pooled into 3; level -1 sums all levels), the
+ * summed event time in ms and the number of launches.  Kinds:
+ * 0 local factor, 1 reduced-matrix assembly, 2 forward solve, 3 reduced
+ * right-hand side, 4 back substitution, 5 top-level BABD direct solve,
+ * 6 FP64 residual, 7 refinement update. */
+bt_status bt_plan_trace(bt_plan plan, int enable);
+bt_status bt_plan_trace_query(bt_plan plan, int kind, int level, double* total_ms, int64_t* launches);
+
+/* Number of kernels the plan has launched since it was created. */
+bt_status bt_plan_launches(bt_plan plan, int64_t* count);
+
+void bt_plan_destroy(bt_plan plan);
+
+/* ---------------------------------------------------------------------
+ * ABD/BABD systems (Sec. 2, Eq. (parpart1) with c = 0, and Sec. 3: one-step
+ * discretisations of linear BVPs).  Unknowns y_0..y_N (m each):
+ *     B0 y_0 + B1 y_N = beta                       (boundary block row 0)
+ *     S_j y_j + R_j y_{j+1} = r_j,  j = 0..N-1    (block rows 1..N)
+ * S, R: [N][m][m]; B0, B1: [m][m].  Right-hand side and solution are
+ * [(N+1)*m][nrhs] with the boundary row first.  The local factorizations
+ * pivot inside each m x m block; the reduced system keeps the boundary row
+ * as a separator (B0 may be singular, e.g. separated boundary conditions)
+ * and the final small reduced system is solved with partial pivoting across
+ * block rows.
+ * ------------------------------------------------------------------- */
+
+bt_status abd_plan_create(abd_plan* plan, int64_t N, int m, int nrhs_max, int prec, int64_t p,
+                          void* stream);
+/* Reads S, R, B0, B1 (kept by reference like bt_factor; B0 and B1 are also
+ * copied into the plan). */
+bt_status abd_factor(abd_plan plan, const double* S, const double* R, const double* B0,
+                     const double* B1);
+bt_status abd_solve(abd_plan plan, const double* RHS, double* Y, int nrhs);
+bt_status abd_residual(abd_plan plan, const double* RHS, const double* Y, double* Rout, int nrhs);
+bt_status abd_refine(abd_plan plan, const double* RHS, double* Y, int nrhs, double tol, int maxit,
+                     int* iters_out, double* relcorr_out);
+bt_status abd_sync(abd_plan plan);
+void abd_plan_destroy(abd_plan plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BT_H */

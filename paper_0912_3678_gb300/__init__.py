@@ -1,0 +1,316 @@
+"""GB300 partition-method solver for structured sparse systems A x = f
+(Amodio & Brugnano, "Parallel Factorizations in Numerical Analysis").
+
+A thin binding over the C ABI of ``include/bt.h``: the functions below have
+the C names and only marshal arguments (torch CUDA tensors -> device
+pointers, the current torch stream -> cudaStream_t).  Every step of the
+solve runs in the CUDA kernels of ``libbt.so``.  ``BtPlan``/``AbdPlan`` wrap
+a plan handle with the same calls as methods.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+from ._lib import BT_STATUS, PREC, BtError
+
+__all__ = ["BtPlan", "AbdPlan", "BtError", "BT_STATUS", "PREC", "load_library",
+           "bt_plan_create", "bt_factor", "bt_solve", "bt_residual", "bt_refine", "bt_sync", "bt_info",
+           "bt_plan_levels", "bt_plan_bytes", "bt_plan_trace", "bt_plan_trace_query", "bt_plan_launches",
+           "KERNEL_KINDS", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
+           "abd_plan_create", "abd_factor", "abd_solve", "abd_residual", "abd_refine", "abd_sync",
+           "abd_plan_destroy"]
+
+
+def load_library():
+    return _lib.load()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor or an int device pointer")
+    if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError("arrays must be contiguous float64 CUDA tensors")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _prec(prec):
+    return PREC[prec] if isinstance(prec, str) else int(prec)
+
+
+# ---------------------------------------------------------------- C names --
+
+def bt_status_string(code: int) -> str:
+    return _lib.load().bt_status_string(code).decode()
+
+
+def bt_plan_create(nblk, m, nrhs_max=1, prec="fp64", p=0, stream=None):
+    h = ctypes.c_void_p()
+    _lib.check(_lib.load().bt_plan_create(ctypes.byref(h), int(nblk), int(m), int(nrhs_max), _prec(prec),
+                                          int(p), _stream(stream)), "bt_plan_create")
+    return h
+
+
+def abd_plan_create(N, m, nrhs_max=1, prec="fp64", p=0, stream=None):
+    h = ctypes.c_void_p()
+    _lib.check(_lib.load().abd_plan_create(ctypes.byref(h), int(N), int(m), int(nrhs_max), _prec(prec),
+                                           int(p), _stream(stream)), "abd_plan_create")
+    return h
+
+
+def bt_factor(plan, B, D, C):
+    _lib.check(_lib.load().bt_factor(plan, _ptr(B), _ptr(D), _ptr(C)), "bt_factor")
+
+
+def abd_factor(plan, S, R, B0, B1):
+    _lib.check(_lib.load().abd_factor(plan, _ptr(S), _ptr(R), _ptr(B0), _ptr(B1)), "abd_factor")
+
+
+def bt_solve(plan, F, X, nrhs):
+    _lib.check(_lib.load().bt_solve(plan, _ptr(F), _ptr(X), int(nrhs)), "bt_solve")
+
+
+def abd_solve(plan, RHS, Y, nrhs):
+    _lib.check(_lib.load().abd_solve(plan, _ptr(RHS), _ptr(Y), int(nrhs)), "abd_solve")
+
+
+def bt_residual(plan, F, X, R, nrhs):
+    _lib.check(_lib.load().bt_residual(plan, _ptr(F), _ptr(X), _ptr(R), int(nrhs)), "bt_residual")
+
+
+def abd_residual(plan, RHS, Y, Rout, nrhs):
+    _lib.check(_lib.load().abd_residual(plan, _ptr(RHS), _ptr(Y), _ptr(Rout), int(nrhs)), "abd_residual")
+
+
+def _refine(fn, name, plan, F, X, nrhs, tol, maxit, raise_on_error):
+    it = ctypes.c_int(0)
+    rc = ctypes.c_double(0.0)
+    code = fn(plan, _ptr(F), _ptr(X), int(nrhs), float(tol), int(maxit), ctypes.byref(it), ctypes.byref(rc))
+    if raise_on_error:
+        _lib.check(code, name)
+    return code, it.value, rc.value
+
+
+def bt_refine(plan, F, X, nrhs, tol=1e-12, maxit=30, raise_on_error=True):
+    return _refine(_lib.load().bt_refine, "bt_refine", plan, F, X, nrhs, tol, maxit, raise_on_error)
+
+
+def abd_refine(plan, RHS, Y, nrhs, tol=1e-12, maxit=30, raise_on_error=True):
+    return _refine(_lib.load().abd_refine, "abd_refine", plan, RHS, Y, nrhs, tol, maxit, raise_on_error)
+
+
+def bt_sync(plan) -> int:
+    return _lib.load().bt_sync(plan)
+
+
+def abd_sync(plan) -> int:
+    return _lib.load().abd_sync(plan)
+
+
+def bt_info(plan):
+    lev = ctypes.c_int(0)
+    part = ctypes.c_int64(0)
+    row = ctypes.c_int64(0)
+    code = _lib.load().bt_info(plan, ctypes.byref(lev), ctypes.byref(part), ctypes.byref(row))
+    return code, lev.value, part.value, row.value
+
+
+def bt_plan_levels(plan):
+    n = ctypes.c_int(0)
+    cap = 64
+    rows = (ctypes.c_int64 * cap)()
+    parts = (ctypes.c_int64 * cap)()
+    _lib.check(_lib.load().bt_plan_levels(plan, ctypes.byref(n), rows, parts, cap), "bt_plan_levels")
+    return [(rows[i], parts[i]) for i in range(min(n.value, cap))]
+
+
+def bt_plan_bytes(plan) -> int:
+    b = ctypes.c_int64(0)
+    _lib.check(_lib.load().bt_plan_bytes(plan, ctypes.byref(b)), "bt_plan_bytes")
+    return b.value
+
+
+def bt_reduced_export(plan, alpha, beta, gamma=None):
+    _lib.check(_lib.load().bt_reduced_export(plan, _ptr(alpha), _ptr(beta), _ptr(gamma)), "bt_reduced_export")
+
+
+KERNEL_KINDS = {"factor": 0, "assemble": 1, "solve_fwd": 2, "assemble_rhs": 3, "solve_bwd": 4,
+                "direct": 5, "residual": 6, "ir_update": 7}
+
+
+def bt_plan_trace(plan, enable=True):
+    _lib.check(_lib.load().bt_plan_trace(plan, 1 if enable else 0), "bt_plan_trace")
+
+
+def bt_plan_trace_query(plan, kind, level=-1):
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    k = KERNEL_KINDS[kind] if isinstance(kind, str) else int(kind)
+    _lib.check(_lib.load().bt_plan_trace_query(plan, k, int(level), ctypes.byref(ms), ctypes.byref(n)),
+               "bt_plan_trace_query")
+    return ms.value, n.value
+
+
+def bt_plan_launches(plan) -> int:
+    n = ctypes.c_int64(0)
+    _lib.check(_lib.load().bt_plan_launches(plan, ctypes.byref(n)), "bt_plan_launches")
+    return n.value
+
+
+def bt_plan_destroy(plan):
+    _lib.load().bt_plan_destroy(plan)
+
+
+def abd_plan_destroy(plan):
+    _lib.load().abd_plan_destroy(plan)
+
+
+# ---------------------------------------------------------------- classes --
+
+class _PlanBase:
+    kind = 0
+
+    def __init__(self, n, m, nrhs_max=1, prec="fp64", p=0, stream=None):
+        import torch
+        self.m = int(m)
+        self.n = int(n)
+        self.nrhs_max = int(nrhs_max)
+        self.prec = prec
+        self.stream = stream
+        self.rows = self.n if self.kind == 0 else self.n + 1
+        create = bt_plan_create if self.kind == 0 else abd_plan_create
+        self.handle = create(n, m, nrhs_max, prec, p, stream)
+        self._keep = ()
+        self._torch = torch
+
+    def _new_like_rhs(self, F):
+        return self._torch.empty_like(F)
+
+    def _nrhs(self, F):
+        return 1 if F.dim() == 1 else F.shape[-1]
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            (bt_plan_destroy if self.kind == 0 else abd_plan_destroy)(self.handle)
+            self.handle = None
+            self._keep = ()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def sync(self):
+        code = bt_sync(self.handle)
+        _lib.check(code, "sync")
+
+    def info(self):
+        return bt_info(self.handle)
+
+    def levels(self):
+        return bt_plan_levels(self.handle)
+
+    def nbytes(self):
+        return bt_plan_bytes(self.handle)
+
+    def trace(self, enable=True):
+        bt_plan_trace(self.handle, enable)
+
+    def trace_query(self, kind, level=-1):
+        return bt_plan_trace_query(self.handle, kind, level)
+
+    def launches(self):
+        return bt_plan_launches(self.handle)
+
+
+class BtPlan(_PlanBase):
+    """Block tridiagonal plan: B_j x_{j-1} + D_j x_j + C_j x_{j+1} = f_j."""
+    kind = 0
+
+    def factor(self, B, D, C):
+        self._keep = (B, D, C)
+        bt_factor(self.handle, B, D, C)
+
+    def solve(self, F, X=None):
+        X = self._new_like_rhs(F) if X is None else X
+        bt_solve(self.handle, F, X, self._nrhs(F))
+        return X
+
+    def residual(self, F, X, R=None):
+        R = self._new_like_rhs(F) if R is None else R
+        bt_residual(self.handle, F, X, R, self._nrhs(F))
+        return R
+
+    def refine(self, F, X=None, tol=1e-12, maxit=30, raise_on_error=True):
+        X = self._new_like_rhs(F) if X is None else X
+        code, it, rc = bt_refine(self.handle, F, X, self._nrhs(F), tol, maxit, raise_on_error)
+        return X, it, rc, code
+
+    def reduced(self):
+        """Top-level reduced matrix (alpha, beta, gamma) of Eq. (redmatr)."""
+        lev = self.levels()
+        q = lev[0][1] - 1
+        t = self._torch
+        dev = self._keep[1].device
+        a = t.empty((q, self.m, self.m), dtype=t.float64, device=dev)
+        b = t.empty_like(a)
+        g = t.empty_like(a)
+        bt_reduced_export(self.handle, a, b, g)
+        return a, b, g
+
+
+class AbdPlan(_PlanBase):
+    """BABD plan: B0 y_0 + B1 y_N = beta;  S_j y_j + R_j y_{j+1} = r_j."""
+    kind = 1
+
+    def factor(self, S, R, B0, B1):
+        self._keep = (S, R, B0, B1)
+        abd_factor(self.handle, S, R, B0, B1)
+
+    def solve(self, RHS, Y=None):
+        Y = self._new_like_rhs(RHS) if Y is None else Y
+        abd_solve(self.handle, RHS, Y, self._nrhs(RHS))
+        return Y
+
+    def residual(self, RHS, Y, Rout=None):
+        Rout = self._new_like_rhs(RHS) if Rout is None else Rout
+        abd_residual(self.handle, RHS, Y, Rout, self._nrhs(RHS))
+        return Rout
+
+    def refine(self, RHS, Y=None, tol=1e-12, maxit=30, raise_on_error=True):
+        Y = self._new_like_rhs(RHS) if Y is None else Y
+        code, it, rc = abd_refine(self.handle, RHS, Y, self._nrhs(RHS), tol, maxit, raise_on_error)
+        return Y, it, rc, code
+
+    def reduced(self):
+        """Top-level reduced BABD matrix of Eq. (redmatr1): alpha [p+1], beta [p+1]
+        (beta[0] is the corner block)."""
+        lev = self.levels()
+        q = lev[0][1] + 1
+        t = self._torch
+        dev = self._keep[0].device
+        a = t.empty((q, self.m, self.m), dtype=t.float64, device=dev)
+        b = t.empty_like(a)
+        bt_reduced_export(self.handle, a, b, None)
+        return a, b

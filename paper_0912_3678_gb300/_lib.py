@@ -1,0 +1,80 @@
+"""ctypes loader for ``_build/libbt.so`` (the C ABI of ``include/bt.h``).
+
+There is no fallback: if the library is missing, importing the binding
+raises, so nothing silently runs off the GPU path."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libbt.so")
+
+BT_STATUS = {
+    0: "BT_OK", 1: "BT_ERR_INVALID", 2: "BT_ERR_NOMEM", 3: "BT_ERR_SINGULAR", 4: "BT_ERR_NONFINITE",
+    5: "BT_ERR_NOT_CONVERGED", 6: "BT_ERR_TIMEOUT", 7: "BT_ERR_CUDA",
+}
+PREC = {"fp64": 0, "fp32_ir": 1, "bf16_ir": 2}
+
+# name -> (restype, argtypes)
+_vp, _i32, _i64, _f64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+_pvp = ctypes.POINTER(ctypes.c_void_p)
+_pi32 = ctypes.POINTER(ctypes.c_int)
+_pi64 = ctypes.POINTER(ctypes.c_int64)
+_pf64 = ctypes.POINTER(ctypes.c_double)
+SIGNATURES = {
+    "bt_status_string": (ctypes.c_char_p, [_i32]),
+    "bt_plan_create": (_i32, [_pvp, _i64, _i32, _i32, _i32, _i64, _vp]),
+    "bt_factor": (_i32, [_vp, _vp, _vp, _vp]),
+    "bt_solve": (_i32, [_vp, _vp, _vp, _i32]),
+    "bt_residual": (_i32, [_vp, _vp, _vp, _vp, _i32]),
+    "bt_refine": (_i32, [_vp, _vp, _vp, _i32, _f64, _i32, _pi32, _pf64]),
+    "bt_sync": (_i32, [_vp]),
+    "bt_info": (_i32, [_vp, _pi32, _pi64, _pi64]),
+    "bt_plan_levels": (_i32, [_vp, _pi32, _pi64, _pi64, _i32]),
+    "bt_plan_bytes": (_i32, [_vp, _pi64]),
+    "bt_reduced_export": (_i32, [_vp, _vp, _vp, _vp]),
+    "bt_plan_trace": (_i32, [_vp, _i32]),
+    "bt_plan_trace_query": (_i32, [_vp, _i32, _i32, _pf64, _pi64]),
+    "bt_plan_launches": (_i32, [_vp, _pi64]),
+    "bt_plan_destroy": (None, [_vp]),
+    "abd_plan_create": (_i32, [_pvp, _i64, _i32, _i32, _i32, _i64, _vp]),
+    "abd_factor": (_i32, [_vp, _vp, _vp, _vp, _vp]),
+    "abd_solve": (_i32, [_vp, _vp, _vp, _i32]),
+    "abd_residual": (_i32, [_vp, _vp, _vp, _vp, _i32]),
+    "abd_refine": (_i32, [_vp, _vp, _vp, _i32, _f64, _i32, _pi32, _pf64]),
+    "abd_sync": (_i32, [_vp]),
+    "abd_plan_destroy": (None, [_vp]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: build it with `python -m paper_0912_3678_gb300.build` "
+            "(nvcc for sm_103a). There is no CPU fallback.")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class BtError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        self.name = BT_STATUS.get(code, f"status {code}")
+        super().__init__(f"{what}: {self.name}")
+
+
+def check(code: int, what: str) -> int:
+    if code != 0:
+        raise BtError(code, what)
+    return code

@@ -1,0 +1,576 @@
+// C ABI: plans, the recursion over reduced systems, solves and refinement.
+#include <cuda_runtime.h>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/bt.h"
+#include "bt_launch.h"
+#include "bt_level.h"
+#include "bt_misc.h"
+
+namespace {
+
+using bt::LevelArgs;
+
+constexpr int kNrhsMax = 32;
+constexpr long long kTopRows = 8;      // a level with at most this many rows is solved by one partition
+constexpr long long kSubLevelRows = 4; // rows per partition on the recursion levels
+
+struct Level {
+    LevelArgs a;
+    bool low = false;   // local factors in FP32
+    long long rows = 0; // block rows stored for this level (BABD: N+1)
+};
+
+}  // namespace
+
+struct bt_plan_s {
+    int kind = 0;   // 0 block tridiagonal, 1 BABD
+    long long N = 0;
+    int m = 0;
+    int nrhs_max = 0;
+    int prec = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    const bt::Launchers* L = nullptr;
+    std::vector<Level> lv;   // lv[0..nlev-1] partitioned levels; lv[nlev] the top
+    int nlev = 0;
+    bool factored = false;
+    // caller's matrices (kept by reference)
+    const double* A0 = nullptr;  // B or S
+    const double* A1 = nullptr;  // D or R
+    const double* A2 = nullptr;  // C
+    // device memory
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
+    long long* status = nullptr;
+    long long* status_host = nullptr;   // pinned
+    double* norms = nullptr;            // [2]
+    double* norms_host = nullptr;       // pinned
+    double* partial = nullptr;          // [2*1024]
+    double* Rbuf = nullptr;
+    double* Dbuf = nullptr;
+    double* B0 = nullptr;               // BABD boundary blocks (copies)
+    double* B1 = nullptr;
+    double* keep = nullptr;             // BABD top-level pivot rows
+    // tracing
+    bool trace = false;
+    struct Rec { int key; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+    long long launches = 0;
+};
+
+namespace {
+
+struct Arena {
+    size_t off = 0;
+    char* base = nullptr;
+    void* take(size_t bytes) {
+        off = (off + 255) & ~size_t(255);
+        void* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+bt_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return BT_OK;
+    if (e == cudaErrorMemoryAllocation) return BT_ERR_NOMEM;
+    return BT_ERR_CUDA;
+}
+
+int sm_count(int dev) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    return n;
+}
+
+// Partition count for a level of `rows` block rows (btri: 1 <= p <= (rows+1)/2;
+// BABD: 1 <= p <= (rows-1)/2 local rows 1..rows-1 with >= 1 local row each).
+long long auto_parts(long long rows, int m, int level, int sms, int kind) {
+    long long cap = (kind == 0) ? (rows + 1) / 2 : (rows - 1) / 2;
+    if (cap < 1) cap = 1;
+    long long target;
+    if (level == 0) {
+        const long long per_sm = (m >= 8) ? 4 : 512;
+        target = (long long)sms * per_sm;
+        const long long kmin = (m >= 8) ? 4 : 8;
+        long long byk = rows / kmin;
+        if (byk < target) target = byk;
+    } else {
+        target = rows / kSubLevelRows;
+    }
+    if (target < 1) target = 1;
+    if (target > cap) target = cap;
+    return target;
+}
+
+// Lay out (or measure, when ar.base == nullptr) the plan's device memory.
+void layout(bt_plan_s* P, Arena& ar) {
+    const int m = P->m;
+    const long long mm = (long long)m * m;
+    const int nr = P->nrhs_max;
+    P->status = (long long*)ar.take(4 * sizeof(long long));
+    P->norms = (double*)ar.take(2 * sizeof(double));
+    P->partial = (double*)ar.take(2 * 1024 * sizeof(double));
+    const long long rows0 = P->lv[0].rows;
+    P->Rbuf = (double*)ar.take(sizeof(double) * rows0 * m * nr);
+    P->Dbuf = (double*)ar.take(sizeof(double) * rows0 * m * nr);
+    if (P->kind == 1) {
+        P->B0 = (double*)ar.take(sizeof(double) * mm);
+        P->B1 = (double*)ar.take(sizeof(double) * mm);
+    }
+    for (int l = 0; l <= P->nlev; ++l) {
+        Level& v = P->lv[l];
+        const size_t ts = v.low ? sizeof(float) : sizeof(double);
+        const bool top = (l == P->nlev);
+        if (!(top && P->kind == 1)) {
+            v.a.Dinv = ar.take(ts * v.rows * mm);
+            if (P->kind == 0) v.a.Y = ar.take(ts * v.rows * mm);
+            v.a.Zc = ar.take(ts * v.rows * mm);
+            if (P->kind == 0) {
+                v.a.Pf = ar.take(ts * v.a.p * mm);
+                v.a.Qf = ar.take(ts * v.a.p * mm);
+                v.a.Hf = ar.take(ts * v.a.p * m * nr);
+            }
+        }
+        if (l >= 1) {
+            // this level's matrix and vectors are owned by the plan
+            Level& u = P->lv[l - 1];
+            if (P->kind == 0) {
+                double* Bn = (double*)ar.take(sizeof(double) * v.rows * mm);
+                double* Dn = (double*)ar.take(sizeof(double) * v.rows * mm);
+                double* Cn = (double*)ar.take(sizeof(double) * v.rows * mm);
+                u.a.Bn = Bn; u.a.Dn = Dn; u.a.Cn = Cn;
+                v.a.B = Bn; v.a.D = Dn; v.a.C = Cn;
+                v.a.shift = 0;
+            } else {
+                // reduced BABD of p rows + boundary row: S', R' hold p blocks
+                double* Sn = (double*)ar.take(sizeof(double) * u.a.p * mm);
+                double* Rn = (double*)ar.take(sizeof(double) * u.a.p * mm);
+                u.a.Bn = Sn; u.a.Dn = Rn;
+                v.a.B = Sn; v.a.D = Rn;
+                v.a.shift = 1;
+            }
+            double* Fn = (double*)ar.take(sizeof(double) * v.rows * m * nr);
+            double* Xn = (double*)ar.take(sizeof(double) * v.rows * m * nr);
+            u.a.Fn = Fn;
+            u.a.Xn = Xn;
+            v.a.F = Fn;
+            v.a.X = Xn;
+        }
+        if (top && P->kind == 1) P->keep = (double*)ar.take(sizeof(double) * v.a.N * m * (3 * m + nr) + 8);
+    }
+}
+
+bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, int prec, int64_t p,
+                      void* stream) {
+    if (!out) return BT_ERR_INVALID;
+    *out = nullptr;
+    const bt::Launchers* L = bt::launchers_for(m);
+    if (!L || nrhs_max < 1 || nrhs_max > kNrhsMax || prec < 0 || prec > 2 || p < 0) return BT_ERR_INVALID;
+    if (kind == 0 && N < 1) return BT_ERR_INVALID;
+    if (kind == 1 && N < 1) return BT_ERR_INVALID;
+    if (kind == 0 && p > (N + 1) / 2 && p > 1) return BT_ERR_INVALID;
+    if (kind == 1 && p > 0 && p > (N - 1) / 2 && p > 1) return BT_ERR_INVALID;
+    if (prec == BT_BF16_IR && m < 16) return BT_ERR_INVALID;
+    bt_plan_s* P = new (std::nothrow) bt_plan_s();
+    if (!P) return BT_ERR_NOMEM;
+    P->kind = kind;
+    P->N = N;
+    P->m = m;
+    P->nrhs_max = nrhs_max;
+    P->prec = prec;
+    P->stream = (cudaStream_t)stream;
+    P->L = L;
+    cudaGetDevice(&P->device);
+    const int sms = sm_count(P->device);
+    // levels
+    long long rows = N;
+    for (int l = 0;; ++l) {
+        Level v;
+        std::memset(&v.a, 0, sizeof(LevelArgs));
+        v.a.mode = kind;
+        v.a.level = l;
+        v.a.N = rows;
+        v.rows = (kind == 0) ? rows : rows + 1;
+        v.low = (l == 0) && (prec != BT_FP64);
+        const bool small = (kind == 0) ? (rows <= kTopRows) : (rows <= kTopRows);
+        long long parts;
+        if (l == 0 && p > 0) parts = p;
+        else parts = small ? 1 : auto_parts(rows, m, l, sms, kind);
+        if (kind == 1 && (small || rows < 3)) parts = 0;   // BABD: direct solve at the top
+        if (kind == 1 && parts == 1 && l > 0) parts = 0;
+        if (kind == 1 && l == 0 && p == 1 && rows >= 3) parts = 1;
+        v.a.p = parts;
+        if (parts > 0) {
+            const long long span = (kind == 0) ? rows : rows - 1;
+            v.a.base = span / parts;
+            v.a.extra = span % parts;
+        }
+        P->lv.push_back(v);
+        if (kind == 0 && parts <= 1) break;
+        if (kind == 1 && parts == 0) break;
+        rows = (kind == 0) ? parts - 1 : parts;
+    }
+    P->nlev = (int)P->lv.size() - 1;
+    if (kind == 0) {
+        // the top level is a single partition; levels below it have >= 2
+    }
+    Arena meas;
+    layout(P, meas);
+    size_t bytes = meas.off + 256;
+    cudaError_t e = cudaMalloc((void**)&P->arena, bytes);
+    if (e != cudaSuccess) {
+        delete P;
+        cudaGetLastError();
+        return from_cuda(e);
+    }
+    P->arena_bytes = bytes;
+    Arena real;
+    real.base = P->arena;
+    layout(P, real);
+    for (auto& v : P->lv) v.a.status = P->status;
+    e = cudaMallocHost((void**)&P->status_host, 4 * sizeof(long long));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&P->norms_host, 2 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->status, 0, 4 * sizeof(long long), P->stream);
+    if (e != cudaSuccess) {
+        cudaFree(P->arena);
+        if (P->status_host) cudaFreeHost(P->status_host);
+        delete P;
+        return from_cuda(e);
+    }
+    *out = P;
+    return BT_OK;
+}
+
+enum Kind { K_FACTOR = 0, K_ASSEMBLE, K_SOLVE_FWD, K_ASSEMBLE_RHS, K_SOLVE_BWD, K_DIRECT, K_RESID, K_IR };
+
+cudaEvent_t take_event(bt_plan_s* P) {
+    if (P->pool_used == P->pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        P->pool.push_back(e);
+    }
+    return P->pool[P->pool_used++];
+}
+
+// Launch through f(), counting kernels and bracketing them with events when tracing.
+template <typename Fn>
+cudaError_t launch(bt_plan_s* P, int kind, int level, int nkernels, Fn&& f) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (P->trace) {
+        a = take_event(P);
+        b = take_event(P);
+        if (a) cudaEventRecord(a, P->stream);
+    }
+    cudaError_t e = f();
+    if (P->trace && a && b) {
+        cudaEventRecord(b, P->stream);
+        P->recs.push_back({kind * 4 + (level < 3 ? level : 3), a, b});
+    }
+    P->launches += nkernels;
+    return e;
+}
+
+bt_status read_status(bt_plan_s* P) {
+    cudaError_t e = cudaMemcpyAsync(P->status_host, P->status, 4 * sizeof(long long), cudaMemcpyDeviceToHost,
+                                    P->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    const long long c = P->status_host[0];
+    if (c == 0) return BT_OK;
+    return (bt_status)c;
+}
+
+// Factor every level: local factorizations and reduced systems.
+bt_status run_factor(bt_plan_s* P) {
+    const bt::Launchers* L = P->L;
+    for (int l = 0; l <= P->nlev; ++l) {
+        Level& v = P->lv[l];
+        if (P->kind == 1 && l == P->nlev) break;   // BABD top: direct solve at solve time
+        cudaError_t e = launch(P, K_FACTOR, l, 1, [&] { return L->factor(v.a, v.low, P->stream); });
+        if (e == cudaSuccess && P->kind == 0 && l < P->nlev)
+            e = launch(P, K_ASSEMBLE, l, 1, [&] { return L->assemble(v.a, v.low, P->stream); });
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    return BT_OK;
+}
+
+// Solve with the factors: F (level-0 rhs) -> X.
+bt_status run_solve(bt_plan_s* P, const double* F, double* X, int nr) {
+    const bt::Launchers* L = P->L;
+    P->lv[0].a.F = F;
+    P->lv[0].a.X = X;
+    for (auto& v : P->lv) v.a.nr = nr;
+    for (int l = 0; l < P->nlev; ++l) {
+        Level& v = P->lv[l];
+        cudaError_t e = launch(P, K_SOLVE_FWD, l, 1, [&] { return L->solve_fwd(v.a, v.low, P->stream); });
+        if (e == cudaSuccess && P->kind == 0)
+            e = launch(P, K_ASSEMBLE_RHS, l, 1, [&] { return L->assemble_rhs(v.a, v.low, P->stream); });
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    Level& t = P->lv[P->nlev];
+    const int lt = P->nlev;
+    cudaError_t e;
+    if (P->kind == 0) {
+        e = launch(P, K_SOLVE_FWD, lt, 1, [&] { return L->solve_fwd(t.a, t.low, P->stream); });
+        if (e == cudaSuccess) e = launch(P, K_SOLVE_BWD, lt, 1, [&] { return L->solve_bwd(t.a, t.low, P->stream); });
+    } else {
+        e = launch(P, K_DIRECT, lt, 1, [&] {
+            return bt::launch_babd_direct((int)t.a.N, P->m, nr, t.a.B, t.a.D, P->B0, P->B1, t.a.F, t.a.X, P->keep,
+                                          P->status, t.a.level, P->stream);
+        });
+    }
+    if (e != cudaSuccess) return from_cuda(e);
+    for (int l = P->nlev - 1; l >= 0; --l) {
+        Level& v = P->lv[l];
+        e = launch(P, K_SOLVE_BWD, l, 1, [&] { return L->solve_bwd(v.a, v.low, P->stream); });
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    return BT_OK;
+}
+
+bt_status run_residual(bt_plan_s* P, const double* F, const double* X, double* R, int nr) {
+    cudaError_t e = launch(P, K_RESID, 0, 1, [&] {
+        if (P->kind == 0) return bt::launch_resid_btri(P->N, P->m, nr, P->A0, P->A1, P->A2, X, F, R, P->stream);
+        return bt::launch_resid_babd(P->N, P->m, nr, P->A0, P->A1, P->B0, P->B1, X, F, R, P->stream);
+    });
+    return from_cuda(e);
+}
+
+bt_status run_refine(bt_plan_s* P, const double* F, double* X, int nr, double tol, int maxit, int* iters,
+                     double* relcorr) {
+    if (iters) *iters = 0;
+    if (relcorr) *relcorr = -1.0;
+    bt_status st = run_solve(P, F, X, nr);
+    if (st != BT_OK) return st;
+    const long long n = P->lv[0].rows * P->m * nr;
+    for (int it = 1; it <= maxit; ++it) {
+        st = run_residual(P, F, X, P->Rbuf, nr);
+        if (st == BT_OK) st = run_solve(P, P->Rbuf, P->Dbuf, nr);
+        if (st != BT_OK) return st;
+        cudaError_t e = launch(P, K_IR, 0, 2,
+                               [&] { return bt::launch_ir_update(n, X, P->Dbuf, P->partial, P->norms, P->stream); });
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(P->norms_host, P->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, P->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        st = read_status(P);   // synchronises
+        if (st != BT_OK) return st;
+        const double dd = P->norms_host[0], xx = P->norms_host[1];
+        const double rel = (xx > 0.0) ? std::sqrt(dd / xx) : std::sqrt(dd);
+        if (iters) *iters = it;
+        if (relcorr) *relcorr = rel;
+        if (!std::isfinite(rel)) return BT_ERR_NONFINITE;
+        if (rel <= tol) return BT_OK;
+    }
+    return BT_ERR_NOT_CONVERGED;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* bt_status_string(bt_status s) {
+    switch (s) {
+        case BT_OK: return "ok";
+        case BT_ERR_INVALID: return "invalid argument";
+        case BT_ERR_NOMEM: return "out of device memory";
+        case BT_ERR_SINGULAR: return "singular pivot block";
+        case BT_ERR_NONFINITE: return "non-finite pivot";
+        case BT_ERR_NOT_CONVERGED: return "refinement did not converge";
+        case BT_ERR_TIMEOUT: return "device wait timed out";
+        case BT_ERR_CUDA: return "CUDA error";
+    }
+    return "unknown status";
+}
+
+bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int prec, int64_t p, void* stream) {
+    return plan_create(plan, 0, nblk, m, nrhs_max, prec, p, stream);
+}
+
+bt_status abd_plan_create(abd_plan* plan, int64_t N, int m, int nrhs_max, int prec, int64_t p, void* stream) {
+    return plan_create(plan, 1, N, m, nrhs_max, prec, p, stream);
+}
+
+bt_status bt_factor(bt_plan P, const double* B, const double* D, const double* C) {
+    if (!P || P->kind != 0 || !D || (P->N > 1 && (!B || !C))) return BT_ERR_INVALID;
+    P->A0 = B;
+    P->A1 = D;
+    P->A2 = C;
+    Level& v = P->lv[0];
+    v.a.B = B;
+    v.a.D = D;
+    v.a.C = C;
+    v.a.shift = 0;
+    cudaError_t e = cudaMemsetAsync(P->status, 0, 4 * sizeof(long long), P->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    bt_status st = run_factor(P);
+    P->factored = (st == BT_OK);
+    return st;
+}
+
+bt_status abd_factor(abd_plan P, const double* S, const double* R, const double* B0, const double* B1) {
+    if (!P || P->kind != 1 || !S || !R || !B0 || !B1) return BT_ERR_INVALID;
+    P->A0 = S;
+    P->A1 = R;
+    const size_t mm = (size_t)P->m * P->m * sizeof(double);
+    cudaError_t e = cudaMemcpyAsync(P->B0, B0, mm, cudaMemcpyDeviceToDevice, P->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P->B1, B1, mm, cudaMemcpyDeviceToDevice, P->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->status, 0, 4 * sizeof(long long), P->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    Level& v = P->lv[0];
+    v.a.B = S;
+    v.a.D = R;
+    v.a.C = nullptr;
+    v.a.shift = 1;
+    bt_status st = run_factor(P);
+    P->factored = (st == BT_OK);
+    return st;
+}
+
+static bt_status check_solve(bt_plan P, int kind, const void* F, const void* X, int nrhs) {
+    if (!P || P->kind != kind || !F || !X || nrhs < 1 || nrhs > P->nrhs_max) return BT_ERR_INVALID;
+    if (!P->factored) return BT_ERR_INVALID;
+    if (F == X) return BT_ERR_INVALID;
+    return BT_OK;
+}
+
+bt_status bt_solve(bt_plan P, const double* F, double* X, int nrhs) {
+    bt_status st = check_solve(P, 0, F, X, nrhs);
+    return st != BT_OK ? st : run_solve(P, F, X, nrhs);
+}
+bt_status abd_solve(abd_plan P, const double* RHS, double* Y, int nrhs) {
+    bt_status st = check_solve(P, 1, RHS, Y, nrhs);
+    return st != BT_OK ? st : run_solve(P, RHS, Y, nrhs);
+}
+bt_status bt_residual(bt_plan P, const double* F, const double* X, double* R, int nrhs) {
+    bt_status st = check_solve(P, 0, F, X, nrhs);
+    if (st == BT_OK && !R) st = BT_ERR_INVALID;
+    return st != BT_OK ? st : run_residual(P, F, X, R, nrhs);
+}
+bt_status abd_residual(abd_plan P, const double* RHS, const double* Y, double* Rout, int nrhs) {
+    bt_status st = check_solve(P, 1, RHS, Y, nrhs);
+    if (st == BT_OK && !Rout) st = BT_ERR_INVALID;
+    return st != BT_OK ? st : run_residual(P, RHS, Y, Rout, nrhs);
+}
+bt_status bt_refine(bt_plan P, const double* F, double* X, int nrhs, double tol, int maxit, int* iters_out,
+                    double* relcorr_out) {
+    bt_status st = check_solve(P, 0, F, X, nrhs);
+    if (st == BT_OK && (maxit < 1 || !(tol >= 0.0))) st = BT_ERR_INVALID;
+    return st != BT_OK ? st : run_refine(P, F, X, nrhs, tol, maxit, iters_out, relcorr_out);
+}
+bt_status abd_refine(abd_plan P, const double* RHS, double* Y, int nrhs, double tol, int maxit, int* iters_out,
+                     double* relcorr_out) {
+    bt_status st = check_solve(P, 1, RHS, Y, nrhs);
+    if (st == BT_OK && (maxit < 1 || !(tol >= 0.0))) st = BT_ERR_INVALID;
+    return st != BT_OK ? st : run_refine(P, RHS, Y, nrhs, tol, maxit, iters_out, relcorr_out);
+}
+
+bt_status bt_sync(bt_plan P) {
+    if (!P) return BT_ERR_INVALID;
+    return read_status(P);
+}
+bt_status abd_sync(abd_plan P) { return bt_sync(P); }
+
+bt_status bt_info(bt_plan P, int* level, int64_t* partition, int64_t* row) {
+    if (!P) return BT_ERR_INVALID;
+    bt_status st = read_status(P);
+    if (level) *level = (int)P->status_host[1];
+    if (partition) *partition = P->status_host[2];
+    if (row) *row = P->status_host[3];
+    return st;
+}
+
+bt_status bt_plan_levels(bt_plan P, int* levels, int64_t* rows, int64_t* parts, int capacity) {
+    if (!P) return BT_ERR_INVALID;
+    if (levels) *levels = P->nlev + 1;
+    for (int l = 0; l <= P->nlev && l < capacity; ++l) {
+        if (rows) rows[l] = P->lv[l].a.N;
+        if (parts) parts[l] = P->lv[l].a.p;
+    }
+    return BT_OK;
+}
+
+bt_status bt_plan_bytes(bt_plan P, int64_t* bytes) {
+    if (!P || !bytes) return BT_ERR_INVALID;
+    *bytes = (int64_t)P->arena_bytes;
+    return BT_OK;
+}
+
+bt_status bt_reduced_export(bt_plan P, double* alpha, double* beta, double* gamma) {
+    if (!P || !P->factored || !alpha || !beta) return BT_ERR_INVALID;
+    if (P->nlev < 1) return BT_ERR_INVALID;
+    const size_t mm = (size_t)P->m * P->m * sizeof(double);
+    const Level& u = P->lv[0];
+    cudaError_t e;
+    if (P->kind == 0) {
+        if (!gamma) return BT_ERR_INVALID;
+        const size_t bytes = mm * (size_t)(u.a.p - 1);
+        e = cudaMemcpyAsync(alpha, u.a.Dn, bytes, cudaMemcpyDeviceToDevice, P->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(beta, u.a.Bn, bytes, cudaMemcpyDeviceToDevice, P->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(gamma, u.a.Cn, bytes, cudaMemcpyDeviceToDevice, P->stream);
+    } else {
+        const size_t bytes = mm * (size_t)u.a.p;
+        e = cudaMemcpyAsync(alpha, P->B0, mm, cudaMemcpyDeviceToDevice, P->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(beta, P->B1, mm, cudaMemcpyDeviceToDevice, P->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((char*)alpha + mm, u.a.Dn, bytes, cudaMemcpyDeviceToDevice, P->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((char*)beta + mm, u.a.Bn, bytes, cudaMemcpyDeviceToDevice, P->stream);
+    }
+    return from_cuda(e);
+}
+
+bt_status bt_plan_trace(bt_plan P, int enable) {
+    if (!P) return BT_ERR_INVALID;
+    cudaError_t e = cudaStreamSynchronize(P->stream);
+    P->recs.clear();
+    P->pool_used = 0;
+    P->trace = enable != 0;
+    return from_cuda(e);
+}
+
+bt_status bt_plan_trace_query(bt_plan P, int kind, int level, double* total_ms, int64_t* launches) {
+    if (!P) return BT_ERR_INVALID;
+    cudaError_t e = cudaStreamSynchronize(P->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    double tot = 0.0;
+    int64_t n = 0;
+    for (const auto& r : P->recs) {
+        if (r.key / 4 != kind) continue;
+        if (level >= 0 && r.key % 4 != (level < 3 ? level : 3)) continue;
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) return from_cuda(e);
+        tot += ms;
+        ++n;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = n;
+    return BT_OK;
+}
+
+bt_status bt_plan_launches(bt_plan P, int64_t* count) {
+    if (!P || !count) return BT_ERR_INVALID;
+    *count = P->launches;
+    return BT_OK;
+}
+
+void bt_plan_destroy(bt_plan P) {
+    if (!P) return;
+    cudaStreamSynchronize(P->stream);
+    for (auto ev : P->pool) cudaEventDestroy(ev);
+    cudaFree(P->arena);
+    if (P->status_host) cudaFreeHost(P->status_host);
+    if (P->norms_host) cudaFreeHost(P->norms_host);
+    delete P;
+}
+void abd_plan_destroy(abd_plan P) { bt_plan_destroy(P); }
+
+}  // extern "C"

@@ -1,0 +1,577 @@
+// Partition-method kernels with one CTA of 8*M threads per partition, for
+// block sizes M in {8, 16, 32}.  All m x m block operations run from shared
+// memory (rows padded to M+1 elements); thread t owns rows
+// (t/M)*R .. (t/M)*R + R-1 of column t%M, R = M/8, so every GEMM keeps all
+// lanes busy on the FP64 (or FP32) FMA pipe.
+//
+// Algorithm (Sec. 2, the LU-type parallel factorization, Eqs. (parfact)-(parblock),
+// with the local block LU applied block row by block row and every pivot
+// block D'_j inverted by Gauss-Jordan elimination with partial pivoting, the
+// LUD/Gauss-Jordan form mentioned in Sec. 2):
+//   forward over the local rows j of a partition:
+//     D'_j  = D_j - B_j Y_{j-1}                (Schur complement update)
+//     Y_j   = D'_j^{-1} C_j                    (fill-in of the upper factor)
+//     Zc_j  = -D'_j^{-1} B_j Zc_{j-1}          (left spike; Zc_s = -D'_s^{-1} B_s)
+//   so that x_j = h_j + Zc_j x_L - Y_j x_{j+1}; h_j = D'_j^{-1}(f_j - B_j h_{j-1}).
+//   backward (full elimination, only the top row is kept):
+//     P_j = Zc_j - Y_j P_{j+1},  Q_j = -Y_j Q_{j+1},  P_{e-1} = Zc_{e-1}, Q_{e-1} = -Y_{e-1}
+//   giving x_first = H + P x_L + Q x_R.  The separator rows then form the
+//   reduced matrix of Eq. (redmatr) (assembled by bt_assemble).
+#pragma once
+#include "bt_device.cuh"
+#include "bt_level.h"
+
+namespace bt {
+
+template <typename T, int M>
+struct Cta {
+    static constexpr int NT = 8 * M;
+    static constexpr int LD = M + 1;
+    static constexpr int R = M / 8;
+    static constexpr int BLK = M * LD;
+    static constexpr int MM = M * M;
+};
+
+// ------------------------------------------------------------ block moves --
+template <typename T, int M>
+__device__ __forceinline__ void load_blk(T* s, const double* g) {
+    using S = Cta<T, M>;
+    for (int idx = threadIdx.x; idx < M * M; idx += S::NT) s[(idx / M) * S::LD + idx % M] = (T)g[idx];
+}
+template <typename T, int M>
+__device__ __forceinline__ void load_blkT(T* s, const T* g) {
+    using S = Cta<T, M>;
+    for (int idx = threadIdx.x; idx < M * M; idx += S::NT) s[(idx / M) * S::LD + idx % M] = g[idx];
+}
+template <typename T, int M, typename G>
+__device__ __forceinline__ void store_blk(G* g, const T* s) {
+    using S = Cta<T, M>;
+    for (int idx = threadIdx.x; idx < M * M; idx += S::NT) g[idx] = (G)s[(idx / M) * S::LD + idx % M];
+}
+
+// Owned elements of thread t: rows r0+q (q < R), column c.
+template <typename T, int M>
+struct Own {
+    int r0, c;
+    __device__ __forceinline__ Own() : r0((threadIdx.x / M) * Cta<T, M>::R), c(threadIdx.x % M) {}
+};
+
+// acc[q] += sgn * (A B)[r0+q][c]
+template <typename T, int M, bool NEG>
+__device__ __forceinline__ void gemm_acc(T (&acc)[Cta<T, M>::R], const T* A, const T* B, const Own<T, M>& o) {
+    using S = Cta<T, M>;
+#pragma unroll 4
+    for (int k = 0; k < M; ++k) {
+        const T b = NEG ? -B[k * S::LD + o.c] : B[k * S::LD + o.c];
+#pragma unroll
+        for (int q = 0; q < S::R; ++q) acc[q] = fmaT<T>(A[(o.r0 + q) * S::LD + k], b, acc[q]);
+    }
+}
+
+template <typename T, int M>
+__device__ __forceinline__ void read_own(T (&v)[Cta<T, M>::R], const T* s, const Own<T, M>& o) {
+#pragma unroll
+    for (int q = 0; q < Cta<T, M>::R; ++q) v[q] = s[(o.r0 + q) * Cta<T, M>::LD + o.c];
+}
+template <typename T, int M>
+__device__ __forceinline__ void write_own(T* s, const T (&v)[Cta<T, M>::R], const Own<T, M>& o) {
+#pragma unroll
+    for (int q = 0; q < Cta<T, M>::R; ++q) s[(o.r0 + q) * Cta<T, M>::LD + o.c] = v[q];
+}
+template <typename T, int M, typename G>
+__device__ __forceinline__ void store_own(G* g, const T (&v)[Cta<T, M>::R], const Own<T, M>& o) {
+#pragma unroll
+    for (int q = 0; q < Cta<T, M>::R; ++q) g[(o.r0 + q) * M + o.c] = (G)v[q];
+}
+template <typename T, int M>
+__device__ __forceinline__ void zero_own(T (&v)[Cta<T, M>::R]) {
+#pragma unroll
+    for (int q = 0; q < Cta<T, M>::R; ++q) v[q] = T(0);
+}
+
+// ------------------------------------------------------------ Gauss-Jordan --
+// In-place inverse of the M x M block a (shared memory) by Gauss-Jordan
+// elimination with partial pivoting (first index of the largest |a_ik|).
+// Row k is swapped with the pivot row before step k; the swaps are undone as
+// column swaps in reverse order at the end.  Returns false (and reports) on a
+// zero or non-finite pivot.  Entered and left with all threads synchronised.
+template <typename T, int M>
+__device__ bool gj_inverse(T* a, T* colk, int* perm, long long* st, int level, long long part,
+                           long long row) {
+    using S = Cta<T, M>;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const Own<T, M> o;
+    bool ok = true;
+    for (int k = 0; k < M; ++k) {
+        if (warp == 0) {
+            unsigned long long key = 0ull;
+            int idx = 1 << 20;
+            if (lane >= k && lane < M) {
+                key = abs_key(a[lane * S::LD + k]);
+                idx = lane;
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long ok2 = __shfl_xor_sync(0xffffffffu, key, off);
+                const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
+                if (ok2 > key || (ok2 == key && oi < idx)) {
+                    key = ok2;
+                    idx = oi;
+                }
+            }
+            const int p = idx;
+            if (p != k) {
+                for (int c = lane; c < M; c += 32) {
+                    const T t = a[k * S::LD + c];
+                    a[k * S::LD + c] = a[p * S::LD + c];
+                    a[p * S::LD + c] = t;
+                }
+            }
+            __syncwarp();
+            T pv = a[k * S::LD + k];
+            if (key == 0ull || nonfinite(pv)) {
+                if (lane == 0) report(st, key == 0ull ? ST_SINGULAR : ST_NONFINITE, level, part, row);
+                pv = T(1);
+                ok = false;
+            }
+            const T r = rcp(pv);
+            for (int i = lane; i < M; i += 32) colk[i] = (i == k) ? T(0) : a[i * S::LD + k];
+            __syncwarp();
+            for (int c = lane; c < M; c += 32) a[k * S::LD + c] = (c == k) ? r : a[k * S::LD + c] * r;
+            if (lane == 0) perm[k] = p;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < S::R; ++q) {
+            const int i = o.r0 + q;
+            if (i != k) {
+                const T l = colk[i];
+                const T akc = a[k * S::LD + o.c];
+                a[i * S::LD + o.c] = (o.c == k) ? -l * akc : fmaT<T>(-l, akc, a[i * S::LD + o.c]);
+            }
+        }
+        __syncthreads();
+    }
+    if (warp == 0 && lane < M) {
+        for (int k = M - 1; k >= 0; --k) {
+            const int p = perm[k];
+            if (p != k) {
+                const T t = a[lane * S::LD + k];
+                a[lane * S::LD + k] = a[lane * S::LD + p];
+                a[lane * S::LD + p] = t;
+            }
+        }
+    }
+    __syncthreads();
+    return ok;
+}
+
+template <typename T, int M>
+constexpr size_t factor_smem_bytes() {
+    return sizeof(T) * (6 * Cta<T, M>::BLK + M) + sizeof(int) * M;
+}
+
+// ------------------------------------------------------------------ factor --
+// One CTA per partition.  Mode 0: block tridiagonal level; mode 1: BABD level
+// (C = 0, so Y = 0 and no backward sweep; the right separator's reduced row
+// of Eq. (redmatr1) is written here: S'[i] = B_e Zc_{e-1}, R'[i] = D_e).
+template <typename T, int M, int MODE>
+__global__ void __launch_bounds__(8 * M) k_factor_cta(const LevelArgs a) {
+    using S = Cta<T, M>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sB = reinterpret_cast<T*>(smem_raw);
+    T* sD = sB + S::BLK;
+    T* sC = sD + S::BLK;
+    T* sY = sC + S::BLK;
+    T* sZ = sY + S::BLK;
+    T* sT = sZ + S::BLK;
+    T* colk = sT + S::BLK;
+    int* perm = reinterpret_cast<int*>(colk + M);
+
+    const long long i = blockIdx.x;
+    const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
+    const Own<T, M> o;
+    T* gDinv = reinterpret_cast<T*>(a.Dinv);
+    T* gY = reinterpret_cast<T*>(a.Y);
+    T* gZ = reinterpret_cast<T*>(a.Zc);
+    const long long MM = S::MM;
+
+    for (long long j = pt.s; j < pt.e; ++j) {
+        const bool first = (j == pt.s);
+        const bool needB = !first || pt.hasL;
+        const bool needC = (MODE == 0) && ((j < pt.e - 1) || pt.hasR);
+        load_blk<T, M>(sD, a.D + (j - a.shift) * MM);
+        if (needB) load_blk<T, M>(sB, a.B + (j - a.shift) * MM);
+        if (needC) load_blk<T, M>(sC, a.C + (j - a.shift) * MM);
+        __syncthreads();
+        if (MODE == 0 && !first) {
+            T acc[S::R];
+            read_own<T, M>(acc, sD, o);
+            gemm_acc<T, M, true>(acc, sB, sY, o);
+            write_own<T, M>(sD, acc, o);
+            __syncthreads();
+        }
+        gj_inverse<T, M>(sD, colk, perm, a.status, a.level, i, j);
+        store_blk<T, M>(gDinv + j * MM, sD);
+        T z[S::R], y[S::R];
+        if (pt.hasL) {
+            if (!first) {
+                T t[S::R];
+                zero_own<T, M>(t);
+                gemm_acc<T, M, false>(t, sB, sZ, o);
+                write_own<T, M>(sT, t, o);
+                __syncthreads();
+            }
+            zero_own<T, M>(z);
+            gemm_acc<T, M, true>(z, sD, first ? sB : sT, o);
+        }
+        if (needC) {
+            zero_own<T, M>(y);
+            gemm_acc<T, M, false>(y, sD, sC, o);
+        }
+        __syncthreads();
+        if (pt.hasL) {
+            write_own<T, M>(sZ, z, o);
+            store_own<T, M>(gZ + j * MM, z, o);
+        }
+        if (needC) {
+            write_own<T, M>(sY, y, o);
+            store_own<T, M>(gY + j * MM, y, o);
+        }
+        __syncthreads();
+    }
+
+    if (MODE == 0) {
+        if (!pt.hasL) return;
+        // backward sweep to the top row: P in sZ, Q in sY
+        {
+            T q[S::R];
+            read_own<T, M>(q, sY, o);
+#pragma unroll
+            for (int u = 0; u < S::R; ++u) q[u] = pt.hasR ? -q[u] : T(0);
+            __syncthreads();
+            write_own<T, M>(sY, q, o);
+            __syncthreads();
+        }
+        for (long long j = pt.e - 2; j >= pt.s; --j) {
+            load_blkT<T, M>(sC, gY + j * MM);
+            load_blkT<T, M>(sB, gZ + j * MM);
+            __syncthreads();
+            T pn[S::R], qn[S::R];
+            read_own<T, M>(pn, sB, o);
+            gemm_acc<T, M, true>(pn, sC, sZ, o);
+            zero_own<T, M>(qn);
+            gemm_acc<T, M, true>(qn, sC, sY, o);
+            __syncthreads();
+            write_own<T, M>(sZ, pn, o);
+            write_own<T, M>(sY, qn, o);
+            __syncthreads();
+        }
+        store_blk<T, M>(reinterpret_cast<T*>(a.Pf) + i * MM, sZ);
+        store_blk<T, M>(reinterpret_cast<T*>(a.Qf) + i * MM, sY);
+    } else {
+        // BABD: reduced row i+1 couples separator e to the left separator
+        const long long e = pt.e;
+        load_blk<T, M>(sB, a.B + (e - a.shift) * MM);
+        __syncthreads();
+        double* Sn = a.Bn + i * MM;
+        double* Rn = a.Dn + i * MM;
+        for (int idx = threadIdx.x; idx < M * M; idx += S::NT) Rn[idx] = a.D[(e - a.shift) * MM + idx];
+        if (pt.e > pt.s) {
+            T acc[S::R];
+            zero_own<T, M>(acc);
+            gemm_acc<T, M, false>(acc, sB, sZ, o);
+            store_own<T, M>(Sn, acc, o);
+        } else {
+            for (int idx = threadIdx.x; idx < M * M; idx += S::NT) Sn[idx] = a.B[(e - a.shift) * MM + idx];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- assemble --
+// Block tridiagonal: the reduced row of separator s (the last row e of
+// partition s) in FP64:
+//   alpha = D_e - B_e Y_{e-1} + C_e P^(s+1)_first,  beta = B_e Zc_{e-1} (s > 0),
+//   gamma = C_e Q^(s+1)_first (s+1 < p-1).
+template <typename T, int M>
+__global__ void __launch_bounds__(8 * M) k_assemble_cta(const LevelArgs a) {
+    using S = Cta<double, M>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sB = reinterpret_cast<double*>(smem_raw);
+    double* sC = sB + S::BLK;
+    double* sY = sC + S::BLK;
+    double* sZ = sY + S::BLK;
+    double* sP = sZ + S::BLK;
+    double* sQ = sP + S::BLK;
+    const long long s = blockIdx.x;
+    const Part pt = part_bounds(0, a.N, a.p, a.base, a.extra, s);
+    const long long e = pt.e;
+    const long long MM = S::MM;
+    const Own<double, M> o;
+    const bool hasBeta = s > 0;
+    const bool hasGamma = (s + 1) < a.p - 1;
+    load_blk<double, M>(sB, a.B + (e - a.shift) * MM);
+    load_blk<double, M>(sC, a.C + (e - a.shift) * MM);
+    {
+        const T* gY = reinterpret_cast<const T*>(a.Y) + (e - 1) * MM;
+        for (int idx = threadIdx.x; idx < M * M; idx += S::NT) sY[(idx / M) * S::LD + idx % M] = (double)gY[idx];
+        const T* gP = reinterpret_cast<const T*>(a.Pf) + (s + 1) * MM;
+        for (int idx = threadIdx.x; idx < M * M; idx += S::NT) sP[(idx / M) * S::LD + idx % M] = (double)gP[idx];
+        if (hasBeta) {
+            const T* gZ = reinterpret_cast<const T*>(a.Zc) + (e - 1) * MM;
+            for (int idx = threadIdx.x; idx < M * M; idx += S::NT) sZ[(idx / M) * S::LD + idx % M] = (double)gZ[idx];
+        }
+        if (hasGamma) {
+            const T* gQ = reinterpret_cast<const T*>(a.Qf) + (s + 1) * MM;
+            for (int idx = threadIdx.x; idx < M * M; idx += S::NT) sQ[(idx / M) * S::LD + idx % M] = (double)gQ[idx];
+        }
+    }
+    __syncthreads();
+    double al[S::R];
+#pragma unroll
+    for (int q = 0; q < S::R; ++q) al[q] = a.D[(e - a.shift) * MM + (o.r0 + q) * M + o.c];
+    gemm_acc<double, M, true>(al, sB, sY, o);
+    gemm_acc<double, M, false>(al, sC, sP, o);
+    store_own<double, M>(a.Dn + s * MM, al, o);
+    double be[S::R], ga[S::R];
+    zero_own<double, M>(be);
+    zero_own<double, M>(ga);
+    if (hasBeta) gemm_acc<double, M, false>(be, sB, sZ, o);
+    if (hasGamma) gemm_acc<double, M, false>(ga, sC, sQ, o);
+    store_own<double, M>(a.Bn + s * MM, be, o);
+    store_own<double, M>(a.Cn + s * MM, ga, o);
+}
+
+// ------------------------------------------------------------------- solve --
+// Elements of an M x nr right-hand-side block owned by thread t: t + u*NT.
+template <int M>
+struct RhsOwn {
+    static constexpr int MAXU = 4;   // nr <= 32
+};
+
+// Forward substitution h_j = D'_j^{-1}(f_j - B_j h_{j-1}); h_j is written to X.
+// Mode 0 with a left separator: backward H_j = h_j - Y_j H_{j+1} to the top row
+// (Hf).  Mode 1: the right separator's reduced right-hand side
+// g = f_e - B_e h_{e-1} (and partition 0 copies the boundary row).
+template <typename T, int M, int MODE>
+__global__ void __launch_bounds__(8 * M) k_solve_fwd_cta(const LevelArgs a) {
+    using S = Cta<T, M>;
+    constexpr int NT = S::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sB = reinterpret_cast<T*>(smem_raw);
+    T* sD = sB + S::BLK;
+    T* sh = sD + S::BLK;          // M x nr
+    T* sv = sh + M * 32;          // M x nr
+    const int nr = a.nr;
+    const int E = M * nr;
+    const long long i = blockIdx.x;
+    const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
+    const long long MM = S::MM;
+    const T* gDinv = reinterpret_cast<const T*>(a.Dinv);
+    for (long long j = pt.s; j < pt.e; ++j) {
+        const bool first = (j == pt.s);
+        load_blkT<T, M>(sD, gDinv + j * MM);
+        if (!first) load_blk<T, M>(sB, a.B + (j - a.shift) * MM);
+        for (int el = threadIdx.x; el < E; el += NT) sv[el] = (T)a.F[j * E + el];
+        __syncthreads();
+        if (!first) {
+            for (int el = threadIdx.x; el < E; el += NT) {
+                const int r = el / nr, c = el % nr;
+                T acc = sv[el];
+#pragma unroll 8
+                for (int k = 0; k < M; ++k) acc = fmaT<T>(-sB[r * S::LD + k], sh[k * nr + c], acc);
+                sv[el] = acc;
+            }
+            __syncthreads();
+        }
+        T h[RhsOwn<M>::MAXU];
+#pragma unroll
+        for (int u = 0; u < RhsOwn<M>::MAXU; ++u) {
+            const int el = threadIdx.x + u * NT;
+            h[u] = T(0);
+            if (el < E) {
+                const int r = el / nr, c = el % nr;
+                T acc = T(0);
+#pragma unroll 8
+                for (int k = 0; k < M; ++k) acc = fmaT<T>(sD[r * S::LD + k], sv[k * nr + c], acc);
+                h[u] = acc;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < RhsOwn<M>::MAXU; ++u) {
+            const int el = threadIdx.x + u * NT;
+            if (el < E) {
+                sh[el] = h[u];
+                a.X[j * E + el] = (double)h[u];
+            }
+        }
+        __syncthreads();
+    }
+    if (MODE == 1) {
+        const long long e = pt.e;
+        if (i == 0)
+            for (int el = threadIdx.x; el < E; el += NT) a.Fn[el] = a.F[el];
+        load_blk<T, M>(sB, a.B + (e - a.shift) * MM);
+        __syncthreads();
+        for (int el = threadIdx.x; el < E; el += NT) {
+            const int r = el / nr, c = el % nr;
+            double acc = a.F[e * E + el];
+            if (pt.e > pt.s) {
+                T t = T(0);
+#pragma unroll 8
+                for (int k = 0; k < M; ++k) t = fmaT<T>(sB[r * S::LD + k], sh[k * nr + c], t);
+                acc -= (double)t;
+            }
+            a.Fn[(i + 1) * E + el] = acc;
+        }
+        return;
+    }
+    if (!pt.hasL) return;
+    const T* gY = reinterpret_cast<const T*>(a.Y);
+    for (long long j = pt.e - 2; j >= pt.s; --j) {
+        load_blkT<T, M>(sB, gY + j * MM);
+        for (int el = threadIdx.x; el < E; el += NT) sv[el] = (T)a.X[j * E + el];
+        __syncthreads();
+        T h[RhsOwn<M>::MAXU];
+#pragma unroll
+        for (int u = 0; u < RhsOwn<M>::MAXU; ++u) {
+            const int el = threadIdx.x + u * NT;
+            h[u] = T(0);
+            if (el < E) {
+                const int r = el / nr, c = el % nr;
+                T acc = sv[el];
+#pragma unroll 8
+                for (int k = 0; k < M; ++k) acc = fmaT<T>(-sB[r * S::LD + k], sh[k * nr + c], acc);
+                h[u] = acc;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < RhsOwn<M>::MAXU; ++u) {
+            const int el = threadIdx.x + u * NT;
+            if (el < E) sh[el] = h[u];
+        }
+        __syncthreads();
+    }
+    T* Hf = reinterpret_cast<T*>(a.Hf) + i * E;
+    for (int el = threadIdx.x; el < E; el += NT) Hf[el] = sh[el];
+}
+
+// Block tridiagonal reduced right-hand side of separator s:
+//   g = f_e - B_e h_{e-1} - C_e H^(s+1)_first   (FP64).
+template <typename T, int M>
+__global__ void __launch_bounds__(8 * M) k_assemble_rhs_cta(const LevelArgs a) {
+    using S = Cta<double, M>;
+    constexpr int NT = S::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sB = reinterpret_cast<double*>(smem_raw);
+    double* sC = sB + S::BLK;
+    double* sh = sC + S::BLK;
+    double* sH = sh + M * 32;
+    const int nr = a.nr;
+    const int E = M * nr;
+    const long long s = blockIdx.x;
+    const Part pt = part_bounds(0, a.N, a.p, a.base, a.extra, s);
+    const long long e = pt.e;
+    const long long MM = S::MM;
+    load_blk<double, M>(sB, a.B + (e - a.shift) * MM);
+    load_blk<double, M>(sC, a.C + (e - a.shift) * MM);
+    const T* Hf = reinterpret_cast<const T*>(a.Hf) + (s + 1) * E;
+    for (int el = threadIdx.x; el < E; el += NT) {
+        sh[el] = a.X[(e - 1) * E + el];
+        sH[el] = (double)Hf[el];
+    }
+    __syncthreads();
+    for (int el = threadIdx.x; el < E; el += NT) {
+        const int r = el / nr, c = el % nr;
+        double acc = a.F[e * E + el];
+#pragma unroll 8
+        for (int k = 0; k < M; ++k) {
+            acc = fma(-sB[r * S::LD + k], sh[k * nr + c], acc);
+            acc = fma(-sC[r * S::LD + k], sH[k * nr + c], acc);
+        }
+        a.Fn[s * E + el] = acc;
+    }
+}
+
+// Back substitution x_j = h_j + Zc_j x_L - Y_j x_{j+1} from the last local row
+// up, with x_L, x_R from the next level's solution; also copies the
+// separator rows owned by this partition into X.
+template <typename T, int M, int MODE>
+__global__ void __launch_bounds__(8 * M) k_solve_bwd_cta(const LevelArgs a) {
+    using S = Cta<T, M>;
+    constexpr int NT = S::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sY = reinterpret_cast<T*>(smem_raw);
+    T* sZ = sY + S::BLK;
+    T* sx = sZ + S::BLK;   // x_{j+1}
+    T* sL = sx + M * 32;   // x_L
+    const int nr = a.nr;
+    const int E = M * nr;
+    const long long i = blockIdx.x;
+    const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
+    const long long MM = S::MM;
+    const long long li = (MODE == 0) ? i - 1 : i;   // next-level index of x_L
+    const long long ri = (MODE == 0) ? i : i + 1;   // next-level index of x_R
+    for (int el = threadIdx.x; el < E; el += NT) {
+        const double xr = pt.hasR ? a.Xn[ri * E + el] : 0.0;
+        sx[el] = (T)xr;
+        sL[el] = pt.hasL ? (T)a.Xn[li * E + el] : T(0);
+        if (pt.hasR) a.X[pt.e * E + el] = xr;
+        if (MODE == 1 && i == 0) a.X[el] = a.Xn[el];
+    }
+    __syncthreads();
+    const T* gY = reinterpret_cast<const T*>(a.Y);
+    const T* gZ = reinterpret_cast<const T*>(a.Zc);
+    for (long long j = pt.e - 1; j >= pt.s; --j) {
+        const bool useY = (MODE == 0) && ((j < pt.e - 1) || pt.hasR);
+        if (useY) load_blkT<T, M>(sY, gY + j * MM);
+        if (pt.hasL) load_blkT<T, M>(sZ, gZ + j * MM);
+        __syncthreads();
+        T xv[RhsOwn<M>::MAXU];
+#pragma unroll
+        for (int u = 0; u < RhsOwn<M>::MAXU; ++u) {
+            const int el = threadIdx.x + u * NT;
+            xv[u] = T(0);
+            if (el < E) {
+                const int r = el / nr, c = el % nr;
+                T acc = (T)a.X[j * E + el];
+                if (useY) {
+#pragma unroll 8
+                    for (int k = 0; k < M; ++k) acc = fmaT<T>(-sY[r * S::LD + k], sx[k * nr + c], acc);
+                }
+                if (pt.hasL) {
+#pragma unroll 8
+                    for (int k = 0; k < M; ++k) acc = fmaT<T>(sZ[r * S::LD + k], sL[k * nr + c], acc);
+                }
+                xv[u] = acc;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < RhsOwn<M>::MAXU; ++u) {
+            const int el = threadIdx.x + u * NT;
+            if (el < E) {
+                sx[el] = xv[u];
+                a.X[j * E + el] = (double)xv[u];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int M>
+constexpr size_t solve_smem_bytes() {
+    return sizeof(T) * (2 * Cta<T, M>::BLK + 2 * M * 32);
+}
+template <int M>
+constexpr size_t assemble_smem_bytes() {
+    return sizeof(double) * (6 * Cta<double, M>::BLK);
+}
+template <int M>
+constexpr size_t assemble_rhs_smem_bytes() {
+    return sizeof(double) * (2 * Cta<double, M>::BLK + 2 * M * 32);
+}
+
+}  // namespace bt

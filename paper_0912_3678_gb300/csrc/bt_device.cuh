@@ -1,0 +1,87 @@
+// Device-side helpers shared by the partition-method kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bt {
+
+enum : int { ST_OK = 0, ST_SINGULAR = 3, ST_NONFINITE = 4, ST_TIMEOUT = 6 };
+
+// Status word (4 x int64): [0] code, [1] level, [2] partition, [3] block row.
+// The first error wins; later ones are dropped.
+__device__ __forceinline__ void report(long long* st, int code, long long level, long long part,
+                                       long long row) {
+    if (st == nullptr) return;
+    if (atomicCAS(reinterpret_cast<unsigned long long*>(st), 0ull, (unsigned long long)code) == 0ull) {
+        st[1] = level;
+        st[2] = part;
+        st[3] = row;
+    }
+}
+
+// 1/x.  For x well inside the float range: a float reciprocal seed r0 refined
+// by one third-order Newton step, r = r0 (1 + e + e^2) with e = 1 - x r0,
+// i.e. the geometric series of 1/(1 - e) truncated after e^2 (relative error
+// about e^3 ~ 2^-66 before the final rounding).  Zero, subnormal, huge and
+// non-finite x take the IEEE division.
+__device__ __forceinline__ double rcp(double x) {
+    const int ex = (__double2hiint(x) >> 20) & 0x7ff;
+    if (ex < 1023 - 120 || ex > 1023 + 120) return 1.0 / x;
+    const float xf = __double2float_rn(x);
+    float r0f;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"(xf));
+    const double r0 = (double)r0f;
+    const double e = fma(-x, r0, 1.0);
+    const double t = fma(e, e, e);
+    return fma(r0, t, r0);
+}
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+
+// |x| as an integer key that orders like |x| for finite x (sign bit cleared).
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long abs_key(float x) {
+    return (unsigned long long)(__float_as_uint(x) & 0x7fffffffu);
+}
+__device__ __forceinline__ bool nonfinite(double x) {
+    return ((__double2hiint(x) >> 20) & 0x7ff) == 0x7ff;
+}
+__device__ __forceinline__ bool nonfinite(float x) {
+    return ((__float_as_uint(x) >> 23) & 0xff) == 0xff;
+}
+
+template <typename T> __device__ __forceinline__ T fmaT(T a, T b, T c);
+template <> __device__ __forceinline__ double fmaT<double>(double a, double b, double c) { return fma(a, b, c); }
+template <> __device__ __forceinline__ float fmaT<float>(float a, float b, float c) { return fmaf(a, b, c); }
+
+// ---------------------------------------------------------------- geometry --
+// Block-tridiagonal level (mode 0): rows 0..N-1 in p partitions; partition i
+// owns base + (i < extra) rows, its last row is the separator for i < p-1.
+// BABD level (mode 1): rows 0..N; rows 1..N-1 are split the same way, the
+// separators are row 0, the last row of partitions 0..p-2, and row N.
+struct Part {
+    long long s, e;   // local rows [s, e); e is the right separator row if hasR
+    bool hasL, hasR;
+};
+
+__device__ __forceinline__ Part part_bounds(int mode, long long N, long long p, long long base,
+                                            long long extra, long long i) {
+    Part q;
+    const long long cnt = base + (i < extra ? 1 : 0);
+    const long long start = i * base + (i < extra ? i : extra);
+    if (mode == 0) {
+        q.s = start;
+        q.hasL = i > 0;
+        q.hasR = i < p - 1;
+        q.e = q.hasR ? start + cnt - 1 : start + cnt;
+    } else {
+        q.s = 1 + start;
+        q.hasL = true;
+        q.hasR = true;
+        q.e = (i < p - 1) ? q.s + cnt - 1 : N;
+    }
+    return q;
+}
+
+}  // namespace bt

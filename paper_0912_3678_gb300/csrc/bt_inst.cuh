@@ -1,0 +1,108 @@
+// Instantiates the launchers of one block order M (included by bt_inst_m*.cu).
+#pragma once
+#include "bt_cta.cuh"
+#include "bt_launch.h"
+#include "bt_tp.cuh"
+
+namespace bt {
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+static inline unsigned grid_for(long long threads, int block) { return (unsigned)((threads + block - 1) / block); }
+
+template <int M>
+struct Inst {
+    template <typename T, int MODE>
+    static cudaError_t factor_t(const LevelArgs& a, cudaStream_t s) {
+        if (a.p <= 0) return cudaSuccess;
+        if constexpr (M >= 8) {
+            const size_t smem = factor_smem_bytes<T, M>();
+            cudaError_t e = set_smem(k_factor_cta<T, M, MODE>, smem);
+            if (e != cudaSuccess) return e;
+            k_factor_cta<T, M, MODE><<<(unsigned)a.p, 8 * M, smem, s>>>(a);
+        } else {
+            k_factor_tp<T, M, MODE><<<grid_for(a.p, 128), 128, 0, s>>>(a);
+        }
+        return cudaGetLastError();
+    }
+    static cudaError_t factor(const LevelArgs& a, bool low, cudaStream_t s) {
+        if (a.mode == 0) return low ? factor_t<float, 0>(a, s) : factor_t<double, 0>(a, s);
+        return low ? factor_t<float, 1>(a, s) : factor_t<double, 1>(a, s);
+    }
+    template <typename T>
+    static cudaError_t assemble_t(const LevelArgs& a, cudaStream_t s) {
+        if (a.p <= 1) return cudaSuccess;
+        if constexpr (M >= 8) {
+            const size_t smem = assemble_smem_bytes<M>();
+            cudaError_t e = set_smem(k_assemble_cta<T, M>, smem);
+            if (e != cudaSuccess) return e;
+            k_assemble_cta<T, M><<<(unsigned)(a.p - 1), 8 * M, smem, s>>>(a);
+        } else {
+            k_assemble_tp<T, M><<<grid_for(a.p - 1, 128), 128, 0, s>>>(a);
+        }
+        return cudaGetLastError();
+    }
+    static cudaError_t assemble(const LevelArgs& a, bool low, cudaStream_t s) {
+        return low ? assemble_t<float>(a, s) : assemble_t<double>(a, s);
+    }
+    template <typename T, int MODE>
+    static cudaError_t solve_fwd_t(const LevelArgs& a, cudaStream_t s) {
+        if (a.p <= 0) return cudaSuccess;
+        if constexpr (M >= 8) {
+            const size_t smem = solve_smem_bytes<T, M>();
+            cudaError_t e = set_smem(k_solve_fwd_cta<T, M, MODE>, smem);
+            if (e != cudaSuccess) return e;
+            k_solve_fwd_cta<T, M, MODE><<<(unsigned)a.p, 8 * M, smem, s>>>(a);
+        } else {
+            k_solve_fwd_tp<T, M, MODE><<<grid_for(a.p * a.nr, 128), 128, 0, s>>>(a);
+        }
+        return cudaGetLastError();
+    }
+    static cudaError_t solve_fwd(const LevelArgs& a, bool low, cudaStream_t s) {
+        if (a.mode == 0) return low ? solve_fwd_t<float, 0>(a, s) : solve_fwd_t<double, 0>(a, s);
+        return low ? solve_fwd_t<float, 1>(a, s) : solve_fwd_t<double, 1>(a, s);
+    }
+    template <typename T>
+    static cudaError_t assemble_rhs_t(const LevelArgs& a, cudaStream_t s) {
+        if (a.p <= 1) return cudaSuccess;
+        if constexpr (M >= 8) {
+            const size_t smem = assemble_rhs_smem_bytes<M>();
+            cudaError_t e = set_smem(k_assemble_rhs_cta<T, M>, smem);
+            if (e != cudaSuccess) return e;
+            k_assemble_rhs_cta<T, M><<<(unsigned)(a.p - 1), 8 * M, smem, s>>>(a);
+        } else {
+            k_assemble_rhs_tp<T, M><<<grid_for((a.p - 1) * a.nr, 128), 128, 0, s>>>(a);
+        }
+        return cudaGetLastError();
+    }
+    static cudaError_t assemble_rhs(const LevelArgs& a, bool low, cudaStream_t s) {
+        return low ? assemble_rhs_t<float>(a, s) : assemble_rhs_t<double>(a, s);
+    }
+    template <typename T, int MODE>
+    static cudaError_t solve_bwd_t(const LevelArgs& a, cudaStream_t s) {
+        if (a.p <= 0) return cudaSuccess;
+        if constexpr (M >= 8) {
+            const size_t smem = solve_smem_bytes<T, M>();
+            cudaError_t e = set_smem(k_solve_bwd_cta<T, M, MODE>, smem);
+            if (e != cudaSuccess) return e;
+            k_solve_bwd_cta<T, M, MODE><<<(unsigned)a.p, 8 * M, smem, s>>>(a);
+        } else {
+            k_solve_bwd_tp<T, M, MODE><<<grid_for(a.p * a.nr, 128), 128, 0, s>>>(a);
+        }
+        return cudaGetLastError();
+    }
+    static cudaError_t solve_bwd(const LevelArgs& a, bool low, cudaStream_t s) {
+        if (a.mode == 0) return low ? solve_bwd_t<float, 0>(a, s) : solve_bwd_t<double, 0>(a, s);
+        return low ? solve_bwd_t<float, 1>(a, s) : solve_bwd_t<double, 1>(a, s);
+    }
+    static const Launchers* table() {
+        static const Launchers L = {factor, assemble, solve_fwd, assemble_rhs, solve_bwd};
+        return &L;
+    }
+};
+
+}  // namespace bt

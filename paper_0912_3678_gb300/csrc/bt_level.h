@@ -1,0 +1,39 @@
+// Arguments of one level of the recursive partition method (host and device).
+#pragma once
+#include <cstdint>
+
+namespace bt {
+
+// One level: a block tridiagonal system (mode 0, block rows 0..N-1) or a
+// BABD system (mode 1, block rows 0..N with row 0 the boundary row and the
+// corner coupling row 0 to row N).  Block row r of the level matrix is read
+// at index r - shift of B/D/C (BABD: B = S, D = R, shift = 1, C unused).
+struct LevelArgs {
+    int mode;
+    int level;
+    long long N, p, base, extra;
+    const double* B;
+    const double* D;
+    const double* C;
+    int shift;
+    // factors of the local blocks, element type T of the level, indexed by block row
+    void* Dinv;     // D'_j^{-1}
+    void* Y;        // D'_j^{-1} C_j
+    void* Zc;       // left spike coefficient: x_j = h_j + Zc_j x_L - Y_j x_{j+1}
+    void* Pf;       // [p][m][m] top-row coefficient on x_L after full elimination
+    void* Qf;       // [p][m][m] top-row coefficient on x_R
+    // next level matrix (FP64)
+    double* Bn;
+    double* Dn;
+    double* Cn;
+    // solve phase
+    const double* F;   // [rows][m][nr] right-hand side of this level
+    double* X;         // [rows][m][nr] solution of this level (holds h_j in between)
+    int nr;
+    double* Fn;        // next level right-hand side
+    const double* Xn;  // next level solution
+    void* Hf;          // [p][m][nr] top-row right-hand side after full elimination (T)
+    long long* status;
+};
+
+}  // namespace bt

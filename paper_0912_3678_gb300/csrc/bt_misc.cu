@@ -1,0 +1,358 @@
+// FP64 residuals, the refinement update with deterministic norms, and the
+// direct solver for the small BABD system at the top of the recursion.
+#include <cuda_runtime.h>
+#include "bt_device.cuh"
+#include "bt_misc.h"
+
+namespace bt {
+
+// r = f - A x for the block tridiagonal A; one thread per entry of [N*m][nr].
+__global__ void __launch_bounds__(256) k_resid_btri(long long N, int m, int nr, const double* __restrict__ B,
+                                                    const double* __restrict__ D, const double* __restrict__ C,
+                                                    const double* __restrict__ X, const double* __restrict__ F,
+                                                    double* __restrict__ R) {
+    const long long el = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = N * m * nr;
+    if (el >= total) return;
+    const long long gr = el / nr;
+    const int c = (int)(el % nr);
+    const long long j = gr / m;
+    const int r = (int)(gr % m);
+    const long long mm = (long long)m * m;
+    double acc = F[el];
+    const double* Drow = D + j * mm + (long long)r * m;
+    const double* xj = X + j * m * nr + c;
+    for (int k = 0; k < m; ++k) acc = fma(-Drow[k], xj[(long long)k * nr], acc);
+    if (j > 0) {
+        const double* Brow = B + j * mm + (long long)r * m;
+        const double* xp = xj - (long long)m * nr;
+        for (int k = 0; k < m; ++k) acc = fma(-Brow[k], xp[(long long)k * nr], acc);
+    }
+    if (j + 1 < N) {
+        const double* Crow = C + j * mm + (long long)r * m;
+        const double* xn = xj + (long long)m * nr;
+        for (int k = 0; k < m; ++k) acc = fma(-Crow[k], xn[(long long)k * nr], acc);
+    }
+    R[el] = acc;
+}
+
+// r = f - A y for the BABD A (rows 0..N, boundary row first).
+__global__ void __launch_bounds__(256) k_resid_babd(long long N, int m, int nr, const double* __restrict__ S,
+                                                    const double* __restrict__ Rm, const double* __restrict__ B0,
+                                                    const double* __restrict__ B1, const double* __restrict__ Y,
+                                                    const double* __restrict__ F, double* __restrict__ Rout) {
+    const long long el = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (N + 1) * m * nr;
+    if (el >= total) return;
+    const long long gr = el / nr;
+    const int c = (int)(el % nr);
+    const long long j = gr / m;
+    const int r = (int)(gr % m);
+    const long long mm = (long long)m * m;
+    double acc = F[el];
+    if (j == 0) {
+        const double* y0 = Y + c;
+        const double* yN = Y + N * m * nr + c;
+        for (int k = 0; k < m; ++k) {
+            acc = fma(-B0[r * m + k], y0[(long long)k * nr], acc);
+            acc = fma(-B1[r * m + k], yN[(long long)k * nr], acc);
+        }
+    } else {
+        const double* Srow = S + (j - 1) * mm + (long long)r * m;
+        const double* Rrow = Rm + (j - 1) * mm + (long long)r * m;
+        const double* yp = Y + (j - 1) * m * nr + c;
+        const double* yj = Y + j * m * nr + c;
+        for (int k = 0; k < m; ++k) {
+            acc = fma(-Srow[k], yp[(long long)k * nr], acc);
+            acc = fma(-Rrow[k], yj[(long long)k * nr], acc);
+        }
+    }
+    Rout[el] = acc;
+}
+
+// x += d; per-block partial sums of |d|^2 and |x|^2 (after the update).
+__global__ void __launch_bounds__(256) k_ir_update(long long n, double* __restrict__ X,
+                                                   const double* __restrict__ Dc, double* __restrict__ partial) {
+    __shared__ double sd[256], sx[256];
+    double ad = 0.0, ax = 0.0;
+    for (long long el = (long long)blockIdx.x * blockDim.x + threadIdx.x; el < n;
+         el += (long long)gridDim.x * blockDim.x) {
+        const double d = Dc[el];
+        const double x = X[el] + d;
+        X[el] = x;
+        ad = fma(d, d, ad);
+        ax = fma(x, x, ax);
+    }
+    sd[threadIdx.x] = ad;
+    sx[threadIdx.x] = ax;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sd[threadIdx.x] += sd[threadIdx.x + s];
+            sx[threadIdx.x] += sx[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = sd[0];
+        partial[2 * blockIdx.x + 1] = sx[0];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_reduce_pairs(int nblocks, const double* __restrict__ partial,
+                                                      double* __restrict__ out) {
+    __shared__ double sd[256], sx[256];
+    double ad = 0.0, ax = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        ad += partial[2 * b];
+        ax += partial[2 * b + 1];
+    }
+    sd[threadIdx.x] = ad;
+    sx[threadIdx.x] = ax;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sd[threadIdx.x] += sd[threadIdx.x + s];
+            sx[threadIdx.x] += sx[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = sd[0];
+        out[1] = sx[0];
+    }
+}
+
+// Direct solve of a small BABD system (rows 0..Np: B0 y_0 + B1 y_Np = f_0;
+// S_j y_j + R_j y_{j+1} = f_{j+1}) in one CTA by Gaussian elimination with
+// partial pivoting restricted to the rows that are nonzero in each pivot
+// column: m rows carried from the previous step (initially the boundary
+// rows, which carry the corner fill-in) and the m rows of block row j+1.
+// Columns of the working rows: [y_j | y_{j+1} | y_Np | rhs].
+// keep: workspace of Np * m * (3m + nr) doubles for the pivot rows.
+__global__ void __launch_bounds__(256) k_babd_direct(int Np, int m, int nr, const double* __restrict__ S,
+                                                     const double* __restrict__ R, const double* __restrict__ B0,
+                                                     const double* __restrict__ B1, const double* __restrict__ F,
+                                                     double* __restrict__ X, double* __restrict__ keep,
+                                                     long long* status, int level) {
+    extern __shared__ __align__(16) double sm[];
+    const int W = 3 * m + nr, H = 2 * m;
+    double* w = sm;
+    double* colk = w + H * W;
+    const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const long long mm = (long long)m * m;
+    const int MW = m * W;
+    for (int idx = tid; idx < MW; idx += NT) {
+        const int r = idx / W, c = idx % W;
+        double v;
+        if (c < m) v = B0[r * m + c];
+        else if (c < 2 * m) v = 0.0;
+        else if (c < 3 * m) v = B1[r * m + (c - 2 * m)];
+        else v = F[r * nr + (c - 3 * m)];
+        w[idx] = v;
+    }
+    __syncthreads();
+    for (int j = 0; j < Np; ++j) {
+        const bool last = (j + 1 == Np);
+        for (int idx = tid; idx < MW; idx += NT) {
+            const int r = idx / W, c = idx % W;
+            double v;
+            if (c < m) v = S[j * mm + r * m + c];
+            else if (c < 2 * m) v = last ? 0.0 : R[j * mm + r * m + (c - m)];
+            else if (c < 3 * m) v = last ? R[j * mm + r * m + (c - 2 * m)] : 0.0;
+            else v = F[((long long)(j + 1) * m + r) * nr + (c - 3 * m)];
+            w[MW + idx] = v;
+        }
+        __syncthreads();
+        for (int k = 0; k < m; ++k) {
+            if (warp == 0) {
+                unsigned long long key = 0ull;
+                int idx = 1 << 20;
+                for (int i = lane; i < H; i += 32) {
+                    if (i >= k) {
+                        const unsigned long long kk = abs_key(w[i * W + k]);
+                        if (kk > key || (kk == key && i < idx)) {
+                            key = kk;
+                            idx = i;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, off);
+                    const int i2 = __shfl_xor_sync(0xffffffffu, idx, off);
+                    if (k2 > key || (k2 == key && i2 < idx)) {
+                        key = k2;
+                        idx = i2;
+                    }
+                }
+                const int p = idx;
+                if (p != k)
+                    for (int c = lane; c < W; c += 32) {
+                        const double t = w[k * W + c];
+                        w[k * W + c] = w[p * W + c];
+                        w[p * W + c] = t;
+                    }
+                __syncwarp();
+                double pv = w[k * W + k];
+                if (key == 0ull || nonfinite(pv)) {
+                    if (lane == 0) report(status, key == 0ull ? ST_SINGULAR : ST_NONFINITE, level, -1, j);
+                    pv = 1.0;
+                }
+                const double rp = rcp(pv);
+                for (int i = lane; i < H; i += 32) colk[i] = (i > k) ? w[i * W + k] * rp : 0.0;
+            }
+            __syncthreads();
+            const int rows = H - k - 1, cols = W - k - 1;
+            for (int idx = tid; idx < rows * cols; idx += NT) {
+                const int i = k + 1 + idx / cols, c = k + 1 + idx % cols;
+                w[i * W + c] = fma(-colk[i], w[k * W + c], w[i * W + c]);
+            }
+            for (int i = k + 1 + tid; i < H; i += NT) w[i * W + k] = 0.0;
+            __syncthreads();
+        }
+        double* kp = keep + (long long)j * MW;
+        for (int idx = tid; idx < MW; idx += NT) kp[idx] = w[idx];
+        __syncthreads();
+        double tmp[16];
+        int u = 0;
+        for (int idx = tid; idx < MW; idx += NT, ++u) {
+            const int r = idx / W, c = idx % W;
+            const double* src = w + (m + r) * W;
+            double v;
+            if (c < m) v = src[m + c];
+            else if (c < 2 * m) v = 0.0;
+            else v = src[c];
+            tmp[u] = v;
+        }
+        __syncthreads();
+        u = 0;
+        for (int idx = tid; idx < MW; idx += NT, ++u) w[idx] = tmp[u];
+        __syncthreads();
+    }
+    // final m x m system in y_Np: Gauss-Jordan with partial pivoting on rows 0..m-1
+    for (int k = 0; k < m; ++k) {
+        const int ck = 2 * m + k;
+        if (warp == 0) {
+            unsigned long long key = 0ull;
+            int idx = 1 << 20;
+            if (lane >= k && lane < m) {
+                key = abs_key(w[lane * W + ck]);
+                idx = lane;
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, off);
+                const int i2 = __shfl_xor_sync(0xffffffffu, idx, off);
+                if (k2 > key || (k2 == key && i2 < idx)) {
+                    key = k2;
+                    idx = i2;
+                }
+            }
+            const int p = idx;
+            if (p != k)
+                for (int c = lane; c < W; c += 32) {
+                    const double t = w[k * W + c];
+                    w[k * W + c] = w[p * W + c];
+                    w[p * W + c] = t;
+                }
+            __syncwarp();
+            double pv = w[k * W + ck];
+            if (key == 0ull || nonfinite(pv)) {
+                if (lane == 0) report(status, key == 0ull ? ST_SINGULAR : ST_NONFINITE, level, -1, Np);
+                pv = 1.0;
+            }
+            const double rp = rcp(pv);
+            __syncwarp();
+            for (int c = 2 * m + lane; c < W; c += 32) w[k * W + c] = (c == ck) ? 1.0 : w[k * W + c] * rp;
+            __syncwarp();
+            for (int i = lane; i < m; i += 32) colk[i] = (i == k) ? 0.0 : w[i * W + ck];
+        }
+        __syncthreads();
+        const int cols = W - 2 * m;
+        for (int idx = tid; idx < m * cols; idx += NT) {
+            const int i = idx / cols, c = 2 * m + idx % cols;
+            if (i != k) w[i * W + c] = fma(-colk[i], w[k * W + c], w[i * W + c]);
+        }
+        __syncthreads();
+    }
+    const long long E = (long long)m * nr;
+    for (int idx = tid; idx < m * nr; idx += NT) {
+        const int r = idx / nr, c = idx % nr;
+        X[(long long)Np * E + idx] = w[r * W + 3 * m + c];
+    }
+    __syncthreads();
+    // back substitution: U_j y_j = rhs_j - P_j y_{j+1} - Q_j y_Np
+    double* t = w;   // m x nr
+    for (int j = Np - 1; j >= 0; --j) {
+        const double* kp = keep + (long long)j * MW;
+        const double* y1 = X + (long long)(j + 1) * E;
+        const double* yN = X + (long long)Np * E;
+        const bool last = (j + 1 == Np);
+        for (int idx = tid; idx < m * nr; idx += NT) {
+            const int r = idx / nr, c = idx % nr;
+            double acc = kp[r * W + 3 * m + c];
+            for (int k = 0; k < m; ++k) {
+                if (!last) acc = fma(-kp[r * W + m + k], y1[k * nr + c], acc);
+                acc = fma(-kp[r * W + 2 * m + k], yN[k * nr + c], acc);
+            }
+            t[idx] = acc;
+        }
+        __syncthreads();
+        double* yj = X + (long long)j * E;
+        for (int c = tid; c < nr; c += NT) {
+            for (int r = m - 1; r >= 0; --r) {
+                double acc = t[r * nr + c];
+                for (int k = r + 1; k < m; ++k) acc = fma(-kp[r * W + k], t[k * nr + c], acc);
+                acc = acc * rcp(kp[r * W + r]);
+                t[r * nr + c] = acc;
+                yj[r * nr + c] = acc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+size_t babd_direct_smem(int m, int nr) { return sizeof(double) * ((size_t)(2 * m) * (3 * m + nr) + 2 * m); }
+
+cudaError_t launch_resid_btri(long long N, int m, int nr, const double* B, const double* D, const double* C,
+                              const double* X, const double* F, double* R, cudaStream_t s) {
+    const long long total = N * m * nr;
+    if (total == 0) return cudaSuccess;
+    k_resid_btri<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(N, m, nr, B, D, C, X, F, R);
+    return cudaGetLastError();
+}
+cudaError_t launch_resid_babd(long long N, int m, int nr, const double* S, const double* Rm, const double* B0,
+                              const double* B1, const double* Y, const double* F, double* Rout, cudaStream_t s) {
+    const long long total = (N + 1) * m * nr;
+    k_resid_babd<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(N, m, nr, S, Rm, B0, B1, Y, F, Rout);
+    return cudaGetLastError();
+}
+int ir_update_blocks(long long n) {
+    long long b = (n + 255) / 256;
+    if (b > 1024) b = 1024;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+cudaError_t launch_ir_update(long long n, double* X, const double* Dc, double* partial, double* out,
+                             cudaStream_t s) {
+    const int nb = ir_update_blocks(n);
+    k_ir_update<<<nb, 256, 0, s>>>(n, X, Dc, partial);
+    k_reduce_pairs<<<1, 256, 0, s>>>(nb, partial, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_babd_direct(int Np, int m, int nr, const double* S, const double* R, const double* B0,
+                               const double* B1, const double* F, double* X, double* keep, long long* status,
+                               int level, cudaStream_t s) {
+    const size_t smem = babd_direct_smem(m, nr);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_babd_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_babd_direct<<<1, 256, smem, s>>>(Np, m, nr, S, R, B0, B1, F, X, keep, status, level);
+    return cudaGetLastError();
+}
+
+}  // namespace bt

@@ -1,0 +1,17 @@
+// Launchers for the FP64 residual, refinement and small direct-solve kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace bt {
+cudaError_t launch_resid_btri(long long N, int m, int nr, const double* B, const double* D, const double* C,
+                              const double* X, const double* F, double* R, cudaStream_t s);
+cudaError_t launch_resid_babd(long long N, int m, int nr, const double* S, const double* Rm, const double* B0,
+                              const double* B1, const double* Y, const double* F, double* Rout, cudaStream_t s);
+int ir_update_blocks(long long n);
+cudaError_t launch_ir_update(long long n, double* X, const double* Dc, double* partial, double* out,
+                             cudaStream_t s);
+size_t babd_direct_smem(int m, int nr);
+cudaError_t launch_babd_direct(int Np, int m, int nr, const double* S, const double* R, const double* B0,
+                               const double* B1, const double* F, double* X, double* keep, long long* status,
+                               int level, cudaStream_t s);
+}  // namespace bt

@@ -1,0 +1,375 @@
+// Partition-method kernels with one thread per partition (factor) or per
+// (partition, right-hand side) pair (solve), for block sizes M in {1, 2, 4}:
+// the m x m blocks live in registers.  Same algorithm and outputs as the
+// CTA kernels in bt_cta.cuh.
+#pragma once
+#include "bt_device.cuh"
+#include "bt_level.h"
+
+namespace bt {
+
+template <typename T, int M>
+struct Reg {
+    static constexpr int MM = M * M;
+};
+
+template <typename T, int M, typename G>
+__device__ __forceinline__ void rld(T (&b)[M * M], const G* g) {
+#pragma unroll
+    for (int u = 0; u < M * M; ++u) b[u] = (T)g[u];
+}
+template <typename T, int M, typename G>
+__device__ __forceinline__ void rst(G* g, const T (&b)[M * M]) {
+#pragma unroll
+    for (int u = 0; u < M * M; ++u) g[u] = (G)b[u];
+}
+// c = sgn * a b (+ c if ACC)
+template <typename T, int M, bool NEG, bool ACC>
+__device__ __forceinline__ void rmm(T (&c)[M * M], const T (&a)[M * M], const T (&b)[M * M]) {
+    T out[M * M];
+#pragma unroll
+    for (int r = 0; r < M; ++r)
+#pragma unroll
+        for (int cc = 0; cc < M; ++cc) {
+            T acc = ACC ? c[r * M + cc] : T(0);
+#pragma unroll
+            for (int k = 0; k < M; ++k) acc = fmaT<T>(NEG ? -a[r * M + k] : a[r * M + k], b[k * M + cc], acc);
+            out[r * M + cc] = acc;
+        }
+#pragma unroll
+    for (int u = 0; u < M * M; ++u) c[u] = out[u];
+}
+
+// In-place Gauss-Jordan inverse with partial pivoting, blocks in registers.
+template <typename T, int M>
+__device__ __forceinline__ void rgj_inverse(T (&a)[M * M], long long* st, int level, long long part,
+                                            long long row) {
+    int perm[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        int p = k;
+        unsigned long long best = abs_key(a[k * M + k]);
+#pragma unroll
+        for (int i = k + 1; i < M; ++i) {
+            const unsigned long long key = abs_key(a[i * M + k]);
+            if (key > best) {
+                best = key;
+                p = i;
+            }
+        }
+#pragma unroll
+        for (int i = k + 1; i < M; ++i) {
+            if (p == i) {
+#pragma unroll
+                for (int c = 0; c < M; ++c) {
+                    const T t = a[k * M + c];
+                    a[k * M + c] = a[i * M + c];
+                    a[i * M + c] = t;
+                }
+            }
+        }
+        perm[k] = p;
+        T pv = a[k * M + k];
+        if (best == 0ull || nonfinite(pv)) {
+            report(st, best == 0ull ? ST_SINGULAR : ST_NONFINITE, level, part, row);
+            pv = T(1);
+        }
+        const T r = rcp(pv);
+#pragma unroll
+        for (int c = 0; c < M; ++c) a[k * M + c] = (c == k) ? r : a[k * M + c] * r;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            if (i == k) continue;
+            const T l = a[i * M + k];
+#pragma unroll
+            for (int c = 0; c < M; ++c) a[i * M + c] = (c == k) ? -l * r : fmaT<T>(-l, a[k * M + c], a[i * M + c]);
+        }
+    }
+#pragma unroll
+    for (int k = M - 1; k >= 0; --k) {
+#pragma unroll
+        for (int i = k + 1; i < M; ++i) {
+            if (perm[k] == i) {
+#pragma unroll
+                for (int r = 0; r < M; ++r) {
+                    const T t = a[r * M + k];
+                    a[r * M + k] = a[r * M + i];
+                    a[r * M + i] = t;
+                }
+            }
+        }
+    }
+}
+
+template <typename T, int M, int MODE>
+__global__ void __launch_bounds__(128) k_factor_tp(const LevelArgs a) {
+    constexpr int MM = M * M;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.p) return;
+    const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
+    T* gDinv = reinterpret_cast<T*>(a.Dinv);
+    T* gY = reinterpret_cast<T*>(a.Y);
+    T* gZ = reinterpret_cast<T*>(a.Zc);
+    T Yp[MM], Zp[MM];
+#pragma unroll
+    for (int u = 0; u < MM; ++u) Yp[u] = Zp[u] = T(0);
+    for (long long j = pt.s; j < pt.e; ++j) {
+        const bool first = (j == pt.s);
+        const bool needB = !first || pt.hasL;
+        const bool needC = (MODE == 0) && ((j < pt.e - 1) || pt.hasR);
+        T Dp[MM], Bj[MM];
+        rld<T, M>(Dp, a.D + (j - a.shift) * MM);
+        if (needB) rld<T, M>(Bj, a.B + (j - a.shift) * MM);
+        if (MODE == 0 && !first) rmm<T, M, true, true>(Dp, Bj, Yp);
+        rgj_inverse<T, M>(Dp, a.status, a.level, i, j);
+        rst<T, M>(gDinv + j * MM, Dp);
+        if (pt.hasL) {
+            if (!first) {
+                T t[MM];
+                rmm<T, M, false, false>(t, Bj, Zp);
+                rmm<T, M, true, false>(Zp, Dp, t);
+            } else {
+                rmm<T, M, true, false>(Zp, Dp, Bj);
+            }
+            rst<T, M>(gZ + j * MM, Zp);
+        }
+        if (needC) {
+            T Cj[MM];
+            rld<T, M>(Cj, a.C + (j - a.shift) * MM);
+            rmm<T, M, false, false>(Yp, Dp, Cj);
+            rst<T, M>(gY + j * MM, Yp);
+        }
+    }
+    if (MODE == 0) {
+        if (!pt.hasL) return;
+        T P[MM], Q[MM];
+#pragma unroll
+        for (int u = 0; u < MM; ++u) {
+            P[u] = Zp[u];
+            Q[u] = pt.hasR ? -Yp[u] : T(0);
+        }
+        for (long long j = pt.e - 2; j >= pt.s; --j) {
+            T Yj[MM], Zj[MM];
+            rld<T, M>(Yj, gY + j * MM);
+            rld<T, M>(Zj, gZ + j * MM);
+            rmm<T, M, true, true>(Zj, Yj, P);
+            rmm<T, M, true, false>(Q, Yj, Q);
+#pragma unroll
+            for (int u = 0; u < MM; ++u) P[u] = Zj[u];
+        }
+        rst<T, M>(reinterpret_cast<T*>(a.Pf) + i * MM, P);
+        rst<T, M>(reinterpret_cast<T*>(a.Qf) + i * MM, Q);
+    } else {
+        const long long e = pt.e;
+        T Be[MM];
+        rld<T, M>(Be, a.B + (e - a.shift) * MM);
+        double* Sn = a.Bn + i * MM;
+        double* Rn = a.Dn + i * MM;
+#pragma unroll
+        for (int u = 0; u < MM; ++u) Rn[u] = a.D[(e - a.shift) * MM + u];
+        if (pt.e > pt.s) {
+            T t[MM];
+            rmm<T, M, false, false>(t, Be, Zp);
+            rst<T, M>(Sn, t);
+        } else {
+#pragma unroll
+            for (int u = 0; u < MM; ++u) Sn[u] = a.B[(e - a.shift) * MM + u];
+        }
+    }
+}
+
+template <typename T, int M>
+__global__ void __launch_bounds__(128) k_assemble_tp(const LevelArgs a) {
+    constexpr int MM = M * M;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.p - 1) return;
+    const Part pt = part_bounds(0, a.N, a.p, a.base, a.extra, s);
+    const long long e = pt.e;
+    double Be[MM], Ce[MM], al[MM], Yl[MM], Pf[MM];
+    rld<double, M>(Be, a.B + (e - a.shift) * MM);
+    rld<double, M>(Ce, a.C + (e - a.shift) * MM);
+    rld<double, M>(al, a.D + (e - a.shift) * MM);
+    rld<double, M>(Yl, reinterpret_cast<const T*>(a.Y) + (e - 1) * MM);
+    rld<double, M>(Pf, reinterpret_cast<const T*>(a.Pf) + (s + 1) * MM);
+    rmm<double, M, true, true>(al, Be, Yl);
+    rmm<double, M, false, true>(al, Ce, Pf);
+    rst<double, M>(a.Dn + s * MM, al);
+    double be[MM], ga[MM];
+#pragma unroll
+    for (int u = 0; u < MM; ++u) be[u] = ga[u] = 0.0;
+    if (s > 0) {
+        double Zl[MM];
+        rld<double, M>(Zl, reinterpret_cast<const T*>(a.Zc) + (e - 1) * MM);
+        rmm<double, M, false, false>(be, Be, Zl);
+    }
+    if (s + 1 < a.p - 1) {
+        double Qf[MM];
+        rld<double, M>(Qf, reinterpret_cast<const T*>(a.Qf) + (s + 1) * MM);
+        rmm<double, M, false, false>(ga, Ce, Qf);
+    }
+    rst<double, M>(a.Bn + s * MM, be);
+    rst<double, M>(a.Cn + s * MM, ga);
+}
+
+// v (M) = sgn * A (M x M) x (M) (+ v if ACC)
+template <typename T, int M, bool NEG, bool ACC>
+__device__ __forceinline__ void rmv(T (&v)[M], const T (&A)[M * M], const T (&x)[M]) {
+    T out[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+        T acc = ACC ? v[r] : T(0);
+#pragma unroll
+        for (int k = 0; k < M; ++k) acc = fmaT<T>(NEG ? -A[r * M + k] : A[r * M + k], x[k], acc);
+        out[r] = acc;
+    }
+#pragma unroll
+    for (int r = 0; r < M; ++r) v[r] = out[r];
+}
+
+template <int M, typename T>
+__device__ __forceinline__ void vld(T (&v)[M], const double* g, int nr) {
+#pragma unroll
+    for (int r = 0; r < M; ++r) v[r] = (T)g[r * nr];
+}
+template <int M, typename T>
+__device__ __forceinline__ void vst(double* g, const T (&v)[M], int nr) {
+#pragma unroll
+    for (int r = 0; r < M; ++r) g[r * nr] = (double)v[r];
+}
+
+template <typename T, int M, int MODE>
+__global__ void __launch_bounds__(128) k_solve_fwd_tp(const LevelArgs a) {
+    constexpr int MM = M * M;
+    const int nr = a.nr;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long i = tid / nr;
+    const int c = (int)(tid % nr);
+    if (i >= a.p) return;
+    const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
+    const long long E = (long long)M * nr;
+    const T* gDinv = reinterpret_cast<const T*>(a.Dinv);
+    T hp[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) hp[r] = T(0);
+    for (long long j = pt.s; j < pt.e; ++j) {
+        T v[M];
+        vld<M, T>(v, a.F + j * E + c, nr);
+        if (j != pt.s) {
+            T Bj[MM];
+            rld<T, M>(Bj, a.B + (j - a.shift) * MM);
+            rmv<T, M, true, true>(v, Bj, hp);
+        }
+        T Di[MM];
+        rld<T, M>(Di, gDinv + j * MM);
+        rmv<T, M, false, false>(hp, Di, v);
+        vst<M, T>(a.X + j * E + c, hp, nr);
+    }
+    if (MODE == 1) {
+        const long long e = pt.e;
+        if (i == 0) {
+#pragma unroll
+            for (int r = 0; r < M; ++r) a.Fn[r * nr + c] = a.F[r * nr + c];
+        }
+        double g[M];
+        vld<M, double>(g, a.F + e * E + c, nr);
+        if (pt.e > pt.s) {
+            T Be[MM], t[M];
+            rld<T, M>(Be, a.B + (e - a.shift) * MM);
+            rmv<T, M, false, false>(t, Be, hp);
+#pragma unroll
+            for (int r = 0; r < M; ++r) g[r] -= (double)t[r];
+        }
+        vst<M, double>(a.Fn + (i + 1) * E + c, g, nr);
+        return;
+    }
+    if (!pt.hasL) return;
+    const T* gY = reinterpret_cast<const T*>(a.Y);
+    for (long long j = pt.e - 2; j >= pt.s; --j) {
+        T h[M], Yj[MM];
+        vld<M, T>(h, a.X + j * E + c, nr);
+        rld<T, M>(Yj, gY + j * MM);
+        rmv<T, M, true, true>(h, Yj, hp);
+#pragma unroll
+        for (int r = 0; r < M; ++r) hp[r] = h[r];
+    }
+    T* Hf = reinterpret_cast<T*>(a.Hf) + i * E + c;
+#pragma unroll
+    for (int r = 0; r < M; ++r) Hf[r * nr] = hp[r];
+}
+
+template <typename T, int M>
+__global__ void __launch_bounds__(128) k_assemble_rhs_tp(const LevelArgs a) {
+    constexpr int MM = M * M;
+    const int nr = a.nr;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long s = tid / nr;
+    const int c = (int)(tid % nr);
+    if (s >= a.p - 1) return;
+    const Part pt = part_bounds(0, a.N, a.p, a.base, a.extra, s);
+    const long long e = pt.e;
+    const long long E = (long long)M * nr;
+    double g[M], h[M], H[M], Be[MM], Ce[MM];
+    vld<M, double>(g, a.F + e * E + c, nr);
+    vld<M, double>(h, a.X + (e - 1) * E + c, nr);
+    const T* Hf = reinterpret_cast<const T*>(a.Hf) + (s + 1) * E + c;
+#pragma unroll
+    for (int r = 0; r < M; ++r) H[r] = (double)Hf[r * nr];
+    rld<double, M>(Be, a.B + (e - a.shift) * MM);
+    rld<double, M>(Ce, a.C + (e - a.shift) * MM);
+    rmv<double, M, true, true>(g, Be, h);
+    rmv<double, M, true, true>(g, Ce, H);
+    vst<M, double>(a.Fn + s * E + c, g, nr);
+}
+
+template <typename T, int M, int MODE>
+__global__ void __launch_bounds__(128) k_solve_bwd_tp(const LevelArgs a) {
+    constexpr int MM = M * M;
+    const int nr = a.nr;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long i = tid / nr;
+    const int c = (int)(tid % nr);
+    if (i >= a.p) return;
+    const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
+    const long long E = (long long)M * nr;
+    const long long li = (MODE == 0) ? i - 1 : i;
+    const long long ri = (MODE == 0) ? i : i + 1;
+    T x[M], xl[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) {
+        x[r] = T(0);
+        xl[r] = T(0);
+    }
+    if (pt.hasR) {
+        double xr[M];
+        vld<M, double>(xr, a.Xn + ri * E + c, nr);
+        vst<M, double>(a.X + pt.e * E + c, xr, nr);
+#pragma unroll
+        for (int r = 0; r < M; ++r) x[r] = (T)xr[r];
+    }
+    if (MODE == 1 && i == 0) {
+#pragma unroll
+        for (int r = 0; r < M; ++r) a.X[r * nr + c] = a.Xn[r * nr + c];
+    }
+    if (pt.hasL) vld<M, T>(xl, a.Xn + li * E + c, nr);
+    const T* gY = reinterpret_cast<const T*>(a.Y);
+    const T* gZ = reinterpret_cast<const T*>(a.Zc);
+    for (long long j = pt.e - 1; j >= pt.s; --j) {
+        T v[M];
+        vld<M, T>(v, a.X + j * E + c, nr);
+        if (MODE == 0 && ((j < pt.e - 1) || pt.hasR)) {
+            T Yj[MM];
+            rld<T, M>(Yj, gY + j * MM);
+            rmv<T, M, true, true>(v, Yj, x);
+        }
+        if (pt.hasL) {
+            T Zj[MM];
+            rld<T, M>(Zj, gZ + j * MM);
+            rmv<T, M, false, true>(v, Zj, xl);
+        }
+#pragma unroll
+        for (int r = 0; r < M; ++r) x[r] = v[r];
+        vst<M, T>(a.X + j * E + c, x, nr);
+    }
+}
+
+}  // namespace bt

@@ -1,0 +1,111 @@
+"""GPU parity of the BABD partition solver (abd_*) against the oracle."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from oracle import partition as P
+from conftest import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve(cuda, b, p=0, prec="fp64"):
+    import paper_0912_3678_gb300 as bt
+    N, m = b.S.shape[0], b.S.shape[1]
+    nr = b.RHS.shape[1]
+    with bt.AbdPlan(N, m, nrhs_max=nr, prec=prec, p=p) as plan:
+        plan.factor(*(to_dev(a, cuda) for a in (b.S, b.R, b.B0, b.B1)))
+        Y = plan.solve(to_dev(b.RHS, cuda))
+        plan.sync()
+        return to_host(Y), plan.levels()
+
+
+@pytest.mark.parametrize("m", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("N,nrhs,sep", [(1, 1, False), (5, 2, False), (9, 1, True), (100, 3, False),
+                                        (777, 1, True)])
+def test_babd_fp64_matches_oracle(cuda, m, N, nrhs, sep):
+    if sep and m == 1:
+        pytest.skip("separated conditions need m >= 2")
+    b = gen.babd_bvp(N, m, nrhs, separated=sep, seed_rep=N + m)
+    Y, lev = _solve(cuda, b)
+    ref = oracle.babd_solve(b.S, b.R, b.B0, b.B1, b.RHS)
+    assert oracle.rel_err(Y, ref) <= 1e-11, lev
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 10, 49])
+def test_babd_invariant_under_p(cuda, p):
+    b = gen.babd_random(100, 4, 2, seed_rep=1)
+    Y, _ = _solve(cuda, b, p=p)
+    ref = oracle.babd_solve(b.S, b.R, b.B0, b.B1, b.RHS)
+    assert oracle.rel_err(Y, ref) <= 1e-11
+
+
+def test_babd_reduced_matrix(cuda):
+    import paper_0912_3678_gb300 as bt
+    b = gen.babd_bvp(40, 4, 1, seed_rep=5)
+    al, be, g, T = P.babd_reduced_blocks(b.S, b.R, b.B0, b.B1, b.RHS, 5)
+    with bt.AbdPlan(40, 4, 1, p=5) as plan:
+        plan.factor(*(to_dev(a, cuda) for a in (b.S, b.R, b.B0, b.B1)))
+        a_, b_ = (to_host(t) for t in plan.reduced())
+    scale = np.abs(T).max()
+    assert np.abs(a_ - al).max() <= 1e-13 * scale
+    assert np.abs(b_ - be).max() <= 1e-13 * scale
+
+
+def test_config3_full_size(cuda):
+    """Trapezoidal BABD, m = 8, N = 2^18 steps: parity with the oracle and the
+    O(h^2) error against the exact solution y(t) = exp(sin 3t) v."""
+    N = 1 << 18
+    b = gen.babd_bvp(N, 8, 1, seed_rep=0)
+    Y, lev = _solve(cuda, b)
+    ref = oracle.babd_solve(b.S, b.R, b.B0, b.B1, b.RHS)
+    assert oracle.rel_err(Y, ref) <= 1e-11
+    h = 1.0 / N
+    assert np.abs(Y - b.Yexact).max() <= 200 * h * h
+
+
+def test_config3_separated_bc_full_size(cuda):
+    N = 1 << 18
+    b = gen.babd_bvp(N, 8, 1, separated=True, seed_rep=1)
+    Y, lev = _solve(cuda, b)
+    ref = oracle.babd_solve(b.S, b.R, b.B0, b.B1, b.RHS)
+    assert oracle.rel_err(Y, ref) <= 1e-11
+
+
+def test_babd_mixed_precision_refinement(cuda):
+    import paper_0912_3678_gb300 as bt
+    b = gen.babd_bvp(5000, 8, 2, seed_rep=3)
+    ref = oracle.babd_solve(b.S, b.R, b.B0, b.B1, b.RHS)
+    with bt.AbdPlan(5000, 8, 2, prec="fp32_ir") as plan:
+        plan.factor(*(to_dev(a, cuda) for a in (b.S, b.R, b.B0, b.B1)))
+        Y, it, rc, code = plan.refine(to_dev(b.RHS, cuda), tol=1e-12, maxit=20)
+    assert code == 0
+    assert oracle.rel_err(to_host(Y), ref) <= 1e-10
+
+
+def test_babd_residual(cuda):
+    import paper_0912_3678_gb300 as bt
+    b = gen.babd_random(60, 8, 2, seed_rep=2)
+    Yr = np.random.default_rng(1).standard_normal(b.RHS.shape)
+    ref = oracle.babd_residual(b.S, b.R, b.B0, b.B1, Yr, b.RHS)
+    with bt.AbdPlan(60, 8, 2) as plan:
+        plan.factor(*(to_dev(a, cuda) for a in (b.S, b.R, b.B0, b.B1)))
+        R = to_host(plan.residual(to_dev(b.RHS, cuda), to_dev(Yr, cuda)))
+    assert np.abs(R - ref).max() <= 1e-13 * (np.abs(b.RHS).max() + 16 * np.abs(Yr).max())
+
+
+def test_ivp_special_case(cuda):
+    """B0 = I, B1 = 0: the time-parallel IVP solve of Sec. 3 equals sequential
+    time stepping (Eq. (My))."""
+    b = gen.babd_bvp(3000, 4, 1, seed_rep=6)
+    b.B0 = np.eye(4)
+    b.B1 = np.zeros((4, 4))
+    Y, _ = _solve(cuda, b)
+    Rb = b.RHS.reshape(3001, 4, 1)
+    y = Rb[0].copy()
+    seq = [y]
+    for j in range(3000):
+        y = np.linalg.solve(b.R[j], Rb[j + 1] - b.S[j] @ y)
+        seq.append(y)
+    assert oracle.rel_err(Y, np.concatenate(seq)) <= 1e-11

@@ -1,0 +1,184 @@
+"""GPU parity of the block tridiagonal partition solver (bt_*) against the
+oracle, element by element on the same seeded inputs.  FP64 path: normwise
+relative error <= 1e-11 (the configs here have kappa <= ~10); mixed precision
+with FP64 refinement: <= 1e-10."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from oracle import partition as P
+from conftest import to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+TOLIR = 1e-10
+
+
+def _solve(cuda, s, p=0, prec="fp64", nrhs=None):
+    import paper_0912_3678_gb300 as bt
+    N, m = s.D.shape[0], s.D.shape[1]
+    nr = s.F.shape[1] if nrhs is None else nrhs
+    B, D, C, F = (to_dev(a, cuda) for a in (s.B, s.D, s.C, s.F))
+    with bt.BtPlan(N, m, nrhs_max=nr, prec=prec, p=p) as plan:
+        plan.factor(B, D, C)
+        X = plan.solve(F)
+        plan.sync()
+        return to_host(X), plan.levels()
+
+
+@pytest.mark.parametrize("m", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("N,nrhs", [(1, 1), (2, 2), (7, 1), (37, 3), (301, 2)])
+def test_btri_fp64_matches_oracle(cuda, m, N, nrhs):
+    s = gen.btri_random(N, m, nrhs, seed_rep=7 * N + m)
+    X, lev = _solve(cuda, s)
+    ref = oracle.btri_solve(s.B, s.D, s.C, s.F)
+    assert oracle.rel_err(X, ref) <= TOL64, lev
+
+
+@pytest.mark.parametrize("m", [1, 4, 16])
+def test_btri_many_partitions_ragged(cuda, m):
+    """Several tiles and a ragged tail: N not divisible by p, multi-level recursion."""
+    N = 4099
+    s = gen.btri_random(N, m, 2, seed_rep=m)
+    X, lev = _solve(cuda, s)
+    assert len(lev) >= 2
+    ref = oracle.btri_solve(s.B, s.D, s.C, s.F)
+    assert oracle.rel_err(X, ref) <= TOL64
+
+
+@pytest.mark.parametrize("m", [1, 8])
+def test_btri_invariant_under_p(cuda, m):
+    N = 61
+    s = gen.btri_random(N, m, 2, seed_rep=3)
+    ref = oracle.btri_solve(s.B, s.D, s.C, s.F)
+    sols = []
+    for p in (1, 2, 3, 7, 30, 31):
+        X, _ = _solve(cuda, s, p=p)
+        assert oracle.rel_err(X, ref) <= TOL64, p
+        sols.append(X)
+    for X in sols[1:]:
+        assert oracle.rel_err(X, sols[0]) <= 1e-13
+
+
+@pytest.mark.parametrize("m,N,p", [(1, 40, 5), (2, 23, 4), (8, 30, 6), (16, 17, 3)])
+def test_reduced_matrix_is_schur_complement(cuda, m, N, p):
+    """The top-level reduced matrix of Eq. (redmatr) equals the Schur complement
+    of the local unknowns (oracle, dense definition)."""
+    import paper_0912_3678_gb300 as bt
+    s = gen.btri_random(N, m, 1, seed_rep=N)
+    A = gen.btri_dense(s.B, s.D, s.C)
+    al, be, ga, g, T = P.btri_reduced_blocks(A, s.F, m, N, p)
+    with bt.BtPlan(N, m, 1, p=p) as plan:
+        plan.factor(*(to_dev(a, cuda) for a in (s.B, s.D, s.C)))
+        a_, b_, g_ = (to_host(t) for t in plan.reduced())
+    scale = np.abs(T).max()
+    assert np.abs(a_ - al).max() <= 1e-13 * scale
+    assert np.abs(b_ - be).max() <= 1e-13 * scale
+    assert np.abs(g_ - ga).max() <= 1e-13 * scale
+
+
+def test_config1_scalar_p64(cuda):
+    """Scalar tridiagonal n = 2^16, p = 64 partitions (the plain method)."""
+    s = gen.tri_sdd(1 << 16, 1, seed_rep=0)
+    sb = gen.BtriSystem(s.dl.reshape(-1, 1, 1), s.d.reshape(-1, 1, 1), s.du.reshape(-1, 1, 1), s.f, s.xstar)
+    X, lev = _solve(cuda, sb, p=64)
+    assert lev[0] == (1 << 16, 64)
+    ref = oracle.tri_solve(s.dl, s.d, s.du, s.f)
+    assert oracle.rel_err(X, ref) <= TOL64
+    # and with the automatic partition count
+    X2, _ = _solve(cuda, sb)
+    assert oracle.rel_err(X2, ref) <= TOL64
+
+
+def test_poisson_closed_form(cuda):
+    """tridiag(-1,2,-1), n = 4096, f = 2: x_i = i (n+1-i); kappa ~ 6.8e6, so the
+    gate is 10 kappa u (any FP64 solver's forward error bound) plus a backward
+    error check."""
+    n = 4096
+    dl, d, du = gen.poisson(n)
+    f = 2.0 * np.ones((n, 1))
+    sb = gen.BtriSystem(dl.reshape(-1, 1, 1), d.reshape(-1, 1, 1), du.reshape(-1, 1, 1), f, None)
+    X, _ = _solve(cuda, sb)
+    i = np.arange(1, n + 1, dtype=float)
+    xe = (i * (n + 1 - i))[:, None]
+    lam = 2 - 2 * np.cos(np.arange(1, n + 1) * np.pi / (n + 1))
+    kappa = lam.max() / lam.min()
+    assert oracle.rel_err(X, xe) <= 10 * kappa * np.finfo(float).eps
+    r = oracle.tri_residual(dl, d, du, X, f)
+    assert np.linalg.norm(r) / (4 * np.linalg.norm(X) + np.linalg.norm(f)) <= 1e-14
+
+
+def test_config2_full_size_fp64(cuda):
+    """Block tridiagonal m = 16, N = 16384 block rows, 8 right-hand sides."""
+    s = gen.btri_random(16384, 16, 8, seed_rep=0)
+    X, lev = _solve(cuda, s)
+    ref = oracle.btri_solve(s.B, s.D, s.C, s.F)
+    assert oracle.rel_err(X, ref) <= TOL64
+
+
+@pytest.mark.parametrize("m,N", [(1, 5000), (4, 999), (8, 700), (16, 1024), (32, 130)])
+def test_mixed_precision_refinement(cuda, m, N):
+    import paper_0912_3678_gb300 as bt
+    s = gen.btri_random(N, m, 3, seed_rep=11)
+    ref = oracle.btri_solve(s.B, s.D, s.C, s.F)
+    B, D, C, F = (to_dev(a, cuda) for a in (s.B, s.D, s.C, s.F))
+    with bt.BtPlan(N, m, 3, prec="fp32_ir") as plan:
+        plan.factor(B, D, C)
+        X0 = to_host(plan.solve(F))
+        X, it, rc, code = plan.refine(F, tol=1e-12, maxit=20)
+    lo = oracle.rel_err(X0, ref)
+    assert 1e-12 < lo < 1e-4            # the unrefined FP32 solve is not FP64-accurate
+    assert code == 0 and 1 <= it <= 6
+    assert oracle.rel_err(to_host(X), ref) <= TOLIR
+
+
+def test_residual_matches_oracle(cuda):
+    import paper_0912_3678_gb300 as bt
+    s = gen.btri_random(300, 8, 4, seed_rep=2)
+    Xr = np.random.default_rng(0).standard_normal(s.F.shape)
+    ref = oracle.btri_residual(s.B, s.D, s.C, Xr, s.F)
+    B, D, C, F, X = (to_dev(a, cuda) for a in (s.B, s.D, s.C, s.F, Xr))
+    with bt.BtPlan(300, 8, 4) as plan:
+        plan.factor(B, D, C)
+        R = to_host(plan.residual(F, X))
+    scale = np.abs(s.F).max() + 3 * 8 * np.abs(Xr).max()
+    assert np.abs(R - ref).max() <= 1e-14 * scale
+
+
+def test_singular_block_is_reported(cuda):
+    """A zero pivot block (host-made fault in the input) sets BT_ERR_SINGULAR."""
+    import paper_0912_3678_gb300 as bt
+    s = gen.btri_random(50, 4, 1, seed_rep=4)
+    s.D[0] = 0.0
+    s.B[1] = 0.0
+    with bt.BtPlan(50, 4, 1, p=1) as plan:
+        plan.factor(*(to_dev(a, cuda) for a in (s.B, s.D, s.C)))
+        code, lev, part, row = plan.info()
+    assert bt.BT_STATUS[code] == "BT_ERR_SINGULAR"
+    assert row == 0
+
+
+def test_nonfinite_input_is_reported(cuda):
+    import paper_0912_3678_gb300 as bt
+    s = gen.btri_random(50, 8, 1, seed_rep=4)
+    s.D[10, 0, 0] = np.nan
+    with bt.BtPlan(50, 8, 1) as plan:
+        plan.factor(*(to_dev(a, cuda) for a in (s.B, s.D, s.C)))
+        code, *_ = plan.info()
+    assert bt.BT_STATUS[code] in ("BT_ERR_NONFINITE", "BT_ERR_SINGULAR")
+
+
+def test_invalid_arguments(cuda):
+    import paper_0912_3678_gb300 as bt
+    with pytest.raises(bt.BtError):
+        bt.BtPlan(10, 3)           # unsupported block order
+    with pytest.raises(bt.BtError):
+        bt.BtPlan(10, 4, nrhs_max=33)
+    with pytest.raises(bt.BtError):
+        bt.BtPlan(10, 4, p=6)      # p > (N+1)/2
+    with bt.BtPlan(10, 4) as plan:
+        F = to_dev(np.zeros((40, 1)), cuda)
+        with pytest.raises(bt.BtError):
+            plan.solve(F)          # not factored
