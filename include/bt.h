@@ -145,6 +145,29 @@ bt_status bt_plan_launches(bt_plan plan, int64_t* count);
 
 void bt_plan_destroy(bt_plan plan);
 
+/* One-shot FP64 factor + solve of a block tridiagonal system that allocates
+ * no device memory.  The paper has no counterpart: this entry point serves
+ * callers that may not call cudaMalloc -- code inside a host application
+ * that owns all device memory through its own pool or budget, or a
+ * latency-critical loop that cannot accept cudaMalloc's implicit device
+ * synchronisation or its possible failure.
+ *   Arguments as for bt_plan_create (prec FP64, p chosen automatically),
+ *   bt_factor and bt_solve: B, D, C [nblk][m][m], F, X [nblk*m][nrhs],
+ *   device pointers owned by the caller; X may not alias F.
+ * Every intermediate lives in one static device array of
+ * BT_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.  If the problem needs more, the call returns
+ * BT_ERR_INVALID before touching the GPU and *required_bytes (may be NULL)
+ * tells how much it would need; e.g. m = 16 fits about a thousand block rows.
+ * The first call on a device looks up the array's device address (with
+ * cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array: calls whose GPU work overlaps race, so callers
+ * must serialise them.  The call synchronises `stream` before returning and
+ * returns the numerical status (BT_ERR_SINGULAR / BT_ERR_NONFINITE). */
+#define BT_NOALLOC_SCRATCH_BYTES (8u << 20)
+bt_status bt_solve_noalloc(int64_t nblk, int m, const double* B, const double* D, const double* C,
+                           const double* F, double* X, int nrhs, void* stream, int64_t* required_bytes);
+
 /* ---------------------------------------------------------------------
  * ABD/BABD systems (Sec. 2, Eq. (parpart1) with c = 0, and Sec. 3: one-step
  * discretisations of linear BVPs).  Unknowns y_0..y_N (m each):

@@ -17,7 +17,7 @@ from ._lib import BT_STATUS, PREC, BtError
 __all__ = ["BtPlan", "AbdPlan", "BtError", "BT_STATUS", "PREC", "load_library",
            "bt_plan_create", "bt_factor", "bt_solve", "bt_residual", "bt_refine", "bt_sync", "bt_info",
            "bt_plan_levels", "bt_plan_bytes", "bt_plan_trace", "bt_plan_trace_query", "bt_plan_launches",
-           "KERNEL_KINDS", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
+           "KERNEL_KINDS", "bt_solve_noalloc", "BT_NOALLOC_SCRATCH_BYTES", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
            "abd_plan_create", "abd_factor", "abd_solve", "abd_residual", "abd_refine", "abd_sync",
            "abd_plan_destroy"]
 
@@ -173,6 +173,18 @@ def bt_plan_launches(plan) -> int:
 
 def bt_plan_destroy(plan):
     _lib.load().bt_plan_destroy(plan)
+
+
+BT_NOALLOC_SCRATCH_BYTES = 8 << 20
+
+
+def bt_solve_noalloc(nblk, m, B, D, C, F, X, nrhs, stream=None):
+    """One-shot FP64 solve with no device allocation (see include/bt.h).
+    Returns (status code, required scratch bytes); does not raise."""
+    req = ctypes.c_int64(0)
+    code = _lib.load().bt_solve_noalloc(int(nblk), int(m), _ptr(B), _ptr(D), _ptr(C), _ptr(F), _ptr(X),
+                                        int(nrhs), _stream(stream), ctypes.byref(req))
+    return code, req.value
 
 
 def abd_plan_destroy(plan):
