@@ -77,6 +77,26 @@ const char* bt_status_string(bt_status s);
 bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int prec, int64_t p,
                          void* stream);
 
+/* Partitioning parameters of plan step A0 (Sec. 2: "p processors"; here the
+ * partition count of every recursion level).  Zero fields take the defaults.
+ *   p0           partitions of the top level (0: ctas_per_sm x SM count,
+ *                capped at nblk/4 for m >= 8 or nblk/8 for m <= 4)
+ *   ctas_per_sm  level-0 partitions per SM when p0 = 0 (default 4 for m >= 8,
+ *                512 for m <= 4, where a partition is one thread)
+ *   sub_rows     block rows per partition on the recursion levels (>= 2, default 4)
+ *   top_rows     a level with at most this many block rows is solved by one
+ *                partition (block tridiagonal) or directly (BABD); default 8 */
+typedef struct {
+    int64_t p0;
+    int ctas_per_sm;
+    int sub_rows;
+    int top_rows;
+} bt_tuning;
+
+/* bt_plan_create with explicit partitioning parameters (NULL = defaults). */
+bt_status bt_plan_create_tuned(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int prec,
+                               const bt_tuning* tuning, void* stream);
+
 /* Factor A = F T G (Eqs. (parfact)-(parblock)): the local block LU of every
  * partition with its fill-in spikes, the reduced matrix of Eq. (redmatr),
  * and recursively its own factorization.  Reads B, D, C; does not modify
@@ -167,6 +187,46 @@ void bt_plan_destroy(bt_plan plan);
 #define BT_NOALLOC_SCRATCH_BYTES (8u << 20)
 bt_status bt_solve_noalloc(int64_t nblk, int m, const double* B, const double* D, const double* C,
                            const double* F, double* X, int nrhs, void* stream, int64_t* required_bytes);
+
+/* ---------------------------------------------------------------------
+ * Batches of independent block tridiagonal systems (the partition method
+ * applied to many systems at once; every system follows Sec. 2 exactly as a
+ * single plan does).  The work of all systems at the same recursion level,
+ * block order and precision runs in one persistent launch over a work list of
+ * (system, partition) items, and the whole run -- factor, solve, and
+ * `ir_sweeps` FP64 refinement sweeps for the BT_FP32_IR/BT_BF16_IR systems --
+ * is captured into one CUDA graph at creation.
+ * ------------------------------------------------------------------- */
+typedef struct {
+    int64_t nblk;      /* block rows N */
+    int m;             /* block order: 1, 2, 4, 8, 16 or 32 */
+    int prec;          /* bt_prec */
+    int nrhs;          /* right-hand sides, 1..32 */
+    const double* B;   /* [N][m][m] device arrays, caller-owned, read-only */
+    const double* D;
+    const double* C;
+    const double* F;   /* [N*m][nrhs] right-hand sides */
+    double* X;         /* [N*m][nrhs] solutions (written by every run) */
+    bt_tuning tuning;  /* partitioning; all zero: about 32 (m >= 8) or 64 block rows per partition */
+} bt_batch_desc;
+typedef struct bt_batch_s* bt_batch;
+
+/* Plan and capture a batch.  The arrays named by the descriptors are bound
+ * into the graph: later runs re-read them (new values in the same arrays are
+ * fine) and must keep them alive.  mem_cap_bytes > 0 bounds the workspace:
+ * systems are split into waves that reuse it in turn (BT_ERR_NOMEM if one
+ * system alone exceeds the cap).  The stream may be NULL. */
+bt_status bt_batch_create(bt_batch* batch, const bt_batch_desc* systems, int count, int ir_sweeps,
+                          int64_t mem_cap_bytes, void* stream);
+/* One graph launch: factor and solve every system (asynchronous). */
+bt_status bt_batch_run(bt_batch batch);
+/* Synchronise; per-system status (may be NULL): numerical failures, and
+ * BT_ERR_NOT_CONVERGED for a refined system whose last correction was larger
+ * than tol relative to its solution; relcorr (may be NULL) receives that
+ * ratio (0 for FP64 systems).  Returns the first failing status or BT_OK. */
+bt_status bt_batch_finish(bt_batch batch, double tol, int* status, double* relcorr);
+bt_status bt_batch_info(bt_batch batch, int* waves, int64_t* graph_nodes, int64_t* bytes);
+void bt_batch_destroy(bt_batch batch);
 
 /* ---------------------------------------------------------------------
  * ABD/BABD systems (Sec. 2, Eq. (parpart1) with c = 0, and Sec. 3: one-step

@@ -12,12 +12,14 @@ from __future__ import annotations
 import ctypes
 
 from . import _lib
-from ._lib import BT_STATUS, PREC, BtError
+from ._lib import BT_STATUS, PREC, BtBatchDesc, BtError, BtTuning
 
 __all__ = ["BtPlan", "AbdPlan", "BtError", "BT_STATUS", "PREC", "load_library",
            "bt_plan_create", "bt_factor", "bt_solve", "bt_residual", "bt_refine", "bt_sync", "bt_info",
            "bt_plan_levels", "bt_plan_bytes", "bt_plan_trace", "bt_plan_trace_query", "bt_plan_launches",
-           "KERNEL_KINDS", "bt_solve_noalloc", "BT_NOALLOC_SCRATCH_BYTES", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
+           "KERNEL_KINDS", "bt_solve_noalloc", "BT_NOALLOC_SCRATCH_BYTES", "bt_plan_create_tuned",
+           "bt_batch_create", "bt_batch_run", "bt_batch_finish", "bt_batch_info", "bt_batch_destroy",
+           "BtBatch", "BtTuning", "BtBatchDesc", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
            "abd_plan_create", "abd_factor", "abd_solve", "abd_residual", "abd_refine", "abd_sync",
            "abd_plan_destroy"]
 
@@ -63,6 +65,56 @@ def bt_plan_create(nblk, m, nrhs_max=1, prec="fp64", p=0, stream=None):
     _lib.check(_lib.load().bt_plan_create(ctypes.byref(h), int(nblk), int(m), int(nrhs_max), _prec(prec),
                                           int(p), _stream(stream)), "bt_plan_create")
     return h
+
+
+def _tuning(t):
+    if t is None:
+        return None
+    if isinstance(t, BtTuning):
+        return t
+    return BtTuning(int(t.get("p0", 0)), int(t.get("ctas_per_sm", 0)), int(t.get("sub_rows", 0)),
+                    int(t.get("top_rows", 0)))
+
+
+def bt_plan_create_tuned(nblk, m, nrhs_max=1, prec="fp64", tuning=None, stream=None):
+    h = ctypes.c_void_p()
+    t = _tuning(tuning)
+    _lib.check(_lib.load().bt_plan_create_tuned(ctypes.byref(h), int(nblk), int(m), int(nrhs_max), _prec(prec),
+                                                ctypes.byref(t) if t is not None else None, _stream(stream)),
+               "bt_plan_create_tuned")
+    return h
+
+
+def bt_batch_create(descs, ir_sweeps=3, mem_cap_bytes=0, stream=None):
+    arr = (BtBatchDesc * len(descs))(*descs)
+    h = ctypes.c_void_p()
+    _lib.check(_lib.load().bt_batch_create(ctypes.byref(h), arr, len(descs), int(ir_sweeps), int(mem_cap_bytes),
+                                           _stream(stream)), "bt_batch_create")
+    return h
+
+
+def bt_batch_run(batch):
+    _lib.check(_lib.load().bt_batch_run(batch), "bt_batch_run")
+
+
+def bt_batch_finish(batch, count, tol=1e-12):
+    st = (ctypes.c_int * count)()
+    rc = (ctypes.c_double * count)()
+    code = _lib.load().bt_batch_finish(batch, float(tol), st, rc)
+    return code, list(st), list(rc)
+
+
+def bt_batch_info(batch):
+    w = ctypes.c_int(0)
+    n = ctypes.c_int64(0)
+    b = ctypes.c_int64(0)
+    _lib.check(_lib.load().bt_batch_info(batch, ctypes.byref(w), ctypes.byref(n), ctypes.byref(b)),
+               "bt_batch_info")
+    return w.value, n.value, b.value
+
+
+def bt_batch_destroy(batch):
+    _lib.load().bt_batch_destroy(batch)
 
 
 def abd_plan_create(N, m, nrhs_max=1, prec="fp64", p=0, stream=None):
@@ -290,6 +342,57 @@ class BtPlan(_PlanBase):
         g = t.empty_like(a)
         bt_reduced_export(self.handle, a, b, g)
         return a, b, g
+
+
+class BtBatch:
+    """Many independent block tridiagonal systems solved by one CUDA-graph
+    launch.  ``systems``: list of dicts with keys B, D, C, F, X (CUDA float64
+    tensors), prec ("fp64" | "fp32_ir" | "bf16_ir") and optional tuning."""
+
+    def __init__(self, systems, ir_sweeps=3, mem_cap_bytes=0, stream=None, tuner=None):
+        descs = []
+        self._keep = []
+        for sd in systems:
+            D = sd["D"]
+            N, m = D.shape[0], D.shape[1]
+            F = sd["F"]
+            nr = 1 if F.dim() == 1 else F.shape[-1]
+            prec = sd.get("prec", "fp64")
+            tun = sd.get("tuning")
+            if tun is None and tuner is not None:
+                tun = tuner(m, N, prec)
+            descs.append(BtBatchDesc(N, m, _prec(prec), nr, _ptr(sd["B"]), _ptr(D), _ptr(sd["C"]), _ptr(F),
+                                     _ptr(sd["X"]), _tuning(tun) or BtTuning(0, 0, 0, 0)))
+            self._keep.append((sd["B"], D, sd["C"], F, sd["X"]))
+        self.count = len(descs)
+        self.handle = bt_batch_create(descs, ir_sweeps, mem_cap_bytes, stream)
+
+    def run(self):
+        bt_batch_run(self.handle)
+
+    def finish(self, tol=1e-12):
+        return bt_batch_finish(self.handle, self.count, tol)
+
+    def info(self):
+        return bt_batch_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            bt_batch_destroy(self.handle)
+            self.handle = None
+            self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class AbdPlan(_PlanBase):

@@ -48,6 +48,26 @@ SIGNATURES = {
     "abd_plan_destroy": (None, [_vp]),
 }
 
+class BtTuning(ctypes.Structure):
+    _fields_ = [("p0", ctypes.c_int64), ("ctas_per_sm", ctypes.c_int), ("sub_rows", ctypes.c_int),
+                ("top_rows", ctypes.c_int)]
+
+
+class BtBatchDesc(ctypes.Structure):
+    _fields_ = [("nblk", ctypes.c_int64), ("m", ctypes.c_int), ("prec", ctypes.c_int), ("nrhs", ctypes.c_int),
+                ("B", ctypes.c_void_p), ("D", ctypes.c_void_p), ("C", ctypes.c_void_p), ("F", ctypes.c_void_p),
+                ("X", ctypes.c_void_p), ("tuning", BtTuning)]
+
+
+SIGNATURES.update({
+    "bt_plan_create_tuned": (_i32, [_pvp, _i64, _i32, _i32, _i32, ctypes.POINTER(BtTuning), _vp]),
+    "bt_batch_create": (_i32, [_pvp, ctypes.POINTER(BtBatchDesc), _i32, _i32, _i64, _vp]),
+    "bt_batch_run": (_i32, [_vp]),
+    "bt_batch_finish": (_i32, [_vp, _f64, _pi32, _pf64]),
+    "bt_batch_info": (_i32, [_vp, _pi32, _pi64, _pi64]),
+    "bt_batch_destroy": (None, [_vp]),
+})
+
 _lib = None
 
 

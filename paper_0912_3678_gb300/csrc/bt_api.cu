@@ -10,14 +10,13 @@
 #include "bt_launch.h"
 #include "bt_level.h"
 #include "bt_misc.h"
+#include "bt_planner.h"
 
 namespace {
 
 using bt::LevelArgs;
 
 constexpr int kNrhsMax = 32;
-constexpr long long kTopRows = 8;      // a level with at most this many rows is solved by one partition
-constexpr long long kSubLevelRows = 4; // rows per partition on the recursion levels
 
 struct Level {
     LevelArgs a;
@@ -90,26 +89,6 @@ int sm_count(int dev) {
     return n;
 }
 
-// Partition count for a level of `rows` block rows (btri: 1 <= p <= (rows+1)/2;
-// BABD: 1 <= p <= (rows-1)/2 local rows 1..rows-1 with >= 1 local row each).
-long long auto_parts(long long rows, int m, int level, int sms, int kind) {
-    long long cap = (kind == 0) ? (rows + 1) / 2 : (rows - 1) / 2;
-    if (cap < 1) cap = 1;
-    long long target;
-    if (level == 0) {
-        const long long per_sm = (m >= 8) ? 4 : 512;
-        target = (long long)sms * per_sm;
-        const long long kmin = (m >= 8) ? 4 : 8;
-        long long byk = rows / kmin;
-        if (byk < target) target = byk;
-    } else {
-        target = rows / kSubLevelRows;
-    }
-    if (target < 1) target = 1;
-    if (target > cap) target = cap;
-    return target;
-}
-
 // Lay out (or measure, when ar.base == nullptr) the plan's device memory.
 void layout(bt_plan_s* P, Arena& ar) {
     const int m = P->m;
@@ -168,8 +147,9 @@ void layout(bt_plan_s* P, Arena& ar) {
     }
 }
 
-bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, int prec, int64_t p,
+bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, int prec, const bt::Tuning& tune,
                       void* stream) {
+    const int64_t p = tune.p0;
     if (!out) return BT_ERR_INVALID;
     *out = nullptr;
     const bt::Launchers* L = bt::launchers_for(m);
@@ -190,33 +170,23 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
     P->L = L;
     cudaGetDevice(&P->device);
     const int sms = sm_count(P->device);
-    // levels
-    long long rows = N;
-    for (int l = 0;; ++l) {
+    std::vector<bt::LevelShape> shapes;
+    if (!bt::plan_shapes(kind, N, m, sms, tune, shapes)) {
+        delete P;
+        return BT_ERR_INVALID;
+    }
+    for (size_t l = 0; l < shapes.size(); ++l) {
         Level v;
         std::memset(&v.a, 0, sizeof(LevelArgs));
         v.a.mode = kind;
-        v.a.level = l;
-        v.a.N = rows;
-        v.rows = (kind == 0) ? rows : rows + 1;
+        v.a.level = (int)l;
+        v.a.N = shapes[l].N;
+        v.a.p = shapes[l].p;
+        v.a.base = shapes[l].base;
+        v.a.extra = shapes[l].extra;
+        v.rows = shapes[l].rows;
         v.low = (l == 0) && (prec != BT_FP64);
-        const bool small = (kind == 0) ? (rows <= kTopRows) : (rows <= kTopRows);
-        long long parts;
-        if (l == 0 && p > 0) parts = p;
-        else parts = small ? 1 : auto_parts(rows, m, l, sms, kind);
-        if (kind == 1 && (small || rows < 3)) parts = 0;   // BABD: direct solve at the top
-        if (kind == 1 && parts == 1 && l > 0) parts = 0;
-        if (kind == 1 && l == 0 && p == 1 && rows >= 3) parts = 1;
-        v.a.p = parts;
-        if (parts > 0) {
-            const long long span = (kind == 0) ? rows : rows - 1;
-            v.a.base = span / parts;
-            v.a.extra = span % parts;
-        }
         P->lv.push_back(v);
-        if (kind == 0 && parts <= 1) break;
-        if (kind == 1 && parts == 0) break;
-        rows = (kind == 0) ? parts - 1 : parts;
     }
     P->nlev = (int)P->lv.size() - 1;
     if (kind == 0) {
@@ -390,12 +360,31 @@ const char* bt_status_string(bt_status s) {
     return "unknown status";
 }
 
+static bt::Tuning to_tuning(const bt_tuning* t, int64_t p) {
+    bt::Tuning u;
+    if (t) {
+        u.p0 = t->p0;
+        u.ctas_per_sm = t->ctas_per_sm;
+        u.sub_rows = t->sub_rows;
+        u.top_rows = t->top_rows;
+    }
+    if (p > 0) u.p0 = p;
+    return u;
+}
+
 bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int prec, int64_t p, void* stream) {
-    return plan_create(plan, 0, nblk, m, nrhs_max, prec, p, stream);
+    return plan_create(plan, 0, nblk, m, nrhs_max, prec, to_tuning(nullptr, p), stream);
+}
+
+bt_status bt_plan_create_tuned(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int prec, const bt_tuning* tuning,
+                               void* stream) {
+    if (tuning && (tuning->p0 < 0 || tuning->ctas_per_sm < 0 || tuning->sub_rows < 0 || tuning->top_rows < 0))
+        return BT_ERR_INVALID;
+    return plan_create(plan, 0, nblk, m, nrhs_max, prec, to_tuning(tuning, 0), stream);
 }
 
 bt_status abd_plan_create(abd_plan* plan, int64_t N, int m, int nrhs_max, int prec, int64_t p, void* stream) {
-    return plan_create(plan, 1, N, m, nrhs_max, prec, p, stream);
+    return plan_create(plan, 1, N, m, nrhs_max, prec, to_tuning(nullptr, p), stream);
 }
 
 bt_status bt_factor(bt_plan P, const double* B, const double* D, const double* C) {

@@ -176,9 +176,8 @@ constexpr size_t factor_smem_bytes() {
 // (C = 0, so Y = 0 and no backward sweep; the right separator's reduced row
 // of Eq. (redmatr1) is written here: S'[i] = B_e Zc_{e-1}, R'[i] = D_e).
 template <typename T, int M, int MODE>
-__global__ void __launch_bounds__(8 * M) k_factor_cta(const LevelArgs a) {
+__device__ __forceinline__ void factor_cta_body(const LevelArgs& a, const long long i, unsigned char* smem_raw) {
     using S = Cta<T, M>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sB = reinterpret_cast<T*>(smem_raw);
     T* sD = sB + S::BLK;
     T* sC = sD + S::BLK;
@@ -188,7 +187,6 @@ __global__ void __launch_bounds__(8 * M) k_factor_cta(const LevelArgs a) {
     T* colk = sT + S::BLK;
     int* perm = reinterpret_cast<int*>(colk + M);
 
-    const long long i = blockIdx.x;
     const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
     const Own<T, M> o;
     T* gDinv = reinterpret_cast<T*>(a.Dinv);
@@ -294,16 +292,14 @@ __global__ void __launch_bounds__(8 * M) k_factor_cta(const LevelArgs a) {
 //   alpha = D_e - B_e Y_{e-1} + C_e P^(s+1)_first,  beta = B_e Zc_{e-1} (s > 0),
 //   gamma = C_e Q^(s+1)_first (s+1 < p-1).
 template <typename T, int M>
-__global__ void __launch_bounds__(8 * M) k_assemble_cta(const LevelArgs a) {
+__device__ __forceinline__ void assemble_cta_body(const LevelArgs& a, const long long s, unsigned char* smem_raw) {
     using S = Cta<double, M>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     double* sB = reinterpret_cast<double*>(smem_raw);
     double* sC = sB + S::BLK;
     double* sY = sC + S::BLK;
     double* sZ = sY + S::BLK;
     double* sP = sZ + S::BLK;
     double* sQ = sP + S::BLK;
-    const long long s = blockIdx.x;
     const Part pt = part_bounds(0, a.N, a.p, a.base, a.extra, s);
     const long long e = pt.e;
     const long long MM = S::MM;
@@ -354,17 +350,15 @@ struct RhsOwn {
 // (Hf).  Mode 1: the right separator's reduced right-hand side
 // g = f_e - B_e h_{e-1} (and partition 0 copies the boundary row).
 template <typename T, int M, int MODE>
-__global__ void __launch_bounds__(8 * M) k_solve_fwd_cta(const LevelArgs a) {
+__device__ __forceinline__ void solve_fwd_cta_body(const LevelArgs& a, const long long i, unsigned char* smem_raw) {
     using S = Cta<T, M>;
     constexpr int NT = S::NT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sB = reinterpret_cast<T*>(smem_raw);
     T* sD = sB + S::BLK;
     T* sh = sD + S::BLK;          // M x nr
     T* sv = sh + M * 32;          // M x nr
     const int nr = a.nr;
     const int E = M * nr;
-    const long long i = blockIdx.x;
     const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
     const long long MM = S::MM;
     const T* gDinv = reinterpret_cast<const T*>(a.Dinv);
@@ -461,17 +455,16 @@ __global__ void __launch_bounds__(8 * M) k_solve_fwd_cta(const LevelArgs a) {
 // Block tridiagonal reduced right-hand side of separator s:
 //   g = f_e - B_e h_{e-1} - C_e H^(s+1)_first   (FP64).
 template <typename T, int M>
-__global__ void __launch_bounds__(8 * M) k_assemble_rhs_cta(const LevelArgs a) {
+__device__ __forceinline__ void assemble_rhs_cta_body(const LevelArgs& a, const long long s,
+                                                      unsigned char* smem_raw) {
     using S = Cta<double, M>;
     constexpr int NT = S::NT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     double* sB = reinterpret_cast<double*>(smem_raw);
     double* sC = sB + S::BLK;
     double* sh = sC + S::BLK;
     double* sH = sh + M * 32;
     const int nr = a.nr;
     const int E = M * nr;
-    const long long s = blockIdx.x;
     const Part pt = part_bounds(0, a.N, a.p, a.base, a.extra, s);
     const long long e = pt.e;
     const long long MM = S::MM;
@@ -499,17 +492,15 @@ __global__ void __launch_bounds__(8 * M) k_assemble_rhs_cta(const LevelArgs a) {
 // up, with x_L, x_R from the next level's solution; also copies the
 // separator rows owned by this partition into X.
 template <typename T, int M, int MODE>
-__global__ void __launch_bounds__(8 * M) k_solve_bwd_cta(const LevelArgs a) {
+__device__ __forceinline__ void solve_bwd_cta_body(const LevelArgs& a, const long long i, unsigned char* smem_raw) {
     using S = Cta<T, M>;
     constexpr int NT = S::NT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sY = reinterpret_cast<T*>(smem_raw);
     T* sZ = sY + S::BLK;
     T* sx = sZ + S::BLK;   // x_{j+1}
     T* sL = sx + M * 32;   // x_L
     const int nr = a.nr;
     const int E = M * nr;
-    const long long i = blockIdx.x;
     const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
     const long long MM = S::MM;
     const long long li = (MODE == 0) ? i - 1 : i;   // next-level index of x_L
@@ -560,6 +551,35 @@ __global__ void __launch_bounds__(8 * M) k_solve_bwd_cta(const LevelArgs a) {
         __syncthreads();
     }
 }
+
+// ---------------------------------------------------------------- wrappers --
+// Single system: CTA b handles partition b.  Batched (persistent): CTA b
+// handles work items b, b + gridDim.x, ... where item w is (system, partition)
+// = work[w] and the system's level is args[work[w].x].
+#define BT_CTA_KERNELS(NAME, BODY, TPL, TARGS)                                                          \
+    template <TPL>                                                                                     \
+    __global__ void __launch_bounds__(8 * M) NAME(const LevelArgs a) {                                 \
+        extern __shared__ __align__(16) unsigned char smem_raw[];                                      \
+        BODY<TARGS>(a, (long long)blockIdx.x, smem_raw);                                                \
+    }                                                                                                  \
+    template <TPL>                                                                                     \
+    __global__ void __launch_bounds__(8 * M)                                                           \
+        NAME##_batch(const LevelArgs* __restrict__ args, const int2* __restrict__ work, int nwork) {   \
+        extern __shared__ __align__(16) unsigned char smem_raw[];                                      \
+        for (int w = blockIdx.x; w < nwork; w += gridDim.x) {                                           \
+            const int2 it = work[w];                                                                   \
+            const LevelArgs a = args[it.x];                                                            \
+            BODY<TARGS>(a, (long long)it.y, smem_raw);                                                  \
+            __syncthreads();                                                                           \
+        }                                                                                              \
+    }
+
+#define BT_COMMA ,
+BT_CTA_KERNELS(k_factor_cta, factor_cta_body, typename T BT_COMMA int M BT_COMMA int MODE, T BT_COMMA M BT_COMMA MODE)
+BT_CTA_KERNELS(k_assemble_cta, assemble_cta_body, typename T BT_COMMA int M, T BT_COMMA M)
+BT_CTA_KERNELS(k_solve_fwd_cta, solve_fwd_cta_body, typename T BT_COMMA int M BT_COMMA int MODE, T BT_COMMA M BT_COMMA MODE)
+BT_CTA_KERNELS(k_assemble_rhs_cta, assemble_rhs_cta_body, typename T BT_COMMA int M, T BT_COMMA M)
+BT_CTA_KERNELS(k_solve_bwd_cta, solve_bwd_cta_body, typename T BT_COMMA int M BT_COMMA int MODE, T BT_COMMA M BT_COMMA MODE)
 
 template <typename T, int M>
 constexpr size_t solve_smem_bytes() {

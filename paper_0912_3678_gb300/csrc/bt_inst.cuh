@@ -99,8 +99,119 @@ struct Inst {
         if (a.mode == 0) return low ? solve_bwd_t<float, 0>(a, s) : solve_bwd_t<double, 0>(a, s);
         return low ? solve_bwd_t<float, 1>(a, s) : solve_bwd_t<double, 1>(a, s);
     }
+    // ------------------------------------------------------------ batched --
+    template <typename K>
+    static cudaError_t launch_cta_b(K k, size_t smem, const LevelArgs* args, const int2* work, int nwork, int grid,
+                                    cudaStream_t s) {
+        if (nwork <= 0) return cudaSuccess;
+        cudaError_t e = set_smem(k, smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid, 8 * M, smem, s>>>(args, work, nwork);
+        return cudaGetLastError();
+    }
+    template <typename K>
+    static cudaError_t launch_tp_b(K k, const LevelArgs* args, const int2* work, int nwork, int grid,
+                                   cudaStream_t s) {
+        if (nwork <= 0) return cudaSuccess;
+        k<<<grid, 128, 0, s>>>(args, work, nwork);
+        return cudaGetLastError();
+    }
+    template <typename T, int MODE>
+    static cudaError_t factor_bt(const LevelArgs* args, const int2* work, int nwork, int grid, cudaStream_t s) {
+        if constexpr (M >= 8)
+            return launch_cta_b(k_factor_cta_batch<T, M, MODE>, factor_smem_bytes<T, M>(), args, work, nwork, grid, s);
+        else
+            return launch_tp_b(k_factor_tp_batch<T, M, MODE>, args, work, nwork, grid, s);
+    }
+    template <typename T>
+    static cudaError_t assemble_bt(const LevelArgs* args, const int2* work, int nwork, int grid, cudaStream_t s) {
+        if constexpr (M >= 8)
+            return launch_cta_b(k_assemble_cta_batch<T, M>, assemble_smem_bytes<M>(), args, work, nwork, grid, s);
+        else
+            return launch_tp_b(k_assemble_tp_batch<T, M>, args, work, nwork, grid, s);
+    }
+    template <typename T, int MODE>
+    static cudaError_t solve_fwd_bt(const LevelArgs* args, const int2* work, int nwork, int grid, cudaStream_t s) {
+        if constexpr (M >= 8)
+            return launch_cta_b(k_solve_fwd_cta_batch<T, M, MODE>, solve_smem_bytes<T, M>(), args, work, nwork, grid, s);
+        else
+            return launch_tp_b(k_solve_fwd_tp_batch<T, M, MODE>, args, work, nwork, grid, s);
+    }
+    template <typename T>
+    static cudaError_t assemble_rhs_bt(const LevelArgs* args, const int2* work, int nwork, int grid,
+                                       cudaStream_t s) {
+        if constexpr (M >= 8)
+            return launch_cta_b(k_assemble_rhs_cta_batch<T, M>, assemble_rhs_smem_bytes<M>(), args, work, nwork,
+                                grid, s);
+        else
+            return launch_tp_b(k_assemble_rhs_tp_batch<T, M>, args, work, nwork, grid, s);
+    }
+    template <typename T, int MODE>
+    static cudaError_t solve_bwd_bt(const LevelArgs* args, const int2* work, int nwork, int grid, cudaStream_t s) {
+        if constexpr (M >= 8)
+            return launch_cta_b(k_solve_bwd_cta_batch<T, M, MODE>, solve_smem_bytes<T, M>(), args, work, nwork, grid, s);
+        else
+            return launch_tp_b(k_solve_bwd_tp_batch<T, M, MODE>, args, work, nwork, grid, s);
+    }
+    static cudaError_t factor_b(const LevelArgs* args, const int2* work, int nwork, int mode, bool low, int grid,
+                                cudaStream_t s) {
+        if (mode == 0)
+            return low ? factor_bt<float, 0>(args, work, nwork, grid, s) : factor_bt<double, 0>(args, work, nwork, grid, s);
+        return low ? factor_bt<float, 1>(args, work, nwork, grid, s) : factor_bt<double, 1>(args, work, nwork, grid, s);
+    }
+    static cudaError_t assemble_b(const LevelArgs* args, const int2* work, int nwork, int mode, bool low, int grid,
+                                  cudaStream_t s) {
+        (void)mode;
+        return low ? assemble_bt<float>(args, work, nwork, grid, s) : assemble_bt<double>(args, work, nwork, grid, s);
+    }
+    static cudaError_t solve_fwd_b(const LevelArgs* args, const int2* work, int nwork, int mode, bool low, int grid,
+                                   cudaStream_t s) {
+        if (mode == 0)
+            return low ? solve_fwd_bt<float, 0>(args, work, nwork, grid, s)
+                       : solve_fwd_bt<double, 0>(args, work, nwork, grid, s);
+        return low ? solve_fwd_bt<float, 1>(args, work, nwork, grid, s)
+                   : solve_fwd_bt<double, 1>(args, work, nwork, grid, s);
+    }
+    static cudaError_t assemble_rhs_b(const LevelArgs* args, const int2* work, int nwork, int mode, bool low,
+                                      int grid, cudaStream_t s) {
+        (void)mode;
+        return low ? assemble_rhs_bt<float>(args, work, nwork, grid, s)
+                   : assemble_rhs_bt<double>(args, work, nwork, grid, s);
+    }
+    static cudaError_t solve_bwd_b(const LevelArgs* args, const int2* work, int nwork, int mode, bool low, int grid,
+                                   cudaStream_t s) {
+        if (mode == 0)
+            return low ? solve_bwd_bt<float, 0>(args, work, nwork, grid, s)
+                       : solve_bwd_bt<double, 0>(args, work, nwork, grid, s);
+        return low ? solve_bwd_bt<float, 1>(args, work, nwork, grid, s)
+                   : solve_bwd_bt<double, 1>(args, work, nwork, grid, s);
+    }
+    static cudaError_t prepare() {
+        if constexpr (M >= 8) {
+            const size_t f64 = factor_smem_bytes<double, M>(), f32 = factor_smem_bytes<float, M>();
+            cudaError_t e = set_smem(k_factor_cta<double, M, 0>, f64);
+            if (e == cudaSuccess) e = set_smem(k_factor_cta<double, M, 1>, f64);
+            if (e == cudaSuccess) e = set_smem(k_factor_cta<float, M, 0>, f32);
+            if (e == cudaSuccess) e = set_smem(k_factor_cta<float, M, 1>, f32);
+            if (e == cudaSuccess) e = set_smem(k_factor_cta_batch<double, M, 0>, f64);
+            if (e == cudaSuccess) e = set_smem(k_factor_cta_batch<double, M, 1>, f64);
+            if (e == cudaSuccess) e = set_smem(k_factor_cta_batch<float, M, 0>, f32);
+            if (e == cudaSuccess) e = set_smem(k_factor_cta_batch<float, M, 1>, f32);
+            return e;
+        }
+        return cudaSuccess;
+    }
     static const Launchers* table() {
-        static const Launchers L = {factor, assemble, solve_fwd, assemble_rhs, solve_bwd};
+        static const Launchers L = {factor, assemble, solve_fwd, assemble_rhs, solve_bwd,
+                                    factor_b, assemble_b, solve_fwd_b, assemble_rhs_b, solve_bwd_b,
+                                    M >= 8,
+                                    M >= 8 ? factor_smem_bytes<double, M>() : 0,
+                                    M >= 8 ? factor_smem_bytes<float, M>() : 0,
+                                    M >= 8 ? assemble_smem_bytes<M>() : 0,
+                                    M >= 8 ? solve_smem_bytes<double, M>() : 0,
+                                    M >= 8 ? solve_smem_bytes<float, M>() : 0,
+                                    M >= 8 ? assemble_rhs_smem_bytes<M>() : 0,
+                                    prepare};
         return &L;
     }
 };

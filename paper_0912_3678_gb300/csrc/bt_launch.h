@@ -12,6 +12,24 @@ struct Launchers {
     cudaError_t (*solve_fwd)(const LevelArgs&, bool low, cudaStream_t);
     cudaError_t (*assemble_rhs)(const LevelArgs&, bool low, cudaStream_t);
     cudaError_t (*solve_bwd)(const LevelArgs&, bool low, cudaStream_t);
+    // Batched (persistent) variants: work[w] = (index into args, unit); `grid`
+    // CTAs stride over the nwork items.  mode is the same for every item.
+    cudaError_t (*factor_b)(const LevelArgs* args, const int2* work, int nwork, int mode, bool low, int grid,
+                            cudaStream_t);
+    cudaError_t (*assemble_b)(const LevelArgs* args, const int2* work, int nwork, int mode, bool low, int grid,
+                              cudaStream_t);
+    cudaError_t (*solve_fwd_b)(const LevelArgs* args, const int2* work, int nwork, int mode, bool low, int grid,
+                               cudaStream_t);
+    cudaError_t (*assemble_rhs_b)(const LevelArgs* args, const int2* work, int nwork, int mode, bool low,
+                                  int grid, cudaStream_t);
+    cudaError_t (*solve_bwd_b)(const LevelArgs* args, const int2* work, int nwork, int mode, bool low, int grid,
+                               cudaStream_t);
+    // CTA-per-unit kernels (m >= 8) or thread-per-unit kernels (m <= 4)
+    bool cta;
+    // dynamic shared memory per CTA of each kernel kind (CTA kernels)
+    size_t smem_factor64, smem_factor32, smem_assemble, smem_solve64, smem_solve32, smem_assemble_rhs;
+    // make sure every kernel of this m has its shared-memory attribute set
+    cudaError_t (*prepare)();
 };
 
 const Launchers* launchers_m1();

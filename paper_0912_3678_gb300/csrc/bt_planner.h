@@ -1,0 +1,65 @@
+// Host-side choice of the recursion levels (partition counts per level).
+#pragma once
+#include <vector>
+
+namespace bt {
+
+struct Tuning {
+    long long p0 = 0;        // level-0 partitions (0: from ctas_per_sm)
+    int ctas_per_sm = 0;     // level-0 target partitions per SM (0: 4 for CTA kernels, 512 for m <= 4)
+    int sub_rows = 0;        // block rows per partition on recursion levels (0: 4)
+    int top_rows = 0;        // a level with at most this many rows is one partition / direct (0: 8)
+};
+
+struct LevelShape {
+    long long N, p, base, extra, rows;
+};
+
+// kind 0: block tridiagonal (last level: one partition); kind 1: BABD (last
+// level: direct solve, p = 0).  Returns false on invalid parameters.
+inline bool plan_shapes(int kind, long long N, int m, int sms, const Tuning& t, std::vector<LevelShape>& out) {
+    out.clear();
+    const long long top_rows = t.top_rows > 0 ? t.top_rows : 8;
+    const long long sub_rows = t.sub_rows >= 2 ? t.sub_rows : 4;
+    const long long per_sm = t.ctas_per_sm > 0 ? t.ctas_per_sm : ((m >= 8) ? 4 : 512);
+    const long long kmin = (m >= 8) ? 4 : 8;
+    long long rows = N;
+    for (int l = 0; l < 64; ++l) {
+        const bool small = rows <= top_rows;
+        long long cap = (kind == 0) ? (rows + 1) / 2 : (rows - 1) / 2;
+        if (cap < 1) cap = 1;
+        long long parts;
+        if (l == 0 && t.p0 > 0) {
+            parts = t.p0;
+            if (kind == 0 && parts > 1 && parts > cap) return false;
+            if (kind == 1 && parts > 1 && parts > cap && rows >= 3) return false;
+        } else if (small) {
+            parts = 1;
+        } else if (l == 0) {
+            parts = (long long)sms * per_sm;
+            if (rows / kmin < parts) parts = rows / kmin;
+        } else {
+            parts = rows / sub_rows;
+        }
+        if (parts < 1) parts = 1;
+        if (!(l == 0 && t.p0 > 0) && parts > cap) parts = cap;
+        if (kind == 1) {
+            if (small || rows < 3) parts = 0;
+            if (parts == 1 && l > 0) parts = 0;
+            if (l == 0 && t.p0 == 1 && rows >= 3) parts = 1;
+        }
+        LevelShape s{rows, parts, 0, 0, kind == 0 ? rows : rows + 1};
+        if (parts > 0) {
+            const long long span = (kind == 0) ? rows : rows - 1;
+            s.base = span / parts;
+            s.extra = span % parts;
+        }
+        out.push_back(s);
+        if (kind == 0 && parts <= 1) return true;
+        if (kind == 1 && parts == 0) return true;
+        rows = (kind == 0) ? parts - 1 : parts;
+    }
+    return false;
+}
+
+}  // namespace bt

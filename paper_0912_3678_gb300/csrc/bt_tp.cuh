@@ -102,9 +102,8 @@ __device__ __forceinline__ void rgj_inverse(T (&a)[M * M], long long* st, int le
 }
 
 template <typename T, int M, int MODE>
-__global__ void __launch_bounds__(128) k_factor_tp(const LevelArgs a) {
+__device__ __forceinline__ void factor_tp_body(const LevelArgs& a, const long long i) {
     constexpr int MM = M * M;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= a.p) return;
     const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
     T* gDinv = reinterpret_cast<T*>(a.Dinv);
@@ -179,9 +178,8 @@ __global__ void __launch_bounds__(128) k_factor_tp(const LevelArgs a) {
 }
 
 template <typename T, int M>
-__global__ void __launch_bounds__(128) k_assemble_tp(const LevelArgs a) {
+__device__ __forceinline__ void assemble_tp_body(const LevelArgs& a, const long long s) {
     constexpr int MM = M * M;
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= a.p - 1) return;
     const Part pt = part_bounds(0, a.N, a.p, a.base, a.extra, s);
     const long long e = pt.e;
@@ -238,10 +236,9 @@ __device__ __forceinline__ void vst(double* g, const T (&v)[M], int nr) {
 }
 
 template <typename T, int M, int MODE>
-__global__ void __launch_bounds__(128) k_solve_fwd_tp(const LevelArgs a) {
+__device__ __forceinline__ void solve_fwd_tp_body(const LevelArgs& a, const long long tid) {
     constexpr int MM = M * M;
     const int nr = a.nr;
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long i = tid / nr;
     const int c = (int)(tid % nr);
     if (i >= a.p) return;
@@ -298,10 +295,9 @@ __global__ void __launch_bounds__(128) k_solve_fwd_tp(const LevelArgs a) {
 }
 
 template <typename T, int M>
-__global__ void __launch_bounds__(128) k_assemble_rhs_tp(const LevelArgs a) {
+__device__ __forceinline__ void assemble_rhs_tp_body(const LevelArgs& a, const long long tid) {
     constexpr int MM = M * M;
     const int nr = a.nr;
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long s = tid / nr;
     const int c = (int)(tid % nr);
     if (s >= a.p - 1) return;
@@ -322,10 +318,9 @@ __global__ void __launch_bounds__(128) k_assemble_rhs_tp(const LevelArgs a) {
 }
 
 template <typename T, int M, int MODE>
-__global__ void __launch_bounds__(128) k_solve_bwd_tp(const LevelArgs a) {
+__device__ __forceinline__ void solve_bwd_tp_body(const LevelArgs& a, const long long tid) {
     constexpr int MM = M * M;
     const int nr = a.nr;
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long i = tid / nr;
     const int c = (int)(tid % nr);
     if (i >= a.p) return;
@@ -371,5 +366,30 @@ __global__ void __launch_bounds__(128) k_solve_bwd_tp(const LevelArgs a) {
         vst<M, T>(a.X + j * E + c, x, nr);
     }
 }
+
+// ---------------------------------------------------------------- wrappers --
+// Single system: global thread t handles unit t (partition, separator or
+// (partition, rhs) pair).  Batched (persistent, grid-stride): item w of the
+// work list is (system, unit).
+#define BT_TP_KERNELS(NAME, BODY, TPL, TARGS)                                                           \
+    template <TPL>                                                                                     \
+    __global__ void __launch_bounds__(128) NAME(const LevelArgs a) {                                   \
+        BODY<TARGS>(a, (long long)blockIdx.x * blockDim.x + threadIdx.x);                               \
+    }                                                                                                  \
+    template <TPL>                                                                                     \
+    __global__ void __launch_bounds__(128)                                                             \
+        NAME##_batch(const LevelArgs* __restrict__ args, const int2* __restrict__ work, int nwork) {   \
+        for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nwork; w += gridDim.x * blockDim.x) {  \
+            const int2 it = work[w];                                                                   \
+            BODY<TARGS>(args[it.x], (long long)it.y);                                                   \
+        }                                                                                              \
+    }
+
+#define BT_TP_COMMA ,
+BT_TP_KERNELS(k_factor_tp, factor_tp_body, typename T BT_TP_COMMA int M BT_TP_COMMA int MODE, T BT_TP_COMMA M BT_TP_COMMA MODE)
+BT_TP_KERNELS(k_assemble_tp, assemble_tp_body, typename T BT_TP_COMMA int M, T BT_TP_COMMA M)
+BT_TP_KERNELS(k_solve_fwd_tp, solve_fwd_tp_body, typename T BT_TP_COMMA int M BT_TP_COMMA int MODE, T BT_TP_COMMA M BT_TP_COMMA MODE)
+BT_TP_KERNELS(k_assemble_rhs_tp, assemble_rhs_tp_body, typename T BT_TP_COMMA int M, T BT_TP_COMMA M)
+BT_TP_KERNELS(k_solve_bwd_tp, solve_bwd_tp_body, typename T BT_TP_COMMA int M BT_TP_COMMA int MODE, T BT_TP_COMMA M BT_TP_COMMA MODE)
 
 }  // namespace bt
