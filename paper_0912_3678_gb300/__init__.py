@@ -312,6 +312,18 @@ class BtPlan(_PlanBase):
     """Block tridiagonal plan: B_j x_{j-1} + D_j x_j + C_j x_{j+1} = f_j."""
     kind = 0
 
+    @classmethod
+    def tuned(cls, nblk, m, nrhs_max=1, prec="fp64", tuning=None, stream=None):
+        """A plan with explicit partitioning parameters (see tune.Tuner)."""
+        import torch
+        self = cls.__new__(cls)
+        self.m, self.n, self.nrhs_max, self.prec, self.stream = int(m), int(nblk), int(nrhs_max), prec, stream
+        self.rows = self.n
+        self.handle = bt_plan_create_tuned(nblk, m, nrhs_max, prec, tuning, stream)
+        self._keep = ()
+        self._torch = torch
+        return self
+
     def factor(self, B, D, C):
         self._keep = (B, D, C)
         bt_factor(self.handle, B, D, C)

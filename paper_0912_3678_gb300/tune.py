@@ -1,0 +1,149 @@
+"""Autotuner for the partitioning parameters (plan step A0): top-level
+partition length, recursion-level partition length and the size at which a
+level is solved by one partition.  Candidates are timed on synthetic
+systems of the requested shape (generated on the device) through the normal
+C-ABI plan calls; the fastest setting is cached per (device SM count, block
+order, precision, log2 of the block-row count) in a JSON file.
+
+    tuner = Tuner()                      # cache in paper_0912_3678_gb300/_build/tune_cache.json
+    t = tuner.tune(m=16, N=16384, prec="fp64")
+    plan = BtPlan.tuned(16384, 16, tuning=t)      # or BtBatch(..., tuner=tuner)
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_CACHE = os.path.join(HERE, "_build", "tune_cache.json")
+
+
+def bucket(N: int) -> int:
+    return int(round(math.log2(max(N, 1))))
+
+
+def default_tuning(m: int, N: int, prec: str = "fp64", batch: bool = False) -> dict:
+    """The built-in heuristic (all zero: the library's own defaults)."""
+    return {"p0": 0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0}
+
+
+class Tuner:
+    def __init__(self, path: str = DEFAULT_CACHE, sm_count: int | None = None):
+        self.path = path
+        self._lock = threading.Lock()
+        self._sm = sm_count
+        self.cache = {}
+        if os.path.exists(path):
+            try:
+                with open(path) as fh:
+                    self.cache = json.load(fh)
+            except (OSError, ValueError):
+                self.cache = {}
+
+    def sm_count(self) -> int:
+        if self._sm is None:
+            import torch
+            self._sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        return self._sm
+
+    def key(self, m: int, N: int, prec: str, nrhs: int = 1) -> str:
+        return f"sm{self.sm_count()}:m{m}:{prec}:n2^{bucket(N)}:r{min(nrhs, 8)}"
+
+    def __call__(self, m: int, N: int, prec: str = "fp64", nrhs: int = 1) -> dict:
+        """Cached tuning for this shape, or the built-in defaults."""
+        hit = self.cache.get(self.key(m, N, prec, nrhs))
+        return dict(hit["tuning"]) if hit else default_tuning(m, N, prec)
+
+    def save(self):
+        with self._lock:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            tmp = self.path + f".tmp{os.getpid()}"
+            with open(tmp, "w") as fh:
+                json.dump(self.cache, fh, indent=1, sort_keys=True)
+            os.replace(tmp, self.path)
+
+    # ------------------------------------------------------------ timing --
+    @staticmethod
+    def _system(m, N, nrhs, device, seed=0):
+        import torch
+        g = torch.Generator(device=device).manual_seed(seed)
+        s = 1.0 / math.sqrt(m)
+        B = torch.randn((N, m, m), generator=g, device=device, dtype=torch.float64) * s
+        C = torch.randn((N, m, m), generator=g, device=device, dtype=torch.float64) * s
+        D = torch.randn((N, m, m), generator=g, device=device, dtype=torch.float64) * s
+        D += 4.0 * torch.eye(m, device=device, dtype=torch.float64)
+        F = torch.randn((N * m, nrhs), generator=g, device=device, dtype=torch.float64)
+        return B, D, C, F
+
+    def time_setting(self, m, N, prec, nrhs, tuning, reps=5, data=None) -> float:
+        """Median ms of one factor + solve (+ refinement for low precision)."""
+        import torch
+
+        from . import BtPlan
+        dev = torch.device("cuda", torch.cuda.current_device())
+        B, D, C, F = data if data is not None else self._system(m, N, nrhs, dev)
+        X = torch.empty_like(F)
+        times = []
+        with BtPlan.tuned(N, m, nrhs_max=nrhs, prec=prec, tuning=tuning) as plan:
+            for r in range(reps + 2):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                plan.factor(B, D, C)
+                if prec == "fp64":
+                    plan.solve(F, X)
+                else:
+                    plan.refine(F, X, tol=1e-12, maxit=30)
+                e1.record()
+                torch.cuda.synchronize()
+                if r >= 2:
+                    times.append(e0.elapsed_time(e1))
+        times.sort()
+        return times[len(times) // 2]
+
+    def candidates_k0(self, m, N):
+        ks = [4, 8, 16, 32, 64, 128, 256] if m >= 8 else [8, 16, 32, 64, 128, 256, 512]
+        out = []
+        for k in ks:
+            p0 = max(1, min(N // k, (N + 1) // 2))
+            if p0 not in [c["p0"] for c in out]:
+                out.append({"p0": p0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0})
+        return out
+
+    def tune(self, m: int, N: int, prec: str = "fp64", nrhs: int = 1, reps: int = 5, force: bool = False) -> dict:
+        """Coordinate search: top-level partition length, then the recursion
+        partition length, then the direct-solve threshold."""
+        k = self.key(m, N, prec, nrhs)
+        if not force and k in self.cache:
+            return dict(self.cache[k]["tuning"])
+        import torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        data = self._system(m, N, nrhs, dev)
+        trials = []
+
+        def run(t):
+            ms = self.time_setting(m, N, prec, nrhs, t, reps, data)
+            trials.append((ms, dict(t)))
+            return ms
+
+        best_t = default_tuning(m, N, prec)
+        best = run(best_t)
+        for t in self.candidates_k0(m, N):
+            ms = run(t)
+            if ms < best:
+                best, best_t = ms, t
+        for sub in (2, 3, 6, 8):
+            t = dict(best_t, sub_rows=sub)
+            ms = run(t)
+            if ms < best:
+                best, best_t = ms, t
+        for top in (2, 4, 16):
+            t = dict(best_t, top_rows=top)
+            ms = run(t)
+            if ms < best:
+                best, best_t = ms, t
+        self.cache[k] = {"tuning": best_t, "ms": best, "trials": len(trials)}
+        self.save()
+        return dict(best_t)
