@@ -123,6 +123,26 @@ bt_status bt_residual(bt_plan plan, const double* F, const double* X, double* R,
 bt_status bt_refine(bt_plan plan, const double* F, double* X, int nrhs, double tol, int maxit,
                     int* iters_out, double* relcorr_out);
 
+/* Asynchronous refinement for schedulers that must not block: enqueue
+ * X = solve(F) and exactly `sweeps` (0..30) corrections { R = F - A X (FP64);
+ * D = solve(R); X += D } on the plan's stream, with no host synchronisation.
+ * Works for block tridiagonal and BABD plans.  bt_refine_result later
+ * synchronises and reports ||D||_F/||X||_F of the last correction: BT_OK if
+ * it is <= tol, BT_ERR_NOT_CONVERGED otherwise (or a numerical status). */
+bt_status bt_refine_async(bt_plan plan, const double* F, double* X, int nrhs, int sweeps);
+bt_status bt_refine_result(bt_plan plan, double tol, double* relcorr_out);
+
+/* Plans on caller-provided device memory (e.g. from a pooling allocator), so
+ * that creating a plan performs no device allocation: bt_plan_workspace_size
+ * returns the bytes a plan of this shape needs (kind 0: block tridiagonal,
+ * n = block rows; kind 1: BABD, n = N), bt_plan_create_in builds the plan in
+ * `workspace` (256-byte aligned, at least that many bytes, owned by the
+ * caller and kept alive until bt_plan_destroy, which does not free it). */
+bt_status bt_plan_workspace_size(int kind, int64_t n, int m, int nrhs_max, int prec, const bt_tuning* tuning,
+                                 int64_t* bytes);
+bt_status bt_plan_create_in(bt_plan* plan, int kind, int64_t n, int m, int nrhs_max, int prec,
+                            const bt_tuning* tuning, void* workspace, int64_t bytes, void* stream);
+
 /* Wait for the plan's stream; return the recorded numerical status. */
 bt_status bt_sync(bt_plan plan);
 

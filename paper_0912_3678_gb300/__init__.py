@@ -19,7 +19,8 @@ __all__ = ["BtPlan", "AbdPlan", "BtError", "BT_STATUS", "PREC", "load_library",
            "bt_plan_levels", "bt_plan_bytes", "bt_plan_trace", "bt_plan_trace_query", "bt_plan_launches",
            "KERNEL_KINDS", "bt_solve_noalloc", "BT_NOALLOC_SCRATCH_BYTES", "bt_plan_create_tuned",
            "bt_batch_create", "bt_batch_run", "bt_batch_finish", "bt_batch_info", "bt_batch_destroy",
-           "BtBatch", "BtTuning", "BtBatchDesc", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
+           "BtBatch", "BtTuning", "BtBatchDesc", "bt_refine_async", "bt_refine_result",
+           "bt_plan_workspace_size", "bt_plan_create_in", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
            "abd_plan_create", "abd_factor", "abd_solve", "abd_residual", "abd_refine", "abd_sync",
            "abd_plan_destroy"]
 
@@ -163,6 +164,39 @@ def bt_refine(plan, F, X, nrhs, tol=1e-12, maxit=30, raise_on_error=True):
 
 def abd_refine(plan, RHS, Y, nrhs, tol=1e-12, maxit=30, raise_on_error=True):
     return _refine(_lib.load().abd_refine, "abd_refine", plan, RHS, Y, nrhs, tol, maxit, raise_on_error)
+
+
+def bt_refine_async(plan, F, X, nrhs, sweeps=2):
+    _lib.check(_lib.load().bt_refine_async(plan, _ptr(F), _ptr(X), int(nrhs), int(sweeps)), "bt_refine_async")
+
+
+def bt_refine_result(plan, tol=1e-12):
+    rc = ctypes.c_double(0.0)
+    code = _lib.load().bt_refine_result(plan, float(tol), ctypes.byref(rc))
+    return code, rc.value
+
+
+def bt_plan_workspace_size(kind, n, m, nrhs_max=1, prec="fp64", tuning=None) -> int:
+    b = ctypes.c_int64(0)
+    t = _tuning(tuning)
+    _lib.check(_lib.load().bt_plan_workspace_size(int(kind), int(n), int(m), int(nrhs_max), _prec(prec),
+                                                  ctypes.byref(t) if t is not None else None, ctypes.byref(b)),
+               "bt_plan_workspace_size")
+    return b.value
+
+
+def bt_plan_create_in(kind, n, m, nrhs_max, prec, workspace, nbytes, tuning=None, stream=None):
+    h = ctypes.c_void_p()
+    t = _tuning(tuning)
+    _lib.check(_lib.load().bt_plan_create_in(ctypes.byref(h), int(kind), int(n), int(m), int(nrhs_max),
+                                             _prec(prec), ctypes.byref(t) if t is not None else None,
+                                             _ptr_any(workspace), int(nbytes), _stream(stream)),
+               "bt_plan_create_in")
+    return h
+
+
+def _ptr_any(t):
+    return t if isinstance(t, int) else t.data_ptr()
 
 
 def bt_sync(plan) -> int:

@@ -45,6 +45,8 @@ struct bt_plan_s {
     // device memory
     char* arena = nullptr;
     size_t arena_bytes = 0;
+    bool own_arena = true;
+    bool pinned = true;
     long long* status = nullptr;
     long long* status_host = nullptr;   // pinned
     double* norms = nullptr;            // [2]
@@ -148,7 +150,7 @@ void layout(bt_plan_s* P, Arena& ar) {
 }
 
 bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, int prec, const bt::Tuning& tune,
-                      void* stream) {
+                      void* stream, void* workspace = nullptr, int64_t ws_bytes = 0, int64_t* need_bytes = nullptr) {
     const int64_t p = tune.p0;
     if (!out) return BT_ERR_INVALID;
     *out = nullptr;
@@ -195,23 +197,51 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
     Arena meas;
     layout(P, meas);
     size_t bytes = meas.off + 256;
-    cudaError_t e = cudaMalloc((void**)&P->arena, bytes);
-    if (e != cudaSuccess) {
+    if (need_bytes) {
+        *need_bytes = (int64_t)bytes;
         delete P;
-        cudaGetLastError();
-        return from_cuda(e);
+        return BT_OK;
+    }
+    cudaError_t e = cudaSuccess;
+    if (workspace) {
+        if (ws_bytes < (int64_t)bytes || ((uintptr_t)workspace & 255u)) {
+            delete P;
+            return BT_ERR_INVALID;
+        }
+        P->arena = (char*)workspace;
+        P->own_arena = false;
+        P->pinned = false;
+    } else {
+        e = cudaMalloc((void**)&P->arena, bytes);
+        if (e != cudaSuccess) {
+            delete P;
+            cudaGetLastError();
+            return from_cuda(e);
+        }
     }
     P->arena_bytes = bytes;
     Arena real;
     real.base = P->arena;
     layout(P, real);
     for (auto& v : P->lv) v.a.status = P->status;
-    e = cudaMallocHost((void**)&P->status_host, 4 * sizeof(long long));
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&P->norms_host, 2 * sizeof(double));
+    if (P->pinned) {
+        e = cudaMallocHost((void**)&P->status_host, 4 * sizeof(long long));
+        if (e == cudaSuccess) e = cudaMallocHost((void**)&P->norms_host, 2 * sizeof(double));
+    } else {
+        P->status_host = new (std::nothrow) long long[4];
+        P->norms_host = new (std::nothrow) double[2];
+        if (!P->status_host || !P->norms_host) e = cudaErrorMemoryAllocation;
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(P->status, 0, 4 * sizeof(long long), P->stream);
     if (e != cudaSuccess) {
-        cudaFree(P->arena);
-        if (P->status_host) cudaFreeHost(P->status_host);
+        if (P->own_arena) cudaFree(P->arena);
+        if (P->pinned) {
+            if (P->status_host) cudaFreeHost(P->status_host);
+            if (P->norms_host) cudaFreeHost(P->norms_host);
+        } else {
+            delete[] P->status_host;
+            delete[] P->norms_host;
+        }
         delete P;
         return from_cuda(e);
     }
@@ -342,6 +372,25 @@ bt_status run_refine(bt_plan_s* P, const double* F, double* X, int nr, double to
     return BT_ERR_NOT_CONVERGED;
 }
 
+// Enqueue X = solve(F) and `sweeps` refinement corrections; no host sync.
+bt_status run_refine_async(bt_plan_s* P, const double* F, double* X, int nr, int sweeps) {
+    bt_status st = run_solve(P, F, X, nr);
+    const long long n = P->lv[0].rows * P->m * nr;
+    for (int it = 0; it < sweeps && st == BT_OK; ++it) {
+        st = run_residual(P, F, X, P->Rbuf, nr);
+        if (st == BT_OK) st = run_solve(P, P->Rbuf, P->Dbuf, nr);
+        if (st != BT_OK) return st;
+        cudaError_t e = launch(P, K_IR, 0, 2,
+                               [&] { return bt::launch_ir_update(n, X, P->Dbuf, P->partial, P->norms, P->stream); });
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    if (sweeps == 0) {
+        cudaError_t e = cudaMemsetAsync(P->norms, 0, 2 * sizeof(double), P->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    return st;
+}
+
 }  // namespace
 
 extern "C" {
@@ -461,6 +510,38 @@ bt_status abd_refine(abd_plan P, const double* RHS, double* Y, int nrhs, double 
     return st != BT_OK ? st : run_refine(P, RHS, Y, nrhs, tol, maxit, iters_out, relcorr_out);
 }
 
+bt_status bt_refine_async(bt_plan P, const double* F, double* X, int nrhs, int sweeps) {
+    bt_status st = check_solve(P, P ? P->kind : 0, F, X, nrhs);
+    if (st == BT_OK && (sweeps < 0 || sweeps > 30)) st = BT_ERR_INVALID;
+    return st != BT_OK ? st : run_refine_async(P, F, X, nrhs, sweeps);
+}
+
+bt_status bt_refine_result(bt_plan P, double tol, double* relcorr_out) {
+    if (!P) return BT_ERR_INVALID;
+    cudaError_t e = cudaMemcpyAsync(P->norms_host, P->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, P->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    bt_status st = read_status(P);
+    const double dd = P->norms_host[0], xx = P->norms_host[1];
+    const double rel = (xx > 0.0) ? std::sqrt(dd / xx) : std::sqrt(dd);
+    if (relcorr_out) *relcorr_out = rel;
+    if (st != BT_OK) return st;
+    if (!std::isfinite(rel)) return BT_ERR_NONFINITE;
+    return rel <= tol ? BT_OK : BT_ERR_NOT_CONVERGED;
+}
+
+bt_status bt_plan_workspace_size(int kind, int64_t n, int m, int nrhs_max, int prec, const bt_tuning* tuning,
+                                 int64_t* bytes) {
+    if (!bytes || (kind != 0 && kind != 1)) return BT_ERR_INVALID;
+    bt_plan tmp = nullptr;
+    return plan_create(&tmp, kind, n, m, nrhs_max, prec, to_tuning(tuning, 0), nullptr, nullptr, 0, bytes);
+}
+
+bt_status bt_plan_create_in(bt_plan* plan, int kind, int64_t n, int m, int nrhs_max, int prec,
+                            const bt_tuning* tuning, void* workspace, int64_t bytes, void* stream) {
+    if (!workspace || (kind != 0 && kind != 1)) return BT_ERR_INVALID;
+    return plan_create(plan, kind, n, m, nrhs_max, prec, to_tuning(tuning, 0), stream, workspace, bytes, nullptr);
+}
+
 bt_status bt_sync(bt_plan P) {
     if (!P) return BT_ERR_INVALID;
     return read_status(P);
@@ -555,9 +636,14 @@ void bt_plan_destroy(bt_plan P) {
     if (!P) return;
     cudaStreamSynchronize(P->stream);
     for (auto ev : P->pool) cudaEventDestroy(ev);
-    cudaFree(P->arena);
-    if (P->status_host) cudaFreeHost(P->status_host);
-    if (P->norms_host) cudaFreeHost(P->norms_host);
+    if (P->own_arena) cudaFree(P->arena);
+    if (P->pinned) {
+        if (P->status_host) cudaFreeHost(P->status_host);
+        if (P->norms_host) cudaFreeHost(P->norms_host);
+    } else {
+        delete[] P->status_host;
+        delete[] P->norms_host;
+    }
     delete P;
 }
 void abd_plan_destroy(abd_plan P) { bt_plan_destroy(P); }
