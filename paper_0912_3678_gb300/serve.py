@@ -264,7 +264,7 @@ class Server:
                     r.Yexact_err = float(r.Yexact_err)
                 f.busy -= 1
                 self.in_use -= vec_b
-                if not self.cache_enabled or f.key not in self.cache:
+                if self.cache.get(f.key) is not f:
                     if f.busy == 0:
                         f.destroy()
                         self.in_use -= f.nbytes
