@@ -155,19 +155,142 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """Config 4: uneven independent systems (n log-uniform, m from {1,4,8,16,32},
+    50/50 FP64 / BF16+refinement), generated on the device, one graph launch
+    per step.  Accuracy: a sample of systems against the oracle."""
+    import torch
+
+    import gen
+    import paper_0912_3678_gb300 as bt
+    from paper_0912_3678_gb300 import build as _build
+    _build.build()
+    dev = torch.device("cuda:0")
+    specs = gen.batch_specs(args.batch_count, nmax=args.batch_nmax)
+    systems, unknowns = [], 0
+    gcpu = torch.Generator(device=dev).manual_seed(20091234 + 4000)
+    for sp in specs:
+        N, m = sp.n // sp.m, sp.m
+        s = 1.0 / m ** 0.5
+        if m == 1:
+            D = torch.rand((N, 1, 1), generator=gcpu, device=dev, dtype=torch.float64) * 2 + 4
+            B = torch.rand((N, 1, 1), generator=gcpu, device=dev, dtype=torch.float64) * 2 - 1
+            C = torch.rand((N, 1, 1), generator=gcpu, device=dev, dtype=torch.float64) * 2 - 1
+        else:
+            B = torch.randn((N, m, m), generator=gcpu, device=dev, dtype=torch.float64) * s
+            C = torch.randn((N, m, m), generator=gcpu, device=dev, dtype=torch.float64) * s
+            D = torch.randn((N, m, m), generator=gcpu, device=dev, dtype=torch.float64) * s
+            D += 4 * torch.eye(m, device=dev, dtype=torch.float64)
+        F = torch.randn((N * m, 1), generator=gcpu, device=dev, dtype=torch.float64)
+        systems.append({"B": B, "D": D, "C": C, "F": F, "X": torch.empty_like(F),
+                        "prec": "bf16_ir" if sp.lowprec else "fp64"})
+        unknowns += N * m
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = bt.BtBatch(systems, ir_sweeps=4, mem_cap_bytes=int(args.batch_memcap_gb * 2 ** 30))
+    t_create = time.perf_counter() - t0
+    waves, nodes, nbytes = b.info()
+    for _ in range(args.warmup):
+        b.run()
+    b.finish()
+    ev = []
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.run()
+        e1.record()
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(c) for a, c in ev) / len(ev)
+    code, status, rel = b.finish()
+    # accuracy on a sample against the oracle
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(0)
+    sample = sorted(rng.choice(len(systems), size=min(24, len(systems)), replace=False).tolist())
+    worst = {"fp64": 0.0, "bf16_ir": 0.0}
+    t_or, n_or = 0.0, 0
+    for k in sample:
+        sd = systems[k]
+        if sd["D"].numel() > 3e7:
+            continue
+        h = {n: sd[n].cpu().numpy() for n in ("B", "D", "C", "F", "X")}
+        t1 = time.perf_counter()
+        ref = oracle.btri_solve(h["B"], h["D"], h["C"], h["F"])
+        t_or += time.perf_counter() - t1
+        n_or += h["F"].size
+        worst[sd["prec"]] = max(worst[sd["prec"]], oracle.rel_err(h["X"], ref))
+    line = {"metric": METRIC, "value": unknowns / (ms / 1e3), "unit": "unknowns/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 + bf16/f32+f64 refinement", "data": "synthetic",
+            "config": {"workload": f"{len(systems)} uneven block tridiagonal systems, n log-uniform "
+                                   f"[1e3,{args.batch_nmax:g}], m in {{1,4,8,16,32}}, 50/50 FP64 / BF16+IR, 1 RHS",
+                       "graph_nodes": nodes, "waves": waves, "workspace_gb": nbytes / 2 ** 30,
+                       "create_s": t_create},
+            "statuses_ok": sum(1 for x in status if x == 0), "systems": len(status),
+            "rel_err_sample_max": worst,
+            "cpu_baseline": {"value": n_or / t_or if t_or else None, "unit": "unknowns/s", "cores": 1,
+                             "kind": "oracle", "sample": f"{len(sample)} systems of the batch"}}
+    print(json.dumps(line))
+    b.close()
+    return 0
+
+
+def run_serve(args):
+    """Config 5: Poisson arrivals of BVP solves (m in {4,8,16}, N log-uniform
+    [1e3, 5e5], 1-32 RHS, 30% factorization reuse) replayed in real time."""
+    import torch
+
+    import gen
+    from paper_0912_3678_gb300 import build as _build
+    from paper_0912_3678_gb300 import serve
+    _build.build()
+    dev = torch.device("cuda:0")
+    warm = serve.requests_from_trace(gen.serve_trace(0.05, rate=200, rep=7), prec=args.serve_prec)
+    srv = serve.Server(dev, mem_cap_bytes=150e9, streams=8)
+    srv.run_trace(warm, realtime=False)
+    srv.close()
+    trace = gen.serve_trace(args.serve_seconds, rate=args.serve_rate, rep=0)
+    reqs = serve.requests_from_trace(trace, prec=args.serve_prec)
+    srv = serve.Server(dev, mem_cap_bytes=150e9, streams=8)
+    st = srv.run_trace(reqs, realtime=True, timeout_s=1800)
+    srv.close()
+    line = {"metric": METRIC, "value": st["unknowns_per_s"], "unit": "unknowns*rhs/s", "n_gpus": 1,
+            "steps": st["requests"], "warmup": len(warm), "ms_per_step": st["mean_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.serve_prec, "data": "synthetic",
+            "config": {"workload": f"served BVP stream, Poisson {args.serve_rate:g} req/s for "
+                                   f"{args.serve_seconds:g} s, m in {{4,8,16}}, N log-uniform [1e3,5e5], "
+                                   "1-32 RHS, 30% reuse, 150 GB cap, 8 streams"},
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "served": st}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="block16", choices=["block16", "babd8", "scalar"])
+    ap.add_argument("--workload", default="block16", choices=["block16", "babd8", "scalar", "batch", "serve"])
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--batch-nmax", type=float, default=1e6)
+    ap.add_argument("--batch-memcap-gb", type=float, default=80.0)
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-prec", default="fp64")
     ap.add_argument("--paths", default="fp64,fp32_ir")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     import torch
     ws, rank, local = _dist()

@@ -48,8 +48,9 @@ typedef enum {
 typedef enum {
     BT_FP64 = 0,     /* every factorization step in FP64 */
     BT_FP32_IR = 1,  /* local factors in FP32, reduced system FP64; solve via FP64 refinement */
-    BT_BF16_IR = 2   /* local Schur-complement products with BF16 operands (FP32 accumulate),
-                        reduced system FP64; solve via FP64 refinement */
+    BT_BF16_IR = 2   /* as BT_FP32_IR, with the local Schur-complement product B_j Y_{j-1}
+                        taken on the tensor cores with BF16 operands and FP32 accumulation
+                        (m >= 16; smaller blocks use the FP32 path) */
 } bt_prec;
 
 typedef struct bt_plan_s* bt_plan;

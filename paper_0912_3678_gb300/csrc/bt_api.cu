@@ -160,7 +160,6 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
     if (kind == 1 && N < 1) return BT_ERR_INVALID;
     if (kind == 0 && p > (N + 1) / 2 && p > 1) return BT_ERR_INVALID;
     if (kind == 1 && p > 0 && p > (N - 1) / 2 && p > 1) return BT_ERR_INVALID;
-    if (prec == BT_BF16_IR && m < 16) return BT_ERR_INVALID;
     bt_plan_s* P = new (std::nothrow) bt_plan_s();
     if (!P) return BT_ERR_NOMEM;
     P->kind = kind;
@@ -188,6 +187,7 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
         v.a.extra = shapes[l].extra;
         v.rows = shapes[l].rows;
         v.low = (l == 0) && (prec != BT_FP64);
+        v.a.bf16 = (l == 0) && (prec == BT_BF16_IR) && (m >= 16) ? 1 : 0;
         P->lv.push_back(v);
     }
     P->nlev = (int)P->lv.size() - 1;

@@ -300,6 +300,7 @@ bt_status bt_batch_create(bt_batch* out, const bt_batch_desc* descs, int count, 
             a.base = s.shapes[l].base;
             a.extra = s.shapes[l].extra;
             a.nr = d.nrhs;
+            a.bf16 = (l == 0 && d.prec == BT_BF16_IR && d.m >= 16) ? 1 : 0;
         }
         s.lv[0].B = d.B;
         s.lv[0].D = d.D;

@@ -18,6 +18,9 @@
 //   giving x_first = H + P x_L + Q x_R.  The separator rows then form the
 //   reduced matrix of Eq. (redmatr) (assembled by bt_assemble).
 #pragma once
+#include <cuda_bf16.h>
+#include <type_traits>
+
 #include "bt_device.cuh"
 #include "bt_level.h"
 
@@ -166,6 +169,47 @@ __device__ bool gj_inverse(T* a, T* colk, int* perm, long long* st, int level, l
     return ok;
 }
 
+// ------------------------------------------------------ BF16 tensor cores --
+// P = A B for M x M FP32 blocks in shared memory, with the operands rounded
+// to BF16 and FP32 accumulation, by warp-level mma.sync m16n8k16 tiles
+// (row-major A, column-major B fragments).  Tiles are spread over the warps.
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const unsigned*>(&v);
+}
+
+template <int M>
+__device__ __forceinline__ void gemm_bf16_tc(float* P, const float* A, const float* B) {
+    constexpr int LD = M + 1;
+    constexpr int MT = M / 16, NTL = M / 8, KS = M / 16;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    for (int tile = warp; tile < MT * NTL; tile += nwarps) {
+        const int mt = tile / NTL, nt = tile % NTL;
+        float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+            const int r0 = mt * 16 + g, k0 = ks * 16 + 2 * t, n0 = nt * 8 + g;
+            const unsigned a0 = pack_bf16(A[r0 * LD + k0], A[r0 * LD + k0 + 1]);
+            const unsigned a1 = pack_bf16(A[(r0 + 8) * LD + k0], A[(r0 + 8) * LD + k0 + 1]);
+            const unsigned a2 = pack_bf16(A[r0 * LD + k0 + 8], A[r0 * LD + k0 + 9]);
+            const unsigned a3 = pack_bf16(A[(r0 + 8) * LD + k0 + 8], A[(r0 + 8) * LD + k0 + 9]);
+            const unsigned b0 = pack_bf16(B[k0 * LD + n0], B[(k0 + 1) * LD + n0]);
+            const unsigned b1 = pack_bf16(B[(k0 + 8) * LD + n0], B[(k0 + 9) * LD + n0]);
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};"
+                : "+f"(c0), "+f"(c1), "+f"(c2), "+f"(c3)
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
+        const int r = mt * 16 + g, c = nt * 8 + 2 * t;
+        P[r * LD + c] = c0;
+        P[r * LD + c + 1] = c1;
+        P[(r + 8) * LD + c] = c2;
+        P[(r + 8) * LD + c + 1] = c3;
+    }
+}
+
 template <typename T, int M>
 constexpr size_t factor_smem_bytes() {
     return sizeof(T) * (6 * Cta<T, M>::BLK + M) + sizeof(int) * M;
@@ -204,10 +248,25 @@ __device__ __forceinline__ void factor_cta_body(const LevelArgs& a, const long l
         __syncthreads();
         if (MODE == 0 && !first) {
             T acc[S::R];
-            read_own<T, M>(acc, sD, o);
-            gemm_acc<T, M, true>(acc, sB, sY, o);
-            write_own<T, M>(sD, acc, o);
-            __syncthreads();
+            if constexpr (std::is_same<T, float>::value && M >= 16) {
+                if (a.bf16) {
+                    gemm_bf16_tc<M>(sT, sB, sY);
+                    __syncthreads();
+                    T pr[S::R];
+                    read_own<T, M>(acc, sD, o);
+                    read_own<T, M>(pr, sT, o);
+#pragma unroll
+                    for (int u = 0; u < S::R; ++u) acc[u] -= pr[u];
+                    write_own<T, M>(sD, acc, o);
+                    __syncthreads();
+                }
+            }
+            if (!a.bf16 || !(std::is_same<T, float>::value && M >= 16)) {
+                read_own<T, M>(acc, sD, o);
+                gemm_acc<T, M, true>(acc, sB, sY, o);
+                write_own<T, M>(sD, acc, o);
+                __syncthreads();
+            }
         }
         gj_inverse<T, M>(sD, colk, perm, a.status, a.level, i, j);
         store_blk<T, M>(gDinv + j * MM, sD);

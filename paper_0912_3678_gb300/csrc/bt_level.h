@@ -11,6 +11,7 @@ namespace bt {
 struct LevelArgs {
     int mode;
     int level;
+    int bf16;          // Schur product B_j Y_{j-1} with BF16 operands on the tensor cores (FP32 levels, m >= 16)
     long long N, p, base, extra;
     const double* B;
     const double* D;

@@ -144,7 +144,7 @@ class _Factor:
 
 
 class Server:
-    def __init__(self, device=None, mem_cap_bytes: float = 150e9, streams: int = 8, sweeps: int = 2,
+    def __init__(self, device=None, mem_cap_bytes: float = 150e9, streams: int = 8, sweeps: int = 3,
                  tol: float = 1e-12, cache: bool = True, check_exact: bool = False, max_inflight: int = 0):
         self.device = torch.device(device or "cuda")
         self.cap = int(mem_cap_bytes)

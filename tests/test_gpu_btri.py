@@ -134,6 +134,29 @@ def test_mixed_precision_refinement(cuda, m, N):
     assert oracle.rel_err(to_host(X), ref) <= TOLIR
 
 
+@pytest.mark.parametrize("m,N", [(16, 2000), (32, 300)])
+def test_bf16_tensor_core_schur_refinement(cuda, m, N):
+    """BF16 operands for the Schur products (tensor cores, FP32 accumulate):
+    the unrefined solve is only a few digits accurate (reported, not gated);
+    FP64 refinement brings it to <= 1e-10."""
+    import paper_0912_3678_gb300 as bt
+    s = gen.btri_random(N, m, 2, seed_rep=13)
+    ref = oracle.btri_solve(s.B, s.D, s.C, s.F)
+    B, D, C, F = (to_dev(a, cuda) for a in (s.B, s.D, s.C, s.F))
+    with bt.BtPlan(N, m, 2, prec="bf16_ir") as plan:
+        plan.factor(B, D, C)
+        lo = oracle.rel_err(to_host(plan.solve(F)), ref)
+        X, it, rc, code = plan.refine(F, tol=1e-12, maxit=30)
+    with bt.BtPlan(N, m, 2, prec="fp32_ir") as plan:
+        plan.factor(B, D, C)
+        lo32 = oracle.rel_err(to_host(plan.solve(F)), ref)
+    print(f"m={m}: unrefined rel err bf16 {lo:.2e}, fp32 {lo32:.2e}; bf16 corrections {it}")
+    assert lo > 10 * lo32              # the BF16 products are really in use
+    assert lo < 0.5
+    assert code == 0
+    assert oracle.rel_err(to_host(X), ref) <= TOLIR
+
+
 def test_residual_matches_oracle(cuda):
     import paper_0912_3678_gb300 as bt
     s = gen.btri_random(300, 8, 4, seed_rep=2)
