@@ -94,53 +94,55 @@ __device__ __forceinline__ void zero_own(T (&v)[Cta<T, M>::R]) {
 
 // ------------------------------------------------------------ Gauss-Jordan --
 // In-place inverse of the M x M block a (shared memory) by Gauss-Jordan
-// elimination with partial pivoting (first index of the largest |a_ik|).
-// Row k is swapped with the pivot row before step k; the swaps are undone as
-// column swaps in reverse order at the end.  Returns false (and reports) on a
-// zero or non-finite pivot.  Entered and left with all threads synchronised.
+// elimination with partial pivoting.  Step k: one warp (warp k mod nwarps, so
+// the serial work rotates over the SM sub-partitions) picks the pivot row p
+// with the largest |a_ik|, i >= k (one redux over 32-bit keys: the top 26
+// magnitude bits of each entry above the row index, so ties and magnitudes
+// equal to 2^-20 relative go to the first row), swaps rows k and p, scales
+// row k by 1/pivot and publishes the multiplier column; then every thread
+// eliminates column k from its rows.  The row swaps are undone as column
+// swaps at the end.  Reports a zero or non-finite pivot.  Entered and left
+// with all threads synchronised.
+template <typename T>
+__device__ __forceinline__ unsigned mag_key(T v);
+template <>
+__device__ __forceinline__ unsigned mag_key<double>(double v) {
+    return (unsigned)(__double2hiint(v) & 0x7fffffff) >> 5;
+}
+template <>
+__device__ __forceinline__ unsigned mag_key<float>(float v) {
+    return (__float_as_uint(v) & 0x7fffffffu) >> 5;
+}
+
 template <typename T, int M>
 __device__ bool gj_inverse(T* a, T* colk, int* perm, long long* st, int level, long long part,
                            long long row) {
     using S = Cta<T, M>;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = S::NT / 32;
     const Own<T, M> o;
     bool ok = true;
     for (int k = 0; k < M; ++k) {
-        if (warp == 0) {
-            unsigned long long key = 0ull;
-            int idx = 1 << 20;
-            if (lane >= k && lane < M) {
-                key = abs_key(a[lane * S::LD + k]);
-                idx = lane;
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const unsigned long long ok2 = __shfl_xor_sync(0xffffffffu, key, off);
-                const int oi = __shfl_xor_sync(0xffffffffu, idx, off);
-                if (ok2 > key || (ok2 == key && oi < idx)) {
-                    key = ok2;
-                    idx = oi;
-                }
-            }
-            const int p = idx;
-            if (p != k) {
-                for (int c = lane; c < M; c += 32) {
-                    const T t = a[k * S::LD + c];
-                    a[k * S::LD + c] = a[p * S::LD + c];
-                    a[p * S::LD + c] = t;
-                }
-            }
-            __syncwarp();
-            T pv = a[k * S::LD + k];
-            if (key == 0ull || nonfinite(pv)) {
-                if (lane == 0) report(st, key == 0ull ? ST_SINGULAR : ST_NONFINITE, level, part, row);
+        if (warp == k % NW) {
+            const T v = (lane < M) ? a[lane * S::LD + k] : T(0);
+            const unsigned key = (lane >= k && lane < M) ? ((mag_key<T>(v) << 5) | (unsigned)(31 - lane)) : 0u;
+            const unsigned best = __reduce_max_sync(0xffffffffu, key);
+            const int p = 31 - (int)(best & 31u);
+            T pv = __shfl_sync(0xffffffffu, v, p);
+            const T vk = __shfl_sync(0xffffffffu, v, k);
+            if (pv == T(0) || nonfinite(pv)) {
+                if (lane == 0) report(st, pv == T(0) ? ST_SINGULAR : ST_NONFINITE, level, part, row);
                 pv = T(1);
                 ok = false;
             }
             const T r = rcp(pv);
-            for (int i = lane; i < M; i += 32) colk[i] = (i == k) ? T(0) : a[i * S::LD + k];
-            __syncwarp();
-            for (int c = lane; c < M; c += 32) a[k * S::LD + c] = (c == k) ? r : a[k * S::LD + c] * r;
+            if (lane < M) {
+                colk[lane] = (lane == k) ? T(0) : (lane == p ? vk : v);
+                const T tk = a[k * S::LD + lane];
+                const T tp = a[p * S::LD + lane];
+                a[p * S::LD + lane] = tk;
+                a[k * S::LD + lane] = (lane == k) ? r : tp * r;
+            }
             if (lane == 0) perm[k] = p;
         }
         __syncthreads();
@@ -212,13 +214,48 @@ __device__ __forceinline__ void gemm_bf16_tc(float* P, const float* A, const flo
 
 template <typename T, int M>
 constexpr size_t factor_smem_bytes() {
-    return sizeof(T) * (6 * Cta<T, M>::BLK + M) + sizeof(int) * M;
+    return sizeof(T) * (7 * Cta<T, M>::BLK + M) + sizeof(int) * M;
 }
 
 // ------------------------------------------------------------------ factor --
 // One CTA per partition.  Mode 0: block tridiagonal level; mode 1: BABD level
 // (C = 0, so Y = 0 and no backward sweep; the right separator's reduced row
 // of Eq. (redmatr1) is written here: S'[i] = B_e Zc_{e-1}, R'[i] = D_e).
+// Per-thread prefetch of the next block row (R elements of each of B, D, C),
+// issued before the current row's work and stored to shared memory after it.
+template <typename T, int M>
+struct RowPrefetch {
+    double b[Cta<T, M>::R], d[Cta<T, M>::R], c[Cta<T, M>::R];
+    __device__ __forceinline__ void load(const double* gB, const double* gD, const double* gC) {
+#pragma unroll
+        for (int u = 0; u < Cta<T, M>::R; ++u) {
+            const int idx = threadIdx.x + u * Cta<T, M>::NT;
+            d[u] = gD[idx];
+            if (gB) b[u] = gB[idx];
+            if (gC) c[u] = gC[idx];
+        }
+    }
+    __device__ __forceinline__ void store(T* sB, T* sD, T* sC, bool hasB, bool hasC) const {
+        using S = Cta<T, M>;
+#pragma unroll
+        for (int u = 0; u < S::R; ++u) {
+            const int idx = threadIdx.x + u * S::NT;
+            const int at = (idx / M) * S::LD + idx % M;
+            sD[at] = (T)d[u];
+            if (hasB) sB[at] = (T)b[u];
+            if (hasC) sC[at] = (T)c[u];
+        }
+    }
+};
+
+// One CTA per partition.  Mode 0: block tridiagonal level; the top-row
+// coupling that the reduced row of the left separator needs is accumulated
+// during the forward sweep: with W_s = C_sep (the left separator row's block
+// coupling it to x_s) and W_{j+1} = -W_j Y_j,
+//   C_sep P_first = sum_j W_j Zc_j   (stored in Pf)  and  C_sep Q_first = W_e (Qf),
+// where x_first = H + P_first x_L + Q_first x_R after full elimination.
+// Mode 1: BABD level (C = 0, so Y = 0); the right separator's reduced row of
+// Eq. (redmatr1) is written here: S'[i] = B_e Zc_{e-1}, R'[i] = D_e.
 template <typename T, int M, int MODE>
 __device__ __forceinline__ void factor_cta_body(const LevelArgs& a, const long long i, unsigned char* smem_raw) {
     using S = Cta<T, M>;
@@ -228,7 +265,8 @@ __device__ __forceinline__ void factor_cta_body(const LevelArgs& a, const long l
     T* sY = sC + S::BLK;
     T* sZ = sY + S::BLK;
     T* sT = sZ + S::BLK;
-    T* colk = sT + S::BLK;
+    T* sW = sT + S::BLK;
+    T* colk = sW + S::BLK;
     int* perm = reinterpret_cast<int*>(colk + M);
 
     const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
@@ -237,17 +275,32 @@ __device__ __forceinline__ void factor_cta_body(const LevelArgs& a, const long l
     T* gY = reinterpret_cast<T*>(a.Y);
     T* gZ = reinterpret_cast<T*>(a.Zc);
     const long long MM = S::MM;
+    const bool wchain = (MODE == 0) && pt.hasL;
+    T cp[S::R];   // sum_j W_j Zc_j (own elements)
+    zero_own<T, M>(cp);
+
+    auto needB = [&](long long j) { return j > pt.s || pt.hasL; };
+    auto needC = [&](long long j) { return (MODE == 0) && ((j < pt.e - 1) || pt.hasR); };
+    if (pt.s < pt.e) {
+        RowPrefetch<T, M> pf;
+        pf.load(needB(pt.s) ? a.B + (pt.s - a.shift) * MM : nullptr, a.D + (pt.s - a.shift) * MM,
+                needC(pt.s) ? a.C + (pt.s - a.shift) * MM : nullptr);
+        pf.store(sB, sD, sC, needB(pt.s), needC(pt.s));
+        if (wchain) load_blk<T, M>(sW, a.C + (pt.s - 1 - a.shift) * MM);   // W_s = C of the left separator row
+    }
+    __syncthreads();
 
     for (long long j = pt.s; j < pt.e; ++j) {
         const bool first = (j == pt.s);
-        const bool needB = !first || pt.hasL;
-        const bool needC = (MODE == 0) && ((j < pt.e - 1) || pt.hasR);
-        load_blk<T, M>(sD, a.D + (j - a.shift) * MM);
-        if (needB) load_blk<T, M>(sB, a.B + (j - a.shift) * MM);
-        if (needC) load_blk<T, M>(sC, a.C + (j - a.shift) * MM);
-        __syncthreads();
+        const bool nC = needC(j);
+        const bool more = (j + 1 < pt.e);
+        RowPrefetch<T, M> pf;
+        if (more)
+            pf.load(needB(j + 1) ? a.B + (j + 1 - a.shift) * MM : nullptr, a.D + (j + 1 - a.shift) * MM,
+                    needC(j + 1) ? a.C + (j + 1 - a.shift) * MM : nullptr);
         if (MODE == 0 && !first) {
             T acc[S::R];
+            bool done = false;
             if constexpr (std::is_same<T, float>::value && M >= 16) {
                 if (a.bf16) {
                     gemm_bf16_tc<M>(sT, sB, sY);
@@ -257,32 +310,32 @@ __device__ __forceinline__ void factor_cta_body(const LevelArgs& a, const long l
                     read_own<T, M>(pr, sT, o);
 #pragma unroll
                     for (int u = 0; u < S::R; ++u) acc[u] -= pr[u];
-                    write_own<T, M>(sD, acc, o);
-                    __syncthreads();
+                    done = true;
                 }
             }
-            if (!a.bf16 || !(std::is_same<T, float>::value && M >= 16)) {
+            if (!done) {
                 read_own<T, M>(acc, sD, o);
                 gemm_acc<T, M, true>(acc, sB, sY, o);
-                write_own<T, M>(sD, acc, o);
-                __syncthreads();
             }
+            // the left-spike product t = B_j Zc_{j-1} does not need D'_j: take it here
+            if (pt.hasL) {
+                T t[S::R];
+                zero_own<T, M>(t);
+                gemm_acc<T, M, false>(t, sB, sZ, o);
+                __syncthreads();
+                write_own<T, M>(sT, t, o);
+            }
+            write_own<T, M>(sD, acc, o);
+            __syncthreads();
         }
         gj_inverse<T, M>(sD, colk, perm, a.status, a.level, i, j);
         store_blk<T, M>(gDinv + j * MM, sD);
         T z[S::R], y[S::R];
         if (pt.hasL) {
-            if (!first) {
-                T t[S::R];
-                zero_own<T, M>(t);
-                gemm_acc<T, M, false>(t, sB, sZ, o);
-                write_own<T, M>(sT, t, o);
-                __syncthreads();
-            }
             zero_own<T, M>(z);
             gemm_acc<T, M, true>(z, sD, first ? sB : sT, o);
         }
-        if (needC) {
+        if (nC) {
             zero_own<T, M>(y);
             gemm_acc<T, M, false>(y, sD, sC, o);
         }
@@ -291,41 +344,28 @@ __device__ __forceinline__ void factor_cta_body(const LevelArgs& a, const long l
             write_own<T, M>(sZ, z, o);
             store_own<T, M>(gZ + j * MM, z, o);
         }
-        if (needC) {
+        if (nC) {
             write_own<T, M>(sY, y, o);
             store_own<T, M>(gY + j * MM, y, o);
         }
+        __syncthreads();
+        if (wchain) {
+            // cp += W_j Zc_j ;  W_{j+1} = -W_j Y_j
+            gemm_acc<T, M, false>(cp, sW, sZ, o);
+            T wn[S::R];
+            zero_own<T, M>(wn);
+            if (nC) gemm_acc<T, M, true>(wn, sW, sY, o);
+            __syncthreads();
+            write_own<T, M>(sW, wn, o);
+        }
+        if (more) pf.store(sB, sD, sC, needB(j + 1), needC(j + 1));
         __syncthreads();
     }
 
     if (MODE == 0) {
         if (!pt.hasL) return;
-        // backward sweep to the top row: P in sZ, Q in sY
-        {
-            T q[S::R];
-            read_own<T, M>(q, sY, o);
-#pragma unroll
-            for (int u = 0; u < S::R; ++u) q[u] = pt.hasR ? -q[u] : T(0);
-            __syncthreads();
-            write_own<T, M>(sY, q, o);
-            __syncthreads();
-        }
-        for (long long j = pt.e - 2; j >= pt.s; --j) {
-            load_blkT<T, M>(sC, gY + j * MM);
-            load_blkT<T, M>(sB, gZ + j * MM);
-            __syncthreads();
-            T pn[S::R], qn[S::R];
-            read_own<T, M>(pn, sB, o);
-            gemm_acc<T, M, true>(pn, sC, sZ, o);
-            zero_own<T, M>(qn);
-            gemm_acc<T, M, true>(qn, sC, sY, o);
-            __syncthreads();
-            write_own<T, M>(sZ, pn, o);
-            write_own<T, M>(sY, qn, o);
-            __syncthreads();
-        }
-        store_blk<T, M>(reinterpret_cast<T*>(a.Pf) + i * MM, sZ);
-        store_blk<T, M>(reinterpret_cast<T*>(a.Qf) + i * MM, sY);
+        store_own<T, M>(reinterpret_cast<T*>(a.Pf) + i * MM, cp, o);
+        store_blk<T, M>(reinterpret_cast<T*>(a.Qf) + i * MM, sW);   // W_e (zero when there is no x_R)
     } else {
         // BABD: reduced row i+1 couples separator e to the left separator
         const long long e = pt.e;
@@ -349,16 +389,15 @@ __device__ __forceinline__ void factor_cta_body(const LevelArgs& a, const long l
 // Block tridiagonal: the reduced row of separator s (the last row e of
 // partition s) in FP64:
 //   alpha = D_e - B_e Y_{e-1} + C_e P^(s+1)_first,  beta = B_e Zc_{e-1} (s > 0),
-//   gamma = C_e Q^(s+1)_first (s+1 < p-1).
+//   gamma = C_e Q^(s+1)_first (s+1 < p-1),
+// where the factor kernel left C_e P_first and C_e Q_first of partition s+1 in
+// Pf and Qf.
 template <typename T, int M>
 __device__ __forceinline__ void assemble_cta_body(const LevelArgs& a, const long long s, unsigned char* smem_raw) {
     using S = Cta<double, M>;
     double* sB = reinterpret_cast<double*>(smem_raw);
-    double* sC = sB + S::BLK;
-    double* sY = sC + S::BLK;
+    double* sY = sB + S::BLK;
     double* sZ = sY + S::BLK;
-    double* sP = sZ + S::BLK;
-    double* sQ = sP + S::BLK;
     const Part pt = part_bounds(0, a.N, a.p, a.base, a.extra, s);
     const long long e = pt.e;
     const long long MM = S::MM;
@@ -366,33 +405,28 @@ __device__ __forceinline__ void assemble_cta_body(const LevelArgs& a, const long
     const bool hasBeta = s > 0;
     const bool hasGamma = (s + 1) < a.p - 1;
     load_blk<double, M>(sB, a.B + (e - a.shift) * MM);
-    load_blk<double, M>(sC, a.C + (e - a.shift) * MM);
     {
         const T* gY = reinterpret_cast<const T*>(a.Y) + (e - 1) * MM;
         for (int idx = threadIdx.x; idx < M * M; idx += S::NT) sY[(idx / M) * S::LD + idx % M] = (double)gY[idx];
-        const T* gP = reinterpret_cast<const T*>(a.Pf) + (s + 1) * MM;
-        for (int idx = threadIdx.x; idx < M * M; idx += S::NT) sP[(idx / M) * S::LD + idx % M] = (double)gP[idx];
         if (hasBeta) {
             const T* gZ = reinterpret_cast<const T*>(a.Zc) + (e - 1) * MM;
             for (int idx = threadIdx.x; idx < M * M; idx += S::NT) sZ[(idx / M) * S::LD + idx % M] = (double)gZ[idx];
         }
-        if (hasGamma) {
-            const T* gQ = reinterpret_cast<const T*>(a.Qf) + (s + 1) * MM;
-            for (int idx = threadIdx.x; idx < M * M; idx += S::NT) sQ[(idx / M) * S::LD + idx % M] = (double)gQ[idx];
-        }
     }
     __syncthreads();
-    double al[S::R];
+    const T* gP = reinterpret_cast<const T*>(a.Pf) + (s + 1) * MM;
+    const T* gQ = reinterpret_cast<const T*>(a.Qf) + (s + 1) * MM;
+    double al[S::R], be[S::R], ga[S::R];
 #pragma unroll
-    for (int q = 0; q < S::R; ++q) al[q] = a.D[(e - a.shift) * MM + (o.r0 + q) * M + o.c];
+    for (int q = 0; q < S::R; ++q) {
+        const long long at = (o.r0 + q) * M + o.c;
+        al[q] = a.D[(e - a.shift) * MM + at] + (double)gP[at];
+        ga[q] = hasGamma ? (double)gQ[at] : 0.0;
+        be[q] = 0.0;
+    }
     gemm_acc<double, M, true>(al, sB, sY, o);
-    gemm_acc<double, M, false>(al, sC, sP, o);
-    store_own<double, M>(a.Dn + s * MM, al, o);
-    double be[S::R], ga[S::R];
-    zero_own<double, M>(be);
-    zero_own<double, M>(ga);
     if (hasBeta) gemm_acc<double, M, false>(be, sB, sZ, o);
-    if (hasGamma) gemm_acc<double, M, false>(ga, sC, sQ, o);
+    store_own<double, M>(a.Dn + s * MM, al, o);
     store_own<double, M>(a.Bn + s * MM, be, o);
     store_own<double, M>(a.Cn + s * MM, ga, o);
 }
@@ -646,7 +680,7 @@ constexpr size_t solve_smem_bytes() {
 }
 template <int M>
 constexpr size_t assemble_smem_bytes() {
-    return sizeof(double) * (6 * Cta<double, M>::BLK);
+    return sizeof(double) * (3 * Cta<double, M>::BLK);
 }
 template <int M>
 constexpr size_t assemble_rhs_smem_bytes() {

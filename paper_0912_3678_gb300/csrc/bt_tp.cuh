@@ -109,9 +109,11 @@ __device__ __forceinline__ void factor_tp_body(const LevelArgs& a, const long lo
     T* gDinv = reinterpret_cast<T*>(a.Dinv);
     T* gY = reinterpret_cast<T*>(a.Y);
     T* gZ = reinterpret_cast<T*>(a.Zc);
-    T Yp[MM], Zp[MM];
+    const bool wchain = (MODE == 0) && pt.hasL;
+    T Yp[MM], Zp[MM], W[MM], CP[MM];
 #pragma unroll
-    for (int u = 0; u < MM; ++u) Yp[u] = Zp[u] = T(0);
+    for (int u = 0; u < MM; ++u) Yp[u] = Zp[u] = W[u] = CP[u] = T(0);
+    if (wchain) rld<T, M>(W, a.C + (pt.s - 1 - a.shift) * MM);   // W_s = C of the left separator row
     for (long long j = pt.s; j < pt.e; ++j) {
         const bool first = (j == pt.s);
         const bool needB = !first || pt.hasL;
@@ -138,26 +140,21 @@ __device__ __forceinline__ void factor_tp_body(const LevelArgs& a, const long lo
             rmm<T, M, false, false>(Yp, Dp, Cj);
             rst<T, M>(gY + j * MM, Yp);
         }
+        if (wchain) {
+            // CP += W_j Zc_j ;  W_{j+1} = -W_j Y_j  (zero after the last row without x_R)
+            rmm<T, M, false, true>(CP, W, Zp);
+            if (needC) {
+                rmm<T, M, true, false>(W, W, Yp);
+            } else {
+#pragma unroll
+                for (int u = 0; u < MM; ++u) W[u] = T(0);
+            }
+        }
     }
     if (MODE == 0) {
         if (!pt.hasL) return;
-        T P[MM], Q[MM];
-#pragma unroll
-        for (int u = 0; u < MM; ++u) {
-            P[u] = Zp[u];
-            Q[u] = pt.hasR ? -Yp[u] : T(0);
-        }
-        for (long long j = pt.e - 2; j >= pt.s; --j) {
-            T Yj[MM], Zj[MM];
-            rld<T, M>(Yj, gY + j * MM);
-            rld<T, M>(Zj, gZ + j * MM);
-            rmm<T, M, true, true>(Zj, Yj, P);
-            rmm<T, M, true, false>(Q, Yj, Q);
-#pragma unroll
-            for (int u = 0; u < MM; ++u) P[u] = Zj[u];
-        }
-        rst<T, M>(reinterpret_cast<T*>(a.Pf) + i * MM, P);
-        rst<T, M>(reinterpret_cast<T*>(a.Qf) + i * MM, Q);
+        rst<T, M>(reinterpret_cast<T*>(a.Pf) + i * MM, CP);
+        rst<T, M>(reinterpret_cast<T*>(a.Qf) + i * MM, W);
     } else {
         const long long e = pt.e;
         T Be[MM];
@@ -183,14 +180,14 @@ __device__ __forceinline__ void assemble_tp_body(const LevelArgs& a, const long 
     if (s >= a.p - 1) return;
     const Part pt = part_bounds(0, a.N, a.p, a.base, a.extra, s);
     const long long e = pt.e;
-    double Be[MM], Ce[MM], al[MM], Yl[MM], Pf[MM];
+    double Be[MM], al[MM], Yl[MM], Pf[MM];
     rld<double, M>(Be, a.B + (e - a.shift) * MM);
-    rld<double, M>(Ce, a.C + (e - a.shift) * MM);
     rld<double, M>(al, a.D + (e - a.shift) * MM);
     rld<double, M>(Yl, reinterpret_cast<const T*>(a.Y) + (e - 1) * MM);
     rld<double, M>(Pf, reinterpret_cast<const T*>(a.Pf) + (s + 1) * MM);
     rmm<double, M, true, true>(al, Be, Yl);
-    rmm<double, M, false, true>(al, Ce, Pf);
+#pragma unroll
+    for (int u = 0; u < MM; ++u) al[u] += Pf[u];
     rst<double, M>(a.Dn + s * MM, al);
     double be[MM], ga[MM];
 #pragma unroll
@@ -200,11 +197,7 @@ __device__ __forceinline__ void assemble_tp_body(const LevelArgs& a, const long 
         rld<double, M>(Zl, reinterpret_cast<const T*>(a.Zc) + (e - 1) * MM);
         rmm<double, M, false, false>(be, Be, Zl);
     }
-    if (s + 1 < a.p - 1) {
-        double Qf[MM];
-        rld<double, M>(Qf, reinterpret_cast<const T*>(a.Qf) + (s + 1) * MM);
-        rmm<double, M, false, false>(ga, Ce, Qf);
-    }
+    if (s + 1 < a.p - 1) rld<double, M>(ga, reinterpret_cast<const T*>(a.Qf) + (s + 1) * MM);
     rst<double, M>(a.Bn + s * MM, be);
     rst<double, M>(a.Cn + s * MM, ga);
 }

@@ -72,17 +72,20 @@ class Request:
 
 
 def build_bvp_device(spec: BvpSpec, N: int, device, stream=None):
-    """(S_j, R_j, B0, B1) of the trapezoidal rule on t_j = j/N, on the device."""
+    """(S_j, R_j, B0, B1) of the trapezoidal rule on t_j = j/N, on the device,
+    built in place (no L(t) array): S_j = -(I + h/2 L(t_j)), R_j = I - h/2 L(t_{j+1})."""
     m = spec.S.shape[0]
     h = 1.0 / N
     with torch.cuda.stream(stream) if stream is not None else _nullctx():
-        Sm = torch.as_tensor(spec.S, dtype=torch.float64, device=device)
+        S0 = torch.as_tensor(spec.S, dtype=torch.float64, device=device)
         K = torch.as_tensor(spec.K, dtype=torch.float64, device=device)
-        t = torch.arange(N + 1, dtype=torch.float64, device=device) * h
-        L = Sm.unsqueeze(0) + torch.cos(2 * math.pi * t).view(-1, 1, 1) * K.unsqueeze(0)
         eye = torch.eye(m, dtype=torch.float64, device=device)
-        Smat = -(eye + 0.5 * h * L[:-1])
-        Rmat = eye - 0.5 * h * L[1:]
+        t = torch.arange(N + 1, dtype=torch.float64, device=device) * h
+        c = torch.cos(2 * math.pi * t).view(-1, 1, 1)
+        Smat = c[:-1] * K.unsqueeze(0)                      # cos(2 pi t_j) K
+        Smat.add_(S0).mul_(-0.5 * h).sub_(eye)
+        Rmat = c[1:] * K.unsqueeze(0)
+        Rmat.add_(S0).mul_(-0.5 * h).add_(eye)
         B0 = torch.as_tensor(spec.B0, dtype=torch.float64, device=device)
         B1 = torch.as_tensor(spec.B1, dtype=torch.float64, device=device)
         return Smat.contiguous(), Rmat.contiguous(), B0.contiguous(), B1.contiguous()
@@ -94,21 +97,22 @@ def build_rhs_device(spec: BvpSpec, N: int, V, device, stream=None):
     m = spec.S.shape[0]
     h = 1.0 / N
     with torch.cuda.stream(stream) if stream is not None else _nullctx():
-        Sm = torch.as_tensor(spec.S, dtype=torch.float64, device=device)
+        S0 = torch.as_tensor(spec.S, dtype=torch.float64, device=device)
         K = torch.as_tensor(spec.K, dtype=torch.float64, device=device)
         Vd = torch.as_tensor(V, dtype=torch.float64, device=device)
         t = torch.arange(N + 1, dtype=torch.float64, device=device) * h
-        L = Sm.unsqueeze(0) + torch.cos(2 * math.pi * t).view(-1, 1, 1) * K.unsqueeze(0)
         e = torch.exp(torch.sin(3 * t)).view(-1, 1, 1)
-        y = e * Vd.unsqueeze(0)
-        dy = (3 * torch.cos(3 * t) * torch.exp(torch.sin(3 * t))).view(-1, 1, 1) * Vd.unsqueeze(0)
-        q = dy - torch.bmm(L, y)
-        r = 0.5 * h * (q[:-1] + q[1:])
+        SV, KV = S0 @ Vd, K @ Vd                                   # L(t) y = e (S0 v + cos K v)
+        q = (3 * torch.cos(3 * t)).view(-1, 1, 1) * Vd.unsqueeze(0)
+        q.sub_(SV.unsqueeze(0)).sub_(torch.cos(2 * math.pi * t).view(-1, 1, 1) * KV.unsqueeze(0)).mul_(e)
+        r = (q[:-1] + q[1:]).mul_(0.5 * h)
         B0 = torch.as_tensor(spec.B0, dtype=torch.float64, device=device)
         B1 = torch.as_tensor(spec.B1, dtype=torch.float64, device=device)
-        beta = B0 @ y[0] + B1 @ y[N]
+        y0, yN = Vd, math.exp(math.sin(3.0)) * Vd
+        beta = B0 @ y0 + B1 @ yN
         rhs = torch.cat([beta.unsqueeze(0), r], dim=0).reshape((N + 1) * m, -1).contiguous()
-        return rhs, y.reshape((N + 1) * m, -1)
+        yex = (e * Vd.unsqueeze(0)).reshape((N + 1) * m, -1)
+        return rhs, yex
 
 
 class _nullctx:
@@ -160,7 +164,9 @@ class Server:
         self.in_use = 0              # bytes of running requests + cached factors
         self.t0 = None
         self._next_stream = 0
-        self.max_inflight = max_inflight if max_inflight > 0 else 4 * streams
+        self.max_inflight = max_inflight if max_inflight > 0 else 2 * streams
+        total = torch.cuda.get_device_properties(self.device).total_memory
+        self.cap = min(self.cap, int(0.7 * total))      # headroom for the caching allocator
         self.peak_in_use = 0
         _lib.load()
 
@@ -175,7 +181,7 @@ class Server:
         m, N = r.m, r.N
         ws = bt_plan_workspace_size(1, N, m, nrhs_max, r.prec)
         mats = 2 * N * m * m * 8 + 2 * m * m * 8
-        vecs = 2 * (N + 1) * m * r.nrhs * 8 + (N + 1) * m * m * 8 * 2   # rhs, solution, build temporaries
+        vecs = 6 * (N + 1) * m * r.nrhs * 8 + (N + 1) * m * m * 8   # rhs, solution, exact, build temporaries
         return ws, mats, vecs
 
     def _evict_for(self, need):

@@ -39,7 +39,7 @@ def _check(host, systems, status, specs):
 def test_batch_mixed_matches_oracle(cuda):
     import paper_0912_3678_gb300 as bt
     systems, host = _systems(cuda, SPECS)
-    with bt.BtBatch(systems, ir_sweeps=3) as b:
+    with bt.BtBatch(systems, ir_sweeps=5) as b:
         waves, nodes, nbytes = b.info()
         assert waves == 1 and nodes > 0
         b.run()
@@ -51,7 +51,7 @@ def test_batch_mixed_matches_oracle(cuda):
 def test_batch_waves_under_memory_cap(cuda):
     import paper_0912_3678_gb300 as bt
     systems, host = _systems(cuda, SPECS, seed=1)
-    with bt.BtBatch(systems, ir_sweeps=3, mem_cap_bytes=6 << 20) as b:
+    with bt.BtBatch(systems, ir_sweeps=5, mem_cap_bytes=6 << 20) as b:
         waves, _, _ = b.info()
         assert waves >= 2
         b.run()
@@ -63,7 +63,7 @@ def test_batch_rerun_with_new_right_hand_sides(cuda):
     import paper_0912_3678_gb300 as bt
     specs = SPECS[:6]
     systems, host = _systems(cuda, specs, seed=2)
-    with bt.BtBatch(systems, ir_sweeps=3) as b:
+    with bt.BtBatch(systems, ir_sweeps=5) as b:
         b.run()
         b.finish()
         rng = np.random.default_rng(5)
