@@ -283,8 +283,11 @@ def main():
     ap.add_argument("--serve-prec", default="fp64")
     ap.add_argument("--paths", default="fp64,fp32_ir")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="use the built-in partitioning instead of the autotuner")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.workload == "serve":
+        os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
@@ -332,8 +335,17 @@ def main():
 
     results = {}
     paths = [p for p in args.paths.split(",") if p]
+    tunings = {}
+    if w["kind"] == "btri" and not args.no_tune:
+        from paper_0912_3678_gb300 import tune
+        tuner = tune.Tuner(os.path.join(ROOT, "paper_0912_3678_gb300", "_build", "tune_cache.json"))
+        for prec in paths:
+            tunings[prec] = tuner.tune(m, N, prec, nrhs=nr, reps=5)
     for prec in paths:
-        plan = Plan(N, m, nrhs_max=nr, prec=prec)
+        if prec in tunings:
+            plan = bt.BtPlan.tuned(N, m, nrhs_max=nr, prec=prec, tuning=tunings[prec])
+        else:
+            plan = Plan(N, m, nrhs_max=nr, prec=prec)
 
         def step():
             plan.factor(*mats)
@@ -491,7 +503,8 @@ def main():
         "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f32+f64",
         "data": "synthetic",
         "config": {"workload": w["desc"], "path": head, "l2": "flushed (256 MB write) between timed steps",
-                   "parallelism": f"replicas x{ws}", "levels": r["levels"]},
+                   "parallelism": f"replicas x{ws}", "levels": r["levels"],
+                   "tuning": tunings.get(head, "built-in")},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": ws * w["unknowns"] / (r["e2e_ms"] / 1e3), "unit": UNIT, "h2d_bytes_per_step": r["h2d"],

@@ -298,24 +298,26 @@ __device__ __forceinline__ void factor_cta_body(const LevelArgs& a, const long l
         if (more)
             pf.load(needB(j + 1) ? a.B + (j + 1 - a.shift) * MM : nullptr, a.D + (j + 1 - a.shift) * MM,
                     needC(j + 1) ? a.C + (j + 1 - a.shift) * MM : nullptr);
-        if (MODE == 0 && !first) {
+        if (!first) {
             T acc[S::R];
-            bool done = false;
-            if constexpr (std::is_same<T, float>::value && M >= 16) {
-                if (a.bf16) {
-                    gemm_bf16_tc<M>(sT, sB, sY);
-                    __syncthreads();
-                    T pr[S::R];
-                    read_own<T, M>(acc, sD, o);
-                    read_own<T, M>(pr, sT, o);
+            if (MODE == 0) {
+                bool done = false;
+                if constexpr (std::is_same<T, float>::value && M >= 16) {
+                    if (a.bf16) {
+                        gemm_bf16_tc<M>(sT, sB, sY);
+                        __syncthreads();
+                        T pr[S::R];
+                        read_own<T, M>(acc, sD, o);
+                        read_own<T, M>(pr, sT, o);
 #pragma unroll
-                    for (int u = 0; u < S::R; ++u) acc[u] -= pr[u];
-                    done = true;
+                        for (int u = 0; u < S::R; ++u) acc[u] -= pr[u];
+                        done = true;
+                    }
                 }
-            }
-            if (!done) {
-                read_own<T, M>(acc, sD, o);
-                gemm_acc<T, M, true>(acc, sB, sY, o);
+                if (!done) {
+                    read_own<T, M>(acc, sD, o);
+                    gemm_acc<T, M, true>(acc, sB, sY, o);
+                }
             }
             // the left-spike product t = B_j Zc_{j-1} does not need D'_j: take it here
             if (pt.hasL) {
@@ -325,7 +327,7 @@ __device__ __forceinline__ void factor_cta_body(const LevelArgs& a, const long l
                 __syncthreads();
                 write_own<T, M>(sT, t, o);
             }
-            write_own<T, M>(sD, acc, o);
+            if (MODE == 0) write_own<T, M>(sD, acc, o);
             __syncthreads();
         }
         gj_inverse<T, M>(sD, colk, perm, a.status, a.level, i, j);

@@ -149,7 +149,8 @@ class _Factor:
 
 class Server:
     def __init__(self, device=None, mem_cap_bytes: float = 150e9, streams: int = 8, sweeps: int = 3,
-                 tol: float = 1e-12, cache: bool = True, check_exact: bool = False, max_inflight: int = 0):
+                 tol: float = 1e-12, cache: bool = True, check_exact: bool = False, max_inflight: int = 0,
+                 keep_results: bool = True):
         self.device = torch.device(device or "cuda")
         self.cap = int(mem_cap_bytes)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
@@ -165,6 +166,7 @@ class Server:
         self.t0 = None
         self._next_stream = 0
         self.max_inflight = max_inflight if max_inflight > 0 else 2 * streams
+        self.keep_results = keep_results
         total = torch.cuda.get_device_properties(self.device).total_memory
         self.cap = min(self.cap, int(0.7 * total))      # headroom for the caching allocator
         self.peak_in_use = 0
@@ -268,6 +270,8 @@ class Server:
                     r.status, r.relcorr = bt_refine_result(f.plan, self.tol)
                 if self.check_exact and torch.is_tensor(r.Yexact_err):
                     r.Yexact_err = float(r.Yexact_err)
+                if not self.keep_results:
+                    r.Y = None
                 f.busy -= 1
                 self.in_use -= vec_b
                 if self.cache.get(f.key) is not f:
@@ -300,8 +304,10 @@ class Server:
         self.cache.clear()
 
     # -------------------------------------------------------------- trace --
-    def run_trace(self, requests, realtime: bool = True, timeout_s: float = 900.0):
-        """Replay requests at their arrival times (or all at once)."""
+    def run_trace(self, requests, realtime: bool = True, timeout_s: float = 900.0, keep_results: bool = False):
+        """Replay requests at their arrival times (or all at once).  Solutions
+        are dropped at retirement unless keep_results."""
+        self.keep_results = keep_results
         self.start()
         pending = sorted(requests, key=lambda r: r.arrival)
         k = 0
