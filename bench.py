@@ -340,7 +340,7 @@ def main():
         from paper_0912_3678_gb300 import tune
         tuner = tune.Tuner(os.path.join(ROOT, "paper_0912_3678_gb300", "_build", "tune_cache.json"))
         for prec in paths:
-            tunings[prec] = tuner.tune(m, N, prec, nrhs=nr, reps=5)
+            tunings[prec] = tuner.tune(m, N, prec, nrhs=nr)
     for prec in paths:
         if prec in tunings:
             plan = bt.BtPlan.tuned(N, m, nrhs_max=nr, prec=prec, tuning=tunings[prec])
