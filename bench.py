@@ -311,6 +311,7 @@ def main():
     if dist is not None:
         dist.barrier()
     import paper_0912_3678_gb300 as bt
+    from paper_0912_3678_gb300 import dist as bdist
 
     w = _workload(args.workload)
     s = w["sys"]
@@ -397,10 +398,7 @@ def main():
         f0_ms, f0_n = plan.trace_query("factor", 0)
         r_ms, r_n = plan.trace_query("residual", 0)
         plan.trace(False)
-        ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        if dist is not None:
-            dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        ms_max = float(ms_t.item())
+        ms_max = bdist.max_over_ranks(ms, dev)
         Xh = X.cpu().numpy().copy()
         results[prec] = dict(ms=ms_max, ms_steps=ms_steps, kinds=kinds, f0=(f0_ms, f0_n), resid=(r_ms, r_n),
                              launches=launches / args.steps, X=Xh, clocks=_clocks_summary(rows, local),
@@ -425,10 +423,7 @@ def main():
             if it >= args.warmup:
                 e2e.append(e0.elapsed_time(e1))
         e2e_ms = sum(e2e) / len(e2e)
-        e2t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        if dist is not None:
-            dist.all_reduce(e2t, op=dist.ReduceOp.MAX)
-        results[prec]["e2e_ms"] = float(e2t.item())
+        results[prec]["e2e_ms"] = bdist.max_over_ranks(e2e_ms, dev)
         results[prec]["h2d"] = sum(int(a.nbytes) for a in mats_h) + int(rhs_h.nbytes)
         results[prec]["d2h"] = int(rhs_h.nbytes)
         plan.close()

@@ -33,9 +33,10 @@ def test_babd_fp64_matches_oracle(cuda, m, N, nrhs, sep):
     assert oracle.rel_err(Y, ref) <= 1e-11, lev
 
 
+@pytest.mark.parametrize("m", [4, 8, 16])
 @pytest.mark.parametrize("p", [1, 2, 3, 10, 49])
-def test_babd_invariant_under_p(cuda, p):
-    b = gen.babd_random(100, 4, 2, seed_rep=1)
+def test_babd_invariant_under_p(cuda, p, m):
+    b = gen.babd_random(100, m, 2, seed_rep=1)
     Y, _ = _solve(cuda, b, p=p)
     ref = oracle.babd_solve(b.S, b.R, b.B0, b.B1, b.RHS)
     assert oracle.rel_err(Y, ref) <= 1e-11

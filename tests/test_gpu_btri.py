@@ -205,3 +205,39 @@ def test_invalid_arguments(cuda):
         F = to_dev(np.zeros((40, 1)), cuda)
         with pytest.raises(bt.BtError):
             plan.solve(F)          # not factored
+
+
+def test_plan_on_caller_workspace_and_async_refine(cuda):
+    """bt_plan_create_in builds the plan in caller memory (no allocation);
+    bt_refine_async + bt_refine_result give the same answer as bt_refine."""
+    import torch
+    import paper_0912_3678_gb300 as bt
+    N, m, nr = 900, 8, 3
+    s = gen.btri_random(N, m, nr, seed_rep=21)
+    ref = oracle.btri_solve(s.B, s.D, s.C, s.F)
+    B, D, C, F = (to_dev(a, cuda) for a in (s.B, s.D, s.C, s.F))
+    need = bt.bt_plan_workspace_size(0, N, m, nr, "fp32_ir")
+    ws = torch.empty(need + 256, dtype=torch.uint8, device=cuda)
+    base = ws.data_ptr() + ((-ws.data_ptr()) % 256)
+    with pytest.raises(bt.BtError):
+        bt.bt_plan_create_in(0, N, m, nr, "fp32_ir", base, need - 1024)
+    plan = bt.bt_plan_create_in(0, N, m, nr, "fp32_ir", base, need)
+    try:
+        bt.bt_factor(plan, B, D, C)
+        X = torch.empty_like(F)
+        bt.bt_refine_async(plan, F, X, nr, 3)
+        code, rel = bt.bt_refine_result(plan, 1e-12)
+        assert code == 0 and rel <= 1e-12
+        assert oracle.rel_err(to_host(X), ref) <= TOLIR
+    finally:
+        bt.bt_plan_destroy(plan)
+    del ws
+
+
+@pytest.mark.parametrize("m", [1, 32])
+def test_largest_rhs_count(cuda, m):
+    """nrhs = 32 (the maximum) with ragged sizes."""
+    N = 1000 if m == 1 else 45
+    s = gen.btri_random(N, m, 32, seed_rep=77)
+    X, _ = _solve(cuda, s)
+    assert oracle.rel_err(X, oracle.btri_solve(s.B, s.D, s.C, s.F)) <= TOL64
