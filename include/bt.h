@@ -144,6 +144,17 @@ bt_status bt_plan_workspace_size(int kind, int64_t n, int m, int nrhs_max, int p
 bt_status bt_plan_create_in(bt_plan* plan, int kind, int64_t n, int m, int nrhs_max, int prec,
                             const bt_tuning* tuning, void* workspace, int64_t bytes, void* stream);
 
+/* Capture one call sequence of the plan into a CUDA graph held by the plan,
+ * so that later runs are one graph launch (no per-kernel launch gaps):
+ *   what = 1: factor (matrices of the last bt_factor/abd_factor) + solve(F -> X)
+ *   what = 2: solve(F -> X) with the current factors
+ *   what = 3: factor + bt_refine_async(F -> X, sweeps)
+ * The pointers are bound into the graph; bt_plan_replay re-runs it on the
+ * plan's stream (new values in the same arrays are picked up).  Capture
+ * synchronises the stream and replaces any earlier graph of the plan. */
+bt_status bt_plan_capture(bt_plan plan, int what, const double* F, double* X, int nrhs, int sweeps);
+bt_status bt_plan_replay(bt_plan plan);
+
 /* Wait for the plan's stream; return the recorded numerical status. */
 bt_status bt_sync(bt_plan plan);
 

@@ -20,7 +20,7 @@ __all__ = ["BtPlan", "AbdPlan", "BtError", "BT_STATUS", "PREC", "load_library",
            "KERNEL_KINDS", "bt_solve_noalloc", "BT_NOALLOC_SCRATCH_BYTES", "bt_plan_create_tuned",
            "bt_batch_create", "bt_batch_run", "bt_batch_finish", "bt_batch_info", "bt_batch_destroy",
            "BtBatch", "BtTuning", "BtBatchDesc", "bt_refine_async", "bt_refine_result",
-           "bt_plan_workspace_size", "bt_plan_create_in", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
+           "bt_plan_workspace_size", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
            "abd_plan_create", "abd_factor", "abd_solve", "abd_residual", "abd_refine", "abd_sync",
            "abd_plan_destroy"]
 
@@ -199,6 +199,18 @@ def _ptr_any(t):
     return t if isinstance(t, int) else t.data_ptr()
 
 
+CAPTURE = {"factor_solve": 1, "solve": 2, "factor_refine": 3}
+
+
+def bt_plan_capture(plan, what, F, X, nrhs, sweeps=0):
+    w = CAPTURE[what] if isinstance(what, str) else int(what)
+    _lib.check(_lib.load().bt_plan_capture(plan, w, _ptr(F), _ptr(X), int(nrhs), int(sweeps)), "bt_plan_capture")
+
+
+def bt_plan_replay(plan):
+    _lib.check(_lib.load().bt_plan_replay(plan), "bt_plan_replay")
+
+
 def bt_sync(plan) -> int:
     return _lib.load().bt_sync(plan)
 
@@ -340,6 +352,13 @@ class _PlanBase:
 
     def launches(self):
         return bt_plan_launches(self.handle)
+
+    def capture(self, what, F, X, sweeps=0):
+        """Record factor/solve (see bt_plan_capture) into a CUDA graph; replay() re-runs it."""
+        bt_plan_capture(self.handle, what, F, X, self._nrhs(F), sweeps)
+
+    def replay(self):
+        bt_plan_replay(self.handle)
 
 
 class BtPlan(_PlanBase):

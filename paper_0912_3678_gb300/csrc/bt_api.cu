@@ -57,6 +57,10 @@ struct bt_plan_s {
     double* B0 = nullptr;               // BABD boundary blocks (copies)
     double* B1 = nullptr;
     double* keep = nullptr;             // BABD top-level pivot rows
+    // captured call sequence
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    long long graph_launches = 0;
     // tracing
     bool trace = false;
     struct Rec { int key; cudaEvent_t a, b; };
@@ -542,6 +546,66 @@ bt_status bt_plan_create_in(bt_plan* plan, int kind, int64_t n, int m, int nrhs_
     return plan_create(plan, kind, n, m, nrhs_max, prec, to_tuning(tuning, 0), stream, workspace, bytes, nullptr);
 }
 
+bt_status bt_plan_capture(bt_plan P, int what, const double* F, double* X, int nrhs, int sweeps) {
+    if (!P || what < 1 || what > 3) return BT_ERR_INVALID;
+    bt_status st = check_solve(P, P->kind, F, X, nrhs);
+    if (st != BT_OK) return st;
+    if (what == 3 && (sweeps < 0 || sweeps > 30)) return BT_ERR_INVALID;
+    if (P->graph_exec) {
+        cudaGraphExecDestroy(P->graph_exec);
+        P->graph_exec = nullptr;
+    }
+    if (P->graph) {
+        cudaGraphDestroy(P->graph);
+        P->graph = nullptr;
+    }
+    cudaError_t e = cudaStreamSynchronize(P->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    // kernels with large shared memory get their attribute before capture
+    e = P->L->prepare();
+    if (e != cudaSuccess) return from_cuda(e);
+    cudaStream_t saved = P->stream, cap = nullptr;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return from_cuda(e);
+    const bool saved_trace = P->trace;
+    const long long l0 = P->launches;
+    P->trace = false;
+    P->stream = cap;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        if (what != 2) {
+            e = cudaMemsetAsync(P->status, 0, 4 * sizeof(long long), cap);
+            if (e == cudaSuccess) st = run_factor(P);
+        }
+        if (e == cudaSuccess && st == BT_OK) {
+            if (what == 3) st = run_refine_async(P, F, X, nrhs, sweeps);
+            else st = run_solve(P, F, X, nrhs);
+        }
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (e == cudaSuccess) e = e2;
+        P->graph = g;
+        if (e == cudaSuccess && st == BT_OK) e = cudaGraphInstantiate(&P->graph_exec, g, 0);
+    }
+    P->stream = saved;
+    P->trace = saved_trace;
+    P->graph_launches = P->launches - l0;
+    P->launches = l0;
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return from_cuda(e);
+    }
+    if (st == BT_OK && what != 2) P->factored = true;
+    return st;
+}
+
+bt_status bt_plan_replay(bt_plan P) {
+    if (!P || !P->graph_exec) return BT_ERR_INVALID;
+    P->launches += P->graph_launches;
+    return from_cuda(cudaGraphLaunch(P->graph_exec, P->stream));
+}
+
 bt_status bt_sync(bt_plan P) {
     if (!P) return BT_ERR_INVALID;
     return read_status(P);
@@ -636,6 +700,8 @@ void bt_plan_destroy(bt_plan P) {
     if (!P) return;
     cudaStreamSynchronize(P->stream);
     for (auto ev : P->pool) cudaEventDestroy(ev);
+    if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
     if (P->own_arena) cudaFree(P->arena);
     if (P->pinned) {
         if (P->status_host) cudaFreeHost(P->status_host);

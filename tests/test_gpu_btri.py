@@ -241,3 +241,27 @@ def test_largest_rhs_count(cuda, m):
     s = gen.btri_random(N, m, 32, seed_rep=77)
     X, _ = _solve(cuda, s)
     assert oracle.rel_err(X, oracle.btri_solve(s.B, s.D, s.C, s.F)) <= TOL64
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_ir"])
+def test_captured_graph_replay(cuda, prec):
+    """bt_plan_capture/bt_plan_replay: the graph re-reads the bound arrays."""
+    import paper_0912_3678_gb300 as bt
+    N, m, nr = 700, 16, 2
+    s = gen.btri_random(N, m, nr, seed_rep=31)
+    B, D, C, F = (to_dev(a, cuda) for a in (s.B, s.D, s.C, s.F))
+    with bt.BtPlan(N, m, nr, prec=prec) as plan:
+        plan.factor(B, D, C)
+        X = plan.solve(F)
+        if prec == "fp64":
+            plan.capture("factor_solve", F, X)
+        else:
+            plan.capture("factor_refine", F, X, sweeps=3)
+        rng = np.random.default_rng(3)
+        for rep in range(2):
+            s.F = rng.standard_normal(s.F.shape)
+            F.copy_(to_dev(s.F, cuda))
+            plan.replay()
+            plan.sync()
+            ref = oracle.btri_solve(s.B, s.D, s.C, s.F)
+            assert oracle.rel_err(to_host(X), ref) <= (TOL64 if prec == "fp64" else TOLIR)
