@@ -86,12 +86,17 @@ bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int p
  *                512 for m <= 4, where a partition is one thread)
  *   sub_rows     block rows per partition on the recursion levels (>= 2, default 4)
  *   top_rows     a level with at most this many block rows is solved by one
- *                partition (block tridiagonal) or directly (BABD); default 8 */
+ *                partition (block tridiagonal) or directly (BABD); default 8
+ *   reduced      solver of the top-level reduced system of a block tridiagonal
+ *                plan with m >= 8: 0 = partitioned again recursively (default),
+ *                1 = block cyclic reduction (the cyclic-reduction variant of
+ *                Sec. 2 with one synchronisation per reduction step) */
 typedef struct {
     int64_t p0;
     int ctas_per_sm;
     int sub_rows;
     int top_rows;
+    int reduced;
 } bt_tuning;
 
 /* bt_plan_create with explicit partitioning parameters (NULL = defaults). */
@@ -188,7 +193,8 @@ bt_status bt_reduced_export(bt_plan plan, double* alpha, double* beta, double* g
  * summed event time in ms and the number of launches.  Kinds:
  * 0 local factor, 1 reduced-matrix assembly, 2 forward solve, 3 reduced
  * right-hand side, 4 back substitution, 5 top-level BABD direct solve,
- * 6 FP64 residual, 7 refinement update. */
+ * 6 FP64 residual, 7 refinement update, 8 cyclic-reduction factor steps,
+ * 9 cyclic-reduction solve steps. */
 bt_status bt_plan_trace(bt_plan plan, int enable);
 bt_status bt_plan_trace_query(bt_plan plan, int kind, int level, double* total_ms, int64_t* launches);
 

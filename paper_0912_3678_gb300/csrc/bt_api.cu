@@ -11,6 +11,7 @@
 #include "bt_level.h"
 #include "bt_misc.h"
 #include "bt_planner.h"
+#include "bt_bcr.cuh"
 
 namespace {
 
@@ -57,6 +58,8 @@ struct bt_plan_s {
     double* B0 = nullptr;               // BABD boundary blocks (copies)
     double* B1 = nullptr;
     double* keep = nullptr;             // BABD top-level pivot rows
+    bool bcr = false;                   // reduced system by block cyclic reduction
+    std::vector<bt::BcrArgs> bl;        // its levels
     // captured call sequence
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -114,7 +117,8 @@ void layout(bt_plan_s* P, Arena& ar) {
         Level& v = P->lv[l];
         const size_t ts = v.low ? sizeof(float) : sizeof(double);
         const bool top = (l == P->nlev);
-        if (!(top && P->kind == 1)) {
+        const bool holder = top && P->bcr;
+        if (!(top && P->kind == 1) && !holder) {
             v.a.Dinv = ar.take(ts * v.rows * mm);
             if (P->kind == 0) v.a.Y = ar.take(ts * v.rows * mm);
             v.a.Zc = ar.take(ts * v.rows * mm);
@@ -150,6 +154,35 @@ void layout(bt_plan_s* P, Arena& ar) {
             v.a.X = Xn;
         }
         if (top && P->kind == 1) P->keep = (double*)ar.take(sizeof(double) * v.a.N * m * (3 * m + nr) + 8);
+    }
+    if (P->bcr) {
+        Level& h = P->lv[P->nlev];
+        long long K = h.a.N;
+        for (size_t q = 0; q < P->bl.size(); ++q) {
+            bt::BcrArgs& b = P->bl[q];
+            b.K = K;
+            b.level = P->nlev + (int)q;
+            b.nr = nr;
+            const long long keep = (K + 1) / 2, odd = (K == 1) ? 1 : K / 2;
+            if (q == 0) {
+                b.B = h.a.B; b.D = h.a.D; b.C = h.a.C;
+                b.F = h.a.F; b.X = h.a.X;
+            }
+            b.Dinv = (double*)ar.take(sizeof(double) * odd * mm);
+            if (K > 1) {
+                b.al = (double*)ar.take(sizeof(double) * keep * mm);
+                b.ga = (double*)ar.take(sizeof(double) * keep * mm);
+                bt::BcrArgs& n = P->bl[q + 1];
+                b.Bn = (double*)ar.take(sizeof(double) * keep * mm);
+                b.Dn = (double*)ar.take(sizeof(double) * keep * mm);
+                b.Cn = (double*)ar.take(sizeof(double) * keep * mm);
+                b.Fn = (double*)ar.take(sizeof(double) * keep * m * nr);
+                double* Xn = (double*)ar.take(sizeof(double) * keep * m * nr);
+                b.Xn = Xn;
+                n.B = b.Bn; n.D = b.Dn; n.C = b.Cn; n.F = b.Fn; n.X = Xn;
+            }
+            K = keep;
+        }
     }
 }
 
@@ -195,6 +228,16 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
         P->lv.push_back(v);
     }
     P->nlev = (int)P->lv.size() - 1;
+    P->bcr = (kind == 0 && P->nlev >= 1 && P->lv[P->nlev].a.p == 0);
+    if (P->bcr) {
+        long long K = P->lv[P->nlev].a.N;
+        int n = 1;
+        while (K > 1) {
+            K = (K + 1) / 2;
+            ++n;
+        }
+        P->bl.assign(n, bt::BcrArgs{});
+    }
     if (kind == 0) {
         // the top level is a single partition; levels below it have >= 2
     }
@@ -228,6 +271,7 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
     real.base = P->arena;
     layout(P, real);
     for (auto& v : P->lv) v.a.status = P->status;
+    for (auto& b : P->bl) b.status = P->status;
     if (P->pinned) {
         e = cudaMallocHost((void**)&P->status_host, 4 * sizeof(long long));
         if (e == cudaSuccess) e = cudaMallocHost((void**)&P->norms_host, 2 * sizeof(double));
@@ -253,7 +297,8 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
     return BT_OK;
 }
 
-enum Kind { K_FACTOR = 0, K_ASSEMBLE, K_SOLVE_FWD, K_ASSEMBLE_RHS, K_SOLVE_BWD, K_DIRECT, K_RESID, K_IR };
+enum Kind { K_FACTOR = 0, K_ASSEMBLE, K_SOLVE_FWD, K_ASSEMBLE_RHS, K_SOLVE_BWD, K_DIRECT, K_RESID, K_IR, K_BCR_FACTOR,
+            K_BCR_SOLVE };
 
 cudaEvent_t take_event(bt_plan_s* P) {
     if (P->pool_used == P->pool.size()) {
@@ -298,6 +343,19 @@ bt_status run_factor(bt_plan_s* P) {
     for (int l = 0; l <= P->nlev; ++l) {
         Level& v = P->lv[l];
         if (P->kind == 1 && l == P->nlev) break;   // BABD top: direct solve at solve time
+        if (P->bcr && l == P->nlev) {
+            // block cyclic reduction of the reduced system
+            for (size_t q = 0; q < P->bl.size(); ++q) {
+                bt::BcrArgs& b = P->bl[q];
+                const long long odd = (b.K == 1) ? 1 : b.K / 2;
+                cudaError_t e = launch(P, K_BCR_FACTOR, b.level, 1, [&] { return L->bcr_inv(b, odd, P->stream); });
+                if (e == cudaSuccess && b.K > 1)
+                    e = launch(P, K_BCR_FACTOR, b.level, 1,
+                               [&] { return L->bcr_update(b, (b.K + 1) / 2, P->stream); });
+                if (e != cudaSuccess) return from_cuda(e);
+            }
+            break;
+        }
         cudaError_t e = launch(P, K_FACTOR, l, 1, [&] { return L->factor(v.a, v.low, P->stream); });
         if (e == cudaSuccess && P->kind == 0 && l < P->nlev)
             e = launch(P, K_ASSEMBLE, l, 1, [&] { return L->assemble(v.a, v.low, P->stream); });
@@ -322,7 +380,19 @@ bt_status run_solve(bt_plan_s* P, const double* F, double* X, int nr) {
     Level& t = P->lv[P->nlev];
     const int lt = P->nlev;
     cudaError_t e;
-    if (P->kind == 0) {
+    if (P->bcr) {
+        e = cudaSuccess;
+        for (size_t q = 0; q < P->bl.size() && e == cudaSuccess; ++q) {
+            bt::BcrArgs& b = P->bl[q];
+            b.nr = nr;
+            e = launch(P, K_BCR_SOLVE, b.level, 1,
+                       [&] { return L->bcr_rhs(b, b.K == 1 ? 1 : (b.K + 1) / 2, P->stream); });
+        }
+        for (int q = (int)P->bl.size() - 2; q >= 0 && e == cudaSuccess; --q) {
+            bt::BcrArgs& b = P->bl[q];
+            e = launch(P, K_BCR_SOLVE, b.level, 1, [&] { return L->bcr_back(b, (b.K + 1) / 2, P->stream); });
+        }
+    } else if (P->kind == 0) {
         e = launch(P, K_SOLVE_FWD, lt, 1, [&] { return L->solve_fwd(t.a, t.low, P->stream); });
         if (e == cudaSuccess) e = launch(P, K_SOLVE_BWD, lt, 1, [&] { return L->solve_bwd(t.a, t.low, P->stream); });
     } else {
@@ -420,6 +490,7 @@ static bt::Tuning to_tuning(const bt_tuning* t, int64_t p) {
         u.ctas_per_sm = t->ctas_per_sm;
         u.sub_rows = t->sub_rows;
         u.top_rows = t->top_rows;
+        u.reduced = t->reduced;
     }
     if (p > 0) u.p0 = p;
     return u;
@@ -431,7 +502,8 @@ bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int p
 
 bt_status bt_plan_create_tuned(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int prec, const bt_tuning* tuning,
                                void* stream) {
-    if (tuning && (tuning->p0 < 0 || tuning->ctas_per_sm < 0 || tuning->sub_rows < 0 || tuning->top_rows < 0))
+    if (tuning && (tuning->p0 < 0 || tuning->ctas_per_sm < 0 || tuning->sub_rows < 0 || tuning->top_rows < 0 ||
+                   tuning->reduced < 0 || tuning->reduced > 1))
         return BT_ERR_INVALID;
     return plan_create(plan, 0, nblk, m, nrhs_max, prec, to_tuning(tuning, 0), stream);
 }

@@ -1,5 +1,6 @@
 // Instantiates the launchers of one block order M (included by bt_inst_m*.cu).
 #pragma once
+#include "bt_bcr.cuh"
 #include "bt_cta.cuh"
 #include "bt_launch.h"
 #include "bt_tp.cuh"
@@ -197,9 +198,38 @@ struct Inst {
             if (e == cudaSuccess) e = set_smem(k_factor_cta_batch<double, M, 1>, f64);
             if (e == cudaSuccess) e = set_smem(k_factor_cta_batch<float, M, 0>, f32);
             if (e == cudaSuccess) e = set_smem(k_factor_cta_batch<float, M, 1>, f32);
+            if (e == cudaSuccess) e = set_smem(k_bcr_inv<M>, bcr_smem_bytes<M>());
+            if (e == cudaSuccess) e = set_smem(k_bcr_update<M>, bcr_smem_bytes<M>());
+            if (e == cudaSuccess) e = set_smem(k_bcr_rhs<M>, bcr_vec_smem_bytes<M>());
+            if (e == cudaSuccess) e = set_smem(k_bcr_back<M>, bcr_vec_smem_bytes<M>());
             return e;
         }
         return cudaSuccess;
+    }
+    // ------------------------------------------------------ cyclic reduction --
+    template <typename K>
+    static cudaError_t launch_bcr(K k, size_t smem, const BcrArgs& a, long long ctas, cudaStream_t s) {
+        if (ctas <= 0) return cudaSuccess;
+        cudaError_t e = set_smem(k, smem);
+        if (e != cudaSuccess) return e;
+        k<<<(unsigned)ctas, 8 * M, smem, s>>>(a);
+        return cudaGetLastError();
+    }
+    static cudaError_t bcr_inv(const BcrArgs& a, long long ctas, cudaStream_t s) {
+        if constexpr (M >= 8) return launch_bcr(k_bcr_inv<M>, bcr_smem_bytes<M>(), a, ctas, s);
+        return cudaErrorNotSupported;
+    }
+    static cudaError_t bcr_update(const BcrArgs& a, long long ctas, cudaStream_t s) {
+        if constexpr (M >= 8) return launch_bcr(k_bcr_update<M>, bcr_smem_bytes<M>(), a, ctas, s);
+        return cudaErrorNotSupported;
+    }
+    static cudaError_t bcr_rhs(const BcrArgs& a, long long ctas, cudaStream_t s) {
+        if constexpr (M >= 8) return launch_bcr(k_bcr_rhs<M>, bcr_vec_smem_bytes<M>(), a, ctas, s);
+        return cudaErrorNotSupported;
+    }
+    static cudaError_t bcr_back(const BcrArgs& a, long long ctas, cudaStream_t s) {
+        if constexpr (M >= 8) return launch_bcr(k_bcr_back<M>, bcr_vec_smem_bytes<M>(), a, ctas, s);
+        return cudaErrorNotSupported;
     }
     static const Launchers* table() {
         static const Launchers L = {factor, assemble, solve_fwd, assemble_rhs, solve_bwd,
@@ -211,7 +241,11 @@ struct Inst {
                                     M >= 8 ? solve_smem_bytes<double, M>() : 0,
                                     M >= 8 ? solve_smem_bytes<float, M>() : 0,
                                     M >= 8 ? assemble_rhs_smem_bytes<M>() : 0,
-                                    prepare};
+                                    prepare,
+                                    M >= 8 ? bcr_inv : nullptr,
+                                    M >= 8 ? bcr_update : nullptr,
+                                    M >= 8 ? bcr_rhs : nullptr,
+                                    M >= 8 ? bcr_back : nullptr};
         return &L;
     }
 };

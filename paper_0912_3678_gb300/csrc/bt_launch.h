@@ -4,6 +4,10 @@
 #include "bt_level.h"
 
 namespace bt {
+struct BcrArgs;
+}
+
+namespace bt {
 
 struct Launchers {
     // low = true: local factors of this level in FP32 (the level's T is float)
@@ -30,6 +34,11 @@ struct Launchers {
     size_t smem_factor64, smem_factor32, smem_assemble, smem_solve64, smem_solve32, smem_assemble_rhs;
     // make sure every kernel of this m has its shared-memory attribute set
     cudaError_t (*prepare)();
+    // block cyclic reduction of the reduced system (m >= 8; null otherwise)
+    cudaError_t (*bcr_inv)(const BcrArgs&, long long ctas, cudaStream_t);
+    cudaError_t (*bcr_update)(const BcrArgs&, long long ctas, cudaStream_t);
+    cudaError_t (*bcr_rhs)(const BcrArgs&, long long ctas, cudaStream_t);
+    cudaError_t (*bcr_back)(const BcrArgs&, long long ctas, cudaStream_t);
 };
 
 const Launchers* launchers_m1();

@@ -9,6 +9,7 @@ struct Tuning {
     int ctas_per_sm = 0;     // level-0 target partitions per SM (0: 4 for CTA kernels, 512 for m <= 4)
     int sub_rows = 0;        // block rows per partition on recursion levels (0: 4)
     int top_rows = 0;        // a level with at most this many rows is one partition / direct (0: 8)
+    int reduced = 0;         // reduced-system solver: 0 recursive partitions, 1 block cyclic reduction
 };
 
 struct LevelShape {
@@ -56,6 +57,13 @@ inline bool plan_shapes(int kind, long long N, int m, int sms, const Tuning& t, 
         }
         out.push_back(s);
         if (kind == 0 && parts <= 1) return true;
+        if (kind == 0 && t.reduced == 1 && m >= 8) {
+            // the reduced system is solved by block cyclic reduction: one more
+            // level that holds it, without partitions
+            const long long n1 = parts - 1;
+            out.push_back(LevelShape{n1, 0, 0, 0, n1});
+            return true;
+        }
         if (kind == 1 && parts == 0) return true;
         rows = (kind == 0) ? parts - 1 : parts;
     }

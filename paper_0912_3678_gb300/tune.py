@@ -26,7 +26,7 @@ def bucket(N: int) -> int:
 
 def default_tuning(m: int, N: int, prec: str = "fp64", batch: bool = False) -> dict:
     """The built-in heuristic (all zero: the library's own defaults)."""
-    return {"p0": 0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0}
+    return {"p0": 0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0, "reduced": 0}
 
 
 class Tuner:
@@ -111,7 +111,7 @@ class Tuner:
         for k in ks:
             p0 = max(1, min(N // k, (N + 1) // 2))
             if p0 not in [c["p0"] for c in out]:
-                out.append({"p0": p0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0})
+                out.append({"p0": p0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0, "reduced": 0})
         return out
 
     def tune(self, m: int, N: int, prec: str = "fp64", nrhs: int = 1, reps: int = 9, force: bool = False) -> dict:
@@ -137,7 +137,16 @@ class Tuner:
             ms = run(t)
             if ms < 0.99 * best:
                 best, best_t = ms, t
+        if m >= 8:
+            # the reduced system by block cyclic reduction, over the same top-level partition counts
+            for t0 in [best_t] + self.candidates_k0(m, N):
+                t = dict(t0, reduced=1)
+                ms = run(t)
+                if ms < 0.99 * best:
+                    best, best_t = ms, t
         for sub in (2, 3, 6, 8):
+            if best_t.get("reduced"):
+                break
             t = dict(best_t, sub_rows=sub)
             ms = run(t)
             if ms < 0.99 * best:

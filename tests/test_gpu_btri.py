@@ -265,3 +265,26 @@ def test_captured_graph_replay(cuda, prec):
             plan.sync()
             ref = oracle.btri_solve(s.B, s.D, s.C, s.F)
             assert oracle.rel_err(to_host(X), ref) <= (TOL64 if prec == "fp64" else TOLIR)
+
+
+@pytest.mark.parametrize("m", [8, 16, 32])
+@pytest.mark.parametrize("N,p", [(9, 2), (64, 3), (301, 7), (2049, 0)])
+def test_cyclic_reduction_of_the_reduced_system(cuda, m, N, p):
+    """Reduced system by block cyclic reduction (bt_tuning.reduced = 1)."""
+    import paper_0912_3678_gb300 as bt
+    s = gen.btri_random(N, m, 3, seed_rep=N + 5 * m)
+    ref = oracle.btri_solve(s.B, s.D, s.C, s.F)
+    B, D, C, F = (to_dev(a, cuda) for a in (s.B, s.D, s.C, s.F))
+    for prec in ("fp64", "fp32_ir"):
+        with bt.BtPlan.tuned(N, m, 3, prec, {"p0": p, "reduced": 1}) as plan:
+            plan.factor(B, D, C)
+            if prec == "fp64":
+                X = plan.solve(F)
+                plan.sync()
+                assert oracle.rel_err(to_host(X), ref) <= TOL64
+            else:
+                X, it, rc, code = plan.refine(F, tol=1e-12, maxit=20)
+                assert code == 0 and oracle.rel_err(to_host(X), ref) <= TOLIR
+            lev = plan.levels()
+            if len(lev) > 1:
+                assert lev[-1][1] == 0          # the holder level of the cyclic reduction
