@@ -424,12 +424,13 @@ def main():
                 kinds[k] = (tot * args.steps / ntr, n)
         f0_ms, f0_n = plan.trace_query("factor", 0)
         r_ms, r_n = plan.trace_query("residual", 0)
+        lvl0 = {k: plan.trace_query(k, 0) for k in ("factor", "solve_fwd", "solve_bwd", "residual")}
         plan.trace(False)
         ms_max = bdist.max_over_ranks(ms, dev)
         results[prec] = dict(ms=ms_max, ms_steps=ms_steps, kinds=kinds, f0=(f0_ms, f0_n), resid=(r_ms, r_n),
                              launches=launches / args.steps, X=Xh, clocks=_clocks_summary(rows, local),
                              wall=wall, levels=plan.levels(), graph=use_graph, sweeps=sweeps[0],
-                             converged=converged)
+                             converged=converged, lvl0=lvl0, ntr=ntr)
         # end to end through the public API with pinned host buffers
         mats_pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in mats_h]
         F_pin = torch.from_numpy(np.ascontiguousarray(rhs_h)).pin_memory()
@@ -489,36 +490,34 @@ def main():
     head = min(ok, key=lambda p: ok[p]["ms"]) if ok else min(results, key=lambda p: results[p]["ms"])
     r = results[head]
     value = ws * w["unknowns"] / (r["ms"] / 1e3)
-    # roofline of the dominant kernel: the level-0 local factorization (FP64 or
-    # FP32 FMA pipe) or, for the refined path, whichever kernel kind took longest
-    kinds_sorted = sorted(r["kinds"].items(), key=lambda kv: -kv[1][0])
-    dom = kinds_sorted[0][0] if kinds_sorted else "factor"
+    # roofline of the dominant level-0 kernel of the headline path (largest
+    # time per step among factor / forward solve / back substitution / FP64
+    # residual), on its algorithmic flop count and the peak of its arithmetic
+    fp64_peak = FP64_PEAK_TFLOPS
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
     if w["kind"] == "btri":
         local_rows = N - (r["levels"][0][1] - 1)
     else:
         local_rows = N - r["levels"][0][1]
-    if dom == "factor" and r["f0"][1]:
-        flops = _factor_flops_per_row(m) * local_rows
-        t_launch = r["f0"][0] / r["f0"][1] / 1e3
-        unit_note = "level-0 local factorization"
-        peak = FP64_PEAK_TFLOPS if head == "fp64" else None
-    elif dom == "residual" and r["resid"][1]:
-        flops = 2.0 * 3 * m * m * nr * N
-        t_launch = r["resid"][0] / r["resid"][1] / 1e3
-        unit_note = "FP64 residual r = f - A x"
-        peak = FP64_PEAK_TFLOPS
-    else:
-        flops, t_launch, unit_note, peak = None, None, dom, None
-    if peak is None and flops is not None:
-        # an FP32 kernel: FP32 FMA peak from 128 lanes/SM
-        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    flops_per = {
+        "factor": _factor_flops_per_row(m) * local_rows,          # (2/3+2+2) m^3 + 4 m^3 per local row
+        "solve_fwd": 6.0 * m * m * nr * local_rows,                # 2 matvecs + top-row sweep per row
+        "solve_bwd": 4.0 * m * m * nr * local_rows,                # 2 matvecs per row
+        "residual": 6.0 * m * m * nr * N,                          # 3 m^2 nrhs FMA per block row, FP64
+    }
+    cand = {k: v for k, v in r["lvl0"].items() if v[1] > 0}
     roof = None
-    if flops is not None:
-        ach = flops / t_launch / 1e12
+    if cand and w["kind"] == "btri":
+        dom = max(cand, key=lambda k: cand[k][0])
+        t_launch = cand[dom][0] / cand[dom][1] / 1e3
+        is64 = head == "fp64" or dom == "residual"
+        peak = fp64_peak if is64 else fp32_peak
+        ach = flops_per[dom] / t_launch / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel": unit_note,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz" if peak < 5 else
-                               "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz"}
+                "traffic": None, "kernel": f"level-0 {dom} ({'FP64' if is64 else 'FP32'})",
+                "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (probe measured 1.20)"
+                                if is64 else "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz"),
+                "launch_ms": t_launch * 1e3}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
