@@ -82,8 +82,9 @@ bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int p
  * partition count of every recursion level).  Zero fields take the defaults.
  *   p0           partitions of the top level (0: ctas_per_sm x SM count,
  *                capped at nblk/4 for m >= 8 or nblk/8 for m <= 4)
- *   ctas_per_sm  level-0 partitions per SM when p0 = 0 (default 4 for m >= 8,
- *                512 for m <= 4, where a partition is one thread)
+ *   ctas_per_sm  level-0 partitions per SM when p0 = 0 (default 12 for m = 8,
+ *                4 for m = 16, 3 for m = 32, 512 for m <= 4 where a partition is
+ *                one thread)
  *   sub_rows     block rows per partition on the recursion levels (>= 2, default 4)
  *   top_rows     a level with at most this many block rows is solved by one
  *                partition (block tridiagonal) or directly (BABD); default 8

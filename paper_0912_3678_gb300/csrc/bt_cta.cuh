@@ -457,12 +457,44 @@ __device__ __forceinline__ void solve_fwd_cta_body(const LevelArgs& a, const lon
     const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
     const long long MM = S::MM;
     const T* gDinv = reinterpret_cast<const T*>(a.Dinv);
+    constexpr int RU = RhsOwn<M>::MAXU;
+    // per-thread prefetch of the next row: D'^{-1} (R), B (R), f (RU)
+    T pD[S::R];
+    double pB[S::R], pf[RU];
+    auto fetch = [&](long long j) {
+#pragma unroll
+        for (int u = 0; u < S::R; ++u) {
+            const int idx = threadIdx.x + u * NT;
+            pD[u] = gDinv[j * MM + idx];
+            pB[u] = (j > pt.s) ? a.B[(j - a.shift) * MM + idx] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            const int el = threadIdx.x + u * NT;
+            pf[u] = (el < E) ? a.F[j * E + el] : 0.0;
+        }
+    };
+    auto stash = [&]() {
+#pragma unroll
+        for (int u = 0; u < S::R; ++u) {
+            const int idx = threadIdx.x + u * NT;
+            const int at = (idx / M) * S::LD + idx % M;
+            sD[at] = pD[u];
+            sB[at] = (T)pB[u];
+        }
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            const int el = threadIdx.x + u * NT;
+            if (el < E) sv[el] = (T)pf[u];
+        }
+    };
+    fetch(pt.s);
+    stash();
+    __syncthreads();
     for (long long j = pt.s; j < pt.e; ++j) {
         const bool first = (j == pt.s);
-        load_blkT<T, M>(sD, gDinv + j * MM);
-        if (!first) load_blk<T, M>(sB, a.B + (j - a.shift) * MM);
-        for (int el = threadIdx.x; el < E; el += NT) sv[el] = (T)a.F[j * E + el];
-        __syncthreads();
+        const bool more = (j + 1 < pt.e);
+        if (more) fetch(j + 1);
         if (!first) {
             for (int el = threadIdx.x; el < E; el += NT) {
                 const int r = el / nr, c = el % nr;
@@ -473,9 +505,9 @@ __device__ __forceinline__ void solve_fwd_cta_body(const LevelArgs& a, const lon
             }
             __syncthreads();
         }
-        T h[RhsOwn<M>::MAXU];
+        T h[RU];
 #pragma unroll
-        for (int u = 0; u < RhsOwn<M>::MAXU; ++u) {
+        for (int u = 0; u < RU; ++u) {
             const int el = threadIdx.x + u * NT;
             h[u] = T(0);
             if (el < E) {
@@ -488,13 +520,14 @@ __device__ __forceinline__ void solve_fwd_cta_body(const LevelArgs& a, const lon
         }
         __syncthreads();
 #pragma unroll
-        for (int u = 0; u < RhsOwn<M>::MAXU; ++u) {
+        for (int u = 0; u < RU; ++u) {
             const int el = threadIdx.x + u * NT;
             if (el < E) {
                 sh[el] = h[u];
                 a.X[j * E + el] = (double)h[u];
             }
         }
+        if (more) stash();
         __syncthreads();
     }
     if (MODE == 1) {
@@ -610,20 +643,53 @@ __device__ __forceinline__ void solve_bwd_cta_body(const LevelArgs& a, const lon
     __syncthreads();
     const T* gY = reinterpret_cast<const T*>(a.Y);
     const T* gZ = reinterpret_cast<const T*>(a.Zc);
-    for (long long j = pt.e - 1; j >= pt.s; --j) {
-        const bool useY = (MODE == 0) && ((j < pt.e - 1) || pt.hasR);
-        if (useY) load_blkT<T, M>(sY, gY + j * MM);
-        if (pt.hasL) load_blkT<T, M>(sZ, gZ + j * MM);
-        __syncthreads();
-        T xv[RhsOwn<M>::MAXU];
+    constexpr int RU = RhsOwn<M>::MAXU;
+    T pY[S::R], pZ[S::R];
+    double ph[RU];
+    auto useY = [&](long long j) { return (MODE == 0) && ((j < pt.e - 1) || pt.hasR); };
+    auto fetch = [&](long long j) {
 #pragma unroll
-        for (int u = 0; u < RhsOwn<M>::MAXU; ++u) {
+        for (int u = 0; u < S::R; ++u) {
+            const int idx = threadIdx.x + u * NT;
+            pY[u] = useY(j) ? gY[j * MM + idx] : T(0);
+            pZ[u] = pt.hasL ? gZ[j * MM + idx] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            const int el = threadIdx.x + u * NT;
+            ph[u] = (el < E) ? a.X[j * E + el] : 0.0;
+        }
+    };
+    auto stash = [&]() {
+#pragma unroll
+        for (int u = 0; u < S::R; ++u) {
+            const int idx = threadIdx.x + u * NT;
+            const int at = (idx / M) * S::LD + idx % M;
+            sY[at] = pY[u];
+            sZ[at] = pZ[u];
+        }
+    };
+    if (pt.e > pt.s) {
+        fetch(pt.e - 1);
+        stash();
+    }
+    __syncthreads();
+    for (long long j = pt.e - 1; j >= pt.s; --j) {
+        const bool uY = useY(j);
+        const bool more = (j - 1 >= pt.s);
+        double hcur[RU];
+#pragma unroll
+        for (int u = 0; u < RU; ++u) hcur[u] = ph[u];
+        if (more) fetch(j - 1);
+        T xv[RU];
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
             const int el = threadIdx.x + u * NT;
             xv[u] = T(0);
             if (el < E) {
                 const int r = el / nr, c = el % nr;
-                T acc = (T)a.X[j * E + el];
-                if (useY) {
+                T acc = (T)hcur[u];
+                if (uY) {
 #pragma unroll 8
                     for (int k = 0; k < M; ++k) acc = fmaT<T>(-sY[r * S::LD + k], sx[k * nr + c], acc);
                 }
@@ -636,13 +702,14 @@ __device__ __forceinline__ void solve_bwd_cta_body(const LevelArgs& a, const lon
         }
         __syncthreads();
 #pragma unroll
-        for (int u = 0; u < RhsOwn<M>::MAXU; ++u) {
+        for (int u = 0; u < RU; ++u) {
             const int el = threadIdx.x + u * NT;
             if (el < E) {
                 sx[el] = xv[u];
                 a.X[j * E + el] = (double)xv[u];
             }
         }
+        if (more) stash();
         __syncthreads();
     }
 }

@@ -22,7 +22,9 @@ inline bool plan_shapes(int kind, long long N, int m, int sms, const Tuning& t, 
     out.clear();
     const long long top_rows = t.top_rows > 0 ? t.top_rows : 8;
     const long long sub_rows = t.sub_rows >= 2 ? t.sub_rows : 4;
-    const long long per_sm = t.ctas_per_sm > 0 ? t.ctas_per_sm : ((m >= 8) ? 4 : 512);
+    // level-0 partitions per SM: enough resident warps to hide the Gauss-Jordan
+    // latency (m = 8: 2 warps per CTA, m = 16: 4, m = 32: 8; m <= 4: threads)
+    const long long per_sm = t.ctas_per_sm > 0 ? t.ctas_per_sm : (m >= 32 ? 3 : m >= 16 ? 4 : m >= 8 ? 12 : 512);
     const long long kmin = (m >= 8) ? 4 : 8;
     long long rows = N;
     for (int l = 0; l < 64; ++l) {
