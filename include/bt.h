@@ -67,7 +67,9 @@ const char* bt_status_string(bt_status s);
  * ------------------------------------------------------------------- */
 
 /* Create a plan on the current CUDA device.
- *   nblk     number of block rows N (>= 1);  m block order, one of 1,2,4,8,16,32.
+ *   nblk     number of block rows N (>= 1);  m block order, 1..32 (orders other
+ *            than 1, 2, 4, 8, 16, 32 are embedded in the next of these with an
+ *            identity tail: the caller's arrays keep order m).
  *   nrhs_max largest nrhs later passed to bt_solve/bt_refine (1..32).
  *   prec     precision of the local factors (bt_prec).
  *   p        number of top-level partitions (Sec. 2, "p processors"); 0 picks
@@ -117,6 +119,15 @@ bt_status bt_factor(bt_plan plan, const double* B, const double* D, const double
  * With a BT_FP32_IR/BT_BF16_IR plan this is the low-precision solve only
  * (use bt_refine for an FP64-accurate result). */
 bt_status bt_solve(bt_plan plan, const double* F, double* X, int nrhs);
+
+/* Banded matrices (Sec. 2: a matrix with s lower and r upper off-diagonals is
+ * block tridiagonal with blocks of order max(s, r)).  Converts the n x n band
+ * matrix in band storage, band[(r + i - k) * n + k] = A[i][k] for
+ * -r <= i - k <= s, into B, D, C of N = ceil(n/m) block rows of order m
+ * (max(s, r, 1) <= m <= 32); unknowns beyond n get identity rows, so right-hand
+ * sides are padded with zeros to N*m rows.  Device arrays, asynchronous. */
+bt_status bt_band_to_blocks(int64_t n, int s, int r, const double* band, int m, double* B, double* D, double* C,
+                            void* stream);
 
 /* R = F - A X in FP64 with the matrices given to the last bt_factor. */
 bt_status bt_residual(bt_plan plan, const double* F, const double* X, double* R, int nrhs);
@@ -183,7 +194,8 @@ bt_status bt_plan_bytes(bt_plan plan, int64_t* bytes);
  *   gamma[s] = T[s][s+1] (gamma[p-2] = 0), each [p-1][m][m] in FP64.
  * For a BABD plan: alpha[i], beta[i] for the p+1 reduced rows of Eq.
  * (redmatr1) (lower block bidiagonal; beta[0] = the corner block),
- * gamma is not written. */
+ * gamma is not written.  Not available for plans whose block order is
+ * embedded in a larger one (BT_ERR_INVALID). */
 bt_status bt_reduced_export(bt_plan plan, double* alpha, double* beta, double* gamma);
 
 /* Tracing.  bt_plan_trace(plan, 1) clears the records and brackets every

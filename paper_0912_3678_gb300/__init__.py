@@ -20,7 +20,8 @@ __all__ = ["BtPlan", "AbdPlan", "BtError", "BT_STATUS", "PREC", "load_library",
            "KERNEL_KINDS", "bt_solve_noalloc", "BT_NOALLOC_SCRATCH_BYTES", "bt_plan_create_tuned",
            "bt_batch_create", "bt_batch_run", "bt_batch_finish", "bt_batch_info", "bt_batch_destroy",
            "BtBatch", "BtTuning", "BtBatchDesc", "bt_refine_async", "bt_refine_result",
-           "bt_plan_workspace_size", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
+           "bt_plan_workspace_size", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay",
+           "bt_band_to_blocks", "band_to_blocks", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
            "abd_plan_create", "abd_factor", "abd_solve", "abd_residual", "abd_refine", "abd_sync",
            "abd_plan_destroy"]
 
@@ -205,6 +206,25 @@ CAPTURE = {"factor_solve": 1, "solve": 2, "factor_refine": 3}
 def bt_plan_capture(plan, what, F, X, nrhs, sweeps=0):
     w = CAPTURE[what] if isinstance(what, str) else int(what)
     _lib.check(_lib.load().bt_plan_capture(plan, w, _ptr(F), _ptr(X), int(nrhs), int(sweeps)), "bt_plan_capture")
+
+
+def bt_band_to_blocks(n, s, r, band, m, B, D, C, stream=None):
+    _lib.check(_lib.load().bt_band_to_blocks(int(n), int(s), int(r), _ptr(band), int(m), _ptr(B), _ptr(D),
+                                             _ptr(C), _stream(stream)), "bt_band_to_blocks")
+
+
+def band_to_blocks(band, s, r, m=None):
+    """Banded matrix (band storage [s + r + 1, n] CUDA float64 tensor) -> block
+    tridiagonal (B, D, C) of order m = max(s, r, 1) (or the given m)."""
+    import torch
+    n = band.shape[1]
+    m = max(s, r, 1) if m is None else m
+    N = (n + m - 1) // m
+    B = torch.empty((N, m, m), dtype=torch.float64, device=band.device)
+    D = torch.empty_like(B)
+    C = torch.empty_like(B)
+    bt_band_to_blocks(n, s, r, band, m, B, D, C)
+    return B, D, C
 
 
 def bt_plan_replay(plan):

@@ -30,7 +30,8 @@ struct Level {
 struct bt_plan_s {
     int kind = 0;   // 0 block tridiagonal, 1 BABD
     long long N = 0;
-    int m = 0;
+    int m = 0;          // block order the kernels run at (1, 2, 4, 8, 16 or 32)
+    int mu = 0;         // block order of the caller's arrays (m >= mu; padded when larger)
     int nrhs_max = 0;
     int prec = 0;
     int device = 0;
@@ -59,6 +60,12 @@ struct bt_plan_s {
     double* B1 = nullptr;
     double* keep = nullptr;             // BABD top-level pivot rows
     bool bcr = false;                   // reduced system by block cyclic reduction
+    bool padded = false;                // caller blocks of order mu embedded in order m
+    double* Ap[3] = {nullptr, nullptr, nullptr};   // padded matrices (B/S, D/R, C)
+    double* Fp = nullptr;               // padded right-hand side / solution / residual
+    double* Xp = nullptr;
+    double* Rp = nullptr;
+    const double* U[4] = {nullptr, nullptr, nullptr, nullptr};   // caller matrices of a padded plan
     std::vector<bt::BcrArgs> bl;        // its levels
     // captured call sequence
     cudaGraph_t graph = nullptr;
@@ -112,6 +119,12 @@ void layout(bt_plan_s* P, Arena& ar) {
     if (P->kind == 1) {
         P->B0 = (double*)ar.take(sizeof(double) * mm);
         P->B1 = (double*)ar.take(sizeof(double) * mm);
+    }
+    if (P->padded) {
+        for (int k = 0; k < (P->kind == 0 ? 3 : 2); ++k) P->Ap[k] = (double*)ar.take(sizeof(double) * P->N * mm);
+        P->Fp = (double*)ar.take(sizeof(double) * rows0 * m * nr);
+        P->Xp = (double*)ar.take(sizeof(double) * rows0 * m * nr);
+        P->Rp = (double*)ar.take(sizeof(double) * rows0 * m * nr);
     }
     for (int l = 0; l <= P->nlev; ++l) {
         Level& v = P->lv[l];
@@ -191,6 +204,12 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
     const int64_t p = tune.p0;
     if (!out) return BT_ERR_INVALID;
     *out = nullptr;
+    const int mu = m;
+    if (m >= 1 && m <= 32) {
+        int M = 1;
+        while (M < m) M *= 2;
+        m = M;
+    }
     const bt::Launchers* L = bt::launchers_for(m);
     if (!L || nrhs_max < 1 || nrhs_max > kNrhsMax || prec < 0 || prec > 2 || p < 0) return BT_ERR_INVALID;
     if (kind == 0 && N < 1) return BT_ERR_INVALID;
@@ -202,6 +221,8 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
     P->kind = kind;
     P->N = N;
     P->m = m;
+    P->mu = mu;
+    P->padded = (mu != m);
     P->nrhs_max = nrhs_max;
     P->prec = prec;
     P->stream = (cudaStream_t)stream;
@@ -514,6 +535,19 @@ bt_status abd_plan_create(abd_plan* plan, int64_t N, int m, int nrhs_max, int pr
 
 bt_status bt_factor(bt_plan P, const double* B, const double* D, const double* C) {
     if (!P || P->kind != 0 || !D || (P->N > 1 && (!B || !C))) return BT_ERR_INVALID;
+    if (P->padded) {
+        P->U[0] = B;
+        P->U[1] = D;
+        P->U[2] = C;
+        cudaError_t e = bt::launch_pad_blocks(P->N, P->mu, P->m, D, P->Ap[1], 1, P->stream);
+        if (e == cudaSuccess && P->N > 1) e = bt::launch_pad_blocks(P->N, P->mu, P->m, B, P->Ap[0], 0, P->stream);
+        if (e == cudaSuccess && P->N > 1) e = bt::launch_pad_blocks(P->N, P->mu, P->m, C, P->Ap[2], 0, P->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        P->launches += 3;
+        B = P->Ap[0];
+        D = P->Ap[1];
+        C = P->Ap[2];
+    }
     P->A0 = B;
     P->A1 = D;
     P->A2 = C;
@@ -531,11 +565,29 @@ bt_status bt_factor(bt_plan P, const double* B, const double* D, const double* C
 
 bt_status abd_factor(abd_plan P, const double* S, const double* R, const double* B0, const double* B1) {
     if (!P || P->kind != 1 || !S || !R || !B0 || !B1) return BT_ERR_INVALID;
+    cudaError_t e = cudaSuccess;
+    if (P->padded) {
+        P->U[0] = S;
+        P->U[1] = R;
+        P->U[2] = B0;
+        P->U[3] = B1;
+        e = bt::launch_pad_blocks(P->N, P->mu, P->m, S, P->Ap[0], 0, P->stream);
+        if (e == cudaSuccess) e = bt::launch_pad_blocks(P->N, P->mu, P->m, R, P->Ap[1], 1, P->stream);
+        if (e == cudaSuccess) e = bt::launch_pad_blocks(1, P->mu, P->m, B0, P->B0, 1, P->stream);
+        if (e == cudaSuccess) e = bt::launch_pad_blocks(1, P->mu, P->m, B1, P->B1, 0, P->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        P->launches += 4;
+        S = P->Ap[0];
+        R = P->Ap[1];
+    } else {
+        P->U[2] = B0;
+        P->U[3] = B1;
+        const size_t mm = (size_t)P->m * P->m * sizeof(double);
+        e = cudaMemcpyAsync(P->B0, B0, mm, cudaMemcpyDeviceToDevice, P->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(P->B1, B1, mm, cudaMemcpyDeviceToDevice, P->stream);
+    }
     P->A0 = S;
     P->A1 = R;
-    const size_t mm = (size_t)P->m * P->m * sizeof(double);
-    cudaError_t e = cudaMemcpyAsync(P->B0, B0, mm, cudaMemcpyDeviceToDevice, P->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(P->B1, B1, mm, cudaMemcpyDeviceToDevice, P->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->status, 0, 4 * sizeof(long long), P->stream);
     if (e != cudaSuccess) return from_cuda(e);
     Level& v = P->lv[0];
@@ -555,41 +607,80 @@ static bt_status check_solve(bt_plan P, int kind, const void* F, const void* X, 
     return BT_OK;
 }
 
+}  // extern "C"
+
+// Padded plans: right-hand sides are embedded before and solutions extracted
+// after the run; fn(F', X') runs on the padded arrays.
+template <typename Fn>
+static bt_status padded_call(bt_plan P, const double* F, double* X, int nrhs, Fn&& fn) {
+    if (!P->padded) return fn(F, X);
+    cudaError_t e = bt::launch_pad_rhs(P->lv[0].rows, P->mu, P->m, nrhs, F, P->Fp, P->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    bt_status st = fn(P->Fp, P->Xp);
+    if (st != BT_OK && st != BT_ERR_NOT_CONVERGED) return st;
+    e = bt::launch_unpad_rhs(P->lv[0].rows, P->mu, P->m, nrhs, P->Xp, X, P->stream);
+    P->launches += 2;
+    return e != cudaSuccess ? from_cuda(e) : st;
+}
+
+static bt_status residual_entry(bt_plan P, const double* F, const double* X, double* R, int nrhs) {
+    if (!P->padded) return run_residual(P, F, X, R, nrhs);
+    cudaError_t e = bt::launch_pad_rhs(P->lv[0].rows, P->mu, P->m, nrhs, F, P->Fp, P->stream);
+    if (e == cudaSuccess) e = bt::launch_pad_rhs(P->lv[0].rows, P->mu, P->m, nrhs, X, P->Xp, P->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    bt_status st = run_residual(P, P->Fp, P->Xp, P->Rp, nrhs);
+    if (st != BT_OK) return st;
+    e = bt::launch_unpad_rhs(P->lv[0].rows, P->mu, P->m, nrhs, P->Rp, R, P->stream);
+    P->launches += 3;
+    return from_cuda(e);
+}
+
+extern "C" {
+
 bt_status bt_solve(bt_plan P, const double* F, double* X, int nrhs) {
     bt_status st = check_solve(P, 0, F, X, nrhs);
-    return st != BT_OK ? st : run_solve(P, F, X, nrhs);
+    if (st != BT_OK) return st;
+    return padded_call(P, F, X, nrhs, [&](const double* f, double* x) { return run_solve(P, f, x, nrhs); });
 }
 bt_status abd_solve(abd_plan P, const double* RHS, double* Y, int nrhs) {
     bt_status st = check_solve(P, 1, RHS, Y, nrhs);
-    return st != BT_OK ? st : run_solve(P, RHS, Y, nrhs);
+    if (st != BT_OK) return st;
+    return padded_call(P, RHS, Y, nrhs, [&](const double* f, double* x) { return run_solve(P, f, x, nrhs); });
 }
 bt_status bt_residual(bt_plan P, const double* F, const double* X, double* R, int nrhs) {
     bt_status st = check_solve(P, 0, F, X, nrhs);
     if (st == BT_OK && !R) st = BT_ERR_INVALID;
-    return st != BT_OK ? st : run_residual(P, F, X, R, nrhs);
+    return st != BT_OK ? st : residual_entry(P, F, X, R, nrhs);
 }
 bt_status abd_residual(abd_plan P, const double* RHS, const double* Y, double* Rout, int nrhs) {
     bt_status st = check_solve(P, 1, RHS, Y, nrhs);
     if (st == BT_OK && !Rout) st = BT_ERR_INVALID;
-    return st != BT_OK ? st : run_residual(P, RHS, Y, Rout, nrhs);
+    return st != BT_OK ? st : residual_entry(P, RHS, Y, Rout, nrhs);
 }
 bt_status bt_refine(bt_plan P, const double* F, double* X, int nrhs, double tol, int maxit, int* iters_out,
                     double* relcorr_out) {
     bt_status st = check_solve(P, 0, F, X, nrhs);
     if (st == BT_OK && (maxit < 1 || !(tol >= 0.0))) st = BT_ERR_INVALID;
-    return st != BT_OK ? st : run_refine(P, F, X, nrhs, tol, maxit, iters_out, relcorr_out);
+    if (st != BT_OK) return st;
+    return padded_call(P, F, X, nrhs, [&](const double* f, double* x) {
+        return run_refine(P, f, x, nrhs, tol, maxit, iters_out, relcorr_out);
+    });
 }
 bt_status abd_refine(abd_plan P, const double* RHS, double* Y, int nrhs, double tol, int maxit, int* iters_out,
                      double* relcorr_out) {
     bt_status st = check_solve(P, 1, RHS, Y, nrhs);
     if (st == BT_OK && (maxit < 1 || !(tol >= 0.0))) st = BT_ERR_INVALID;
-    return st != BT_OK ? st : run_refine(P, RHS, Y, nrhs, tol, maxit, iters_out, relcorr_out);
+    if (st != BT_OK) return st;
+    return padded_call(P, RHS, Y, nrhs, [&](const double* f, double* x) {
+        return run_refine(P, f, x, nrhs, tol, maxit, iters_out, relcorr_out);
+    });
 }
 
 bt_status bt_refine_async(bt_plan P, const double* F, double* X, int nrhs, int sweeps) {
     bt_status st = check_solve(P, P ? P->kind : 0, F, X, nrhs);
     if (st == BT_OK && (sweeps < 0 || sweeps > 30)) st = BT_ERR_INVALID;
-    return st != BT_OK ? st : run_refine_async(P, F, X, nrhs, sweeps);
+    if (st != BT_OK) return st;
+    return padded_call(P, F, X, nrhs, [&](const double* f, double* x) { return run_refine_async(P, f, x, nrhs, sweeps); });
 }
 
 bt_status bt_refine_result(bt_plan P, double tol, double* relcorr_out) {
@@ -647,11 +738,30 @@ bt_status bt_plan_capture(bt_plan P, int what, const double* F, double* X, int n
     if (e == cudaSuccess) {
         if (what != 2) {
             e = cudaMemsetAsync(P->status, 0, 4 * sizeof(long long), cap);
+            if (e == cudaSuccess && P->padded) {
+                // the graph re-embeds the caller's matrices before factoring
+                if (P->kind == 0) {
+                    e = bt::launch_pad_blocks(P->N, P->mu, P->m, P->U[1], P->Ap[1], 1, cap);
+                    if (e == cudaSuccess && P->N > 1) e = bt::launch_pad_blocks(P->N, P->mu, P->m, P->U[0], P->Ap[0], 0, cap);
+                    if (e == cudaSuccess && P->N > 1) e = bt::launch_pad_blocks(P->N, P->mu, P->m, P->U[2], P->Ap[2], 0, cap);
+                } else {
+                    e = bt::launch_pad_blocks(P->N, P->mu, P->m, P->U[0], P->Ap[0], 0, cap);
+                    if (e == cudaSuccess) e = bt::launch_pad_blocks(P->N, P->mu, P->m, P->U[1], P->Ap[1], 1, cap);
+                    if (e == cudaSuccess) e = bt::launch_pad_blocks(1, P->mu, P->m, P->U[2], P->B0, 1, cap);
+                    if (e == cudaSuccess) e = bt::launch_pad_blocks(1, P->mu, P->m, P->U[3], P->B1, 0, cap);
+                }
+            }
+            if (e == cudaSuccess && P->kind == 1 && !P->padded) {
+                const size_t mm = (size_t)P->m * P->m * sizeof(double);
+                e = cudaMemcpyAsync(P->B0, P->U[2], mm, cudaMemcpyDeviceToDevice, cap);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(P->B1, P->U[3], mm, cudaMemcpyDeviceToDevice, cap);
+            }
             if (e == cudaSuccess) st = run_factor(P);
         }
         if (e == cudaSuccess && st == BT_OK) {
-            if (what == 3) st = run_refine_async(P, F, X, nrhs, sweeps);
-            else st = run_solve(P, F, X, nrhs);
+            st = padded_call(P, F, X, nrhs, [&](const double* f, double* x) {
+                return what == 3 ? run_refine_async(P, f, x, nrhs, sweeps) : run_solve(P, f, x, nrhs);
+            });
         }
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
@@ -670,6 +780,14 @@ bt_status bt_plan_capture(bt_plan P, int what, const double* F, double* X, int n
     }
     if (st == BT_OK && what != 2) P->factored = true;
     return st;
+}
+
+bt_status bt_band_to_blocks(int64_t n, int s, int r, const double* band, int m, double* B, double* D, double* C,
+                            void* stream) {
+    if (n < 1 || s < 0 || r < 0 || m < 1 || m > 32 || m < s || m < r || !band || !B || !D || !C)
+        return BT_ERR_INVALID;
+    const long long N = (n + m - 1) / m;
+    return from_cuda(bt::launch_band_to_blocks(n, s, r, band, N, m, B, D, C, (cudaStream_t)stream));
 }
 
 bt_status bt_plan_replay(bt_plan P) {
@@ -710,7 +828,7 @@ bt_status bt_plan_bytes(bt_plan P, int64_t* bytes) {
 }
 
 bt_status bt_reduced_export(bt_plan P, double* alpha, double* beta, double* gamma) {
-    if (!P || !P->factored || !alpha || !beta) return BT_ERR_INVALID;
+    if (!P || !P->factored || !alpha || !beta || P->padded) return BT_ERR_INVALID;
     if (P->nlev < 1) return BT_ERR_INVALID;
     const size_t mm = (size_t)P->m * P->m * sizeof(double);
     const Level& u = P->lv[0];

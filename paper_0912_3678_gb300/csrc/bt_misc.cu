@@ -356,3 +356,96 @@ cudaError_t launch_babd_direct(int Np, int m, int nr, const double* S, const dou
 }
 
 }  // namespace bt
+
+namespace bt {
+
+// out[j] (M x M) = [[in[j], 0], [0, tail]] for j < N (in: m x m), tail = I or 0.
+__global__ void __launch_bounds__(256) k_pad_blocks(long long N, int m, int M, const double* __restrict__ in,
+                                                    double* __restrict__ out, int identity_tail) {
+    const long long MM = (long long)M * M;
+    const long long total = N * MM;
+    for (long long el = (long long)blockIdx.x * blockDim.x + threadIdx.x; el < total;
+         el += (long long)gridDim.x * blockDim.x) {
+        const long long j = el / MM;
+        const int r = (int)((el % MM) / M), c = (int)(el % M);
+        double v;
+        if (r < m && c < m) v = in[j * m * m + (long long)r * m + c];
+        else v = (identity_tail && r == c) ? 1.0 : 0.0;
+        out[el] = v;
+    }
+}
+
+// Right-hand sides [rows][m][nr] <-> [rows][M][nr] (zero padding).
+__global__ void __launch_bounds__(256) k_pad_rhs(long long rows, int m, int M, int nr, const double* __restrict__ in,
+                                                 double* __restrict__ out) {
+    const long long total = rows * M * nr;
+    for (long long el = (long long)blockIdx.x * blockDim.x + threadIdx.x; el < total;
+         el += (long long)gridDim.x * blockDim.x) {
+        const long long j = el / ((long long)M * nr);
+        const int r = (int)((el / nr) % M), c = (int)(el % nr);
+        out[el] = (r < m) ? in[(j * m + r) * nr + c] : 0.0;
+    }
+}
+__global__ void __launch_bounds__(256) k_unpad_rhs(long long rows, int m, int M, int nr, const double* __restrict__ in,
+                                                   double* __restrict__ out) {
+    const long long total = rows * m * nr;
+    for (long long el = (long long)blockIdx.x * blockDim.x + threadIdx.x; el < total;
+         el += (long long)gridDim.x * blockDim.x) {
+        const long long j = el / ((long long)m * nr);
+        const int r = (int)((el / nr) % m), c = (int)(el % nr);
+        out[el] = in[(j * M + r) * nr + c];
+    }
+}
+
+// Banded matrix (s sub-, r super-diagonals) in band storage band[(r + i - k) * n + k] = A[i][k]
+// -> block tridiagonal blocks of order m >= max(s, r), N = ceil(n / m); unknowns beyond n get
+// an identity row.
+__global__ void __launch_bounds__(256) k_band_to_blocks(long long n, int s, int r, const double* __restrict__ band,
+                                                        long long N, int m, double* __restrict__ B,
+                                                        double* __restrict__ D, double* __restrict__ C) {
+    const long long mm = (long long)m * m;
+    const long long total = N * mm;
+    for (long long el = (long long)blockIdx.x * blockDim.x + threadIdx.x; el < total;
+         el += (long long)gridDim.x * blockDim.x) {
+        const long long j = el / mm;
+        const int a = (int)((el % mm) / m), b = (int)(el % m);
+        const long long i = j * m + a;   // global row
+        for (int blk = 0; blk < 3; ++blk) {
+            const long long k = (j + blk - 1) * m + b;   // global column in block column j-1, j, j+1
+            double v = 0.0;
+            if (i < n && k >= 0 && k < n && i - k <= s && k - i <= r) v = band[(long long)(r + i - k) * n + k];
+            if (blk == 1 && i >= n && a == b) v = 1.0;
+            double* dst = (blk == 0) ? B : (blk == 1) ? D : C;
+            dst[el] = v;
+        }
+    }
+}
+
+static unsigned grid_stride(long long total) {
+    long long g = (total + 255) / 256;
+    if (g > 4096) g = 4096;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+cudaError_t launch_pad_blocks(long long N, int m, int M, const double* in, double* out, int identity_tail,
+                              cudaStream_t s) {
+    if (N <= 0) return cudaSuccess;
+    k_pad_blocks<<<grid_stride(N * M * M), 256, 0, s>>>(N, m, M, in, out, identity_tail);
+    return cudaGetLastError();
+}
+cudaError_t launch_pad_rhs(long long rows, int m, int M, int nr, const double* in, double* out, cudaStream_t s) {
+    k_pad_rhs<<<grid_stride(rows * M * nr), 256, 0, s>>>(rows, m, M, nr, in, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_unpad_rhs(long long rows, int m, int M, int nr, const double* in, double* out, cudaStream_t s) {
+    k_unpad_rhs<<<grid_stride(rows * m * nr), 256, 0, s>>>(rows, m, M, nr, in, out);
+    return cudaGetLastError();
+}
+cudaError_t launch_band_to_blocks(long long n, int s_, int r, const double* band, long long N, int m, double* B,
+                                  double* D, double* C, cudaStream_t s) {
+    k_band_to_blocks<<<grid_stride(N * m * m), 256, 0, s>>>(n, s_, r, band, N, m, B, D, C);
+    return cudaGetLastError();
+}
+
+}  // namespace bt

@@ -15,3 +15,12 @@ cudaError_t launch_babd_direct(int Np, int m, int nr, const double* S, const dou
                                const double* B1, const double* F, double* X, double* keep, long long* status,
                                int level, cudaStream_t s);
 }  // namespace bt
+
+namespace bt {
+cudaError_t launch_pad_blocks(long long N, int m, int M, const double* in, double* out, int identity_tail,
+                              cudaStream_t s);
+cudaError_t launch_pad_rhs(long long rows, int m, int M, int nr, const double* in, double* out, cudaStream_t s);
+cudaError_t launch_unpad_rhs(long long rows, int m, int M, int nr, const double* in, double* out, cudaStream_t s);
+cudaError_t launch_band_to_blocks(long long n, int s, int r, const double* band, long long N, int m, double* B,
+                                  double* D, double* C, cudaStream_t stream);
+}  // namespace bt
