@@ -186,8 +186,14 @@ def run_batch(args):
                         "prec": "bf16_ir" if sp.lowprec else "fp64"})
         unknowns += N * m
     torch.cuda.synchronize()
+    from paper_0912_3678_gb300 import tune
+    cap = int(args.batch_memcap_gb * 2 ** 30)
+    if args.no_tune:
+        k0, ktimes = 32, {}
+    else:
+        k0, ktimes = tune.tune_batch(systems, ir_sweeps=4, mem_cap_bytes=cap)
     t0 = time.perf_counter()
-    b = bt.BtBatch(systems, ir_sweeps=4, mem_cap_bytes=int(args.batch_memcap_gb * 2 ** 30))
+    b = bt.BtBatch(systems, ir_sweeps=4, mem_cap_bytes=cap, tuner=tune.batch_tuner(k0))
     t_create = time.perf_counter() - t0
     waves, nodes, nbytes = b.info()
     for _ in range(args.warmup):
@@ -228,7 +234,8 @@ def run_batch(args):
             "config": {"workload": f"{len(systems)} uneven block tridiagonal systems, n log-uniform "
                                    f"[1e3,{args.batch_nmax:g}], m in {{1,4,8,16,32}}, 50/50 FP64 / BF16+IR, 1 RHS",
                        "graph_nodes": nodes, "waves": waves, "workspace_gb": nbytes / 2 ** 30,
-                       "create_s": t_create},
+                       "create_s": t_create, "partition_rows": k0,
+                       "tuning_ms": {str(k): v for k, v in ktimes.items()}},
             "statuses_ok": sum(1 for x in status if x == 0), "systems": len(status),
             "rel_err_sample_max": worst,
             "cpu_baseline": {"value": n_or / t_or if t_or else None, "unit": "unknowns/s", "cores": 1,

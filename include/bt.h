@@ -93,13 +93,16 @@ bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int p
  *   reduced      solver of the top-level reduced system of a block tridiagonal
  *                plan with m >= 8: 0 = partitioned again recursively (default),
  *                1 = block cyclic reduction (the cyclic-reduction variant of
- *                Sec. 2 with one synchronisation per reduction step) */
+ *                Sec. 2 with one synchronisation per reduction step)
+ *   tp_block     CTA shape of the thread-per-partition kernels used for m <= 4:
+ *                threads per CTA, 64, 128 or 256 (0: 128) */
 typedef struct {
     int64_t p0;
     int ctas_per_sm;
     int sub_rows;
     int top_rows;
     int reduced;
+    int tp_block;
 } bt_tuning;
 
 /* bt_plan_create with explicit partitioning parameters (NULL = defaults). */
@@ -258,7 +261,9 @@ typedef struct {
     const double* C;
     const double* F;   /* [N*m][nrhs] right-hand sides */
     double* X;         /* [N*m][nrhs] solutions (written by every run) */
-    bt_tuning tuning;  /* partitioning; all zero: about 32 (m >= 8) or 64 block rows per partition */
+    bt_tuning tuning;  /* partitioning (p0, ctas_per_sm, sub_rows, top_rows; `reduced` and `tp_block`
+                          are not used by batches); all zero: about 32 (m >= 8) or 64 block rows
+                          per top-level partition */
 } bt_batch_desc;
 typedef struct bt_batch_s* bt_batch;
 

@@ -75,7 +75,7 @@ def _tuning(t):
     if isinstance(t, BtTuning):
         return t
     return BtTuning(int(t.get("p0", 0)), int(t.get("ctas_per_sm", 0)), int(t.get("sub_rows", 0)),
-                    int(t.get("top_rows", 0)), int(t.get("reduced", 0)))
+                    int(t.get("top_rows", 0)), int(t.get("reduced", 0)), int(t.get("tp_block", 0)))
 
 
 def bt_plan_create_tuned(nblk, m, nrhs_max=1, prec="fp64", tuning=None, stream=None):
@@ -447,7 +447,7 @@ class BtBatch:
             if tun is None and tuner is not None:
                 tun = tuner(m, N, prec)
             descs.append(BtBatchDesc(N, m, _prec(prec), nr, _ptr(sd["B"]), _ptr(D), _ptr(sd["C"]), _ptr(F),
-                                     _ptr(sd["X"]), _tuning(tun) or BtTuning(0, 0, 0, 0, 0)))
+                                     _ptr(sd["X"]), _tuning(tun) or BtTuning(0, 0, 0, 0, 0, 0)))
             self._keep.append((sd["B"], D, sd["C"], F, sd["X"]))
         self.count = len(descs)
         self.handle = bt_batch_create(descs, ir_sweeps, mem_cap_bytes, stream)

@@ -246,6 +246,7 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
         v.rows = shapes[l].rows;
         v.low = (l == 0) && (prec != BT_FP64);
         v.a.bf16 = (l == 0) && (prec == BT_BF16_IR) && (m >= 16) ? 1 : 0;
+        v.a.tpb = tune.tp_block;
         P->lv.push_back(v);
     }
     P->nlev = (int)P->lv.size() - 1;
@@ -512,6 +513,7 @@ static bt::Tuning to_tuning(const bt_tuning* t, int64_t p) {
         u.sub_rows = t->sub_rows;
         u.top_rows = t->top_rows;
         u.reduced = t->reduced;
+        u.tp_block = t->tp_block;
     }
     if (p > 0) u.p0 = p;
     return u;
@@ -524,7 +526,9 @@ bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int p
 bt_status bt_plan_create_tuned(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int prec, const bt_tuning* tuning,
                                void* stream) {
     if (tuning && (tuning->p0 < 0 || tuning->ctas_per_sm < 0 || tuning->sub_rows < 0 || tuning->top_rows < 0 ||
-                   tuning->reduced < 0 || tuning->reduced > 1))
+                   tuning->reduced < 0 || tuning->reduced > 1 ||
+                   !(tuning->tp_block == 0 || tuning->tp_block == 64 || tuning->tp_block == 128 ||
+                     tuning->tp_block == 256)))
         return BT_ERR_INVALID;
     return plan_create(plan, 0, nblk, m, nrhs_max, prec, to_tuning(tuning, 0), stream);
 }

@@ -14,6 +14,7 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 }
 
 static inline unsigned grid_for(long long threads, int block) { return (unsigned)((threads + block - 1) / block); }
+static inline int tpb(const LevelArgs& a) { return (a.tpb == 64 || a.tpb == 256) ? a.tpb : 128; }
 
 template <int M>
 struct Inst {
@@ -26,7 +27,7 @@ struct Inst {
             if (e != cudaSuccess) return e;
             k_factor_cta<T, M, MODE><<<(unsigned)a.p, 8 * M, smem, s>>>(a);
         } else {
-            k_factor_tp<T, M, MODE><<<grid_for(a.p, 128), 128, 0, s>>>(a);
+            k_factor_tp<T, M, MODE><<<grid_for(a.p, tpb(a)), tpb(a), 0, s>>>(a);
         }
         return cudaGetLastError();
     }
@@ -43,7 +44,7 @@ struct Inst {
             if (e != cudaSuccess) return e;
             k_assemble_cta<T, M><<<(unsigned)(a.p - 1), 8 * M, smem, s>>>(a);
         } else {
-            k_assemble_tp<T, M><<<grid_for(a.p - 1, 128), 128, 0, s>>>(a);
+            k_assemble_tp<T, M><<<grid_for(a.p - 1, tpb(a)), tpb(a), 0, s>>>(a);
         }
         return cudaGetLastError();
     }
@@ -59,7 +60,7 @@ struct Inst {
             if (e != cudaSuccess) return e;
             k_solve_fwd_cta<T, M, MODE><<<(unsigned)a.p, 8 * M, smem, s>>>(a);
         } else {
-            k_solve_fwd_tp<T, M, MODE><<<grid_for(a.p * a.nr, 128), 128, 0, s>>>(a);
+            k_solve_fwd_tp<T, M, MODE><<<grid_for(a.p * a.nr, tpb(a)), tpb(a), 0, s>>>(a);
         }
         return cudaGetLastError();
     }
@@ -76,7 +77,7 @@ struct Inst {
             if (e != cudaSuccess) return e;
             k_assemble_rhs_cta<T, M><<<(unsigned)(a.p - 1), 8 * M, smem, s>>>(a);
         } else {
-            k_assemble_rhs_tp<T, M><<<grid_for((a.p - 1) * a.nr, 128), 128, 0, s>>>(a);
+            k_assemble_rhs_tp<T, M><<<grid_for((a.p - 1) * a.nr, tpb(a)), tpb(a), 0, s>>>(a);
         }
         return cudaGetLastError();
     }
@@ -92,7 +93,7 @@ struct Inst {
             if (e != cudaSuccess) return e;
             k_solve_bwd_cta<T, M, MODE><<<(unsigned)a.p, 8 * M, smem, s>>>(a);
         } else {
-            k_solve_bwd_tp<T, M, MODE><<<grid_for(a.p * a.nr, 128), 128, 0, s>>>(a);
+            k_solve_bwd_tp<T, M, MODE><<<grid_for(a.p * a.nr, tpb(a)), tpb(a), 0, s>>>(a);
         }
         return cudaGetLastError();
     }

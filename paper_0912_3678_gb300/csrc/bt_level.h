@@ -11,6 +11,7 @@ namespace bt {
 struct LevelArgs {
     int mode;
     int level;
+    int tpb;           // threads per CTA of the thread-per-partition kernels (m <= 4): 64, 128 or 256
     int bf16;          // Schur product B_j Y_{j-1} with BF16 operands on the tensor cores (FP32 levels, m >= 16)
     long long N, p, base, extra;
     const double* B;

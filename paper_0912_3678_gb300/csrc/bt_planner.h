@@ -10,6 +10,7 @@ struct Tuning {
     int sub_rows = 0;        // block rows per partition on recursion levels (0: 4)
     int top_rows = 0;        // a level with at most this many rows is one partition / direct (0: 8)
     int reduced = 0;         // reduced-system solver: 0 recursive partitions, 1 block cyclic reduction
+    int tp_block = 0;        // threads per CTA of the thread-per-partition kernels (0: 128)
 };
 
 struct LevelShape {

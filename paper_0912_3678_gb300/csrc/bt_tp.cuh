@@ -366,11 +366,11 @@ __device__ __forceinline__ void solve_bwd_tp_body(const LevelArgs& a, const long
 // work list is (system, unit).
 #define BT_TP_KERNELS(NAME, BODY, TPL, TARGS)                                                           \
     template <TPL>                                                                                     \
-    __global__ void __launch_bounds__(128) NAME(const LevelArgs a) {                                   \
+    __global__ void __launch_bounds__(256) NAME(const LevelArgs a) {                                   \
         BODY<TARGS>(a, (long long)blockIdx.x * blockDim.x + threadIdx.x);                               \
     }                                                                                                  \
     template <TPL>                                                                                     \
-    __global__ void __launch_bounds__(128)                                                             \
+    __global__ void __launch_bounds__(256)                                                             \
         NAME##_batch(const LevelArgs* __restrict__ args, const int2* __restrict__ work, int nwork) {   \
         for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nwork; w += gridDim.x * blockDim.x) {  \
             const int2 it = work[w];                                                                   \

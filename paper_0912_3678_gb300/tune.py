@@ -1,5 +1,7 @@
 """Autotuner for the partitioning parameters (plan step A0): top-level
-partition length, recursion-level partition length and the size at which a
+partition length, the reduced-system solver (recursive partitions or block
+cyclic reduction) and recursion-level partition length (the recursion depth),
+the CTA shape of the thread-per-partition kernels, and the size at which a
 level is solved by one partition.  Candidates are timed on synthetic
 systems of the requested shape (generated on the device) through the normal
 C-ABI plan calls; the fastest setting is cached per (device SM count, block
@@ -26,7 +28,7 @@ def bucket(N: int) -> int:
 
 def default_tuning(m: int, N: int, prec: str = "fp64", batch: bool = False) -> dict:
     """The built-in heuristic (all zero: the library's own defaults)."""
-    return {"p0": 0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0, "reduced": 0}
+    return {"p0": 0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0, "reduced": 0, "tp_block": 0}
 
 
 class Tuner:
@@ -111,7 +113,7 @@ class Tuner:
         for k in ks:
             p0 = max(1, min(N // k, (N + 1) // 2))
             if p0 not in [c["p0"] for c in out]:
-                out.append({"p0": p0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0, "reduced": 0})
+                out.append({"p0": p0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0, "reduced": 0, "tp_block": 0})
         return out
 
     def tune(self, m: int, N: int, prec: str = "fp64", nrhs: int = 1, reps: int = 9, force: bool = False) -> dict:
@@ -151,6 +153,13 @@ class Tuner:
             ms = run(t)
             if ms < 0.99 * best:
                 best, best_t = ms, t
+        if m <= 4:
+            # CTA shape of the thread-per-partition kernels
+            for tpb in (64, 256):
+                t = dict(best_t, tp_block=tpb)
+                ms = run(t)
+                if ms < 0.99 * best:
+                    best, best_t = ms, t
         for top in (2, 4, 16):
             t = dict(best_t, top_rows=top)
             ms = run(t)
@@ -159,3 +168,36 @@ class Tuner:
         self.cache[k] = {"tuning": best_t, "ms": best, "trials": len(trials)}
         self.save()
         return dict(best_t)
+
+
+def batch_tuner(k0: int):
+    """Per-system tuning of a batch with top-level partitions of about k0 block rows."""
+    def f(m, N, prec):
+        p0 = max(1, min(N // k0, (N + 1) // 2)) if N > 8 else 1
+        return {"p0": p0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0, "reduced": 0, "tp_block": 0}
+    return f
+
+
+def tune_batch(systems, ir_sweeps=3, mem_cap_bytes=0, ks=(16, 32, 64, 128), reps=2):
+    """Pick the top-level partition length of a batch by timing one graph
+    launch per candidate; returns (k0, {k0: ms})."""
+    import torch
+
+    from . import BtBatch
+    times = {}
+    for k0 in ks:
+        with BtBatch(systems, ir_sweeps=ir_sweeps, mem_cap_bytes=mem_cap_bytes, tuner=batch_tuner(k0)) as b:
+            b.run()
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                b.run()
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            times[k0] = best
+    k = min(times, key=times.get)
+    return k, times
