@@ -38,8 +38,13 @@ UNIT = "unknowns*rhs/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 
 
-def _workload(name: str):
+def _workload(name: str, m_opt=None, N_opt=None, nr_opt=None):
     import gen
+    if name == "block":
+        N, m, nr = N_opt or 16384, m_opt or 16, nr_opt or 8
+        s = gen.btri_random(N, m, nr, seed_rep=0)
+        return dict(kind="btri", N=N, m=m, nrhs=nr, sys=s, unknowns=N * m * nr,
+                    desc=f"block tridiagonal m={m}, N={N} block rows (n={N * m}), {nr} RHS; D=4I+G/sqrt(m), B,C=G/sqrt(m)")
     if name == "block16":
         N, m, nr = 16384, 16, 8
         s = gen.btri_random(N, m, nr, seed_rep=0)
@@ -125,7 +130,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    w = _workload(args.workload)
+    w = _workload(args.workload, args.m, args.N, args.nrhs)
     s = w["sys"]
 
     def step():
@@ -281,7 +286,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="block16", choices=["block16", "babd8", "scalar", "batch", "serve"])
+    ap.add_argument("--workload", default="block16", choices=["block16", "block", "babd8", "scalar", "batch", "serve"])
+    ap.add_argument("--m", type=int, default=None, help="block order of --workload block")
+    ap.add_argument("--N", type=int, default=None, help="block rows of --workload block")
+    ap.add_argument("--nrhs", type=int, default=None, help="right-hand sides of --workload block")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-nmax", type=float, default=1e6)
     ap.add_argument("--batch-memcap-gb", type=float, default=80.0)
@@ -321,7 +329,7 @@ def main():
     import paper_0912_3678_gb300 as bt
     from paper_0912_3678_gb300 import dist as bdist
 
-    w = _workload(args.workload)
+    w = _workload(args.workload, args.m, args.N, args.nrhs)
     s = w["sys"]
     N, m, nr = w["N"], w["m"], w["nrhs"]
     stream = torch.cuda.current_stream(dev)
