@@ -136,11 +136,14 @@ bt_status bt_band_to_blocks(int64_t n, int s, int r, const double* band, int m, 
 bt_status bt_residual(bt_plan plan, const double* F, const double* X, double* R, int nrhs);
 
 /* Iterative refinement to FP64 accuracy: X = solve(F); repeat
- * { R = F - A X (FP64); D = solve(R); X += D } until ||D||_F <= tol ||X||_F
- * or maxit corrections.  SYNCHRONISES every iteration (two norms copied to
- * the host).  iters_out (may be NULL): corrections applied;
- * relcorr_out (may be NULL): last ||D||_F/||X||_F.
- * Returns BT_ERR_NOT_CONVERGED after maxit, or a recorded numerical status. */
+ * { R = F - A X (FP64); stop if the normwise backward error
+ *   ||R||_inf / (||A||_inf ||X||_inf + ||F||_inf) <= eta_tol (see
+ *   bt_plan_set_backward_tol) or if the last correction had
+ *   ||D||_F <= tol ||X||_F; else D = solve(R); X += D } for at most maxit
+ * corrections.  SYNCHRONISES once per round (a few norms copied to the host).
+ * iters_out (may be NULL): corrections applied; relcorr_out (may be NULL):
+ * last ||D||_F/||X||_F (-1 if none).  Returns BT_ERR_NOT_CONVERGED after
+ * maxit, or a recorded numerical status. */
 bt_status bt_refine(bt_plan plan, const double* F, double* X, int nrhs, double tol, int maxit,
                     int* iters_out, double* relcorr_out);
 
@@ -152,6 +155,13 @@ bt_status bt_refine(bt_plan plan, const double* F, double* X, int nrhs, double t
  * it is <= tol, BT_ERR_NOT_CONVERGED otherwise (or a numerical status). */
 bt_status bt_refine_async(bt_plan plan, const double* F, double* X, int nrhs, int sweeps);
 bt_status bt_refine_result(bt_plan plan, double tol, double* relcorr_out);
+
+/* Backward-error threshold of the refinement stopping test (default, when
+ * eta_tol < 0: 4 (3m + 1) u with u = 2^-53, a few roundings per residual
+ * term).  The async variant also ends with a residual of the result, and
+ * bt_refine_result accepts it when that backward error is below the
+ * threshold or the last correction is below tol. */
+bt_status bt_plan_set_backward_tol(bt_plan plan, double eta_tol);
 
 /* Plans on caller-provided device memory (e.g. from a pooling allocator), so
  * that creating a plan performs no device allocation: bt_plan_workspace_size

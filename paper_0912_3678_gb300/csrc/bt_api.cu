@@ -51,8 +51,13 @@ struct bt_plan_s {
     bool pinned = true;
     long long* status = nullptr;
     long long* status_host = nullptr;   // pinned
-    double* norms = nullptr;            // [2]
-    double* norms_host = nullptr;       // pinned
+    double* norms = nullptr;            // [2] ||d||^2, ||x||^2 of the last correction
+    double* norms_host = nullptr;       // pinned: [2] norms, then [3] residual maxima, [3] ||A||_inf
+    unsigned long long* rmax = nullptr; // [3] max |r|, |x|, |f| of the last residual (bit patterns)
+    unsigned long long* amax = nullptr; // [3] ||A||_inf (bit pattern) in [0]
+    bool anorm_valid = false;
+    int async_sweeps = 0;
+    double eta_tol = -1.0;              // backward-error stopping threshold (< 0: default)
     double* partial = nullptr;          // [2*1024]
     double* Rbuf = nullptr;
     double* Dbuf = nullptr;
@@ -112,6 +117,8 @@ void layout(bt_plan_s* P, Arena& ar) {
     const int nr = P->nrhs_max;
     P->status = (long long*)ar.take(4 * sizeof(long long));
     P->norms = (double*)ar.take(2 * sizeof(double));
+    P->rmax = (unsigned long long*)ar.take(3 * sizeof(unsigned long long));
+    P->amax = (unsigned long long*)ar.take(3 * sizeof(unsigned long long));
     P->partial = (double*)ar.take(2 * 1024 * sizeof(double));
     const long long rows0 = P->lv[0].rows;
     P->Rbuf = (double*)ar.take(sizeof(double) * rows0 * m * nr);
@@ -296,10 +303,10 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
     for (auto& b : P->bl) b.status = P->status;
     if (P->pinned) {
         e = cudaMallocHost((void**)&P->status_host, 4 * sizeof(long long));
-        if (e == cudaSuccess) e = cudaMallocHost((void**)&P->norms_host, 2 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMallocHost((void**)&P->norms_host, 8 * sizeof(double));
     } else {
         P->status_host = new (std::nothrow) long long[4];
-        P->norms_host = new (std::nothrow) double[2];
+        P->norms_host = new (std::nothrow) double[8];
         if (!P->status_host || !P->norms_host) e = cudaErrorMemoryAllocation;
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(P->status, 0, 4 * sizeof(long long), P->stream);
@@ -432,45 +439,98 @@ bt_status run_solve(bt_plan_s* P, const double* F, double* X, int nr) {
     return BT_OK;
 }
 
-bt_status run_residual(bt_plan_s* P, const double* F, const double* X, double* R, int nr) {
+bt_status run_residual(bt_plan_s* P, const double* F, const double* X, double* R, int nr,
+                       unsigned long long* maxout = nullptr) {
+    if (maxout) {
+        cudaError_t e = cudaMemsetAsync(maxout, 0, 3 * sizeof(unsigned long long), P->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
     cudaError_t e = launch(P, K_RESID, 0, 1, [&] {
-        if (P->kind == 0) return bt::launch_resid_btri(P->N, P->m, nr, P->A0, P->A1, P->A2, X, F, R, P->stream);
-        return bt::launch_resid_babd(P->N, P->m, nr, P->A0, P->A1, P->B0, P->B1, X, F, R, P->stream);
+        if (P->kind == 0)
+            return bt::launch_resid_btri(P->N, P->m, nr, P->A0, P->A1, P->A2, X, F, R, P->stream, maxout);
+        return bt::launch_resid_babd(P->N, P->m, nr, P->A0, P->A1, P->B0, P->B1, X, F, R, P->stream, maxout);
     });
     return from_cuda(e);
 }
 
+// ||A||_inf of the factored matrices (once per factorization).
+bt_status ensure_anorm(bt_plan_s* P, bool force) {
+    if (P->anorm_valid && !force) return BT_OK;
+    cudaError_t e = cudaMemsetAsync(P->amax, 0, 3 * sizeof(unsigned long long), P->stream);
+    if (e == cudaSuccess)
+        e = launch(P, K_RESID, 0, 1, [&] {
+            return bt::launch_norm_inf(P->kind, P->N, P->m, P->A0, P->A1, P->A2, P->B0, P->B1, P->amax, P->stream);
+        });
+    if (e != cudaSuccess) return from_cuda(e);
+    P->anorm_valid = true;
+    return BT_OK;
+}
+
+double eta_threshold(const bt_plan_s* P) {
+    if (P->eta_tol >= 0.0) return P->eta_tol;
+    // a few units of FP64 rounding per term of a residual row (3m terms)
+    return 4.0 * (3.0 * P->m + 1.0) * 1.1102230246251565e-16;
+}
+
+// Copy norms (2), residual maxima (3) and ||A||_inf to the host (async).
+cudaError_t fetch_norms(bt_plan_s* P) {
+    cudaError_t e = cudaMemcpyAsync(P->norms_host, P->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, P->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P->norms_host + 2, P->rmax, 3 * sizeof(double), cudaMemcpyDeviceToHost, P->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P->norms_host + 5, P->amax, sizeof(double), cudaMemcpyDeviceToHost, P->stream);
+    return e;
+}
+
+// Normwise backward error ||r||_inf / (||A||_inf ||x||_inf + ||f||_inf) from the host copies.
+double backward_error(const bt_plan_s* P) {
+    const double rm = P->norms_host[2], xm = P->norms_host[3], fm = P->norms_host[4], am = P->norms_host[5];
+    const double den = am * xm + fm;
+    return den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
+}
+
 bt_status run_refine(bt_plan_s* P, const double* F, double* X, int nr, double tol, int maxit, int* iters,
                      double* relcorr) {
+    // x = solve(f); then repeat: r = f - A x (FP64); stop when the normwise
+    // backward error of x, or the last correction relative to x, is small;
+    // otherwise d = solve(r), x += d.  One host synchronisation per round.
     if (iters) *iters = 0;
     if (relcorr) *relcorr = -1.0;
-    bt_status st = run_solve(P, F, X, nr);
+    bt_status st = ensure_anorm(P, false);
+    if (st == BT_OK) st = run_solve(P, F, X, nr);
     if (st != BT_OK) return st;
     const long long n = P->lv[0].rows * P->m * nr;
-    for (int it = 1; it <= maxit; ++it) {
-        st = run_residual(P, F, X, P->Rbuf, nr);
-        if (st == BT_OK) st = run_solve(P, P->Rbuf, P->Dbuf, nr);
+    const double eta_tol = eta_threshold(P);
+    cudaError_t e = cudaMemsetAsync(P->norms, 0, 2 * sizeof(double), P->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    for (int it = 0;; ++it) {
+        st = run_residual(P, F, X, P->Rbuf, nr, P->rmax);
         if (st != BT_OK) return st;
-        cudaError_t e = launch(P, K_IR, 0, 2,
-                               [&] { return bt::launch_ir_update(n, X, P->Dbuf, P->partial, P->norms, P->stream); });
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(P->norms_host, P->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, P->stream);
+        e = fetch_norms(P);
         if (e != cudaSuccess) return from_cuda(e);
         st = read_status(P);   // synchronises
         if (st != BT_OK) return st;
+        const double eta = backward_error(P);
         const double dd = P->norms_host[0], xx = P->norms_host[1];
-        const double rel = (xx > 0.0) ? std::sqrt(dd / xx) : std::sqrt(dd);
+        const double rel = (it == 0) ? -1.0 : ((xx > 0.0) ? std::sqrt(dd / xx) : std::sqrt(dd));
         if (iters) *iters = it;
         if (relcorr) *relcorr = rel;
-        if (!std::isfinite(rel)) return BT_ERR_NONFINITE;
-        if (rel <= tol) return BT_OK;
+        if (!std::isfinite(eta) || (it > 0 && !std::isfinite(rel))) return BT_ERR_NONFINITE;
+        if (eta <= eta_tol) return BT_OK;
+        if (it > 0 && rel <= tol) return BT_OK;
+        if (it == maxit) return BT_ERR_NOT_CONVERGED;
+        st = run_solve(P, P->Rbuf, P->Dbuf, nr);
+        if (st != BT_OK) return st;
+        e = launch(P, K_IR, 0, 2,
+                   [&] { return bt::launch_ir_update(n, X, P->Dbuf, P->partial, P->norms, P->stream); });
+        if (e != cudaSuccess) return from_cuda(e);
     }
-    return BT_ERR_NOT_CONVERGED;
 }
 
 // Enqueue X = solve(F) and `sweeps` refinement corrections; no host sync.
 bt_status run_refine_async(bt_plan_s* P, const double* F, double* X, int nr, int sweeps) {
-    bt_status st = run_solve(P, F, X, nr);
+    bt_status st = ensure_anorm(P, false);
+    if (st == BT_OK) st = run_solve(P, F, X, nr);
     const long long n = P->lv[0].rows * P->m * nr;
     for (int it = 0; it < sweeps && st == BT_OK; ++it) {
         st = run_residual(P, F, X, P->Rbuf, nr);
@@ -484,6 +544,9 @@ bt_status run_refine_async(bt_plan_s* P, const double* F, double* X, int nr, int
         cudaError_t e = cudaMemsetAsync(P->norms, 0, 2 * sizeof(double), P->stream);
         if (e != cudaSuccess) return from_cuda(e);
     }
+    // final residual of the result: its backward error decides convergence
+    if (st == BT_OK) st = run_residual(P, F, X, P->Rbuf, nr, P->rmax);
+    P->async_sweeps = sweeps;
     return st;
 }
 
@@ -562,6 +625,7 @@ bt_status bt_factor(bt_plan P, const double* B, const double* D, const double* C
     v.a.shift = 0;
     cudaError_t e = cudaMemsetAsync(P->status, 0, 4 * sizeof(long long), P->stream);
     if (e != cudaSuccess) return from_cuda(e);
+    P->anorm_valid = false;
     bt_status st = run_factor(P);
     P->factored = (st == BT_OK);
     return st;
@@ -599,6 +663,7 @@ bt_status abd_factor(abd_plan P, const double* S, const double* R, const double*
     v.a.D = R;
     v.a.C = nullptr;
     v.a.shift = 1;
+    P->anorm_valid = false;
     bt_status st = run_factor(P);
     P->factored = (st == BT_OK);
     return st;
@@ -689,15 +754,24 @@ bt_status bt_refine_async(bt_plan P, const double* F, double* X, int nrhs, int s
 
 bt_status bt_refine_result(bt_plan P, double tol, double* relcorr_out) {
     if (!P) return BT_ERR_INVALID;
-    cudaError_t e = cudaMemcpyAsync(P->norms_host, P->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, P->stream);
+    cudaError_t e = fetch_norms(P);
     if (e != cudaSuccess) return from_cuda(e);
     bt_status st = read_status(P);
     const double dd = P->norms_host[0], xx = P->norms_host[1];
     const double rel = (xx > 0.0) ? std::sqrt(dd / xx) : std::sqrt(dd);
-    if (relcorr_out) *relcorr_out = rel;
+    if (relcorr_out) *relcorr_out = (P->async_sweeps > 0) ? rel : -1.0;
     if (st != BT_OK) return st;
-    if (!std::isfinite(rel)) return BT_ERR_NONFINITE;
-    return rel <= tol ? BT_OK : BT_ERR_NOT_CONVERGED;
+    const double eta = backward_error(P);
+    if (!std::isfinite(eta)) return BT_ERR_NONFINITE;
+    if (eta <= eta_threshold(P)) return BT_OK;
+    if (P->async_sweeps > 0 && std::isfinite(rel) && rel <= tol) return BT_OK;
+    return BT_ERR_NOT_CONVERGED;
+}
+
+bt_status bt_plan_set_backward_tol(bt_plan P, double eta_tol) {
+    if (!P) return BT_ERR_INVALID;
+    P->eta_tol = eta_tol;
+    return BT_OK;
 }
 
 bt_status bt_plan_workspace_size(int kind, int64_t n, int m, int nrhs_max, int prec, const bt_tuning* tuning,
@@ -761,6 +835,7 @@ bt_status bt_plan_capture(bt_plan P, int what, const double* F, double* X, int n
                 if (e == cudaSuccess) e = cudaMemcpyAsync(P->B1, P->U[3], mm, cudaMemcpyDeviceToDevice, cap);
             }
             if (e == cudaSuccess) st = run_factor(P);
+            if (e == cudaSuccess && st == BT_OK && what == 3) st = ensure_anorm(P, true);
         }
         if (e == cudaSuccess && st == BT_OK) {
             st = padded_call(P, F, X, nrhs, [&](const double* f, double* x) {

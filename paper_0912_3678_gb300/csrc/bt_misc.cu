@@ -6,14 +6,42 @@
 
 namespace bt {
 
+// Largest of |r|, |x|, |f| over the block, merged into out[0..2] with an
+// integer atomicMax on the bit patterns (monotone for non-negative doubles,
+// so the result does not depend on the order).
+__device__ __forceinline__ void block_max3(double r, double x, double f, unsigned long long* out) {
+    __shared__ double sm[3][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        r = fmax(r, __shfl_xor_sync(0xffffffffu, r, off));
+        x = fmax(x, __shfl_xor_sync(0xffffffffu, x, off));
+        f = fmax(f, __shfl_xor_sync(0xffffffffu, f, off));
+    }
+    if (lane == 0) {
+        sm[0][warp] = r;
+        sm[1][warp] = x;
+        sm[2][warp] = f;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, sm[threadIdx.x][w]);
+        atomicMax(out + threadIdx.x, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
 // r = f - A x for the block tridiagonal A; one thread per entry of [N*m][nr].
 __global__ void __launch_bounds__(256) k_resid_btri(long long N, int m, int nr, const double* __restrict__ B,
                                                     const double* __restrict__ D, const double* __restrict__ C,
                                                     const double* __restrict__ X, const double* __restrict__ F,
-                                                    double* __restrict__ R) {
+                                                    double* __restrict__ R, unsigned long long* maxout) {
     const long long el = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long total = N * m * nr;
-    if (el >= total) return;
+    if (el >= total) {
+        if (maxout) block_max3(0.0, 0.0, 0.0, maxout);
+        return;
+    }
     const long long gr = el / nr;
     const int c = (int)(el % nr);
     const long long j = gr / m;
@@ -34,16 +62,21 @@ __global__ void __launch_bounds__(256) k_resid_btri(long long N, int m, int nr, 
         for (int k = 0; k < m; ++k) acc = fma(-Crow[k], xn[(long long)k * nr], acc);
     }
     R[el] = acc;
+    if (maxout) block_max3(fabs(acc), fabs(X[el]), fabs(F[el]), maxout);
 }
 
 // r = f - A y for the BABD A (rows 0..N, boundary row first).
 __global__ void __launch_bounds__(256) k_resid_babd(long long N, int m, int nr, const double* __restrict__ S,
                                                     const double* __restrict__ Rm, const double* __restrict__ B0,
                                                     const double* __restrict__ B1, const double* __restrict__ Y,
-                                                    const double* __restrict__ F, double* __restrict__ Rout) {
+                                                    const double* __restrict__ F, double* __restrict__ Rout,
+                                                    unsigned long long* maxout) {
     const long long el = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long total = (N + 1) * m * nr;
-    if (el >= total) return;
+    if (el >= total) {
+        if (maxout) block_max3(0.0, 0.0, 0.0, maxout);
+        return;
+    }
     const long long gr = el / nr;
     const int c = (int)(el % nr);
     const long long j = gr / m;
@@ -68,6 +101,35 @@ __global__ void __launch_bounds__(256) k_resid_babd(long long N, int m, int nr, 
         }
     }
     Rout[el] = acc;
+    if (maxout) block_max3(fabs(acc), fabs(Y[el]), fabs(F[el]), maxout);
+}
+
+// ||A||_inf = max row sum of |A| (block tridiagonal: B, D, C rows; BABD:
+// row block 0 = [B0 | B1], row block j+1 = [S_j | R_j]); one thread per row.
+__global__ void __launch_bounds__(256) k_norm_inf(int kind, long long N, int m, const double* __restrict__ A0,
+                                                  const double* __restrict__ A1, const double* __restrict__ A2,
+                                                  const double* __restrict__ B0, const double* __restrict__ B1,
+                                                  unsigned long long* out) {
+    const long long rows = (kind == 0) ? N * m : (N + 1) * m;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double sum = 0.0;
+    if (i < rows) {
+        const long long j = i / m;
+        const int r = (int)(i % m);
+        const long long mm = (long long)m * m;
+        if (kind == 0) {
+            for (int k = 0; k < m; ++k) {
+                sum += fabs(A1[j * mm + r * m + k]);
+                if (j > 0) sum += fabs(A0[j * mm + r * m + k]);
+                if (j + 1 < N) sum += fabs(A2[j * mm + r * m + k]);
+            }
+        } else if (j == 0) {
+            for (int k = 0; k < m; ++k) sum += fabs(B0[r * m + k]) + fabs(B1[r * m + k]);
+        } else {
+            for (int k = 0; k < m; ++k) sum += fabs(A0[(j - 1) * mm + r * m + k]) + fabs(A1[(j - 1) * mm + r * m + k]);
+        }
+    }
+    block_max3(sum, 0.0, 0.0, out);
 }
 
 // x += d; per-block partial sums of |d|^2 and |x|^2 (after the update).
@@ -316,16 +378,24 @@ __global__ void __launch_bounds__(256) k_babd_direct(int Np, int m, int nr, cons
 size_t babd_direct_smem(int m, int nr) { return sizeof(double) * ((size_t)(2 * m) * (3 * m + nr) + 2 * m); }
 
 cudaError_t launch_resid_btri(long long N, int m, int nr, const double* B, const double* D, const double* C,
-                              const double* X, const double* F, double* R, cudaStream_t s) {
+                              const double* X, const double* F, double* R, cudaStream_t s,
+                              unsigned long long* maxout) {
     const long long total = N * m * nr;
     if (total == 0) return cudaSuccess;
-    k_resid_btri<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(N, m, nr, B, D, C, X, F, R);
+    k_resid_btri<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(N, m, nr, B, D, C, X, F, R, maxout);
     return cudaGetLastError();
 }
 cudaError_t launch_resid_babd(long long N, int m, int nr, const double* S, const double* Rm, const double* B0,
-                              const double* B1, const double* Y, const double* F, double* Rout, cudaStream_t s) {
+                              const double* B1, const double* Y, const double* F, double* Rout, cudaStream_t s,
+                              unsigned long long* maxout) {
     const long long total = (N + 1) * m * nr;
-    k_resid_babd<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(N, m, nr, S, Rm, B0, B1, Y, F, Rout);
+    k_resid_babd<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(N, m, nr, S, Rm, B0, B1, Y, F, Rout, maxout);
+    return cudaGetLastError();
+}
+cudaError_t launch_norm_inf(int kind, long long N, int m, const double* A0, const double* A1, const double* A2,
+                            const double* B0, const double* B1, unsigned long long* out, cudaStream_t s) {
+    const long long rows = (kind == 0) ? N * m : (N + 1) * m;
+    k_norm_inf<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(kind, N, m, A0, A1, A2, B0, B1, out);
     return cudaGetLastError();
 }
 int ir_update_blocks(long long n) {

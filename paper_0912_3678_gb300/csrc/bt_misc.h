@@ -3,10 +3,15 @@
 #include <cuda_runtime.h>
 
 namespace bt {
+// maxout (may be null): [3] bit patterns of max |r|, max |x|, max |f| (atomicMax, zero it first)
 cudaError_t launch_resid_btri(long long N, int m, int nr, const double* B, const double* D, const double* C,
-                              const double* X, const double* F, double* R, cudaStream_t s);
+                              const double* X, const double* F, double* R, cudaStream_t s,
+                              unsigned long long* maxout = nullptr);
 cudaError_t launch_resid_babd(long long N, int m, int nr, const double* S, const double* Rm, const double* B0,
-                              const double* B1, const double* Y, const double* F, double* Rout, cudaStream_t s);
+                              const double* B1, const double* Y, const double* F, double* Rout, cudaStream_t s,
+                              unsigned long long* maxout = nullptr);
+cudaError_t launch_norm_inf(int kind, long long N, int m, const double* A0, const double* A1, const double* A2,
+                            const double* B0, const double* B1, unsigned long long* out, cudaStream_t s);
 int ir_update_blocks(long long n);
 cudaError_t launch_ir_update(long long n, double* X, const double* Dc, double* partial, double* out,
                              cudaStream_t s);

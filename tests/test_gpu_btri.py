@@ -288,3 +288,28 @@ def test_cyclic_reduction_of_the_reduced_system(cuda, m, N, p):
             lev = plan.levels()
             if len(lev) > 1:
                 assert lev[-1][1] == 0          # the holder level of the cyclic reduction
+
+
+def test_refinement_stops_on_backward_error(cuda):
+    """FP32 factors of a well-conditioned system: one correction brings the
+    normwise backward error below 4(3m+1)u, so bt_refine stops after it;
+    with the backward-error test switched off it needs the correction test."""
+    import paper_0912_3678_gb300 as bt
+    from paper_0912_3678_gb300 import _lib
+    N, m = 3000, 16
+    s = gen.btri_random(N, m, 2, seed_rep=17)
+    ref = oracle.btri_solve(s.B, s.D, s.C, s.F)
+    B, D, C, F = (to_dev(a, cuda) for a in (s.B, s.D, s.C, s.F))
+    with bt.BtPlan(N, m, 2, prec="fp32_ir") as plan:
+        plan.factor(B, D, C)
+        X, it, rc, code = plan.refine(F, tol=1e-12)
+        assert code == 0 and it == 1
+        assert oracle.rel_err(to_host(X), ref) <= TOLIR
+        _lib.load().bt_plan_set_backward_tol(plan.handle, 0.0)
+        X2, it2, rc2, code2 = plan.refine(F, tol=1e-12)
+        assert code2 == 0 and it2 >= 2 and rc2 <= 1e-12
+        assert oracle.rel_err(to_host(X2), ref) <= TOLIR
+    with bt.BtPlan(N, m, 2, prec="fp64") as plan:
+        plan.factor(B, D, C)
+        X, it, rc, code = plan.refine(F)
+        assert code == 0 and it == 0       # the FP64 solve is already backward stable
