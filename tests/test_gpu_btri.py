@@ -196,7 +196,9 @@ def test_nonfinite_input_is_reported(cuda):
 def test_invalid_arguments(cuda):
     import paper_0912_3678_gb300 as bt
     with pytest.raises(bt.BtError):
-        bt.BtPlan(10, 3)           # unsupported block order
+        bt.BtPlan(10, 33)          # block order above 32
+    with pytest.raises(bt.BtError):
+        bt.BtPlan(10, 0)
     with pytest.raises(bt.BtError):
         bt.BtPlan(10, 4, nrhs_max=33)
     with pytest.raises(bt.BtError):

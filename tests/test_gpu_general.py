@@ -72,7 +72,8 @@ def test_banded_matches_dense_solve(cuda, s, r):
         plan.factor(B, D, C)
         X = to_host(plan.solve(to_dev(fp, cuda)))
         plan.sync()
-    assert np.abs(X[n:]).max() == 0.0
+    if X.shape[0] > n:
+        assert np.abs(X[n:]).max() == 0.0      # padded unknowns
     assert oracle.rel_err(X[:n], ref) <= 1e-11
 
 
