@@ -415,11 +415,9 @@ cudaError_t launch_babd_direct(int Np, int m, int nr, const double* S, const dou
                                const double* B1, const double* F, double* X, double* keep, long long* status,
                                int level, cudaStream_t s) {
     const size_t smem = babd_direct_smem(m, nr);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_babd_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (smem > 48 * 1024) {   // per device and cheap: set it whenever it is needed
+        cudaError_t e = cudaFuncSetAttribute(k_babd_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     k_babd_direct<<<1, 256, smem, s>>>(Np, m, nr, S, R, B0, B1, F, X, keep, status, level);
     return cudaGetLastError();
