@@ -179,6 +179,11 @@ class Server:
     def _key(self, r: Request):
         return (r.problem_id, r.N, r.m, r.prec)
 
+    def footprint(self, r: Request) -> int:
+        """Device bytes a request needs while it runs (plan workspace, matrices, vectors)."""
+        ws, mats, vecs = self._footprint(r, _round_nrhs(r.nrhs))
+        return ws + mats + vecs
+
     def _footprint(self, r: Request, nrhs_max):
         m, N = r.m, r.N
         ws = bt_plan_workspace_size(1, N, m, nrhs_max, r.prec)
@@ -218,6 +223,13 @@ class Server:
                 f = None
         ws_b, mat_b, vec_b = self._footprint(r, _round_nrhs(r.nrhs))
         need = vec_b + (0 if f is not None else ws_b + mat_b)
+        if need > self.cap:
+            # can never fit: fail it now instead of holding the queue
+            r.status = 2            # BT_ERR_NOMEM
+            r.t_admit = r.t_done = self.now()
+            r.Y = None
+            self.done.append(r)
+            return True
         if self.in_use + need > self.cap and not self._evict_for(need):
             return False
         if f is not None:

@@ -76,7 +76,8 @@ def test_alone_equals_mix_and_oracle(cuda):
 def test_memory_admission_respects_cap(cuda):
     from paper_0912_3678_gb300 import serve
     reqs = _requests(8, seed=3, precs=("fp64",))
-    cap = 40 << 20
+    probe = serve.Server(cuda, streams=1)
+    cap = int(1.5 * max(probe.footprint(r) for r in reqs))   # about one request at a time
     srv = serve.Server(cuda, mem_cap_bytes=cap, streams=4, cache=False)
     for r in reqs:
         srv.submit(r)
@@ -84,6 +85,13 @@ def test_memory_admission_respects_cap(cuda):
     assert srv.stats()["failed"] == 0
     assert srv.peak_in_use <= cap
     srv.close()
+    # a request larger than the cap is refused at once (BT_ERR_NOMEM), not queued forever
+    tiny = serve.Server(cuda, mem_cap_bytes=1 << 20, streams=2)
+    r = _requests(1, seed=4, precs=("fp64",))[0]
+    tiny.submit(r)
+    tiny.drain(timeout_s=30)
+    assert r.status == 2
+    tiny.close()
 
 
 def test_trace_replay_reports_latency(cuda):
