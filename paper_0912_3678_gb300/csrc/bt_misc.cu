@@ -38,31 +38,35 @@ __global__ void __launch_bounds__(256) k_resid_btri(long long N, int m, int nr, 
                                                     double* __restrict__ R, unsigned long long* maxout) {
     const long long el = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long total = N * m * nr;
-    if (el >= total) {
-        if (maxout) block_max3(0.0, 0.0, 0.0, maxout);
-        return;
+    double ar = 0.0, ax = 0.0, af = 0.0;
+    if (el < total) {
+        const long long gr = el / nr;
+        const int c = (int)(el % nr);
+        const long long j = gr / m;
+        const int r = (int)(gr % m);
+        const long long mm = (long long)m * m;
+        double acc = F[el];
+        const double* Drow = D + j * mm + (long long)r * m;
+        const double* xj = X + j * m * nr + c;
+        for (int k = 0; k < m; ++k) acc = fma(-Drow[k], xj[(long long)k * nr], acc);
+        if (j > 0) {
+            const double* Brow = B + j * mm + (long long)r * m;
+            const double* xp = xj - (long long)m * nr;
+            for (int k = 0; k < m; ++k) acc = fma(-Brow[k], xp[(long long)k * nr], acc);
+        }
+        if (j + 1 < N) {
+            const double* Crow = C + j * mm + (long long)r * m;
+            const double* xn = xj + (long long)m * nr;
+            for (int k = 0; k < m; ++k) acc = fma(-Crow[k], xn[(long long)k * nr], acc);
+        }
+        R[el] = acc;
+        ar = fabs(acc);
+        ax = fabs(X[el]);
+        af = fabs(F[el]);
     }
-    const long long gr = el / nr;
-    const int c = (int)(el % nr);
-    const long long j = gr / m;
-    const int r = (int)(gr % m);
-    const long long mm = (long long)m * m;
-    double acc = F[el];
-    const double* Drow = D + j * mm + (long long)r * m;
-    const double* xj = X + j * m * nr + c;
-    for (int k = 0; k < m; ++k) acc = fma(-Drow[k], xj[(long long)k * nr], acc);
-    if (j > 0) {
-        const double* Brow = B + j * mm + (long long)r * m;
-        const double* xp = xj - (long long)m * nr;
-        for (int k = 0; k < m; ++k) acc = fma(-Brow[k], xp[(long long)k * nr], acc);
-    }
-    if (j + 1 < N) {
-        const double* Crow = C + j * mm + (long long)r * m;
-        const double* xn = xj + (long long)m * nr;
-        for (int k = 0; k < m; ++k) acc = fma(-Crow[k], xn[(long long)k * nr], acc);
-    }
-    R[el] = acc;
-    if (maxout) block_max3(fabs(acc), fabs(X[el]), fabs(F[el]), maxout);
+    // every thread of the block reaches this one call site (warp shuffles and
+    // the block barrier inside must not be split across branches)
+    if (maxout) block_max3(ar, ax, af, maxout);
 }
 
 // r = f - A y for the BABD A (rows 0..N, boundary row first).
@@ -73,35 +77,37 @@ __global__ void __launch_bounds__(256) k_resid_babd(long long N, int m, int nr, 
                                                     unsigned long long* maxout) {
     const long long el = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long total = (N + 1) * m * nr;
-    if (el >= total) {
-        if (maxout) block_max3(0.0, 0.0, 0.0, maxout);
-        return;
-    }
-    const long long gr = el / nr;
-    const int c = (int)(el % nr);
-    const long long j = gr / m;
-    const int r = (int)(gr % m);
-    const long long mm = (long long)m * m;
-    double acc = F[el];
-    if (j == 0) {
-        const double* y0 = Y + c;
-        const double* yN = Y + N * m * nr + c;
-        for (int k = 0; k < m; ++k) {
-            acc = fma(-B0[r * m + k], y0[(long long)k * nr], acc);
-            acc = fma(-B1[r * m + k], yN[(long long)k * nr], acc);
+    double ar = 0.0, ay = 0.0, af = 0.0;
+    if (el < total) {
+        const long long gr = el / nr;
+        const int c = (int)(el % nr);
+        const long long j = gr / m;
+        const int r = (int)(gr % m);
+        const long long mm = (long long)m * m;
+        double acc = F[el];
+        if (j == 0) {
+            const double* y0 = Y + c;
+            const double* yN = Y + N * m * nr + c;
+            for (int k = 0; k < m; ++k) {
+                acc = fma(-B0[r * m + k], y0[(long long)k * nr], acc);
+                acc = fma(-B1[r * m + k], yN[(long long)k * nr], acc);
+            }
+        } else {
+            const double* Srow = S + (j - 1) * mm + (long long)r * m;
+            const double* Rrow = Rm + (j - 1) * mm + (long long)r * m;
+            const double* yp = Y + (j - 1) * m * nr + c;
+            const double* yj = Y + j * m * nr + c;
+            for (int k = 0; k < m; ++k) {
+                acc = fma(-Srow[k], yp[(long long)k * nr], acc);
+                acc = fma(-Rrow[k], yj[(long long)k * nr], acc);
+            }
         }
-    } else {
-        const double* Srow = S + (j - 1) * mm + (long long)r * m;
-        const double* Rrow = Rm + (j - 1) * mm + (long long)r * m;
-        const double* yp = Y + (j - 1) * m * nr + c;
-        const double* yj = Y + j * m * nr + c;
-        for (int k = 0; k < m; ++k) {
-            acc = fma(-Srow[k], yp[(long long)k * nr], acc);
-            acc = fma(-Rrow[k], yj[(long long)k * nr], acc);
-        }
+        Rout[el] = acc;
+        ar = fabs(acc);
+        ay = fabs(Y[el]);
+        af = fabs(F[el]);
     }
-    Rout[el] = acc;
-    if (maxout) block_max3(fabs(acc), fabs(Y[el]), fabs(F[el]), maxout);
+    if (maxout) block_max3(ar, ay, af, maxout);   // one call site for the whole block
 }
 
 // ||A||_inf = max row sum of |A| (block tridiagonal: B, D, C rows; BABD:
