@@ -220,7 +220,7 @@ bt_status bt_reduced_export(bt_plan plan, double* alpha, double* beta, double* g
  * 0 local factor, 1 reduced-matrix assembly, 2 forward solve, 3 reduced
  * right-hand side, 4 back substitution, 5 top-level BABD direct solve,
  * 6 FP64 residual, 7 refinement update, 8 cyclic-reduction factor steps,
- * 9 cyclic-reduction solve steps. */
+ * 9 cyclic-reduction solve steps, 10 ||A||_inf for the backward error. */
 bt_status bt_plan_trace(bt_plan plan, int enable);
 bt_status bt_plan_trace_query(bt_plan plan, int kind, int level, double* total_ms, int64_t* launches);
 

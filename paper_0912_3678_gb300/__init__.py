@@ -267,7 +267,8 @@ def bt_reduced_export(plan, alpha, beta, gamma=None):
 
 
 KERNEL_KINDS = {"factor": 0, "assemble": 1, "solve_fwd": 2, "assemble_rhs": 3, "solve_bwd": 4,
-                "direct": 5, "residual": 6, "ir_update": 7, "bcr_factor": 8, "bcr_solve": 9}
+                "direct": 5, "residual": 6, "ir_update": 7, "bcr_factor": 8, "bcr_solve": 9,
+                "norm": 10}
 
 
 def bt_plan_trace(plan, enable=True):

@@ -18,6 +18,8 @@ namespace {
 using bt::LevelArgs;
 
 constexpr int kNrhsMax = 32;
+constexpr int kSlotWords = 3 * bt::kMaxSlots;        // words of one maxima slot array
+constexpr int kHostNorms = 2 + 2 * kSlotWords;       // pinned host copy: norms, rmax, amax
 
 struct Level {
     LevelArgs a;
@@ -52,9 +54,9 @@ struct bt_plan_s {
     long long* status = nullptr;
     long long* status_host = nullptr;   // pinned
     double* norms = nullptr;            // [2] ||d||^2, ||x||^2 of the last correction
-    double* norms_host = nullptr;       // pinned: [2] norms, then [3] residual maxima, [3] ||A||_inf
-    unsigned long long* rmax = nullptr; // [3] max |r|, |x|, |f| of the last residual (bit patterns)
-    unsigned long long* amax = nullptr; // [3] ||A||_inf (bit pattern) in [0]
+    double* norms_host = nullptr;       // pinned: [2] norms, then the rmax and amax slots
+    unsigned long long* rmax = nullptr; // [kMaxSlots][3] max |r|, |x|, |f| of the last residual (bit patterns)
+    unsigned long long* amax = nullptr; // [kMaxSlots][3] ||A||_inf (bit pattern) in word 0
     bool anorm_valid = false;
     int async_sweeps = 0;
     double eta_tol = -1.0;              // backward-error stopping threshold (< 0: default)
@@ -117,8 +119,8 @@ void layout(bt_plan_s* P, Arena& ar) {
     const int nr = P->nrhs_max;
     P->status = (long long*)ar.take(4 * sizeof(long long));
     P->norms = (double*)ar.take(2 * sizeof(double));
-    P->rmax = (unsigned long long*)ar.take(3 * sizeof(unsigned long long));
-    P->amax = (unsigned long long*)ar.take(3 * sizeof(unsigned long long));
+    P->rmax = (unsigned long long*)ar.take(kSlotWords * sizeof(unsigned long long));
+    P->amax = (unsigned long long*)ar.take(kSlotWords * sizeof(unsigned long long));
     P->partial = (double*)ar.take(2 * 1024 * sizeof(double));
     const long long rows0 = P->lv[0].rows;
     P->Rbuf = (double*)ar.take(sizeof(double) * rows0 * m * nr);
@@ -303,10 +305,10 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
     for (auto& b : P->bl) b.status = P->status;
     if (P->pinned) {
         e = cudaMallocHost((void**)&P->status_host, 4 * sizeof(long long));
-        if (e == cudaSuccess) e = cudaMallocHost((void**)&P->norms_host, 8 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMallocHost((void**)&P->norms_host, kHostNorms * sizeof(double));
     } else {
         P->status_host = new (std::nothrow) long long[4];
-        P->norms_host = new (std::nothrow) double[8];
+        P->norms_host = new (std::nothrow) double[kHostNorms];
         if (!P->status_host || !P->norms_host) e = cudaErrorMemoryAllocation;
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(P->status, 0, 4 * sizeof(long long), P->stream);
@@ -327,7 +329,7 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
 }
 
 enum Kind { K_FACTOR = 0, K_ASSEMBLE, K_SOLVE_FWD, K_ASSEMBLE_RHS, K_SOLVE_BWD, K_DIRECT, K_RESID, K_IR, K_BCR_FACTOR,
-            K_BCR_SOLVE };
+            K_BCR_SOLVE, K_NORM };
 
 cudaEvent_t take_event(bt_plan_s* P) {
     if (P->pool_used == P->pool.size()) {
@@ -442,7 +444,7 @@ bt_status run_solve(bt_plan_s* P, const double* F, double* X, int nr) {
 bt_status run_residual(bt_plan_s* P, const double* F, const double* X, double* R, int nr,
                        unsigned long long* maxout = nullptr) {
     if (maxout) {
-        cudaError_t e = cudaMemsetAsync(maxout, 0, 3 * sizeof(unsigned long long), P->stream);
+        cudaError_t e = cudaMemsetAsync(maxout, 0, kSlotWords * sizeof(unsigned long long), P->stream);
         if (e != cudaSuccess) return from_cuda(e);
     }
     cudaError_t e = launch(P, K_RESID, 0, 1, [&] {
@@ -456,9 +458,9 @@ bt_status run_residual(bt_plan_s* P, const double* F, const double* X, double* R
 // ||A||_inf of the factored matrices (once per factorization).
 bt_status ensure_anorm(bt_plan_s* P, bool force) {
     if (P->anorm_valid && !force) return BT_OK;
-    cudaError_t e = cudaMemsetAsync(P->amax, 0, 3 * sizeof(unsigned long long), P->stream);
+    cudaError_t e = cudaMemsetAsync(P->amax, 0, kSlotWords * sizeof(unsigned long long), P->stream);
     if (e == cudaSuccess)
-        e = launch(P, K_RESID, 0, 1, [&] {
+        e = launch(P, K_NORM, 0, 1, [&] {
             return bt::launch_norm_inf(P->kind, P->N, P->m, P->A0, P->A1, P->A2, P->B0, P->B1, P->amax, P->stream);
         });
     if (e != cudaSuccess) return from_cuda(e);
@@ -472,19 +474,30 @@ double eta_threshold(const bt_plan_s* P) {
     return 4.0 * (3.0 * P->m + 1.0) * 1.1102230246251565e-16;
 }
 
-// Copy norms (2), residual maxima (3) and ||A||_inf to the host (async).
+// Copy the correction norms (2) and the residual and ||A||_inf slots to the host (async).
 cudaError_t fetch_norms(bt_plan_s* P) {
     cudaError_t e = cudaMemcpyAsync(P->norms_host, P->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, P->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(P->norms_host + 2, P->rmax, 3 * sizeof(double), cudaMemcpyDeviceToHost, P->stream);
+        e = cudaMemcpyAsync(P->norms_host + 2, P->rmax, kSlotWords * sizeof(double), cudaMemcpyDeviceToHost,
+                            P->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(P->norms_host + 5, P->amax, sizeof(double), cudaMemcpyDeviceToHost, P->stream);
+        e = cudaMemcpyAsync(P->norms_host + 2 + kSlotWords, P->amax, kSlotWords * sizeof(double),
+                            cudaMemcpyDeviceToHost, P->stream);
     return e;
+}
+
+// Maximum of word w over the slots of a copied slot array.
+double slot_max(const double* slots, int w) {
+    double v = 0.0;
+    for (int q = 0; q < bt::kMaxSlots; ++q) v = std::fmax(v, slots[3 * q + w]);
+    return v;
 }
 
 // Normwise backward error ||r||_inf / (||A||_inf ||x||_inf + ||f||_inf) from the host copies.
 double backward_error(const bt_plan_s* P) {
-    const double rm = P->norms_host[2], xm = P->norms_host[3], fm = P->norms_host[4], am = P->norms_host[5];
+    const double* rs = P->norms_host + 2;
+    const double* as = P->norms_host + 2 + kSlotWords;
+    const double rm = slot_max(rs, 0), xm = slot_max(rs, 1), fm = slot_max(rs, 2), am = slot_max(as, 0);
     const double den = am * xm + fm;
     return den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
 }

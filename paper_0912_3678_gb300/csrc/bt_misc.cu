@@ -6,9 +6,10 @@
 
 namespace bt {
 
-// Largest of |r|, |x|, |f| over the block, merged into out[0..2] with an
-// integer atomicMax on the bit patterns (monotone for non-negative doubles,
-// so the result does not depend on the order).
+// Largest of |r|, |x|, |f| over the block, merged into slot (block mod
+// kMaxSlots) of out with an integer atomicMax on the bit patterns (monotone for
+// non-negative doubles, so the result does not depend on the order).  Every
+// thread of the block must call it, from one call site.
 __device__ __forceinline__ void block_max3(double r, double x, double f, unsigned long long* out) {
     __shared__ double sm[3][8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -27,7 +28,8 @@ __device__ __forceinline__ void block_max3(double r, double x, double f, unsigne
     if (threadIdx.x < 3) {
         double v = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, sm[threadIdx.x][w]);
-        atomicMax(out + threadIdx.x, (unsigned long long)__double_as_longlong(v));
+        unsigned long long* slot = out + 3 * (blockIdx.x % kMaxSlots);
+        atomicMax(slot + threadIdx.x, (unsigned long long)__double_as_longlong(v));
     }
 }
 
@@ -111,31 +113,41 @@ __global__ void __launch_bounds__(256) k_resid_babd(long long N, int m, int nr, 
 }
 
 // ||A||_inf = max row sum of |A| (block tridiagonal: B, D, C rows; BABD:
-// row block 0 = [B0 | B1], row block j+1 = [S_j | R_j]); one thread per row.
+// row block 0 = [B0 | B1], row block j+1 = [S_j | R_j]).  The blocks are
+// row-major, so each of the arrays is a list of rows of m contiguous entries;
+// lane l of a warp takes entry 32w + l, a warp step covers 32/m whole rows
+// (m divides 32) with coalesced loads, and a shuffle reduction over each group
+// of m lanes finishes the row sums.
 __global__ void __launch_bounds__(256) k_norm_inf(int kind, long long N, int m, const double* __restrict__ A0,
                                                   const double* __restrict__ A1, const double* __restrict__ A2,
                                                   const double* __restrict__ B0, const double* __restrict__ B1,
                                                   unsigned long long* out) {
     const long long rows = (kind == 0) ? N * m : (N + 1) * m;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double sum = 0.0;
-    if (i < rows) {
-        const long long j = i / m;
-        const int r = (int)(i % m);
-        const long long mm = (long long)m * m;
-        if (kind == 0) {
-            for (int k = 0; k < m; ++k) {
-                sum += fabs(A1[j * mm + r * m + k]);
-                if (j > 0) sum += fabs(A0[j * mm + r * m + k]);
-                if (j + 1 < N) sum += fabs(A2[j * mm + r * m + k]);
+    const long long total = rows * m;
+    const long long mm = (long long)m * m;
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    double best = 0.0;
+    for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < total;
+         base += warps * 32) {   // uniform within the warp
+        const long long e = base + lane;
+        double s = 0.0;
+        if (e < total) {
+            const long long j = e / mm;
+            if (kind == 0) {
+                s = fabs(A1[e]);
+                if (j > 0) s += fabs(A0[e]);
+                if (j + 1 < N) s += fabs(A2[e]);
+            } else if (j == 0) {
+                s = fabs(B0[e]) + fabs(B1[e]);
+            } else {
+                s = fabs(A0[e - mm]) + fabs(A1[e - mm]);
             }
-        } else if (j == 0) {
-            for (int k = 0; k < m; ++k) sum += fabs(B0[r * m + k]) + fabs(B1[r * m + k]);
-        } else {
-            for (int k = 0; k < m; ++k) sum += fabs(A0[(j - 1) * mm + r * m + k]) + fabs(A1[(j - 1) * mm + r * m + k]);
         }
+        for (int off = 1; off < m; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        best = fmax(best, s);
     }
-    block_max3(sum, 0.0, 0.0, out);
+    block_max3(best, 0.0, 0.0, out);
 }
 
 // x += d; per-block partial sums of |d|^2 and |x|^2 (after the update).
@@ -400,8 +412,12 @@ cudaError_t launch_resid_babd(long long N, int m, int nr, const double* S, const
 }
 cudaError_t launch_norm_inf(int kind, long long N, int m, const double* A0, const double* A1, const double* A2,
                             const double* B0, const double* B1, unsigned long long* out, cudaStream_t s) {
-    const long long rows = (kind == 0) ? N * m : (N + 1) * m;
-    k_norm_inf<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(kind, N, m, A0, A1, A2, B0, B1, out);
+    if (m < 1 || m > 32 || (32 % m) != 0) return cudaErrorInvalidValue;
+    const long long total = ((kind == 0) ? N * m : (N + 1) * m) * m;
+    long long nb = (total + 255) / 256;
+    if (nb > 2048) nb = 2048;
+    if (nb < 1) nb = 1;
+    k_norm_inf<<<(unsigned)nb, 256, 0, s>>>(kind, N, m, A0, A1, A2, B0, B1, out);
     return cudaGetLastError();
 }
 int ir_update_blocks(long long n) {

@@ -3,13 +3,18 @@
 #include <cuda_runtime.h>
 
 namespace bt {
-// maxout (may be null): [3] bit patterns of max |r|, max |x|, max |f| (atomicMax, zero it first)
+// Maxima are merged with integer atomicMax into kMaxSlots slots of 3 words
+// (slot = block index mod kMaxSlots, spreading the atomics); the caller zeroes
+// them first and takes the maximum over the slots.
+constexpr int kMaxSlots = 32;
+// maxout (may be null): [kMaxSlots][3] bit patterns of max |r|, max |x|, max |f|
 cudaError_t launch_resid_btri(long long N, int m, int nr, const double* B, const double* D, const double* C,
                               const double* X, const double* F, double* R, cudaStream_t s,
                               unsigned long long* maxout = nullptr);
 cudaError_t launch_resid_babd(long long N, int m, int nr, const double* S, const double* Rm, const double* B0,
                               const double* B1, const double* Y, const double* F, double* Rout, cudaStream_t s,
                               unsigned long long* maxout = nullptr);
+// out: [kMaxSlots][3], ||A||_inf (bit pattern) in word 0 of each slot
 cudaError_t launch_norm_inf(int kind, long long N, int m, const double* A0, const double* A1, const double* A2,
                             const double* B0, const double* B1, unsigned long long* out, cudaStream_t s);
 int ir_update_blocks(long long n);
