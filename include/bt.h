@@ -163,6 +163,13 @@ bt_status bt_refine_result(bt_plan plan, double tol, double* relcorr_out);
  * threshold or the last correction is below tol. */
 bt_status bt_plan_set_backward_tol(bt_plan plan, double eta_tol);
 
+/* ||A||_inf of the matrices given to the last bt_factor / abd_factor, as the
+ * stopping test uses it: FP32 row sums of the entries truncated toward zero
+ * (relative error below 1e-5).  Synchronises the plan's stream.  For a plan
+ * whose block order is embedded in a larger one the identity tail of the
+ * padded blocks contributes rows of sum 1. */
+bt_status bt_plan_anorm(bt_plan plan, double* anorm_out);
+
 /* Plans on caller-provided device memory (e.g. from a pooling allocator), so
  * that creating a plan performs no device allocation: bt_plan_workspace_size
  * returns the bytes a plan of this shape needs (kind 0: block tridiagonal,

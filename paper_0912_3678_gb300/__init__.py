@@ -20,7 +20,7 @@ __all__ = ["BtPlan", "AbdPlan", "BtError", "BT_STATUS", "PREC", "load_library",
            "KERNEL_KINDS", "bt_solve_noalloc", "BT_NOALLOC_SCRATCH_BYTES", "bt_plan_create_tuned",
            "bt_batch_create", "bt_batch_run", "bt_batch_finish", "bt_batch_info", "bt_batch_destroy",
            "BtBatch", "BtTuning", "BtBatchDesc", "bt_refine_async", "bt_refine_result",
-           "bt_plan_workspace_size", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay",
+           "bt_plan_workspace_size", "bt_plan_anorm", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay",
            "bt_band_to_blocks", "band_to_blocks", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
            "abd_plan_create", "abd_factor", "abd_solve", "abd_residual", "abd_refine", "abd_sync",
            "abd_plan_destroy"]
@@ -175,6 +175,13 @@ def bt_refine_result(plan, tol=1e-12):
     rc = ctypes.c_double(0.0)
     code = _lib.load().bt_refine_result(plan, float(tol), ctypes.byref(rc))
     return code, rc.value
+
+
+def bt_plan_anorm(plan) -> float:
+    """||A||_inf of the factored matrices as the refinement stopping test uses it."""
+    v = ctypes.c_double(0.0)
+    _lib.check(_lib.load().bt_plan_anorm(plan, ctypes.byref(v)), "bt_plan_anorm")
+    return v.value
 
 
 def bt_plan_workspace_size(kind, n, m, nrhs_max=1, prec="fp64", tuning=None) -> int:
@@ -417,6 +424,9 @@ class BtPlan(_PlanBase):
         code, it, rc = bt_refine(self.handle, F, X, self._nrhs(F), tol, maxit, raise_on_error)
         return X, it, rc, code
 
+    def anorm(self) -> float:
+        return bt_plan_anorm(self.handle)
+
     def reduced(self):
         """Top-level reduced matrix (alpha, beta, gamma) of Eq. (redmatr)."""
         lev = self.levels()
@@ -503,6 +513,9 @@ class AbdPlan(_PlanBase):
         Y = self._new_like_rhs(RHS) if Y is None else Y
         code, it, rc = abd_refine(self.handle, RHS, Y, self._nrhs(RHS), tol, maxit, raise_on_error)
         return Y, it, rc, code
+
+    def anorm(self) -> float:
+        return bt_plan_anorm(self.handle)
 
     def reduced(self):
         """Top-level reduced BABD matrix of Eq. (redmatr1): alpha [p+1], beta [p+1]

@@ -72,6 +72,7 @@ SIGNATURES.update({
     "bt_band_to_blocks": (_i32, [_i64, _i32, _i32, _vp, _i32, _vp, _vp, _vp, _vp]),
     "bt_refine_result": (_i32, [_vp, _f64, _pf64]),
     "bt_plan_set_backward_tol": (_i32, [_vp, _f64]),
+    "bt_plan_anorm": (_i32, [_vp, _vp]),
     "bt_plan_workspace_size": (_i32, [_i32, _i64, _i32, _i32, _i32, ctypes.POINTER(BtTuning), _pi64]),
     "bt_plan_create_in": (_i32, [_pvp, _i32, _i64, _i32, _i32, _i32, ctypes.POINTER(BtTuning), _vp, _i64, _vp]),
 })

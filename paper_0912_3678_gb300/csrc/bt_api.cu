@@ -781,6 +781,19 @@ bt_status bt_refine_result(bt_plan P, double tol, double* relcorr_out) {
     return BT_ERR_NOT_CONVERGED;
 }
 
+bt_status bt_plan_anorm(bt_plan P, double* anorm_out) {
+    if (!P || !anorm_out) return BT_ERR_INVALID;
+    if (!P->factored) return BT_ERR_INVALID;
+    bt_status st = ensure_anorm(P, false);
+    if (st != BT_OK) return st;
+    cudaError_t e = fetch_norms(P);
+    if (e != cudaSuccess) return from_cuda(e);
+    st = read_status(P);
+    if (st != BT_OK) return st;
+    *anorm_out = slot_max(P->norms_host + 2 + kSlotWords, 0);
+    return BT_OK;
+}
+
 bt_status bt_plan_set_backward_tol(bt_plan P, double eta_tol) {
     if (!P) return BT_ERR_INVALID;
     P->eta_tol = eta_tol;

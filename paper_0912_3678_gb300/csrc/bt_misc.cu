@@ -6,18 +6,27 @@
 
 namespace bt {
 
-// Largest of |r|, |x|, |f| over the block, merged into slot (block mod
-// kMaxSlots) of out with an integer atomicMax on the bit patterns (monotone for
-// non-negative doubles, so the result does not depend on the order).  Every
+// |v| as an integer key: the bit pattern with the sign cleared orders
+// non-negative doubles like their values (integer pipes only, no FP64 work).
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+    return a > b ? a : b;
+}
+
+// Largest of the keys r, x, f over the block, merged into slot (block mod
+// kMaxSlots) of out with an integer atomicMax (order-independent).  Every
 // thread of the block must call it, from one call site.
-__device__ __forceinline__ void block_max3(double r, double x, double f, unsigned long long* out) {
-    __shared__ double sm[3][8];
+__device__ __forceinline__ void block_max3(unsigned long long r, unsigned long long x, unsigned long long f,
+                                           unsigned long long* out) {
+    __shared__ unsigned long long sm[3][8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        r = fmax(r, __shfl_xor_sync(0xffffffffu, r, off));
-        x = fmax(x, __shfl_xor_sync(0xffffffffu, x, off));
-        f = fmax(f, __shfl_xor_sync(0xffffffffu, f, off));
+        r = umax64(r, __shfl_xor_sync(0xffffffffu, r, off));
+        x = umax64(x, __shfl_xor_sync(0xffffffffu, x, off));
+        f = umax64(f, __shfl_xor_sync(0xffffffffu, f, off));
     }
     if (lane == 0) {
         sm[0][warp] = r;
@@ -26,10 +35,9 @@ __device__ __forceinline__ void block_max3(double r, double x, double f, unsigne
     }
     __syncthreads();
     if (threadIdx.x < 3) {
-        double v = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, sm[threadIdx.x][w]);
-        unsigned long long* slot = out + 3 * (blockIdx.x % kMaxSlots);
-        atomicMax(slot + threadIdx.x, (unsigned long long)__double_as_longlong(v));
+        unsigned long long v = 0ull;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = umax64(v, sm[threadIdx.x][w]);
+        atomicMax(out + 3 * (blockIdx.x % kMaxSlots) + threadIdx.x, v);
     }
 }
 
@@ -40,7 +48,7 @@ __global__ void __launch_bounds__(256) k_resid_btri(long long N, int m, int nr, 
                                                     double* __restrict__ R, unsigned long long* maxout) {
     const long long el = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long total = N * m * nr;
-    double ar = 0.0, ax = 0.0, af = 0.0;
+    unsigned long long ar = 0ull, ax = 0ull, af = 0ull;
     if (el < total) {
         const long long gr = el / nr;
         const int c = (int)(el % nr);
@@ -62,9 +70,9 @@ __global__ void __launch_bounds__(256) k_resid_btri(long long N, int m, int nr, 
             for (int k = 0; k < m; ++k) acc = fma(-Crow[k], xn[(long long)k * nr], acc);
         }
         R[el] = acc;
-        ar = fabs(acc);
-        ax = fabs(X[el]);
-        af = fabs(F[el]);
+        ar = abs_bits(acc);
+        ax = abs_bits(X[el]);
+        af = abs_bits(F[el]);
     }
     // every thread of the block reaches this one call site (warp shuffles and
     // the block barrier inside must not be split across branches)
@@ -79,7 +87,7 @@ __global__ void __launch_bounds__(256) k_resid_babd(long long N, int m, int nr, 
                                                     unsigned long long* maxout) {
     const long long el = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long total = (N + 1) * m * nr;
-    double ar = 0.0, ay = 0.0, af = 0.0;
+    unsigned long long ar = 0ull, ay = 0ull, af = 0ull;
     if (el < total) {
         const long long gr = el / nr;
         const int c = (int)(el % nr);
@@ -105,19 +113,33 @@ __global__ void __launch_bounds__(256) k_resid_babd(long long N, int m, int nr, 
             }
         }
         Rout[el] = acc;
-        ar = fabs(acc);
-        ay = fabs(Y[el]);
-        af = fabs(F[el]);
+        ar = abs_bits(acc);
+        ay = abs_bits(Y[el]);
+        af = abs_bits(F[el]);
     }
     if (maxout) block_max3(ar, ay, af, maxout);   // one call site for the whole block
 }
 
+// |v| truncated to FP32 by integer operations (no FP64 work): exponent
+// rebiased, mantissa cut to its top 20 bits, magnitudes below the FP32 normal
+// range flushed to zero and above it clamped to 2^127.  Never above |v|.
+__device__ __forceinline__ float abs_trunc_f32(double v) {
+    const unsigned hi = (unsigned)__double2hiint(v) & 0x7fffffffu;
+    const int e = (int)(hi >> 20) - 1023 + 127;
+    if (e <= 0) return 0.0f;
+    if (e >= 255) return __uint_as_float(254u << 23);
+    return __uint_as_float(((unsigned)e << 23) | ((hi & 0xfffffu) << 3));
+}
+
 // ||A||_inf = max row sum of |A| (block tridiagonal: B, D, C rows; BABD:
-// row block 0 = [B0 | B1], row block j+1 = [S_j | R_j]).  The blocks are
-// row-major, so each of the arrays is a list of rows of m contiguous entries;
-// lane l of a warp takes entry 32w + l, a warp step covers 32/m whole rows
-// (m divides 32) with coalesced loads, and a shuffle reduction over each group
-// of m lanes finishes the row sums.
+// row block 0 = [B0 | B1], row block j+1 = [S_j | R_j]), in FP32 from entries
+// truncated toward zero: relative error below 1e-5 (it only enters the
+// backward-error stopping threshold, where a slightly smaller norm makes the
+// test slightly stricter).  The
+// blocks are row-major, so each array is a list of rows of m contiguous
+// entries; lane l of a warp takes entry 32w + l, a warp step covers 32/m whole
+// rows (m divides 32) with coalesced loads, and a shuffle reduction over each
+// group of m lanes finishes the row sums.
 __global__ void __launch_bounds__(256) k_norm_inf(int kind, long long N, int m, const double* __restrict__ A0,
                                                   const double* __restrict__ A1, const double* __restrict__ A2,
                                                   const double* __restrict__ B0, const double* __restrict__ B1,
@@ -127,27 +149,28 @@ __global__ void __launch_bounds__(256) k_norm_inf(int kind, long long N, int m, 
     const long long mm = (long long)m * m;
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
-    double best = 0.0;
+    float best = 0.0f;
     for (long long base = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < total;
          base += warps * 32) {   // uniform within the warp
         const long long e = base + lane;
-        double s = 0.0;
+        float s = 0.0f;
         if (e < total) {
             const long long j = e / mm;
             if (kind == 0) {
-                s = fabs(A1[e]);
-                if (j > 0) s += fabs(A0[e]);
-                if (j + 1 < N) s += fabs(A2[e]);
+                s = abs_trunc_f32(A1[e]);
+                if (j > 0) s += abs_trunc_f32(A0[e]);
+                if (j + 1 < N) s += abs_trunc_f32(A2[e]);
             } else if (j == 0) {
-                s = fabs(B0[e]) + fabs(B1[e]);
+                s = abs_trunc_f32(B0[e]) + abs_trunc_f32(B1[e]);
             } else {
-                s = fabs(A0[e - mm]) + fabs(A1[e - mm]);
+                s = abs_trunc_f32(A0[e - mm]) + abs_trunc_f32(A1[e - mm]);
             }
         }
         for (int off = 1; off < m; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        best = fmax(best, s);
+        best = fmaxf(best, s);
     }
-    block_max3(best, 0.0, 0.0, out);
+    // as a double bit pattern so that the slots hold doubles like the residual maxima
+    block_max3(abs_bits((double)best), 0ull, 0ull, out);
 }
 
 // x += d; per-block partial sums of |d|^2 and |x|^2 (after the update).

@@ -110,3 +110,15 @@ def test_ivp_special_case(cuda):
         y = np.linalg.solve(b.R[j], Rb[j + 1] - b.S[j] @ y)
         seq.append(y)
     assert oracle.rel_err(Y, np.concatenate(seq)) <= 1e-11
+
+
+def test_babd_anorm_matches_numpy(cuda):
+    import paper_0912_3678_gb300 as bt
+    b = gen.babd_random(300, 8, 1, seed_rep=4)
+    rows = np.concatenate([np.abs(b.B0).sum(1) + np.abs(b.B1).sum(1),
+                           (np.abs(b.S).sum(2) + np.abs(b.R).sum(2)).ravel()])
+    exact = rows.max()
+    with bt.AbdPlan(300, 8, 1) as plan:
+        plan.factor(*(to_dev(a, cuda) for a in (b.S, b.R, b.B0, b.B1)))
+        got = plan.anorm()
+    assert abs(got - exact) <= 1e-5 * exact

@@ -326,3 +326,21 @@ def test_refinement_stops_on_backward_error(cuda):
         plan.factor(B, D, C)
         X, it, rc, code = plan.refine(F)
         assert code == 0 and it == 0       # the FP64 solve is already backward stable
+
+
+@pytest.mark.parametrize("m", [1, 5, 16])
+def test_anorm_matches_numpy(cuda, m):
+    """||A||_inf used by the stopping test (FP32 sums of truncated entries)
+    agrees with the exact row-sum norm to 1e-5 relative."""
+    import paper_0912_3678_gb300 as bt
+    N = 777
+    s = gen.btri_random(N, m, 1, seed_rep=23)
+    s.D[5] *= 40.0                                  # one dominant block row
+    rows = np.abs(s.D).sum(2)
+    rows[1:] += np.abs(s.B[1:]).sum(2)
+    rows[:-1] += np.abs(s.C[:-1]).sum(2)
+    exact = rows.max()
+    with bt.BtPlan(N, m, 1) as plan:
+        plan.factor(*(to_dev(a, cuda) for a in (s.B, s.D, s.C)))
+        got = plan.anorm()
+    assert abs(got - exact) <= 1e-5 * exact
