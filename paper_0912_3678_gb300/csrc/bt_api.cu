@@ -378,11 +378,9 @@ bt_status run_factor(bt_plan_s* P) {
             // block cyclic reduction of the reduced system
             for (size_t q = 0; q < P->bl.size(); ++q) {
                 bt::BcrArgs& b = P->bl[q];
-                const long long odd = (b.K == 1) ? 1 : b.K / 2;
-                cudaError_t e = launch(P, K_BCR_FACTOR, b.level, 1, [&] { return L->bcr_inv(b, odd, P->stream); });
-                if (e == cudaSuccess && b.K > 1)
-                    e = launch(P, K_BCR_FACTOR, b.level, 1,
-                               [&] { return L->bcr_update(b, (b.K + 1) / 2, P->stream); });
+                const long long ctas = (b.K == 1) ? 1 : (b.K + 1) / 2;
+                cudaError_t e =
+                    launch(P, K_BCR_FACTOR, b.level, 1, [&] { return L->bcr_factor(b, ctas, P->stream); });
                 if (e != cudaSuccess) return from_cuda(e);
             }
             break;

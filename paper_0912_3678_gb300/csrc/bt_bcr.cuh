@@ -32,88 +32,198 @@ struct BcrArgs {
     long long* status;
 };
 
-template <int M>
-constexpr size_t bcr_smem_bytes() {
-    return sizeof(double) * (4 * Cta<double, M>::BLK + M) + sizeof(int) * M;
+// The reduced levels are small, so these kernels are built for latency: each
+// FP64 dot product of length M is split over four partial sums (dependency
+// chains of M/4 instead of M), and one launch per level does the whole
+// elimination step.
+
+__device__ __forceinline__ void grp_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// Inverse of the odd rows (q -> row 2q+1), or of the single row when K == 1.
-template <int M>
-__global__ void __launch_bounds__(8 * M) k_bcr_inv(const BcrArgs a) {
-    using S = Cta<double, M>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* sD = reinterpret_cast<double*>(smem_raw);
-    double* colk = sD + 4 * S::BLK;
-    int* perm = reinterpret_cast<int*>(colk + M);
-    const long long q = blockIdx.x;
-    const long long row = (a.K == 1) ? 0 : 2 * q + 1;
-    if (row >= a.K) return;
-    load_blk<double, M>(sD, a.D + row * S::MM);
-    __syncthreads();
-    gj_inverse<double, M>(sD, colk, perm, a.status, a.level, -2, row);
-    store_blk<double, M>(a.Dinv + q * S::MM, sD);
-}
-
-// Update of the kept row 2q: alpha, gamma, D', B', C'.
-template <int M>
-__global__ void __launch_bounds__(8 * M) k_bcr_update(const BcrArgs a) {
-    using S = Cta<double, M>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* s0 = reinterpret_cast<double*>(smem_raw);
-    double* s1 = s0 + S::BLK;
-    double* sal = s1 + S::BLK;
-    double* sga = sal + S::BLK;
-    const long long q = blockIdx.x;
-    const long long r = 2 * q;
-    const bool left = q >= 1;
-    const bool right = r + 1 < a.K;
-    const long long MM = S::MM;
-    const Own<double, M> o;
-    double al[S::R], ga[S::R];
-    zero_own<double, M>(al);
-    zero_own<double, M>(ga);
-    if (left) {
-        load_blk<double, M>(s0, a.B + r * MM);
-        load_blk<double, M>(s1, a.Dinv + (q - 1) * MM);
-        __syncthreads();
-        gemm_acc<double, M, true>(al, s0, s1, o);
-        __syncthreads();
-    }
-    if (right) {
-        load_blk<double, M>(s0, a.C + r * MM);
-        load_blk<double, M>(s1, a.Dinv + q * MM);
-        __syncthreads();
-        gemm_acc<double, M, true>(ga, s0, s1, o);
-        __syncthreads();
-    }
-    write_own<double, M>(sal, al, o);
-    write_own<double, M>(sga, ga, o);
-    store_own<double, M>(a.al + q * MM, al, o);
-    store_own<double, M>(a.ga + q * MM, ga, o);
-    double d[S::R], bn[S::R], cn[S::R];
+// acc[q] += sgn * (A B)[r0+q][c] over four partial sums.
+template <int M, bool NEG>
+__device__ __forceinline__ void gemm_lat(double (&acc)[M / 8], const double* A, const double* B, int r0, int c) {
+    constexpr int LD = M + 1, R = M / 8;
+    double p[R][4];
 #pragma unroll
-    for (int u = 0; u < S::R; ++u) d[u] = a.D[r * MM + (o.r0 + u) * M + o.c];
-    zero_own<double, M>(bn);
-    zero_own<double, M>(cn);
+    for (int q = 0; q < R; ++q)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) p[q][u] = 0.0;
+#pragma unroll
+    for (int k = 0; k < M; k += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const double b = NEG ? -B[(k + u) * LD + c] : B[(k + u) * LD + c];
+#pragma unroll
+            for (int q = 0; q < R; ++q) p[q][u] = fma(A[(r0 + q) * LD + k + u], b, p[q][u]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) acc[q] += (p[q][0] + p[q][1]) + (p[q][2] + p[q][3]);
+}
+
+// sum_k A[row][k] v[k * nr] over four partial sums (A in shared memory, row-padded).
+template <int M>
+__device__ __forceinline__ double dot_lat(const double* Arow, const double* v, int nr) {
+    double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+#pragma unroll
+    for (int k = 0; k < M; k += 4) {
+        p0 = fma(Arow[k], v[k * nr], p0);
+        p1 = fma(Arow[k + 1], v[(k + 1) * nr], p1);
+        p2 = fma(Arow[k + 2], v[(k + 2) * nr], p2);
+        p3 = fma(Arow[k + 3], v[(k + 3) * nr], p3);
+    }
+    return (p0 + p1) + (p2 + p3);
+}
+
+// Gauss-Jordan inverse with partial pivoting (the steps of gj_inverse) run by
+// a group of 8M threads (group-local index gtid) synchronised on named
+// barrier `bar`, so that two groups of one CTA invert two blocks at once.
+template <int M>
+__device__ void gj_inverse_grp(double* a, double* colk, int* perm, long long* st, int level, long long row,
+                               int gtid, int bar) {
+    using S = Cta<double, M>;
+    constexpr int NT = S::NT, NW = NT / 32, LD = S::LD;
+    const int lane = gtid & 31, warp = gtid >> 5;
+    const int r0 = (gtid / M) * S::R, c = gtid % M;
+    for (int k = 0; k < M; ++k) {
+        if (warp == k % NW) {
+            const double v = (lane < M) ? a[lane * LD + k] : 0.0;
+            const unsigned key = (lane >= k && lane < M) ? ((mag_key<double>(v) << 5) | (unsigned)(31 - lane)) : 0u;
+            const unsigned best = __reduce_max_sync(0xffffffffu, key);
+            const int p = 31 - (int)(best & 31u);
+            double pv = __shfl_sync(0xffffffffu, v, p);
+            const double vk = __shfl_sync(0xffffffffu, v, k);
+            if (pv == 0.0 || nonfinite(pv)) {
+                if (lane == 0) report(st, pv == 0.0 ? ST_SINGULAR : ST_NONFINITE, level, -2, row);
+                pv = 1.0;
+            }
+            const double r = rcp(pv);
+            if (lane < M) {
+                colk[lane] = (lane == k) ? 0.0 : (lane == p ? vk : v);
+                const double tk = a[k * LD + lane];
+                const double tp = a[p * LD + lane];
+                a[p * LD + lane] = tk;
+                a[k * LD + lane] = (lane == k) ? r : tp * r;
+            }
+            if (lane == 0) perm[k] = p;
+        }
+        grp_sync(bar, NT);
+#pragma unroll
+        for (int q = 0; q < S::R; ++q) {
+            const int i = r0 + q;
+            if (i != k) {
+                const double l = colk[i];
+                const double akc = a[k * LD + c];
+                a[i * LD + c] = (c == k) ? -l * akc : fma(-l, akc, a[i * LD + c]);
+            }
+        }
+        grp_sync(bar, NT);
+    }
+    if (warp == 0 && lane < M) {
+        for (int k = M - 1; k >= 0; --k) {
+            const int p = perm[k];
+            if (p != k) {
+                const double t = a[lane * LD + k];
+                a[lane * LD + k] = a[lane * LD + p];
+                a[lane * LD + p] = t;
+            }
+        }
+    }
+    grp_sync(bar, NT);
+}
+
+template <int M>
+constexpr size_t bcr_factor_smem_bytes() {
+    return sizeof(double) * (11 * Cta<double, M>::BLK + 2 * M) + sizeof(int) * 2 * M;
+}
+
+// One reduction step for kept row r = 2q, by 16M threads in two groups:
+// group 0 inverts the left odd neighbour r-1 and forms alpha_q with its
+// products alpha C_{r-1} and B' = alpha B_{r-1}; group 1 inverts the right odd
+// neighbour r+1 (stored as Dinv[q]) and forms gamma_q, gamma B_{r+1} and
+// C' = gamma C_{r+1}; then D' = D_r + alpha C_{r-1} + gamma B_{r+1}.  Each odd
+// row is inverted by both kept rows next to it, which costs one extra block
+// inverse per kept row and saves a launch and a grid-wide dependency per level.
+// With K == 1 group 0 inverts the single row into Dinv[0].
+template <int M>
+__global__ void __launch_bounds__(16 * M) k_bcr_factor(const BcrArgs a) {
+    using S = Cta<double, M>;
+    constexpr int NT = S::NT, BLK = S::BLK, LD = S::LD, R = S::R;
+    constexpr long long MM = S::MM;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* base = reinterpret_cast<double*>(smem_raw);
+    const int g = threadIdx.x / NT, gtid = threadIdx.x % NT;
+    double* sI = base + g * 5 * BLK;   // block being inverted
+    double* sO = sI + BLK;             // B_r (group 0) or C_r (group 1)
+    double* sP = sI + 2 * BLK;         // C_{r-1} or B_{r+1}
+    double* sQ = sI + 3 * BLK;         // B_{r-1} or C_{r+1}
+    double* sM = sI + 4 * BLK;         // alpha or gamma
+    double* sT = base + 10 * BLK;      // alpha C_{r-1} from group 0
+    double* colk = base + 11 * BLK + g * M;
+    int* perm = reinterpret_cast<int*>(base + 11 * BLK + 2 * M) + g * M;
+    const int r0 = (gtid / M) * R, c = gtid % M;
+    auto load = [&](double* dst, const double* src) {
+        for (int idx = gtid; idx < M * M; idx += NT) dst[(idx / M) * LD + idx % M] = src[idx];
+    };
+    if (a.K == 1) {
+        if (g == 0) {
+            load(sI, a.D);
+            grp_sync(1, NT);
+            gj_inverse_grp<M>(sI, colk, perm, a.status, a.level, 0, gtid, 1);
+            for (int idx = gtid; idx < M * M; idx += NT) a.Dinv[idx] = sI[(idx / M) * LD + idx % M];
+        }
+        return;
+    }
+    const long long q = blockIdx.x, r = 2 * q;
+    const bool has = (g == 0) ? (q >= 1) : (r + 1 < a.K);
+    const bool hasQ = (g == 0) ? (r - 1 >= 1) : (r + 2 < a.K);
+    double t[R], o2[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) t[u] = o2[u] = 0.0;
+    double* mult_out = (g == 0 ? a.al : a.ga) + q * MM;
+    double* o2_out = (g == 0 ? a.Bn : a.Cn) + q * MM;
+    if (has) {
+        const long long nb = (g == 0) ? r - 1 : r + 1;
+        load(sI, a.D + nb * MM);
+        load(sO, (g == 0 ? a.B : a.C) + r * MM);
+        load(sP, (g == 0 ? a.C : a.B) + nb * MM);
+        if (hasQ) load(sQ, (g == 0 ? a.B : a.C) + nb * MM);
+        grp_sync(1 + g, NT);
+        gj_inverse_grp<M>(sI, colk, perm, a.status, a.level, nb, gtid, 1 + g);
+        if (g == 1)
+            for (int idx = gtid; idx < M * M; idx += NT) a.Dinv[q * MM + idx] = sI[(idx / M) * LD + idx % M];
+        double mult[R];
+#pragma unroll
+        for (int u = 0; u < R; ++u) mult[u] = 0.0;
+        gemm_lat<M, true>(mult, sO, sI, r0, c);
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            sM[(r0 + u) * LD + c] = mult[u];
+            mult_out[(r0 + u) * M + c] = mult[u];
+        }
+        grp_sync(1 + g, NT);
+        gemm_lat<M, false>(t, sM, sP, r0, c);
+        if (hasQ) gemm_lat<M, false>(o2, sM, sQ, r0, c);
+    } else {
+#pragma unroll
+        for (int u = 0; u < R; ++u) mult_out[(r0 + u) * M + c] = 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < R; ++u) o2_out[(r0 + u) * M + c] = o2[u];
+    if (g == 0) {
+#pragma unroll
+        for (int u = 0; u < R; ++u) sT[(r0 + u) * LD + c] = t[u];
+    }
     __syncthreads();
-    if (left) {
-        load_blk<double, M>(s0, a.C + (r - 1) * MM);
-        load_blk<double, M>(s1, a.B + (r - 1) * MM);
-        __syncthreads();
-        gemm_acc<double, M, false>(d, sal, s0, o);
-        if (r - 1 >= 1) gemm_acc<double, M, false>(bn, sal, s1, o);
-        __syncthreads();
+    if (g == 1) {
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            const int i = r0 + u;
+            a.Dn[q * MM + i * M + c] = (a.D[r * MM + i * M + c] + sT[i * LD + c]) + t[u];
+        }
     }
-    if (right) {
-        load_blk<double, M>(s0, a.B + (r + 1) * MM);
-        load_blk<double, M>(s1, a.C + (r + 1) * MM);
-        __syncthreads();
-        gemm_acc<double, M, false>(d, sga, s0, o);
-        if (r + 2 < a.K) gemm_acc<double, M, false>(cn, sga, s1, o);
-    }
-    store_own<double, M>(a.Dn + q * MM, d, o);
-    store_own<double, M>(a.Bn + q * MM, bn, o);
-    store_own<double, M>(a.Cn + q * MM, cn, o);
 }
 
 // f'_q = f_{2q} + alpha_q f_{2q-1} + gamma_q f_{2q+1}; with K == 1: x = D^{-1} f.
@@ -135,9 +245,7 @@ __global__ void __launch_bounds__(8 * M) k_bcr_rhs(const BcrArgs a) {
         __syncthreads();
         for (int el = threadIdx.x; el < E; el += S::NT) {
             const int rr = el / nr, c = el % nr;
-            double acc = 0.0;
-            for (int k = 0; k < M; ++k) acc = fma(s0[rr * S::LD + k], v0[k * nr + c], acc);
-            a.X[el] = acc;
+            a.X[el] = dot_lat<M>(s0 + rr * S::LD, v0 + c, nr);
         }
         return;
     }
@@ -152,12 +260,9 @@ __global__ void __launch_bounds__(8 * M) k_bcr_rhs(const BcrArgs a) {
     __syncthreads();
     for (int el = threadIdx.x; el < E; el += S::NT) {
         const int rr = el / nr, c = el % nr;
-        double acc = a.F[r * E + el];
-        if (left)
-            for (int k = 0; k < M; ++k) acc = fma(s0[rr * S::LD + k], v0[k * nr + c], acc);
-        if (right)
-            for (int k = 0; k < M; ++k) acc = fma(s1[rr * S::LD + k], v1[k * nr + c], acc);
-        a.Fn[q * E + el] = acc;
+        const double dl = left ? dot_lat<M>(s0 + rr * S::LD, v0 + c, nr) : 0.0;
+        const double dr = right ? dot_lat<M>(s1 + rr * S::LD, v1 + c, nr) : 0.0;
+        a.Fn[q * E + el] = a.F[r * E + el] + (dl + dr);
     }
 }
 
@@ -190,18 +295,14 @@ __global__ void __launch_bounds__(8 * M) k_bcr_back(const BcrArgs a) {
     __syncthreads();
     for (int el = threadIdx.x; el < E; el += S::NT) {
         const int rr = el / nr, c = el % nr;
-        double acc = a.F[r * E + el];
-        for (int k = 0; k < M; ++k) acc = fma(-s0[rr * S::LD + k], v0[k * nr + c], acc);
-        if (right)
-            for (int k = 0; k < M; ++k) acc = fma(-s1[rr * S::LD + k], v1[k * nr + c], acc);
-        t[el] = acc;
+        const double bl = dot_lat<M>(s0 + rr * S::LD, v0 + c, nr);
+        const double cr = right ? dot_lat<M>(s1 + rr * S::LD, v1 + c, nr) : 0.0;
+        t[el] = a.F[r * E + el] - (bl + cr);
     }
     __syncthreads();
     for (int el = threadIdx.x; el < E; el += S::NT) {
         const int rr = el / nr, c = el % nr;
-        double acc = 0.0;
-        for (int k = 0; k < M; ++k) acc = fma(s2[rr * S::LD + k], t[k * nr + c], acc);
-        a.X[r * E + el] = acc;
+        a.X[r * E + el] = dot_lat<M>(s2 + rr * S::LD, t + c, nr);
     }
 }
 

@@ -199,8 +199,7 @@ struct Inst {
             if (e == cudaSuccess) e = set_smem(k_factor_cta_batch<double, M, 1>, f64);
             if (e == cudaSuccess) e = set_smem(k_factor_cta_batch<float, M, 0>, f32);
             if (e == cudaSuccess) e = set_smem(k_factor_cta_batch<float, M, 1>, f32);
-            if (e == cudaSuccess) e = set_smem(k_bcr_inv<M>, bcr_smem_bytes<M>());
-            if (e == cudaSuccess) e = set_smem(k_bcr_update<M>, bcr_smem_bytes<M>());
+            if (e == cudaSuccess) e = set_smem(k_bcr_factor<M>, bcr_factor_smem_bytes<M>());
             if (e == cudaSuccess) e = set_smem(k_bcr_rhs<M>, bcr_vec_smem_bytes<M>());
             if (e == cudaSuccess) e = set_smem(k_bcr_back<M>, bcr_vec_smem_bytes<M>());
             return e;
@@ -209,19 +208,16 @@ struct Inst {
     }
     // ------------------------------------------------------ cyclic reduction --
     template <typename K>
-    static cudaError_t launch_bcr(K k, size_t smem, const BcrArgs& a, long long ctas, cudaStream_t s) {
+    static cudaError_t launch_bcr(K k, size_t smem, const BcrArgs& a, long long ctas, cudaStream_t s,
+                                  int threads = 8 * M) {
         if (ctas <= 0) return cudaSuccess;
         cudaError_t e = set_smem(k, smem);
         if (e != cudaSuccess) return e;
-        k<<<(unsigned)ctas, 8 * M, smem, s>>>(a);
+        k<<<(unsigned)ctas, threads, smem, s>>>(a);
         return cudaGetLastError();
     }
-    static cudaError_t bcr_inv(const BcrArgs& a, long long ctas, cudaStream_t s) {
-        if constexpr (M >= 8) return launch_bcr(k_bcr_inv<M>, bcr_smem_bytes<M>(), a, ctas, s);
-        return cudaErrorNotSupported;
-    }
-    static cudaError_t bcr_update(const BcrArgs& a, long long ctas, cudaStream_t s) {
-        if constexpr (M >= 8) return launch_bcr(k_bcr_update<M>, bcr_smem_bytes<M>(), a, ctas, s);
+    static cudaError_t bcr_factor(const BcrArgs& a, long long ctas, cudaStream_t s) {
+        if constexpr (M >= 8) return launch_bcr(k_bcr_factor<M>, bcr_factor_smem_bytes<M>(), a, ctas, s, 16 * M);
         return cudaErrorNotSupported;
     }
     static cudaError_t bcr_rhs(const BcrArgs& a, long long ctas, cudaStream_t s) {
@@ -243,8 +239,7 @@ struct Inst {
                                     M >= 8 ? solve_smem_bytes<float, M>() : 0,
                                     M >= 8 ? assemble_rhs_smem_bytes<M>() : 0,
                                     prepare,
-                                    M >= 8 ? bcr_inv : nullptr,
-                                    M >= 8 ? bcr_update : nullptr,
+                                    M >= 8 ? bcr_factor : nullptr,
                                     M >= 8 ? bcr_rhs : nullptr,
                                     M >= 8 ? bcr_back : nullptr};
         return &L;

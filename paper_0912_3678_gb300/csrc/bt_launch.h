@@ -35,8 +35,7 @@ struct Launchers {
     // make sure every kernel of this m has its shared-memory attribute set
     cudaError_t (*prepare)();
     // block cyclic reduction of the reduced system (m >= 8; null otherwise)
-    cudaError_t (*bcr_inv)(const BcrArgs&, long long ctas, cudaStream_t);
-    cudaError_t (*bcr_update)(const BcrArgs&, long long ctas, cudaStream_t);
+    cudaError_t (*bcr_factor)(const BcrArgs&, long long ctas, cudaStream_t);   // one reduction step
     cudaError_t (*bcr_rhs)(const BcrArgs&, long long ctas, cudaStream_t);
     cudaError_t (*bcr_back)(const BcrArgs&, long long ctas, cudaStream_t);
 };
