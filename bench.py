@@ -299,6 +299,8 @@ def main():
     ap.add_argument("--paths", default="fp64,fp32_ir")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="use the built-in partitioning instead of the autotuner")
+    ap.add_argument("--tuning", default=None,
+                    help='fixed partitioning for every path instead of the autotuner, as JSON, e.g. {"p0": 608, "reduced": 1}')
     ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of one CUDA graph per step")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -353,7 +355,11 @@ def main():
     results = {}
     paths = [p for p in args.paths.split(",") if p]
     tunings = {}
-    if w["kind"] == "btri" and not args.no_tune:
+    if w["kind"] == "btri" and args.tuning:
+        fixed = json.loads(args.tuning)
+        for prec in paths:
+            tunings[prec] = dict(fixed)
+    elif w["kind"] == "btri" and not args.no_tune:
         from paper_0912_3678_gb300 import tune
         tuner = tune.Tuner(os.path.join(ROOT, "paper_0912_3678_gb300", "_build", "tune_cache.json"))
         for prec in paths:

@@ -19,18 +19,17 @@ __device__ __forceinline__ void report(long long* st, int code, long long level,
     }
 }
 
-// 1/x.  For x well inside the float range: a float reciprocal seed r0 refined
-// by one third-order Newton step, r = r0 (1 + e + e^2) with e = 1 - x r0,
-// i.e. the geometric series of 1/(1 - e) truncated after e^2 (relative error
-// about e^3 ~ 2^-66 before the final rounding).  Zero, subnormal, huge and
-// non-finite x take the IEEE division.
+// 1/x.  A hardware reciprocal seed r0 (rcp.approx.ftz.f64, relative error
+// below 2^-19 over the normal range) refined by one third-order Newton step,
+// r = r0 (1 + e + e^2) with e = 1 - x r0, i.e. the geometric series of
+// 1/(1 - e) truncated after e^2 (relative error about e^3 before the final
+// rounding).  Zero, subnormal, huge (1/x subnormal) and non-finite x take the
+// IEEE division.
 __device__ __forceinline__ double rcp(double x) {
     const int ex = (__double2hiint(x) >> 20) & 0x7ff;
-    if (ex < 1023 - 120 || ex > 1023 + 120) return 1.0 / x;
-    const float xf = __double2float_rn(x);
-    float r0f;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0f) : "f"(xf));
-    const double r0 = (double)r0f;
+    if (ex < 1 || ex > 2044) return 1.0 / x;
+    double r0;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r0) : "d"(x));
     const double e = fma(-x, r0, 1.0);
     const double t = fma(e, e, e);
     return fma(r0, t, r0);
