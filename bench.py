@@ -300,7 +300,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="use the built-in partitioning instead of the autotuner")
     ap.add_argument("--tuning", default=None,
-                    help='fixed partitioning for every path instead of the autotuner, as JSON, e.g. {"p0": 608, "reduced": 1}')
+                    help="fixed partitioning for every path instead of the autotuner: key=value pairs "
+                         "of bt_tuning, e.g. p0=608,reduced=1")
     ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of one CUDA graph per step")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -356,7 +357,7 @@ def main():
     paths = [p for p in args.paths.split(",") if p]
     tunings = {}
     if w["kind"] == "btri" and args.tuning:
-        fixed = json.loads(args.tuning)
+        fixed = {k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(",") if kv)}
         for prec in paths:
             tunings[prec] = dict(fixed)
     elif w["kind"] == "btri" and not args.no_tune:
