@@ -9,6 +9,8 @@
 // and after the single remaining row is solved the odd rows are recovered:
 //   x_{2q+1} = D_{2q+1}^{-1} (f_{2q+1} - B_{2q+1} x_{2q} - C_{2q+1} x_{2q+2}).
 #pragma once
+#include <cooperative_groups.h>
+
 #include "bt_cta.cuh"
 
 namespace bt {
@@ -36,10 +38,6 @@ struct BcrArgs {
 // FP64 dot product of length M is split over four partial sums (dependency
 // chains of M/4 instead of M), and one launch per level does the whole
 // elimination step.
-
-__device__ __forceinline__ void grp_sync(int id, int nthreads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
 
 // acc[q] += sgn * (A B)[r0+q][c] over four partial sums.
 template <int M, bool NEG>
@@ -77,106 +75,50 @@ __device__ __forceinline__ double dot_lat(const double* Arow, const double* v, i
     return (p0 + p1) + (p2 + p3);
 }
 
-// Gauss-Jordan inverse with partial pivoting (the steps of gj_inverse) run by
-// a group of 8M threads (group-local index gtid) synchronised on named
-// barrier `bar`, so that two groups of one CTA invert two blocks at once.
-template <int M>
-__device__ void gj_inverse_grp(double* a, double* colk, int* perm, long long* st, int level, long long row,
-                               int gtid, int bar) {
-    using S = Cta<double, M>;
-    constexpr int NT = S::NT, NW = NT / 32, LD = S::LD;
-    const int lane = gtid & 31, warp = gtid >> 5;
-    const int r0 = (gtid / M) * S::R, c = gtid % M;
-    for (int k = 0; k < M; ++k) {
-        if (warp == k % NW) {
-            const double v = (lane < M) ? a[lane * LD + k] : 0.0;
-            const unsigned key = (lane >= k && lane < M) ? ((mag_key<double>(v) << 5) | (unsigned)(31 - lane)) : 0u;
-            const unsigned best = __reduce_max_sync(0xffffffffu, key);
-            const int p = 31 - (int)(best & 31u);
-            double pv = __shfl_sync(0xffffffffu, v, p);
-            const double vk = __shfl_sync(0xffffffffu, v, k);
-            if (pv == 0.0 || nonfinite(pv)) {
-                if (lane == 0) report(st, pv == 0.0 ? ST_SINGULAR : ST_NONFINITE, level, -2, row);
-                pv = 1.0;
-            }
-            const double r = rcp(pv);
-            if (lane < M) {
-                colk[lane] = (lane == k) ? 0.0 : (lane == p ? vk : v);
-                const double tk = a[k * LD + lane];
-                const double tp = a[p * LD + lane];
-                a[p * LD + lane] = tk;
-                a[k * LD + lane] = (lane == k) ? r : tp * r;
-            }
-            if (lane == 0) perm[k] = p;
-        }
-        grp_sync(bar, NT);
-#pragma unroll
-        for (int q = 0; q < S::R; ++q) {
-            const int i = r0 + q;
-            if (i != k) {
-                const double l = colk[i];
-                const double akc = a[k * LD + c];
-                a[i * LD + c] = (c == k) ? -l * akc : fma(-l, akc, a[i * LD + c]);
-            }
-        }
-        grp_sync(bar, NT);
-    }
-    if (warp == 0 && lane < M) {
-        for (int k = M - 1; k >= 0; --k) {
-            const int p = perm[k];
-            if (p != k) {
-                const double t = a[lane * LD + k];
-                a[lane * LD + k] = a[lane * LD + p];
-                a[lane * LD + p] = t;
-            }
-        }
-    }
-    grp_sync(bar, NT);
-}
-
 template <int M>
 constexpr size_t bcr_factor_smem_bytes() {
-    return sizeof(double) * (11 * Cta<double, M>::BLK + 2 * M) + sizeof(int) * 2 * M;
+    return sizeof(double) * (6 * Cta<double, M>::BLK + M) + sizeof(int) * M;
 }
 
-// One reduction step for kept row r = 2q, by 16M threads in two groups:
-// group 0 inverts the left odd neighbour r-1 and forms alpha_q with its
-// products alpha C_{r-1} and B' = alpha B_{r-1}; group 1 inverts the right odd
-// neighbour r+1 (stored as Dinv[q]) and forms gamma_q, gamma B_{r+1} and
-// C' = gamma C_{r+1}; then D' = D_r + alpha C_{r-1} + gamma B_{r+1}.  Each odd
-// row is inverted by both kept rows next to it, which costs one extra block
-// inverse per kept row and saves a launch and a grid-wide dependency per level.
-// With K == 1 group 0 inverts the single row into Dinv[0].
+// One reduction step for kept row r = 2q by a cluster of two CTAs on two SMs
+// (one CTA per SM holds the FP64 pipe about half busy on this work, so the
+// two sides of the elimination are split): rank 0 inverts the left odd
+// neighbour r-1 and forms alpha_q, alpha C_{r-1} and B' = alpha B_{r-1};
+// rank 1 inverts the right odd neighbour r+1 (stored as Dinv[q]) and forms
+// gamma_q, gamma B_{r+1} and C' = gamma C_{r+1}; after a cluster barrier rank 1
+// reads alpha C_{r-1} from rank 0's shared memory and writes
+// D' = D_r + alpha C_{r-1} + gamma B_{r+1}.  Each odd row is inverted by the
+// clusters of both kept rows next to it (one launch and no grid-wide
+// dependency per level).  With K == 1 rank 0 inverts the single row into Dinv[0].
 template <int M>
-__global__ void __launch_bounds__(16 * M) k_bcr_factor(const BcrArgs a) {
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(8 * M) k_bcr_factor(const BcrArgs a) {
     using S = Cta<double, M>;
     constexpr int NT = S::NT, BLK = S::BLK, LD = S::LD, R = S::R;
     constexpr long long MM = S::MM;
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* base = reinterpret_cast<double*>(smem_raw);
-    const int g = threadIdx.x / NT, gtid = threadIdx.x % NT;
-    double* sI = base + g * 5 * BLK;   // block being inverted
-    double* sO = sI + BLK;             // B_r (group 0) or C_r (group 1)
-    double* sP = sI + 2 * BLK;         // C_{r-1} or B_{r+1}
-    double* sQ = sI + 3 * BLK;         // B_{r-1} or C_{r+1}
-    double* sM = sI + 4 * BLK;         // alpha or gamma
-    double* sT = base + 10 * BLK;      // alpha C_{r-1} from group 0
-    double* colk = base + 11 * BLK + g * M;
-    int* perm = reinterpret_cast<int*>(base + 11 * BLK + 2 * M) + g * M;
-    const int r0 = (gtid / M) * R, c = gtid % M;
-    auto load = [&](double* dst, const double* src) {
-        for (int idx = gtid; idx < M * M; idx += NT) dst[(idx / M) * LD + idx % M] = src[idx];
-    };
+    double* sI = reinterpret_cast<double*>(smem_raw);   // block being inverted
+    double* sO = sI + BLK;                               // B_r (rank 0) or C_r (rank 1)
+    double* sP = sI + 2 * BLK;                           // C_{r-1} or B_{r+1}
+    double* sQ = sI + 3 * BLK;                           // B_{r-1} or C_{r+1}
+    double* sM = sI + 4 * BLK;                           // alpha or gamma
+    double* sT = sI + 5 * BLK;                           // alpha C_{r-1} or gamma B_{r+1}
+    double* colk = sI + 6 * BLK;
+    int* perm = reinterpret_cast<int*>(colk + M);
+    const int g = (int)cl.block_rank();
+    const Own<double, M> o;
+    const long long q = blockIdx.x / 2;
     if (a.K == 1) {
         if (g == 0) {
-            load(sI, a.D);
-            grp_sync(1, NT);
-            gj_inverse_grp<M>(sI, colk, perm, a.status, a.level, 0, gtid, 1);
-            for (int idx = gtid; idx < M * M; idx += NT) a.Dinv[idx] = sI[(idx / M) * LD + idx % M];
+            load_blk<double, M>(sI, a.D);
+            __syncthreads();
+            gj_inverse<double, M>(sI, colk, perm, a.status, a.level, -2, 0);
+            store_blk<double, M>(a.Dinv, sI);
         }
         return;
     }
-    const long long q = blockIdx.x, r = 2 * q;
+    const long long r = 2 * q;
     const bool has = (g == 0) ? (q >= 1) : (r + 1 < a.K);
     const bool hasQ = (g == 0) ? (r - 1 >= 1) : (r + 2 < a.K);
     double t[R], o2[R];
@@ -186,44 +128,39 @@ __global__ void __launch_bounds__(16 * M) k_bcr_factor(const BcrArgs a) {
     double* o2_out = (g == 0 ? a.Bn : a.Cn) + q * MM;
     if (has) {
         const long long nb = (g == 0) ? r - 1 : r + 1;
-        load(sI, a.D + nb * MM);
-        load(sO, (g == 0 ? a.B : a.C) + r * MM);
-        load(sP, (g == 0 ? a.C : a.B) + nb * MM);
-        if (hasQ) load(sQ, (g == 0 ? a.B : a.C) + nb * MM);
-        grp_sync(1 + g, NT);
-        gj_inverse_grp<M>(sI, colk, perm, a.status, a.level, nb, gtid, 1 + g);
-        if (g == 1)
-            for (int idx = gtid; idx < M * M; idx += NT) a.Dinv[q * MM + idx] = sI[(idx / M) * LD + idx % M];
+        load_blk<double, M>(sI, a.D + nb * MM);
+        load_blk<double, M>(sO, (g == 0 ? a.B : a.C) + r * MM);
+        load_blk<double, M>(sP, (g == 0 ? a.C : a.B) + nb * MM);
+        if (hasQ) load_blk<double, M>(sQ, (g == 0 ? a.B : a.C) + nb * MM);
+        __syncthreads();
+        gj_inverse<double, M>(sI, colk, perm, a.status, a.level, -2, nb);
+        if (g == 1) store_blk<double, M>(a.Dinv + q * MM, sI);
         double mult[R];
 #pragma unroll
         for (int u = 0; u < R; ++u) mult[u] = 0.0;
-        gemm_lat<M, true>(mult, sO, sI, r0, c);
-#pragma unroll
-        for (int u = 0; u < R; ++u) {
-            sM[(r0 + u) * LD + c] = mult[u];
-            mult_out[(r0 + u) * M + c] = mult[u];
-        }
-        grp_sync(1 + g, NT);
-        gemm_lat<M, false>(t, sM, sP, r0, c);
-        if (hasQ) gemm_lat<M, false>(o2, sM, sQ, r0, c);
+        gemm_lat<M, true>(mult, sO, sI, o.r0, o.c);
+        write_own<double, M>(sM, mult, o);
+        store_own<double, M>(mult_out, mult, o);
+        __syncthreads();
+        gemm_lat<M, false>(t, sM, sP, o.r0, o.c);
+        if (hasQ) gemm_lat<M, false>(o2, sM, sQ, o.r0, o.c);
     } else {
-#pragma unroll
-        for (int u = 0; u < R; ++u) mult_out[(r0 + u) * M + c] = 0.0;
+        double z[R];
+        zero_own<double, M>(z);
+        store_own<double, M>(mult_out, z, o);
     }
-#pragma unroll
-    for (int u = 0; u < R; ++u) o2_out[(r0 + u) * M + c] = o2[u];
-    if (g == 0) {
-#pragma unroll
-        for (int u = 0; u < R; ++u) sT[(r0 + u) * LD + c] = t[u];
-    }
-    __syncthreads();
+    store_own<double, M>(o2_out, o2, o);
+    write_own<double, M>(sT, t, o);
+    cl.sync();   // rank 0's alpha C_{r-1} is visible to rank 1
     if (g == 1) {
+        const double* rT = cl.map_shared_rank(sT, 0);
 #pragma unroll
         for (int u = 0; u < R; ++u) {
-            const int i = r0 + u;
-            a.Dn[q * MM + i * M + c] = (a.D[r * MM + i * M + c] + sT[i * LD + c]) + t[u];
+            const int i = o.r0 + u;
+            a.Dn[q * MM + i * M + o.c] = (a.D[r * MM + i * M + o.c] + rT[i * LD + o.c]) + t[u];
         }
     }
+    cl.sync();   // rank 0 keeps its shared memory until rank 1 has read it
 }
 
 // f'_q = f_{2q} + alpha_q f_{2q-1} + gamma_q f_{2q+1}; with K == 1: x = D^{-1} f.

@@ -208,16 +208,15 @@ struct Inst {
     }
     // ------------------------------------------------------ cyclic reduction --
     template <typename K>
-    static cudaError_t launch_bcr(K k, size_t smem, const BcrArgs& a, long long ctas, cudaStream_t s,
-                                  int threads = 8 * M) {
+    static cudaError_t launch_bcr(K k, size_t smem, const BcrArgs& a, long long ctas, cudaStream_t s) {
         if (ctas <= 0) return cudaSuccess;
         cudaError_t e = set_smem(k, smem);
         if (e != cudaSuccess) return e;
-        k<<<(unsigned)ctas, threads, smem, s>>>(a);
+        k<<<(unsigned)ctas, 8 * M, smem, s>>>(a);
         return cudaGetLastError();
     }
     static cudaError_t bcr_factor(const BcrArgs& a, long long ctas, cudaStream_t s) {
-        if constexpr (M >= 8) return launch_bcr(k_bcr_factor<M>, bcr_factor_smem_bytes<M>(), a, ctas, s, 16 * M);
+        if constexpr (M >= 8) return launch_bcr(k_bcr_factor<M>, bcr_factor_smem_bytes<M>(), a, 2 * ctas, s);
         return cudaErrorNotSupported;
     }
     static cudaError_t bcr_rhs(const BcrArgs& a, long long ctas, cudaStream_t s) {
