@@ -95,7 +95,18 @@ bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int p
  *                1 = block cyclic reduction (the cyclic-reduction variant of
  *                Sec. 2 with one synchronisation per reduction step)
  *   tp_block     CTA shape of the thread-per-partition kernels used for m <= 4:
- *                threads per CTA, 64, 128 or 256 (0: 128) */
+ *                threads per CTA, 64, 128 or 256 (0: 128)
+ *   local        local factorization of a block tridiagonal plan with m >= 8:
+ *                0 = block LU with fill-in spikes (default); L >= 1 = cyclic
+ *                reduction inside partitions of 2^L block rows (the
+ *                cyclic-reduction factorization of Sec. 2: no fill-in spikes;
+ *                the separators are the block rows at multiples of 2^L).  All
+ *                partitions take their reduction steps together, one launch
+ *                per step; the steps run in the plan's local precision (FP32
+ *                for BT_FP32_IR and BT_BF16_IR) and the reduced system left
+ *                after L steps is solved by FP64 cyclic reduction.  L is capped
+ *                so that at least the last block row is FP64.  p0, ctas_per_sm,
+ *                sub_rows, top_rows and reduced are then unused. */
 typedef struct {
     int64_t p0;
     int ctas_per_sm;
@@ -103,6 +114,7 @@ typedef struct {
     int top_rows;
     int reduced;
     int tp_block;
+    int local;
 } bt_tuning;
 
 /* bt_plan_create with explicit partitioning parameters (NULL = defaults). */
@@ -214,8 +226,12 @@ bt_status bt_plan_bytes(bt_plan plan, int64_t* bytes);
  *   gamma[s] = T[s][s+1] (gamma[p-2] = 0), each [p-1][m][m] in FP64.
  * For a BABD plan: alpha[i], beta[i] for the p+1 reduced rows of Eq.
  * (redmatr1) (lower block bidiagonal; beta[0] = the corner block),
- * gamma is not written.  Not available for plans whose block order is
- * embedded in a larger one (BT_ERR_INVALID). */
+ * gamma is not written.  For a plan with local cyclic reduction
+ * (bt_tuning.local = L) of BT_FP64 precision: the system left on the K
+ * separators (block rows 0, 2^L, 2*2^L, ... < nblk), K = nblk halved L times
+ * rounding up, in the same form (alpha, beta, gamma each [K][m][m]).  Not
+ * available for plans whose block order is embedded in a larger one
+ * (BT_ERR_INVALID). */
 bt_status bt_reduced_export(bt_plan plan, double* alpha, double* beta, double* gamma);
 
 /* Tracing.  bt_plan_trace(plan, 1) clears the records and brackets every

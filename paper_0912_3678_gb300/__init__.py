@@ -75,7 +75,8 @@ def _tuning(t):
     if isinstance(t, BtTuning):
         return t
     return BtTuning(int(t.get("p0", 0)), int(t.get("ctas_per_sm", 0)), int(t.get("sub_rows", 0)),
-                    int(t.get("top_rows", 0)), int(t.get("reduced", 0)), int(t.get("tp_block", 0)))
+                    int(t.get("top_rows", 0)), int(t.get("reduced", 0)), int(t.get("tp_block", 0)),
+                    int(t.get("local", 0)))
 
 
 def bt_plan_create_tuned(nblk, m, nrhs_max=1, prec="fp64", tuning=None, stream=None):
@@ -401,6 +402,7 @@ class BtPlan(_PlanBase):
         self.m, self.n, self.nrhs_max, self.prec, self.stream = int(m), int(nblk), int(nrhs_max), prec, stream
         self.rows = self.n
         self.handle = bt_plan_create_tuned(nblk, m, nrhs_max, prec, tuning, stream)
+        self._local = int((tuning or {}).get("local", 0)) if isinstance(tuning, (dict, type(None))) else int(tuning.local)
         self._keep = ()
         self._torch = torch
         return self
@@ -428,9 +430,17 @@ class BtPlan(_PlanBase):
         return bt_plan_anorm(self.handle)
 
     def reduced(self):
-        """Top-level reduced matrix (alpha, beta, gamma) of Eq. (redmatr)."""
+        """Top-level reduced matrix (alpha, beta, gamma) of Eq. (redmatr); with
+        local cyclic reduction, the FP64 system on the separators."""
         lev = self.levels()
         q = lev[0][1] - 1
+        if getattr(self, "_local", 0) > 0:
+            steps, K = 0, self.n
+            while K > 1:
+                K, steps = (K + 1) // 2, steps + 1
+            q = self.n
+            for _ in range(min(self._local, steps)):
+                q = (q + 1) // 2
         t = self._torch
         dev = self._keep[1].device
         a = t.empty((q, self.m, self.m), dtype=t.float64, device=dev)
@@ -458,7 +468,7 @@ class BtBatch:
             if tun is None and tuner is not None:
                 tun = tuner(m, N, prec)
             descs.append(BtBatchDesc(N, m, _prec(prec), nr, _ptr(sd["B"]), _ptr(D), _ptr(sd["C"]), _ptr(F),
-                                     _ptr(sd["X"]), _tuning(tun) or BtTuning(0, 0, 0, 0, 0, 0)))
+                                     _ptr(sd["X"]), _tuning(tun) or BtTuning(0, 0, 0, 0, 0, 0, 0)))
             self._keep.append((sd["B"], D, sd["C"], F, sd["X"]))
         self.count = len(descs)
         self.handle = bt_batch_create(descs, ir_sweeps, mem_cap_bytes, stream)

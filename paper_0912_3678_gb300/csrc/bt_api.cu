@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 #include <cmath>
 #include <cstdint>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -67,6 +68,7 @@ struct bt_plan_s {
     double* B1 = nullptr;
     double* keep = nullptr;             // BABD top-level pivot rows
     bool bcr = false;                   // reduced system by block cyclic reduction
+    int local = 0;                      // level-0 local cyclic-reduction steps (plans without partition levels)
     bool padded = false;                // caller blocks of order mu embedded in order m
     double* Ap[3] = {nullptr, nullptr, nullptr};   // padded matrices (B/S, D/R, C)
     double* Fp = nullptr;               // padded right-hand side / solution / residual
@@ -185,19 +187,24 @@ void layout(bt_plan_s* P, Arena& ar) {
             b.K = K;
             b.level = P->nlev + (int)q;
             b.nr = nr;
+            // factor storage in the level's arithmetic type, the next level's
+            // matrix in its input type
+            const int md = b.mode;
+            const size_t tsz = (md == bt::BCR_F64) ? sizeof(double) : sizeof(float);
+            const size_t osz = (md == bt::BCR_F32_FIRST || md == bt::BCR_F32) ? sizeof(float) : sizeof(double);
             const long long keep = (K + 1) / 2, odd = (K == 1) ? 1 : K / 2;
             if (q == 0) {
                 b.B = h.a.B; b.D = h.a.D; b.C = h.a.C;
                 b.F = h.a.F; b.X = h.a.X;
             }
-            b.Dinv = (double*)ar.take(sizeof(double) * odd * mm);
+            b.Dinv = ar.take(tsz * odd * mm);
             if (K > 1) {
-                b.al = (double*)ar.take(sizeof(double) * keep * mm);
-                b.ga = (double*)ar.take(sizeof(double) * keep * mm);
+                b.al = ar.take(tsz * keep * mm);
+                b.ga = ar.take(tsz * keep * mm);
                 bt::BcrArgs& n = P->bl[q + 1];
-                b.Bn = (double*)ar.take(sizeof(double) * keep * mm);
-                b.Dn = (double*)ar.take(sizeof(double) * keep * mm);
-                b.Cn = (double*)ar.take(sizeof(double) * keep * mm);
+                b.Bn = ar.take(osz * keep * mm);
+                b.Dn = ar.take(osz * keep * mm);
+                b.Cn = ar.take(osz * keep * mm);
                 b.Fn = (double*)ar.take(sizeof(double) * keep * m * nr);
                 double* Xn = (double*)ar.take(sizeof(double) * keep * m * nr);
                 b.Xn = Xn;
@@ -259,7 +266,7 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
         P->lv.push_back(v);
     }
     P->nlev = (int)P->lv.size() - 1;
-    P->bcr = (kind == 0 && P->nlev >= 1 && P->lv[P->nlev].a.p == 0);
+    P->bcr = (kind == 0 && P->lv[P->nlev].a.p == 0 && (P->nlev >= 1 || tune.local > 0));
     if (P->bcr) {
         long long K = P->lv[P->nlev].a.N;
         int n = 1;
@@ -268,6 +275,19 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
             ++n;
         }
         P->bl.assign(n, bt::BcrArgs{});
+        // local cyclic-reduction steps (level 0 only): at least the last row stays FP64
+        P->local = (P->nlev == 0) ? std::min(tune.local, n - 1) : 0;
+        const bool lo = prec != BT_FP64;
+        for (int q = 0; q < n; ++q) {
+            int mode = bt::BCR_F64;
+            if (lo && q < P->local) {
+                if (P->local == 1) mode = bt::BCR_F32_ONLY;
+                else if (q == 0) mode = bt::BCR_F32_FIRST;
+                else if (q == P->local - 1) mode = bt::BCR_F32_LAST;
+                else mode = bt::BCR_F32;
+            }
+            P->bl[q].mode = mode;
+        }
     }
     if (kind == 0) {
         // the top level is a single partition; levels below it have >= 2
@@ -375,7 +395,13 @@ bt_status run_factor(bt_plan_s* P) {
         Level& v = P->lv[l];
         if (P->kind == 1 && l == P->nlev) break;   // BABD top: direct solve at solve time
         if (P->bcr && l == P->nlev) {
-            // block cyclic reduction of the reduced system
+            // block cyclic reduction of the reduced system (or of the whole
+            // matrix: local cyclic reduction, then the reduced system)
+            if (P->nlev == 0) {
+                P->bl[0].B = v.a.B;
+                P->bl[0].D = v.a.D;
+                P->bl[0].C = v.a.C;
+            }
             for (size_t q = 0; q < P->bl.size(); ++q) {
                 bt::BcrArgs& b = P->bl[q];
                 const long long ctas = (b.K == 1) ? 1 : (b.K + 1) / 2;
@@ -411,6 +437,10 @@ bt_status run_solve(bt_plan_s* P, const double* F, double* X, int nr) {
     cudaError_t e;
     if (P->bcr) {
         e = cudaSuccess;
+        if (P->nlev == 0) {
+            P->bl[0].F = F;
+            P->bl[0].X = X;
+        }
         for (size_t q = 0; q < P->bl.size() && e == cudaSuccess; ++q) {
             bt::BcrArgs& b = P->bl[q];
             b.nr = nr;
@@ -588,6 +618,7 @@ static bt::Tuning to_tuning(const bt_tuning* t, int64_t p) {
         u.top_rows = t->top_rows;
         u.reduced = t->reduced;
         u.tp_block = t->tp_block;
+        u.local = t->local;
     }
     if (p > 0) u.p0 = p;
     return u;
@@ -600,7 +631,7 @@ bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int p
 bt_status bt_plan_create_tuned(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int prec, const bt_tuning* tuning,
                                void* stream) {
     if (tuning && (tuning->p0 < 0 || tuning->ctas_per_sm < 0 || tuning->sub_rows < 0 || tuning->top_rows < 0 ||
-                   tuning->reduced < 0 || tuning->reduced > 1 ||
+                   tuning->reduced < 0 || tuning->reduced > 1 || tuning->local < 0 || tuning->local > 62 ||
                    !(tuning->tp_block == 0 || tuning->tp_block == 64 || tuning->tp_block == 128 ||
                      tuning->tp_block == 256)))
         return BT_ERR_INVALID;
@@ -932,8 +963,18 @@ bt_status bt_plan_bytes(bt_plan P, int64_t* bytes) {
 
 bt_status bt_reduced_export(bt_plan P, double* alpha, double* beta, double* gamma) {
     if (!P || !P->factored || !alpha || !beta || P->padded) return BT_ERR_INVALID;
-    if (P->nlev < 1) return BT_ERR_INVALID;
     const size_t mm = (size_t)P->m * P->m * sizeof(double);
+    if (P->kind == 0 && P->nlev == 0 && P->bcr && P->local > 0) {
+        // local cyclic reduction: the FP64 system left on the separators
+        const bt::BcrArgs& b = P->bl[P->local];
+        if (!gamma || b.mode != bt::BCR_F64) return BT_ERR_INVALID;
+        const size_t bytes = mm * (size_t)b.K;
+        cudaError_t e = cudaMemcpyAsync(alpha, b.D, bytes, cudaMemcpyDeviceToDevice, P->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(beta, b.B, bytes, cudaMemcpyDeviceToDevice, P->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(gamma, b.C, bytes, cudaMemcpyDeviceToDevice, P->stream);
+        return from_cuda(e);
+    }
+    if (P->nlev < 1) return BT_ERR_INVALID;
     const Level& u = P->lv[0];
     cudaError_t e;
     if (P->kind == 0) {

@@ -199,9 +199,9 @@ struct Inst {
             if (e == cudaSuccess) e = set_smem(k_factor_cta_batch<double, M, 1>, f64);
             if (e == cudaSuccess) e = set_smem(k_factor_cta_batch<float, M, 0>, f32);
             if (e == cudaSuccess) e = set_smem(k_factor_cta_batch<float, M, 1>, f32);
-            if (e == cudaSuccess) e = set_smem(k_bcr_factor<M>, bcr_factor_smem_bytes<M>());
-            if (e == cudaSuccess) e = set_smem(k_bcr_rhs<M>, bcr_vec_smem_bytes<M>());
-            if (e == cudaSuccess) e = set_smem(k_bcr_back<M>, bcr_vec_smem_bytes<M>());
+            if (e == cudaSuccess) e = set_smem(k_bcr_factor<double, double, double, M>, bcr_factor_smem_bytes<double, M>());
+            if (e == cudaSuccess) e = set_smem(k_bcr_rhs<double, M>, bcr_vec_smem_bytes<double, M>());
+            if (e == cudaSuccess) e = set_smem(k_bcr_back<double, double, M>, bcr_vec_smem_bytes<double, M>());
             return e;
         }
         return cudaSuccess;
@@ -216,15 +216,34 @@ struct Inst {
         return cudaGetLastError();
     }
     static cudaError_t bcr_factor(const BcrArgs& a, long long ctas, cudaStream_t s) {
-        if constexpr (M >= 8) return launch_bcr(k_bcr_factor<M>, bcr_factor_smem_bytes<M>(), a, 2 * ctas, s);
+        if constexpr (M >= 8) {
+            constexpr size_t s64 = bcr_factor_smem_bytes<double, M>(), s32 = bcr_factor_smem_bytes<float, M>();
+            switch (a.mode) {
+                case BCR_F64: return launch_bcr(k_bcr_factor<double, double, double, M>, s64, a, 2 * ctas, s);
+                case BCR_F32_FIRST: return launch_bcr(k_bcr_factor<float, double, float, M>, s32, a, 2 * ctas, s);
+                case BCR_F32: return launch_bcr(k_bcr_factor<float, float, float, M>, s32, a, 2 * ctas, s);
+                case BCR_F32_LAST: return launch_bcr(k_bcr_factor<float, float, double, M>, s32, a, 2 * ctas, s);
+                case BCR_F32_ONLY: return launch_bcr(k_bcr_factor<float, double, double, M>, s32, a, 2 * ctas, s);
+                default: return cudaErrorInvalidValue;
+            }
+        }
         return cudaErrorNotSupported;
     }
     static cudaError_t bcr_rhs(const BcrArgs& a, long long ctas, cudaStream_t s) {
-        if constexpr (M >= 8) return launch_bcr(k_bcr_rhs<M>, bcr_vec_smem_bytes<M>(), a, ctas, s);
+        if constexpr (M >= 8) {
+            if (a.mode == BCR_F64) return launch_bcr(k_bcr_rhs<double, M>, bcr_vec_smem_bytes<double, M>(), a, ctas, s);
+            return launch_bcr(k_bcr_rhs<float, M>, bcr_vec_smem_bytes<float, M>(), a, ctas, s);
+        }
         return cudaErrorNotSupported;
     }
     static cudaError_t bcr_back(const BcrArgs& a, long long ctas, cudaStream_t s) {
-        if constexpr (M >= 8) return launch_bcr(k_bcr_back<M>, bcr_vec_smem_bytes<M>(), a, ctas, s);
+        if constexpr (M >= 8) {
+            constexpr size_t s64 = bcr_vec_smem_bytes<double, M>(), s32 = bcr_vec_smem_bytes<float, M>();
+            if (a.mode == BCR_F64) return launch_bcr(k_bcr_back<double, double, M>, s64, a, ctas, s);
+            if (a.mode == BCR_F32_FIRST || a.mode == BCR_F32_ONLY)
+                return launch_bcr(k_bcr_back<float, double, M>, s32, a, ctas, s);
+            return launch_bcr(k_bcr_back<float, float, M>, s32, a, ctas, s);
+        }
         return cudaErrorNotSupported;
     }
     static const Launchers* table() {

@@ -11,6 +11,7 @@ struct Tuning {
     int top_rows = 0;        // a level with at most this many rows is one partition / direct (0: 8)
     int reduced = 0;         // reduced-system solver: 0 recursive partitions, 1 block cyclic reduction
     int tp_block = 0;        // threads per CTA of the thread-per-partition kernels (0: 128)
+    int local = 0;           // level-0 local factorization: 0 block LU + spikes, L >= 1 cyclic reduction of 2^L rows
 };
 
 struct LevelShape {
@@ -21,6 +22,13 @@ struct LevelShape {
 // level: direct solve, p = 0).  Returns false on invalid parameters.
 inline bool plan_shapes(int kind, long long N, int m, int sms, const Tuning& t, std::vector<LevelShape>& out) {
     out.clear();
+    if (kind == 0 && t.local > 0) {
+        // local cyclic reduction: no partition levels; the whole matrix is
+        // one level handled by the cyclic-reduction kernels
+        if (m < 8 || t.local > 62) return false;
+        out.push_back(LevelShape{N, 0, 0, 0, N});
+        return true;
+    }
     const long long top_rows = t.top_rows > 0 ? t.top_rows : 8;
     const long long sub_rows = t.sub_rows >= 2 ? t.sub_rows : 4;
     // level-0 partitions per SM: enough resident warps to hide the Gauss-Jordan
