@@ -238,7 +238,7 @@ bt_status bt_reduced_export(bt_plan plan, double* alpha, double* beta, double* g
  * later kernel launch of the plan with a pair of CUDA events on the plan's
  * stream; bt_plan_trace(plan, 0) stops recording.  bt_plan_trace_query
  * synchronises and returns, for kernel kind `kind` at recursion level
- * `level` (levels >= 3 are pooled into 3; level -1 sums all levels), the
+ * `level` (levels >= 63 are pooled into 63; level -1 sums all levels), the
  * summed event time in ms and the number of launches.  Kinds:
  * 0 local factor, 1 reduced-matrix assembly, 2 forward solve, 3 reduced
  * right-hand side, 4 back substitution, 5 top-level BABD direct solve,

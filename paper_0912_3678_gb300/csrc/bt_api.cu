@@ -372,7 +372,7 @@ cudaError_t launch(bt_plan_s* P, int kind, int level, int nkernels, Fn&& f) {
     cudaError_t e = f();
     if (P->trace && a && b) {
         cudaEventRecord(b, P->stream);
-        P->recs.push_back({kind * 4 + (level < 3 ? level : 3), a, b});
+        P->recs.push_back({kind * 64 + (level < 63 ? level : 63), a, b});
     }
     P->launches += nkernels;
     return e;
@@ -1011,8 +1011,8 @@ bt_status bt_plan_trace_query(bt_plan P, int kind, int level, double* total_ms, 
     double tot = 0.0;
     int64_t n = 0;
     for (const auto& r : P->recs) {
-        if (r.key / 4 != kind) continue;
-        if (level >= 0 && r.key % 4 != (level < 3 ? level : 3)) continue;
+        if (r.key / 64 != kind) continue;
+        if (level >= 0 && r.key % 64 != (level < 63 ? level : 63)) continue;
         float ms = 0.f;
         e = cudaEventElapsedTime(&ms, r.a, r.b);
         if (e != cudaSuccess) return from_cuda(e);

@@ -1,6 +1,8 @@
 """Autotuner for the partitioning parameters (plan step A0): top-level
-partition length, the reduced-system solver (recursive partitions or block
-cyclic reduction) and recursion-level partition length (the recursion depth),
+partition length, the local factorization (block LU with spikes, or cyclic
+reduction inside partitions of 2^L block rows), the reduced-system solver
+(recursive partitions or block cyclic reduction) and recursion-level
+partition length (the recursion depth),
 the CTA shape of the thread-per-partition kernels, and the size at which a
 level is solved by one partition.  Candidates are timed on synthetic
 systems of the requested shape (generated on the device) through the normal
@@ -28,7 +30,7 @@ def bucket(N: int) -> int:
 
 def default_tuning(m: int, N: int, prec: str = "fp64", batch: bool = False) -> dict:
     """The built-in heuristic (all zero: the library's own defaults)."""
-    return {"p0": 0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0, "reduced": 0, "tp_block": 0}
+    return {"p0": 0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0, "reduced": 0, "tp_block": 0, "local": 0}
 
 
 class Tuner:
@@ -113,7 +115,8 @@ class Tuner:
         for k in ks:
             p0 = max(1, min(N // k, (N + 1) // 2))
             if p0 not in [c["p0"] for c in out]:
-                out.append({"p0": p0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0, "reduced": 0, "tp_block": 0})
+                out.append({"p0": p0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0, "reduced": 0, "tp_block": 0,
+                            "local": 0})
         return out
 
     def tune(self, m: int, N: int, prec: str = "fp64", nrhs: int = 1, reps: int = 9, force: bool = False) -> dict:
@@ -146,8 +149,14 @@ class Tuner:
                 ms = run(t)
                 if ms < 0.99 * best:
                     best, best_t = ms, t
+            # local cyclic reduction inside partitions of 2^L block rows
+            for L in (3, 4, 5, 6, 7, 8):
+                t = dict(default_tuning(m, N, prec), local=L)
+                ms = run(t)
+                if ms < 0.99 * best:
+                    best, best_t = ms, t
         for sub in (2, 3, 6, 8):
-            if best_t.get("reduced"):
+            if best_t.get("reduced") or best_t.get("local"):
                 break
             t = dict(best_t, sub_rows=sub)
             ms = run(t)
@@ -161,6 +170,8 @@ class Tuner:
                 if ms < 0.99 * best:
                     best, best_t = ms, t
         for top in (2, 4, 16):
+            if best_t.get("local"):
+                break
             t = dict(best_t, top_rows=top)
             ms = run(t)
             if ms < 0.99 * best:
@@ -174,7 +185,7 @@ def batch_tuner(k0: int):
     """Per-system tuning of a batch with top-level partitions of about k0 block rows."""
     def f(m, N, prec):
         p0 = max(1, min(N // k0, (N + 1) // 2)) if N > 8 else 1
-        return {"p0": p0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0, "reduced": 0, "tp_block": 0}
+        return {"p0": p0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0, "reduced": 0, "tp_block": 0, "local": 0}
     return f
 
 
