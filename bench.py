@@ -64,6 +64,15 @@ def _workload(name: str, m_opt=None, N_opt=None, nr_opt=None):
     raise SystemExit(f"unknown workload {name}")
 
 
+# DRAM bytes (read + written) per launch of the dominant kernel, from one ncu
+# capture of that launch in the same configuration (workload, path, kernel,
+# level-0 partitions): profiles/factor_cta_fp64_m16_block16.md.  Any other
+# configuration reports null; an entry is dropped when its kernel changes.
+MEASURED_TRAFFIC = {
+    ("block16", "fp64", "factor", 608): 150.3e6,
+}
+
+
 def _factor_flops_per_row(m: int) -> float:
     # algorithmic count per local block row: block-Thomas factorization
     # (2/3 + 2 + 2) m^3 plus the left spike 4 m^3
@@ -521,22 +530,31 @@ def main():
         local_rows = N - (r["levels"][0][1] - 1)
     else:
         local_rows = N - r["levels"][0][1]
-    flops_per = {
-        "factor": _factor_flops_per_row(m) * local_rows,          # (2/3+2+2) m^3 + 4 m^3 per local row
-        "solve_fwd": 6.0 * m * m * nr * local_rows,                # 2 matvecs + top-row sweep per row
-        "solve_bwd": 4.0 * m * m * nr * local_rows,                # 2 matvecs per row
-        "residual": 6.0 * m * m * nr * N,                          # 3 m^2 nrhs FMA per block row, FP64
-    }
+    if w["kind"] == "btri":
+        flops_per = {
+            "factor": _factor_flops_per_row(m) * local_rows,          # (2/3+2+2) m^3 + 4 m^3 per local row
+            "solve_fwd": 6.0 * m * m * nr * local_rows,                # 2 matvecs + top-row sweep per row
+            "solve_bwd": 4.0 * m * m * nr * local_rows,                # 2 matvecs per row
+            "residual": 6.0 * m * m * nr * N,                          # 3 m^2 nrhs FMA per block row, FP64
+        }
+    else:
+        flops_per = {
+            "factor": (2.0 / 3.0 + 4.0) * m ** 3 * local_rows,         # LU of R_j, propagator, spike product
+            "solve_fwd": 4.0 * m * m * nr * local_rows,                # 2 matvecs per step
+            "solve_bwd": 2.0 * m * m * nr * local_rows,                # 1 matvec per step
+            "residual": 4.0 * m * m * nr * (N + 1),                    # 2 m^2 nrhs FMA per block row, FP64
+        }
     cand = {k: v for k, v in r["lvl0"].items() if v[1] > 0}
     roof = None
-    if cand and w["kind"] == "btri":
+    if cand:
         dom = max(cand, key=lambda k: cand[k][0])
         t_launch = cand[dom][0] / cand[dom][1] / 1e3
         is64 = head == "fp64" or dom == "residual"
         peak = fp64_peak if is64 else fp32_peak
         ach = flops_per[dom] / t_launch / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel": f"level-0 {dom} ({'FP64' if is64 else 'FP32'})",
+                "traffic": MEASURED_TRAFFIC.get((args.workload, head, dom, r["levels"][0][1])),
+                "kernel": f"level-0 {dom} ({'FP64' if is64 else 'FP32'})",
                 "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (probe measured 1.20)"
                                 if is64 else "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz"),
                 "launch_ms": t_launch * 1e3}
