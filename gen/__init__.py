@@ -145,6 +145,24 @@ def btri_random(N: int, m: int, nrhs: int = 1, seed_rep: int = 0, rng=None,
     return BtriSystem(B, D, C, btri_matvec(B, D, C, Xs), Xs)
 
 
+def btri_nondominant(N: int, m: int, nrhs: int = 1, seed_rep: int = 0, zero_frac: float = 0.1,
+                     rng=None) -> BtriSystem:
+    """Block tridiagonal system that is not block diagonally dominant, with a
+    fraction of exactly singular diagonal blocks: B_j, C_j, D_j = G/sqrt(m),
+    G ~ N(0,1), and D_j = 0 for about zero_frac of the block rows (block LU
+    without interchanges breaks down there).  X* ~ N(0,1), F = A X*."""
+    rng = rng if rng is not None else rng_for(7, seed_rep)
+    s = 1.0 / math.sqrt(m)
+    B = rng.standard_normal((N, m, m)) * s
+    D = rng.standard_normal((N, m, m)) * s
+    C = rng.standard_normal((N, m, m)) * s
+    D[rng.random(N) < zero_frac] = 0.0
+    B[0] = 0.0
+    C[N - 1] = 0.0
+    Xs = rng.standard_normal((N * m, nrhs))
+    return BtriSystem(B, D, C, btri_matvec(B, D, C, Xs), Xs)
+
+
 # --------------------------------------------------------------------- BABD --
 
 @dataclass

@@ -106,7 +106,21 @@ bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int p
  *                for BT_FP32_IR and BT_BF16_IR) and the reduced system left
  *                after L steps is solved by FP64 cyclic reduction.  L is capped
  *                so that at least the last block row is FP64.  p0, ctas_per_sm,
- *                sub_rows, top_rows and reduced are then unused. */
+ *                sub_rows, top_rows and reduced are then unused.
+ *   pivot        1 = pivoted partitions (the variant of Sec. 2 for matrices
+ *                with singular or ill-conditioned local blocks): when the
+ *                local factorization of a partition meets a pivot block whose
+ *                Gauss-Jordan pivot is at most tau times the largest entry of
+ *                that block row (bt_plan_set_pivot_tol, default 1e-3), the
+ *                factorization of the partition stops there, the row becomes
+ *                one more separator and the partition is factored again as
+ *                two; the enlarged reduced system (at most 2 p0 + 15 block
+ *                rows) is solved by Gaussian elimination with partial
+ *                pivoting over pairs of block rows.  bt_factor then
+ *                synchronises once per splitting pass; reduced and local are
+ *                unused; graph capture only of solves (what = 2).  If more
+ *                rows break down than the reduced system has room for,
+ *                bt_factor returns BT_ERR_SINGULAR. */
 typedef struct {
     int64_t p0;
     int ctas_per_sm;
@@ -115,6 +129,7 @@ typedef struct {
     int reduced;
     int tp_block;
     int local;
+    int pivot;
 } bt_tuning;
 
 /* bt_plan_create with explicit partitioning parameters (NULL = defaults). */
@@ -174,6 +189,12 @@ bt_status bt_refine_result(bt_plan plan, double tol, double* relcorr_out);
  * bt_refine_result accepts it when that backward error is below the
  * threshold or the last correction is below tol. */
 bt_status bt_plan_set_backward_tol(bt_plan plan, double eta_tol);
+
+/* Breakdown threshold tau of a plan created with bt_tuning.pivot = 1
+ * (0 <= tau < 1; default 1e-3): larger values split partitions more often
+ * (more separators, smaller multipliers).  Takes effect at the next
+ * bt_factor.  BT_ERR_INVALID for other plans. */
+bt_status bt_plan_set_pivot_tol(bt_plan plan, double tau);
 
 /* ||A||_inf of the matrices given to the last bt_factor / abd_factor, as the
  * stopping test uses it: FP32 row sums of the entries truncated toward zero

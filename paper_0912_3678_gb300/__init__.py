@@ -20,7 +20,7 @@ __all__ = ["BtPlan", "AbdPlan", "BtError", "BT_STATUS", "PREC", "load_library",
            "KERNEL_KINDS", "bt_solve_noalloc", "BT_NOALLOC_SCRATCH_BYTES", "bt_plan_create_tuned",
            "bt_batch_create", "bt_batch_run", "bt_batch_finish", "bt_batch_info", "bt_batch_destroy",
            "BtBatch", "BtTuning", "BtBatchDesc", "bt_refine_async", "bt_refine_result",
-           "bt_plan_workspace_size", "bt_plan_anorm", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay",
+           "bt_plan_workspace_size", "bt_plan_anorm", "bt_plan_set_pivot_tol", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay",
            "bt_band_to_blocks", "band_to_blocks", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
            "abd_plan_create", "abd_factor", "abd_solve", "abd_residual", "abd_refine", "abd_sync",
            "abd_plan_destroy"]
@@ -76,7 +76,7 @@ def _tuning(t):
         return t
     return BtTuning(int(t.get("p0", 0)), int(t.get("ctas_per_sm", 0)), int(t.get("sub_rows", 0)),
                     int(t.get("top_rows", 0)), int(t.get("reduced", 0)), int(t.get("tp_block", 0)),
-                    int(t.get("local", 0)))
+                    int(t.get("local", 0)), int(t.get("pivot", 0)))
 
 
 def bt_plan_create_tuned(nblk, m, nrhs_max=1, prec="fp64", tuning=None, stream=None):
@@ -176,6 +176,10 @@ def bt_refine_result(plan, tol=1e-12):
     rc = ctypes.c_double(0.0)
     code = _lib.load().bt_refine_result(plan, float(tol), ctypes.byref(rc))
     return code, rc.value
+
+
+def bt_plan_set_pivot_tol(plan, tau: float):
+    _lib.check(_lib.load().bt_plan_set_pivot_tol(plan, float(tau)), "bt_plan_set_pivot_tol")
 
 
 def bt_plan_anorm(plan) -> float:
@@ -468,7 +472,7 @@ class BtBatch:
             if tun is None and tuner is not None:
                 tun = tuner(m, N, prec)
             descs.append(BtBatchDesc(N, m, _prec(prec), nr, _ptr(sd["B"]), _ptr(D), _ptr(sd["C"]), _ptr(F),
-                                     _ptr(sd["X"]), _tuning(tun) or BtTuning(0, 0, 0, 0, 0, 0, 0)))
+                                     _ptr(sd["X"]), _tuning(tun) or BtTuning(0, 0, 0, 0, 0, 0, 0, 0)))
             self._keep.append((sd["B"], D, sd["C"], F, sd["X"]))
         self.count = len(descs)
         self.handle = bt_batch_create(descs, ir_sweeps, mem_cap_bytes, stream)

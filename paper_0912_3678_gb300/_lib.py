@@ -51,7 +51,7 @@ SIGNATURES = {
 class BtTuning(ctypes.Structure):
     _fields_ = [("p0", ctypes.c_int64), ("ctas_per_sm", ctypes.c_int), ("sub_rows", ctypes.c_int),
                 ("top_rows", ctypes.c_int), ("reduced", ctypes.c_int), ("tp_block", ctypes.c_int),
-                ("local", ctypes.c_int)]
+                ("local", ctypes.c_int), ("pivot", ctypes.c_int)]
 
 
 class BtBatchDesc(ctypes.Structure):
@@ -74,6 +74,7 @@ SIGNATURES.update({
     "bt_refine_result": (_i32, [_vp, _f64, _pf64]),
     "bt_plan_set_backward_tol": (_i32, [_vp, _f64]),
     "bt_plan_anorm": (_i32, [_vp, _vp]),
+    "bt_plan_set_pivot_tol": (_i32, [_vp, _f64]),
     "bt_plan_workspace_size": (_i32, [_i32, _i64, _i32, _i32, _i32, ctypes.POINTER(BtTuning), _pi64]),
     "bt_plan_create_in": (_i32, [_pvp, _i32, _i64, _i32, _i32, _i32, ctypes.POINTER(BtTuning), _vp, _i64, _vp]),
 })

@@ -26,6 +26,7 @@ struct Level {
     LevelArgs a;
     bool low = false;   // local factors in FP32
     long long rows = 0; // block rows stored for this level (BABD: N+1)
+    long long pcap = 0; // partitions the level's buffers hold (pivoted level 0: room for splits)
 };
 
 }  // namespace
@@ -69,6 +70,13 @@ struct bt_plan_s {
     double* keep = nullptr;             // BABD top-level pivot rows
     bool bcr = false;                   // reduced system by block cyclic reduction
     int local = 0;                      // level-0 local cyclic-reduction steps (plans without partition levels)
+    // pivoted partitions: level 0 split at breakdown rows, reduced system by banded GEPP
+    bool pivot = false;
+    double pivot_tau = 1e-3;
+    long long p_init = 0, base_init = 0, extra_init = 0;
+    long long* starts_dev = nullptr;    // [pcap+1]
+    long long* brk_dev = nullptr;       // [pcap]
+    std::vector<long long> starts_host, brk_host;
     bool padded = false;                // caller blocks of order mu embedded in order m
     double* Ap[3] = {nullptr, nullptr, nullptr};   // padded matrices (B/S, D/R, C)
     double* Fp = nullptr;               // padded right-hand side / solution / residual
@@ -141,15 +149,16 @@ void layout(bt_plan_s* P, Arena& ar) {
         Level& v = P->lv[l];
         const size_t ts = v.low ? sizeof(float) : sizeof(double);
         const bool top = (l == P->nlev);
-        const bool holder = top && P->bcr;
+        const bool holder = top && (P->bcr || P->pivot);
         if (!(top && P->kind == 1) && !holder) {
+            const long long pa = std::max(v.a.p, v.pcap);
             v.a.Dinv = ar.take(ts * v.rows * mm);
             if (P->kind == 0) v.a.Y = ar.take(ts * v.rows * mm);
             v.a.Zc = ar.take(ts * v.rows * mm);
             if (P->kind == 0) {
-                v.a.Pf = ar.take(ts * v.a.p * mm);
-                v.a.Qf = ar.take(ts * v.a.p * mm);
-                v.a.Hf = ar.take(ts * v.a.p * m * nr);
+                v.a.Pf = ar.take(ts * pa * mm);
+                v.a.Qf = ar.take(ts * pa * mm);
+                v.a.Hf = ar.take(ts * pa * m * nr);
             }
         }
         if (l >= 1) {
@@ -178,6 +187,13 @@ void layout(bt_plan_s* P, Arena& ar) {
             v.a.X = Xn;
         }
         if (top && P->kind == 1) P->keep = (double*)ar.take(sizeof(double) * v.a.N * m * (3 * m + nr) + 8);
+        if (top && P->pivot) P->keep = (double*)ar.take(sizeof(double) * v.rows * m * (3 * m + nr) + 8);
+    }
+    if (P->pivot) {
+        const long long pc = P->lv[0].pcap;
+        P->starts_dev = (long long*)ar.take(sizeof(long long) * (pc + 1));
+        P->brk_dev = (long long*)ar.take(sizeof(long long) * pc);
+        P->lv[0].a.starts = P->starts_dev;
     }
     if (P->bcr) {
         Level& h = P->lv[P->nlev];
@@ -246,9 +262,27 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
     cudaGetDevice(&P->device);
     const int sms = sm_count(P->device);
     std::vector<bt::LevelShape> shapes;
-    if (!bt::plan_shapes(kind, N, m, sms, tune, shapes)) {
+    P->pivot = (kind == 0 && tune.pivot > 0);
+    bt::Tuning tsh = tune;
+    if (P->pivot) {
+        tsh.reduced = 0;
+        tsh.local = 0;
+    }
+    if (!bt::plan_shapes(kind, N, m, sms, tsh, shapes)) {
         delete P;
         return BT_ERR_INVALID;
+    }
+    long long pcap = 0;
+    if (P->pivot) {
+        // level 0 as planned; its reduced system (which breakdown splits may
+        // enlarge up to pcap - 1 block rows) by the pivoted direct solver
+        const bt::LevelShape s0 = shapes[0];
+        shapes.resize(1);
+        pcap = std::min<long long>(N + 1, 2 * s0.p + 16);
+        shapes.push_back(bt::LevelShape{s0.p - 1, 0, 0, 0, std::max<long long>(pcap - 1, 1)});
+        P->p_init = s0.p;
+        P->base_init = s0.base;
+        P->extra_init = s0.extra;
     }
     for (size_t l = 0; l < shapes.size(); ++l) {
         Level v;
@@ -263,10 +297,11 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
         v.low = (l == 0) && (prec != BT_FP64);
         v.a.bf16 = (l == 0) && (prec == BT_BF16_IR) && (m >= 16) ? 1 : 0;
         v.a.tpb = tune.tp_block;
+        if (P->pivot && l == 0) v.pcap = pcap;
         P->lv.push_back(v);
     }
     P->nlev = (int)P->lv.size() - 1;
-    P->bcr = (kind == 0 && P->lv[P->nlev].a.p == 0 && (P->nlev >= 1 || tune.local > 0));
+    P->bcr = !P->pivot && (kind == 0 && P->lv[P->nlev].a.p == 0 && (P->nlev >= 1 || tune.local > 0));
     if (P->bcr) {
         long long K = P->lv[P->nlev].a.N;
         int n = 1;
@@ -389,7 +424,75 @@ bt_status read_status(bt_plan_s* P) {
 }
 
 // Factor every level: local factorizations and reduced systems.
+// Pivoted partitions (the variant of Sec. 2 for matrices whose local blocks may
+// be singular or ill-conditioned): factor level 0; every partition whose local
+// factorization broke down at some block row (a pivot below tau times the
+// largest entry of the row's blocks) is split there, that row becoming one
+// more separator of the reduced system; repeat until no partition breaks
+// down.  The reduced system (at most pcap - 1 block rows) is solved by banded
+// GEPP at solve time.  One host synchronisation per pass.
+bt_status run_factor_pivoted(bt_plan_s* P) {
+    const bt::Launchers* L = P->L;
+    Level& v = P->lv[0];
+    Level& t = P->lv[1];
+    const long long N = v.a.N, pcap = v.pcap;
+    long long p = P->p_init;
+    std::vector<long long>& st = P->starts_host;
+    st.assign(p + 1, 0);
+    for (long long i = 0; i < p; ++i) st[i] = i * P->base_init + std::min(i, P->extra_init);
+    st[p] = N;
+    v.a.brk = P->brk_dev;
+    v.a.tau = P->pivot_tau;
+    bt_status res = BT_OK;
+    for (int pass = 0;; ++pass) {
+        v.a.p = p;
+        t.a.N = p - 1;
+        cudaError_t e = cudaMemcpyAsync(P->starts_dev, st.data(), sizeof(long long) * (p + 1),
+                                        cudaMemcpyHostToDevice, P->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(P->brk_dev, 0x7f, sizeof(long long) * p, P->stream);
+        if (e == cudaSuccess) e = launch(P, K_FACTOR, 0, 1, [&] { return L->factor(v.a, v.low, P->stream); });
+        P->brk_host.assign(p, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(P->brk_host.data(), P->brk_dev, sizeof(long long) * p, cudaMemcpyDeviceToHost,
+                                P->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        bt_status sst = read_status(P);   // synchronises
+        if (sst != BT_OK) return sst;
+        std::vector<long long> nst;
+        nst.reserve(p + 2);
+        long long splits = 0;
+        for (long long i = 0; i < p; ++i) {
+            nst.push_back(st[i]);
+            const long long j = P->brk_host[i];
+            if (j >= st[i] && j < st[i + 1]) {
+                nst.push_back(j + 1);   // block row j closes a partition as its separator
+                ++splits;
+            }
+        }
+        nst.push_back(N);
+        if (splits == 0) break;
+        if (p + splits > pcap) {
+            // more breakdowns than the reduced system has room for
+            res = BT_ERR_SINGULAR;
+            break;
+        }
+        st.swap(nst);
+        p += splits;
+    }
+    v.a.brk = nullptr;
+    if (res != BT_OK) {
+        // the status word carries it for bt_info / the next synchronising call
+        long long code[4] = {BT_ERR_SINGULAR, 0, -1, -1};
+        cudaMemcpyAsync(P->status, code, sizeof(code), cudaMemcpyHostToDevice, P->stream);
+        cudaStreamSynchronize(P->stream);
+        return res;
+    }
+    cudaError_t e = launch(P, K_ASSEMBLE, 0, 1, [&] { return L->assemble(v.a, v.low, P->stream); });
+    return from_cuda(e);
+}
+
 bt_status run_factor(bt_plan_s* P) {
+    if (P->pivot) return run_factor_pivoted(P);
     const bt::Launchers* L = P->L;
     for (int l = 0; l <= P->nlev; ++l) {
         Level& v = P->lv[l];
@@ -451,6 +554,13 @@ bt_status run_solve(bt_plan_s* P, const double* F, double* X, int nr) {
             bt::BcrArgs& b = P->bl[q];
             e = launch(P, K_BCR_SOLVE, b.level, 1, [&] { return L->bcr_back(b, (b.K + 1) / 2, P->stream); });
         }
+    } else if (P->pivot) {
+        e = cudaSuccess;
+        if (t.a.N >= 1)
+            e = launch(P, K_DIRECT, lt, 1, [&] {
+                return bt::launch_btri_direct((int)t.a.N, P->m, nr, t.a.B, t.a.D, t.a.C, t.a.F, t.a.X, P->keep,
+                                              P->status, t.a.level, P->stream);
+            });
     } else if (P->kind == 0) {
         e = launch(P, K_SOLVE_FWD, lt, 1, [&] { return L->solve_fwd(t.a, t.low, P->stream); });
         if (e == cudaSuccess) e = launch(P, K_SOLVE_BWD, lt, 1, [&] { return L->solve_bwd(t.a, t.low, P->stream); });
@@ -619,6 +729,7 @@ static bt::Tuning to_tuning(const bt_tuning* t, int64_t p) {
         u.reduced = t->reduced;
         u.tp_block = t->tp_block;
         u.local = t->local;
+        u.pivot = t->pivot;
     }
     if (p > 0) u.p0 = p;
     return u;
@@ -631,7 +742,7 @@ bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int p
 bt_status bt_plan_create_tuned(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int prec, const bt_tuning* tuning,
                                void* stream) {
     if (tuning && (tuning->p0 < 0 || tuning->ctas_per_sm < 0 || tuning->sub_rows < 0 || tuning->top_rows < 0 ||
-                   tuning->reduced < 0 || tuning->reduced > 1 || tuning->local < 0 || tuning->local > 62 ||
+                   tuning->reduced < 0 || tuning->reduced > 1 || tuning->local < 0 || tuning->local > 62 || tuning->pivot < 0 || tuning->pivot > 1 ||
                    !(tuning->tp_block == 0 || tuning->tp_block == 64 || tuning->tp_block == 128 ||
                      tuning->tp_block == 256)))
         return BT_ERR_INVALID;
@@ -823,6 +934,12 @@ bt_status bt_plan_anorm(bt_plan P, double* anorm_out) {
     return BT_OK;
 }
 
+bt_status bt_plan_set_pivot_tol(bt_plan P, double tau) {
+    if (!P || !P->pivot || !(tau >= 0.0) || !(tau < 1.0)) return BT_ERR_INVALID;
+    P->pivot_tau = tau;
+    return BT_OK;
+}
+
 bt_status bt_plan_set_backward_tol(bt_plan P, double eta_tol) {
     if (!P) return BT_ERR_INVALID;
     P->eta_tol = eta_tol;
@@ -844,6 +961,7 @@ bt_status bt_plan_create_in(bt_plan* plan, int kind, int64_t n, int m, int nrhs_
 
 bt_status bt_plan_capture(bt_plan P, int what, const double* F, double* X, int nrhs, int sweeps) {
     if (!P || what < 1 || what > 3) return BT_ERR_INVALID;
+    if (P->pivot && what != 2) return BT_ERR_INVALID;   // the pivoted factorization synchronises
     bt_status st = check_solve(P, P->kind, F, X, nrhs);
     if (st != BT_OK) return st;
     if (what == 3 && (sweeps < 0 || sweeps > 30)) return BT_ERR_INVALID;

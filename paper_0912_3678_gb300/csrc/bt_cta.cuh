@@ -113,10 +113,25 @@ template <>
 __device__ __forceinline__ unsigned mag_key<float>(float v) {
     return (__float_as_uint(v) & 0x7fffffffu) >> 5;
 }
+// A magnitude (truncated, never above it) back from its key.
+template <typename T>
+__device__ __forceinline__ T key_value(unsigned k);
+template <>
+__device__ __forceinline__ double key_value<double>(unsigned k) {
+    return __hiloint2double((int)(k << 5), 0);
+}
+template <>
+__device__ __forceinline__ float key_value<float>(unsigned k) {
+    return __uint_as_float(k << 5);
+}
 
+// Pivoted levels pass brk: a pivot with |pivot| <= thr is then a breakdown of
+// the partition's local factorization at this row (the smallest such row of
+// the partition is kept in brk[part], and the partition is split there), not
+// an error.
 template <typename T, int M>
 __device__ bool gj_inverse(T* a, T* colk, int* perm, long long* st, int level, long long part,
-                           long long row) {
+                           long long row, long long* brk = nullptr, T thr = T(0)) {
     using S = Cta<T, M>;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = S::NT / 32;
@@ -130,8 +145,16 @@ __device__ bool gj_inverse(T* a, T* colk, int* perm, long long* st, int level, l
             const int p = 31 - (int)(best & 31u);
             T pv = __shfl_sync(0xffffffffu, v, p);
             const T vk = __shfl_sync(0xffffffffu, v, k);
-            if (pv == T(0) || nonfinite(pv)) {
-                if (lane == 0) report(st, pv == T(0) ? ST_SINGULAR : ST_NONFINITE, level, part, row);
+            if (nonfinite(pv)) {
+                if (lane == 0) report(st, ST_NONFINITE, level, part, row);
+                pv = T(1);
+                ok = false;
+            } else if (brk != nullptr && !(abs_key(pv) > abs_key(thr))) {
+                if (lane == 0) atomicMin(brk + part, row);
+                pv = T(1);
+                ok = false;
+            } else if (pv == T(0)) {
+                if (lane == 0) report(st, ST_SINGULAR, level, part, row);
                 pv = T(1);
                 ok = false;
             }
@@ -269,7 +292,7 @@ __device__ __forceinline__ void factor_cta_body(const LevelArgs& a, const long l
     T* colk = sW + S::BLK;
     int* perm = reinterpret_cast<int*>(colk + M);
 
-    const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
+    const Part pt = part_bounds(a, MODE, i);
     const Own<T, M> o;
     T* gDinv = reinterpret_cast<T*>(a.Dinv);
     T* gY = reinterpret_cast<T*>(a.Y);
@@ -286,8 +309,8 @@ __device__ __forceinline__ void factor_cta_body(const LevelArgs& a, const long l
         pf.load(needB(pt.s) ? a.B + (pt.s - a.shift) * MM : nullptr, a.D + (pt.s - a.shift) * MM,
                 needC(pt.s) ? a.C + (pt.s - a.shift) * MM : nullptr);
         pf.store(sB, sD, sC, needB(pt.s), needC(pt.s));
-        if (wchain) load_blk<T, M>(sW, a.C + (pt.s - 1 - a.shift) * MM);   // W_s = C of the left separator row
     }
+    if (wchain) load_blk<T, M>(sW, a.C + (pt.s - 1 - a.shift) * MM);   // W_s = C of the left separator row
     __syncthreads();
 
     for (long long j = pt.s; j < pt.e; ++j) {
@@ -330,7 +353,27 @@ __device__ __forceinline__ void factor_cta_body(const LevelArgs& a, const long l
             if (MODE == 0) write_own<T, M>(sD, acc, o);
             __syncthreads();
         }
-        gj_inverse<T, M>(sD, colk, perm, a.status, a.level, i, j);
+        T thr = T(0);
+        if (a.brk != nullptr) {
+            // breakdown threshold: tau times the largest entry of B_j, D'_j, C_j
+            unsigned mk = 0u;
+#pragma unroll
+            for (int q = 0; q < S::R; ++q) {
+                const int at = (o.r0 + q) * S::LD + o.c;
+                mk = max(mk, mag_key<T>(sD[at]));
+                if (needB(j)) mk = max(mk, mag_key<T>(sB[at]));
+                if (nC) mk = max(mk, mag_key<T>(sC[at]));
+            }
+            mk = __reduce_max_sync(0xffffffffu, mk);
+            unsigned* red = reinterpret_cast<unsigned*>(perm);
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mk;
+            __syncthreads();
+            unsigned bm = 0u;
+            for (int w = 0; w < S::NT / 32; ++w) bm = max(bm, red[w]);
+            __syncthreads();
+            thr = (T)a.tau * key_value<T>(bm);
+        }
+        gj_inverse<T, M>(sD, colk, perm, a.status, a.level, i, j, a.brk, thr);
         store_blk<T, M>(gDinv + j * MM, sD);
         T z[S::R], y[S::R];
         if (pt.hasL) {
@@ -400,14 +443,15 @@ __device__ __forceinline__ void assemble_cta_body(const LevelArgs& a, const long
     double* sB = reinterpret_cast<double*>(smem_raw);
     double* sY = sB + S::BLK;
     double* sZ = sY + S::BLK;
-    const Part pt = part_bounds(0, a.N, a.p, a.base, a.extra, s);
+    const Part pt = part_bounds(a, 0, s);
     const long long e = pt.e;
     const long long MM = S::MM;
     const Own<double, M> o;
     const bool hasBeta = s > 0;
     const bool hasGamma = (s + 1) < a.p - 1;
+    const bool local = pt.e > pt.s;   // partition s has local rows before its separator
     load_blk<double, M>(sB, a.B + (e - a.shift) * MM);
-    {
+    if (local) {
         const T* gY = reinterpret_cast<const T*>(a.Y) + (e - 1) * MM;
         for (int idx = threadIdx.x; idx < M * M; idx += S::NT) sY[(idx / M) * S::LD + idx % M] = (double)gY[idx];
         if (hasBeta) {
@@ -426,8 +470,12 @@ __device__ __forceinline__ void assemble_cta_body(const LevelArgs& a, const long
         ga[q] = hasGamma ? (double)gQ[at] : 0.0;
         be[q] = 0.0;
     }
-    gemm_acc<double, M, true>(al, sB, sY, o);
-    if (hasBeta) gemm_acc<double, M, false>(be, sB, sZ, o);
+    if (local) {
+        gemm_acc<double, M, true>(al, sB, sY, o);
+        if (hasBeta) gemm_acc<double, M, false>(be, sB, sZ, o);
+    } else if (hasBeta) {
+        read_own<double, M>(be, sB, o);   // the separator couples directly to the previous one
+    }
     store_own<double, M>(a.Dn + s * MM, al, o);
     store_own<double, M>(a.Bn + s * MM, be, o);
     store_own<double, M>(a.Cn + s * MM, ga, o);
@@ -454,7 +502,7 @@ __device__ __forceinline__ void solve_fwd_cta_body(const LevelArgs& a, const lon
     T* sv = sh + M * 32;          // M x nr
     const int nr = a.nr;
     const int E = M * nr;
-    const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
+    const Part pt = part_bounds(a, MODE, i);
     const long long MM = S::MM;
     const T* gDinv = reinterpret_cast<const T*>(a.Dinv);
     constexpr int RU = RhsOwn<M>::MAXU;
@@ -488,8 +536,10 @@ __device__ __forceinline__ void solve_fwd_cta_body(const LevelArgs& a, const lon
             if (el < E) sv[el] = (T)pf[u];
         }
     };
-    fetch(pt.s);
-    stash();
+    if (pt.s < pt.e) {
+        fetch(pt.s);
+        stash();
+    }
     __syncthreads();
     for (long long j = pt.s; j < pt.e; ++j) {
         const bool first = (j == pt.s);
@@ -550,6 +600,12 @@ __device__ __forceinline__ void solve_fwd_cta_body(const LevelArgs& a, const lon
         return;
     }
     if (!pt.hasL) return;
+    if (pt.e == pt.s) {
+        // no local rows: nothing between the two separators
+        T* Hf = reinterpret_cast<T*>(a.Hf) + i * E;
+        for (int el = threadIdx.x; el < E; el += NT) Hf[el] = T(0);
+        return;
+    }
     const T* gY = reinterpret_cast<const T*>(a.Y);
     for (long long j = pt.e - 2; j >= pt.s; --j) {
         load_blkT<T, M>(sB, gY + j * MM);
@@ -593,14 +649,15 @@ __device__ __forceinline__ void assemble_rhs_cta_body(const LevelArgs& a, const 
     double* sH = sh + M * 32;
     const int nr = a.nr;
     const int E = M * nr;
-    const Part pt = part_bounds(0, a.N, a.p, a.base, a.extra, s);
+    const Part pt = part_bounds(a, 0, s);
     const long long e = pt.e;
     const long long MM = S::MM;
     load_blk<double, M>(sB, a.B + (e - a.shift) * MM);
     load_blk<double, M>(sC, a.C + (e - a.shift) * MM);
     const T* Hf = reinterpret_cast<const T*>(a.Hf) + (s + 1) * E;
+    const bool local = pt.e > pt.s;
     for (int el = threadIdx.x; el < E; el += NT) {
-        sh[el] = a.X[(e - 1) * E + el];
+        sh[el] = local ? a.X[(e - 1) * E + el] : 0.0;
         sH[el] = (double)Hf[el];
     }
     __syncthreads();
@@ -629,7 +686,7 @@ __device__ __forceinline__ void solve_bwd_cta_body(const LevelArgs& a, const lon
     T* sL = sx + M * 32;   // x_L
     const int nr = a.nr;
     const int E = M * nr;
-    const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
+    const Part pt = part_bounds(a, MODE, i);
     const long long MM = S::MM;
     const long long li = (MODE == 0) ? i - 1 : i;   // next-level index of x_L
     const long long ri = (MODE == 0) ? i : i + 1;   // next-level index of x_R

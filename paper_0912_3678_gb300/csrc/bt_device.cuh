@@ -3,6 +3,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "bt_level.h"
+
 namespace bt {
 
 enum : int { ST_OK = 0, ST_SINGULAR = 3, ST_NONFINITE = 4, ST_TIMEOUT = 6 };
@@ -43,6 +45,17 @@ __device__ __forceinline__ unsigned long long abs_key(double x) {
 __device__ __forceinline__ unsigned long long abs_key(float x) {
     return (unsigned long long)(__float_as_uint(x) & 0x7fffffffu);
 }
+// The magnitude back from abs_key.
+template <typename T>
+__device__ __forceinline__ T key_abs(unsigned long long k);
+template <>
+__device__ __forceinline__ double key_abs<double>(unsigned long long k) {
+    return __longlong_as_double((long long)k);
+}
+template <>
+__device__ __forceinline__ float key_abs<float>(unsigned long long k) {
+    return __uint_as_float((unsigned)k);
+}
 __device__ __forceinline__ bool nonfinite(double x) {
     return ((__double2hiint(x) >> 20) & 0x7ff) == 0x7ff;
 }
@@ -81,6 +94,22 @@ __device__ __forceinline__ Part part_bounds(int mode, long long N, long long p, 
         q.e = (i < p - 1) ? q.s + cnt - 1 : N;
     }
     return q;
+}
+
+// Bounds of partition i of a level: explicit starts (pivoted levels, where a
+// partition may have no local rows: only its separator, or nothing at the end)
+// or the uniform split.
+__device__ __forceinline__ Part part_bounds(const LevelArgs& a, int mode, long long i) {
+    if (a.starts != nullptr) {
+        Part q;
+        const long long start = a.starts[i], cnt = a.starts[i + 1] - start;
+        q.s = start;
+        q.hasL = i > 0;
+        q.hasR = i < a.p - 1;
+        q.e = q.hasR ? start + cnt - 1 : start + cnt;
+        return q;
+    }
+    return part_bounds(mode, a.N, a.p, a.base, a.extra, i);
 }
 
 }  // namespace bt

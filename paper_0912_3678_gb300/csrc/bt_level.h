@@ -36,6 +36,10 @@ struct LevelArgs {
     const double* Xn;  // next level solution
     void* Hf;          // [p][m][nr] top-row right-hand side after full elimination (T)
     long long* status;
+    // pivoted partitions (mode 0): explicit partition starts and breakdown rows
+    const long long* starts;   // [p+1] first block row of each partition (null: uniform split)
+    long long* brk;            // [p] first local row whose pivot block broke down (null: report singular)
+    double tau;                // breakdown: |pivot| <= tau * max |entry| of the pivot block
 };
 
 }  // namespace bt

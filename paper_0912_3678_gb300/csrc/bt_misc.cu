@@ -416,6 +416,141 @@ __global__ void __launch_bounds__(256) k_babd_direct(int Np, int m, int nr, cons
     }
 }
 
+// Direct solve of a small block tridiagonal system (K block rows) by Gaussian
+// elimination with partial pivoting, row interchanges being confined to two
+// consecutive block rows (the banded form of GEPP: after the interchanges, row
+// block j of U reaches block columns j, j+1 and j+2).  One CTA.  The working
+// window holds 2m rows of [x_j | x_{j+1} | x_{j+2} | f]; per block column the
+// m pivot rows go to keep ([K][m][3m+nr]) for the back substitution.  The
+// top of a pivoted recursion, where a reduced system may have singular
+// diagonal blocks that block elimination without interchanges cannot pass.
+__global__ void __launch_bounds__(256) k_btri_direct(int K, int m, int nr, const double* __restrict__ B,
+                                                     const double* __restrict__ D, const double* __restrict__ C,
+                                                     const double* __restrict__ F, double* __restrict__ X,
+                                                     double* __restrict__ keep, long long* status, int level) {
+    extern __shared__ __align__(16) double sm[];
+    const int W = 3 * m + nr;
+    double* w = sm;
+    double* colk = w + 2 * m * W;
+    const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const long long mm = (long long)m * m;
+    const int MW = m * W;
+    // block row j in the window frame of block column j-1 (rows m..2m-1) or j (rows 0..m-1)
+    auto load_row = [&](int j, double* dst, bool shifted) {
+        for (int idx = tid; idx < MW; idx += NT) {
+            const int r = idx / W, c = idx % W;
+            double v = 0.0;
+            if (c < 3 * m) {
+                const int blk = c / m, cc = c % m;   // window block column
+                const int col = shifted ? (j - 1 + blk) : (j + blk);
+                if (col == j - 1) v = B[j * mm + r * m + cc];
+                else if (col == j) v = D[j * mm + r * m + cc];
+                else if (col == j + 1 && j + 1 < K) v = C[j * mm + r * m + cc];
+            } else {
+                v = F[((long long)j * m + r) * nr + (c - 3 * m)];
+            }
+            dst[idx] = v;
+        }
+    };
+    load_row(0, w, false);
+    __syncthreads();
+    for (int j = 0; j < K; ++j) {
+        const bool more = (j + 1 < K);
+        if (more) load_row(j + 1, w + MW, true);
+        __syncthreads();
+        const int H = more ? 2 * m : m;
+        for (int k = 0; k < m; ++k) {
+            if (warp == 0) {
+                unsigned long long key = 0ull;
+                int idx = 1 << 20;
+                for (int i = k + lane; i < H; i += 32) {
+                    const unsigned long long kk = abs_key(w[i * W + k]);
+                    if (kk > key || (kk == key && i < idx)) {
+                        key = kk;
+                        idx = i;
+                    }
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, off);
+                    const int i2 = __shfl_xor_sync(0xffffffffu, idx, off);
+                    if (k2 > key || (k2 == key && i2 < idx)) {
+                        key = k2;
+                        idx = i2;
+                    }
+                }
+                const int p = (idx < H) ? idx : k;
+                if (p != k)
+                    for (int c = lane; c < W; c += 32) {
+                        const double t = w[k * W + c];
+                        w[k * W + c] = w[p * W + c];
+                        w[p * W + c] = t;
+                    }
+                __syncwarp();
+                double pv = w[k * W + k];
+                if (key == 0ull || nonfinite(pv)) {
+                    if (lane == 0) report(status, key == 0ull ? ST_SINGULAR : ST_NONFINITE, level, -1, j);
+                    pv = 1.0;
+                    if (lane == 0) w[k * W + k] = 1.0;
+                }
+                const double rp = rcp(pv);
+                for (int i = lane; i < H; i += 32) colk[i] = (i > k) ? w[i * W + k] * rp : 0.0;
+            }
+            __syncthreads();
+            const int rows = H - k - 1, cols = W - k - 1;
+            for (int idx = tid; idx < rows * cols; idx += NT) {
+                const int i = k + 1 + idx / cols, c = k + 1 + idx % cols;
+                w[i * W + c] = fma(-colk[i], w[k * W + c], w[i * W + c]);
+            }
+            for (int i = k + 1 + tid; i < H; i += NT) w[i * W + k] = 0.0;
+            __syncthreads();
+        }
+        double* kp = keep + (long long)j * MW;
+        for (int idx = tid; idx < MW; idx += NT) kp[idx] = w[idx];
+        __syncthreads();
+        if (more) {
+            // the m rows left over move up one block column: [x_{j+1} | x_{j+2} | 0 | f]
+            for (int idx = tid; idx < MW; idx += NT) {
+                const int r = idx / W, c = idx % W;
+                const double* src = w + (m + r) * W;
+                double v;
+                if (c < 2 * m) v = src[m + c];
+                else if (c < 3 * m) v = 0.0;
+                else v = src[c];
+                w[idx] = v;   // rows 0..m-1 are not read again in this pass
+            }
+            __syncthreads();
+        }
+    }
+    // back substitution: x_j = U_jj^{-1} (g_j - U_{j,j+1} x_{j+1} - U_{j,j+2} x_{j+2}), U_jj upper triangular
+    const long long E = (long long)m * nr;
+    double* t = w;   // m x nr
+    for (int j = K - 1; j >= 0; --j) {
+        const double* kp = keep + (long long)j * MW;
+        for (int el = tid; el < m * nr; el += NT) {
+            const int r = el / nr, c = el % nr;
+            double acc = kp[r * W + 3 * m + c];
+            if (j + 1 < K)
+                for (int k = 0; k < m; ++k) acc = fma(-kp[r * W + m + k], X[(long long)(j + 1) * E + k * nr + c], acc);
+            if (j + 2 < K)
+                for (int k = 0; k < m; ++k)
+                    acc = fma(-kp[r * W + 2 * m + k], X[(long long)(j + 2) * E + k * nr + c], acc);
+            t[el] = acc;
+        }
+        __syncthreads();
+        for (int r = m - 1; r >= 0; --r) {
+            for (int c = tid; c < nr; c += NT) {
+                double acc = t[r * nr + c];
+                for (int k = r + 1; k < m; ++k) acc = fma(-kp[r * W + k], t[k * nr + c], acc);
+                t[r * nr + c] = acc * rcp(kp[r * W + r]);
+            }
+            __syncthreads();
+        }
+        for (int el = tid; el < m * nr; el += NT) X[(long long)j * E + el] = t[el];
+        __syncthreads();
+    }
+}
+
 size_t babd_direct_smem(int m, int nr) { return sizeof(double) * ((size_t)(2 * m) * (3 * m + nr) + 2 * m); }
 
 cudaError_t launch_resid_btri(long long N, int m, int nr, const double* B, const double* D, const double* C,
@@ -454,6 +589,18 @@ cudaError_t launch_ir_update(long long n, double* X, const double* Dc, double* p
     const int nb = ir_update_blocks(n);
     k_ir_update<<<nb, 256, 0, s>>>(n, X, Dc, partial);
     k_reduce_pairs<<<1, 256, 0, s>>>(nb, partial, out);
+    return cudaGetLastError();
+}
+size_t btri_direct_smem(int m, int nr) { return sizeof(double) * ((size_t)(2 * m) * (3 * m + nr) + 2 * m); }
+cudaError_t launch_btri_direct(int K, int m, int nr, const double* B, const double* D, const double* C,
+                               const double* F, double* X, double* keep, long long* status, int level,
+                               cudaStream_t s) {
+    const size_t smem = btri_direct_smem(m, nr);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_btri_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_btri_direct<<<1, 256, smem, s>>>(K, m, nr, B, D, C, F, X, keep, status, level);
     return cudaGetLastError();
 }
 cudaError_t launch_babd_direct(int Np, int m, int nr, const double* S, const double* R, const double* B0,

@@ -21,6 +21,12 @@ int ir_update_blocks(long long n);
 cudaError_t launch_ir_update(long long n, double* X, const double* Dc, double* partial, double* out,
                              cudaStream_t s);
 size_t babd_direct_smem(int m, int nr);
+// Small block tridiagonal system (K block rows) by banded GEPP in one CTA;
+// keep: [K][m][3m+nr] doubles of workspace.
+size_t btri_direct_smem(int m, int nr);
+cudaError_t launch_btri_direct(int K, int m, int nr, const double* B, const double* D, const double* C,
+                               const double* F, double* X, double* keep, long long* status, int level,
+                               cudaStream_t s);
 cudaError_t launch_babd_direct(int Np, int m, int nr, const double* S, const double* R, const double* B0,
                                const double* B1, const double* F, double* X, double* keep, long long* status,
                                int level, cudaStream_t s);

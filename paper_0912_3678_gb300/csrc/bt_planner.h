@@ -12,6 +12,7 @@ struct Tuning {
     int reduced = 0;         // reduced-system solver: 0 recursive partitions, 1 block cyclic reduction
     int tp_block = 0;        // threads per CTA of the thread-per-partition kernels (0: 128)
     int local = 0;           // level-0 local factorization: 0 block LU + spikes, L >= 1 cyclic reduction of 2^L rows
+    int pivot = 0;           // 1: partitions split at breakdown rows, reduced system by banded GEPP
 };
 
 struct LevelShape {

@@ -41,9 +41,11 @@ __device__ __forceinline__ void rmm(T (&c)[M * M], const T (&a)[M * M], const T 
 }
 
 // In-place Gauss-Jordan inverse with partial pivoting, blocks in registers.
+// brk != null (pivoted levels): a pivot with |pivot| <= thr marks a breakdown
+// of the partition at this row (atomicMin into brk[part]) instead of an error.
 template <typename T, int M>
 __device__ __forceinline__ void rgj_inverse(T (&a)[M * M], long long* st, int level, long long part,
-                                            long long row) {
+                                            long long row, long long* brk = nullptr, T thr = T(0)) {
     int perm[M];
 #pragma unroll
     for (int k = 0; k < M; ++k) {
@@ -70,8 +72,14 @@ __device__ __forceinline__ void rgj_inverse(T (&a)[M * M], long long* st, int le
         }
         perm[k] = p;
         T pv = a[k * M + k];
-        if (best == 0ull || nonfinite(pv)) {
-            report(st, best == 0ull ? ST_SINGULAR : ST_NONFINITE, level, part, row);
+        if (nonfinite(pv)) {
+            report(st, ST_NONFINITE, level, part, row);
+            pv = T(1);
+        } else if (brk != nullptr && !(abs_key(pv) > abs_key(thr))) {
+            atomicMin(brk + part, row);
+            pv = T(1);
+        } else if (best == 0ull) {
+            report(st, ST_SINGULAR, level, part, row);
             pv = T(1);
         }
         const T r = rcp(pv);
@@ -105,7 +113,7 @@ template <typename T, int M, int MODE>
 __device__ __forceinline__ void factor_tp_body(const LevelArgs& a, const long long i) {
     constexpr int MM = M * M;
     if (i >= a.p) return;
-    const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
+    const Part pt = part_bounds(a, MODE, i);
     T* gDinv = reinterpret_cast<T*>(a.Dinv);
     T* gY = reinterpret_cast<T*>(a.Y);
     T* gZ = reinterpret_cast<T*>(a.Zc);
@@ -122,7 +130,23 @@ __device__ __forceinline__ void factor_tp_body(const LevelArgs& a, const long lo
         rld<T, M>(Dp, a.D + (j - a.shift) * MM);
         if (needB) rld<T, M>(Bj, a.B + (j - a.shift) * MM);
         if (MODE == 0 && !first) rmm<T, M, true, true>(Dp, Bj, Yp);
-        rgj_inverse<T, M>(Dp, a.status, a.level, i, j);
+        T thr = T(0);
+        if (a.brk != nullptr) {
+            // breakdown threshold: tau times the largest entry of B_j, D'_j, C_j
+            unsigned long long mk = 0ull;
+#pragma unroll
+            for (int u = 0; u < MM; ++u) {
+                mk = max(mk, abs_key(Dp[u]));
+                if (needB) mk = max(mk, abs_key(Bj[u]));
+            }
+            if (needC) {
+                const double* gC = a.C + (j - a.shift) * MM;
+#pragma unroll
+                for (int u = 0; u < MM; ++u) mk = max(mk, abs_key((T)gC[u]));
+            }
+            thr = (T)a.tau * key_abs<T>(mk);
+        }
+        rgj_inverse<T, M>(Dp, a.status, a.level, i, j, a.brk, thr);
         rst<T, M>(gDinv + j * MM, Dp);
         if (pt.hasL) {
             if (!first) {
@@ -178,24 +202,31 @@ template <typename T, int M>
 __device__ __forceinline__ void assemble_tp_body(const LevelArgs& a, const long long s) {
     constexpr int MM = M * M;
     if (s >= a.p - 1) return;
-    const Part pt = part_bounds(0, a.N, a.p, a.base, a.extra, s);
+    const Part pt = part_bounds(a, 0, s);
     const long long e = pt.e;
-    double Be[MM], al[MM], Yl[MM], Pf[MM];
+    const bool local = pt.e > pt.s;   // partition s has local rows before its separator
+    double Be[MM], al[MM], Pf[MM];
     rld<double, M>(Be, a.B + (e - a.shift) * MM);
     rld<double, M>(al, a.D + (e - a.shift) * MM);
-    rld<double, M>(Yl, reinterpret_cast<const T*>(a.Y) + (e - 1) * MM);
     rld<double, M>(Pf, reinterpret_cast<const T*>(a.Pf) + (s + 1) * MM);
-    rmm<double, M, true, true>(al, Be, Yl);
+    if (local) {
+        double Yl[MM];
+        rld<double, M>(Yl, reinterpret_cast<const T*>(a.Y) + (e - 1) * MM);
+        rmm<double, M, true, true>(al, Be, Yl);
+    }
 #pragma unroll
     for (int u = 0; u < MM; ++u) al[u] += Pf[u];
     rst<double, M>(a.Dn + s * MM, al);
     double be[MM], ga[MM];
 #pragma unroll
     for (int u = 0; u < MM; ++u) be[u] = ga[u] = 0.0;
-    if (s > 0) {
+    if (s > 0 && local) {
         double Zl[MM];
         rld<double, M>(Zl, reinterpret_cast<const T*>(a.Zc) + (e - 1) * MM);
         rmm<double, M, false, false>(be, Be, Zl);
+    } else if (s > 0) {
+#pragma unroll
+        for (int u = 0; u < MM; ++u) be[u] = Be[u];   // direct coupling to the previous separator
     }
     if (s + 1 < a.p - 1) rld<double, M>(ga, reinterpret_cast<const T*>(a.Qf) + (s + 1) * MM);
     rst<double, M>(a.Bn + s * MM, be);
@@ -235,7 +266,7 @@ __device__ __forceinline__ void solve_fwd_tp_body(const LevelArgs& a, const long
     const long long i = tid / nr;
     const int c = (int)(tid % nr);
     if (i >= a.p) return;
-    const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
+    const Part pt = part_bounds(a, MODE, i);
     const long long E = (long long)M * nr;
     const T* gDinv = reinterpret_cast<const T*>(a.Dinv);
     T hp[M];
@@ -294,12 +325,17 @@ __device__ __forceinline__ void assemble_rhs_tp_body(const LevelArgs& a, const l
     const long long s = tid / nr;
     const int c = (int)(tid % nr);
     if (s >= a.p - 1) return;
-    const Part pt = part_bounds(0, a.N, a.p, a.base, a.extra, s);
+    const Part pt = part_bounds(a, 0, s);
     const long long e = pt.e;
     const long long E = (long long)M * nr;
     double g[M], h[M], H[M], Be[MM], Ce[MM];
     vld<M, double>(g, a.F + e * E + c, nr);
-    vld<M, double>(h, a.X + (e - 1) * E + c, nr);
+    if (pt.e > pt.s) {
+        vld<M, double>(h, a.X + (e - 1) * E + c, nr);
+    } else {
+#pragma unroll
+        for (int r = 0; r < M; ++r) h[r] = 0.0;
+    }
     const T* Hf = reinterpret_cast<const T*>(a.Hf) + (s + 1) * E + c;
 #pragma unroll
     for (int r = 0; r < M; ++r) H[r] = (double)Hf[r * nr];
@@ -317,7 +353,7 @@ __device__ __forceinline__ void solve_bwd_tp_body(const LevelArgs& a, const long
     const long long i = tid / nr;
     const int c = (int)(tid % nr);
     if (i >= a.p) return;
-    const Part pt = part_bounds(MODE, a.N, a.p, a.base, a.extra, i);
+    const Part pt = part_bounds(a, MODE, i);
     const long long E = (long long)M * nr;
     const long long li = (MODE == 0) ? i - 1 : i;
     const long long ri = (MODE == 0) ? i : i + 1;
