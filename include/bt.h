@@ -114,8 +114,10 @@ bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int p
  *                that block row (bt_plan_set_pivot_tol, default 1e-3), the
  *                factorization of the partition stops there, the row becomes
  *                one more separator and the partition is factored again as
- *                two; the enlarged reduced system (at most 2 p0 + 15 block
- *                rows) is solved by Gaussian elimination with partial
+ *                two (one pass finds every breakdown: after one the local
+ *                factorization restarts at the next row); the enlarged
+ *                reduced system (at most max(2 p0, nblk/16) + 15 block rows)
+ *                is solved by Gaussian elimination with partial
  *                pivoting over pairs of block rows.  bt_factor then
  *                synchronises once per splitting pass; reduced and local are
  *                unused; graph capture only of solves (what = 2).  If more

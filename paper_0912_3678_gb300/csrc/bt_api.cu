@@ -75,7 +75,8 @@ struct bt_plan_s {
     double pivot_tau = 1e-3;
     long long p_init = 0, base_init = 0, extra_init = 0;
     long long* starts_dev = nullptr;    // [pcap+1]
-    long long* brk_dev = nullptr;       // [pcap]
+    long long* brk_dev = nullptr;       // [1 + brk_cap]: breakdown count and rows
+    long long brk_cap = 0;
     std::vector<long long> starts_host, brk_host;
     bool padded = false;                // caller blocks of order mu embedded in order m
     double* Ap[3] = {nullptr, nullptr, nullptr};   // padded matrices (B/S, D/R, C)
@@ -192,7 +193,8 @@ void layout(bt_plan_s* P, Arena& ar) {
     if (P->pivot) {
         const long long pc = P->lv[0].pcap;
         P->starts_dev = (long long*)ar.take(sizeof(long long) * (pc + 1));
-        P->brk_dev = (long long*)ar.take(sizeof(long long) * pc);
+        P->brk_cap = 4 * pc;
+        P->brk_dev = (long long*)ar.take(sizeof(long long) * (P->brk_cap + 1));
         P->lv[0].a.starts = P->starts_dev;
     }
     if (P->bcr) {
@@ -278,7 +280,7 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
         // enlarge up to pcap - 1 block rows) by the pivoted direct solver
         const bt::LevelShape s0 = shapes[0];
         shapes.resize(1);
-        pcap = std::min<long long>(N + 1, 2 * s0.p + 16);
+        pcap = std::min<long long>(N + 1, std::max<long long>(2 * s0.p, N / 16) + 16);
         shapes.push_back(bt::LevelShape{s0.p - 1, 0, 0, 0, std::max<long long>(pcap - 1, 1)});
         P->p_init = s0.p;
         P->base_init = s0.base;
@@ -442,6 +444,7 @@ bt_status run_factor_pivoted(bt_plan_s* P) {
     for (long long i = 0; i < p; ++i) st[i] = i * P->base_init + std::min(i, P->extra_init);
     st[p] = N;
     v.a.brk = P->brk_dev;
+    v.a.brk_cap = P->brk_cap;
     v.a.tau = P->pivot_tau;
     bt_status res = BT_OK;
     for (int pass = 0;; ++pass) {
@@ -449,35 +452,33 @@ bt_status run_factor_pivoted(bt_plan_s* P) {
         t.a.N = p - 1;
         cudaError_t e = cudaMemcpyAsync(P->starts_dev, st.data(), sizeof(long long) * (p + 1),
                                         cudaMemcpyHostToDevice, P->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(P->brk_dev, 0x7f, sizeof(long long) * p, P->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(P->brk_dev, 0, sizeof(long long), P->stream);
         if (e == cudaSuccess) e = launch(P, K_FACTOR, 0, 1, [&] { return L->factor(v.a, v.low, P->stream); });
-        P->brk_host.assign(p, 0);
+        P->brk_host.assign(P->brk_cap + 1, 0);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(P->brk_host.data(), P->brk_dev, sizeof(long long) * p, cudaMemcpyDeviceToHost,
-                                P->stream);
+            e = cudaMemcpyAsync(P->brk_host.data(), P->brk_dev, sizeof(long long) * (P->brk_cap + 1),
+                                cudaMemcpyDeviceToHost, P->stream);
         if (e != cudaSuccess) return from_cuda(e);
         bt_status sst = read_status(P);   // synchronises
         if (sst != BT_OK) return sst;
-        std::vector<long long> nst;
-        nst.reserve(p + 2);
-        long long splits = 0;
-        for (long long i = 0; i < p; ++i) {
-            nst.push_back(st[i]);
-            const long long j = P->brk_host[i];
-            if (j >= st[i] && j < st[i + 1]) {
-                nst.push_back(j + 1);   // block row j closes a partition as its separator
-                ++splits;
-            }
-        }
+        const long long cnt = std::min(P->brk_host[0], P->brk_cap);
+        if (cnt == 0) break;
+        std::vector<long long> rows(P->brk_host.begin() + 1, P->brk_host.begin() + 1 + cnt);
+        std::sort(rows.begin(), rows.end());
+        rows.erase(std::unique(rows.begin(), rows.end()), rows.end());
+        // every breakdown row closes a partition as its separator: new start j + 1
+        std::vector<long long> nst(st.begin(), st.end() - 1);
+        for (long long j : rows) nst.push_back(j + 1);
+        std::sort(nst.begin(), nst.end());
         nst.push_back(N);
-        if (splits == 0) break;
-        if (p + splits > pcap) {
+        const long long np = (long long)nst.size() - 1;
+        if (np > pcap || pass > 64) {
             // more breakdowns than the reduced system has room for
             res = BT_ERR_SINGULAR;
             break;
         }
         st.swap(nst);
-        p += splits;
+        p = np;
     }
     v.a.brk = nullptr;
     if (res != BT_OK) {

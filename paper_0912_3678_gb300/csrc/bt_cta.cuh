@@ -126,12 +126,12 @@ __device__ __forceinline__ float key_value<float>(unsigned k) {
 }
 
 // Pivoted levels pass brk: a pivot with |pivot| <= thr is then a breakdown of
-// the partition's local factorization at this row (the smallest such row of
-// the partition is kept in brk[part], and the partition is split there), not
-// an error.
+// the partition's local factorization at this row (record_breakdown; the
+// partition is split there), not an error.
+
 template <typename T, int M>
 __device__ bool gj_inverse(T* a, T* colk, int* perm, long long* st, int level, long long part,
-                           long long row, long long* brk = nullptr, T thr = T(0)) {
+                           long long row, long long* brk = nullptr, T thr = T(0), long long cap = 0) {
     using S = Cta<T, M>;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = S::NT / 32;
@@ -150,7 +150,7 @@ __device__ bool gj_inverse(T* a, T* colk, int* perm, long long* st, int level, l
                 pv = T(1);
                 ok = false;
             } else if (brk != nullptr && !(abs_key(pv) > abs_key(thr))) {
-                if (lane == 0) atomicMin(brk + part, row);
+                if (lane == 0) record_breakdown(brk, cap, row);
                 pv = T(1);
                 ok = false;
             } else if (pv == T(0)) {
@@ -373,7 +373,10 @@ __device__ __forceinline__ void factor_cta_body(const LevelArgs& a, const long l
             __syncthreads();
             thr = (T)a.tau * key_value<T>(bm);
         }
-        gj_inverse<T, M>(sD, colk, perm, a.status, a.level, i, j, a.brk, thr);
+        const bool ok = gj_inverse<T, M>(sD, colk, perm, a.status, a.level, i, j, a.brk, thr, a.brk_cap);
+        // after a breakdown the local factorization restarts at the next row (as
+        // if this row were a separator), so one pass finds every breakdown
+        const bool restart = (a.brk != nullptr) && __syncthreads_or(!ok);
         store_blk<T, M>(gDinv + j * MM, sD);
         T z[S::R], y[S::R];
         if (pt.hasL) {
@@ -390,6 +393,7 @@ __device__ __forceinline__ void factor_cta_body(const LevelArgs& a, const long l
             store_own<T, M>(gZ + j * MM, z, o);
         }
         if (nC) {
+            if (restart) zero_own<T, M>(y);
             write_own<T, M>(sY, y, o);
             store_own<T, M>(gY + j * MM, y, o);
         }

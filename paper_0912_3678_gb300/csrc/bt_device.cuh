@@ -38,6 +38,14 @@ __device__ __forceinline__ double rcp(double x) {
 }
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 
+// Append block row `row` to a breakdown list: brk[0] counts, brk[1..cap] hold
+// the rows (a row may appear more than once; entries past cap are dropped and
+// found again by the next factorization pass).
+__device__ __forceinline__ void record_breakdown(long long* brk, long long cap, long long row) {
+    const unsigned long long k = atomicAdd(reinterpret_cast<unsigned long long*>(brk), 1ull);
+    if ((long long)k < cap) brk[1 + k] = row;
+}
+
 // |x| as an integer key that orders like |x| for finite x (sign bit cleared).
 __device__ __forceinline__ unsigned long long abs_key(double x) {
     return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;

@@ -38,8 +38,9 @@ struct LevelArgs {
     long long* status;
     // pivoted partitions (mode 0): explicit partition starts and breakdown rows
     const long long* starts;   // [p+1] first block row of each partition (null: uniform split)
-    long long* brk;            // [p] first local row whose pivot block broke down (null: report singular)
-    double tau;                // breakdown: |pivot| <= tau * max |entry| of the pivot block
+    long long* brk;            // breakdown list: [0] count, [1..brk_cap] block rows (null: report singular)
+    long long brk_cap;
+    double tau;                // breakdown: |pivot| <= tau * largest entry of the row's blocks
 };
 
 }  // namespace bt

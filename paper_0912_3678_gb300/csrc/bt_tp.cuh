@@ -44,9 +44,11 @@ __device__ __forceinline__ void rmm(T (&c)[M * M], const T (&a)[M * M], const T 
 // brk != null (pivoted levels): a pivot with |pivot| <= thr marks a breakdown
 // of the partition at this row (atomicMin into brk[part]) instead of an error.
 template <typename T, int M>
-__device__ __forceinline__ void rgj_inverse(T (&a)[M * M], long long* st, int level, long long part,
-                                            long long row, long long* brk = nullptr, T thr = T(0)) {
+__device__ __forceinline__ bool rgj_inverse(T (&a)[M * M], long long* st, int level, long long part,
+                                            long long row, long long* brk = nullptr, T thr = T(0),
+                                            long long cap = 0) {
     int perm[M];
+    bool ok = true;
 #pragma unroll
     for (int k = 0; k < M; ++k) {
         int p = k;
@@ -75,12 +77,15 @@ __device__ __forceinline__ void rgj_inverse(T (&a)[M * M], long long* st, int le
         if (nonfinite(pv)) {
             report(st, ST_NONFINITE, level, part, row);
             pv = T(1);
+            ok = false;
         } else if (brk != nullptr && !(abs_key(pv) > abs_key(thr))) {
-            atomicMin(brk + part, row);
+            if (ok) record_breakdown(brk, cap, row);
             pv = T(1);
+            ok = false;
         } else if (best == 0ull) {
             report(st, ST_SINGULAR, level, part, row);
             pv = T(1);
+            ok = false;
         }
         const T r = rcp(pv);
 #pragma unroll
@@ -107,6 +112,7 @@ __device__ __forceinline__ void rgj_inverse(T (&a)[M * M], long long* st, int le
             }
         }
     }
+    return ok;
 }
 
 template <typename T, int M, int MODE>
@@ -146,7 +152,7 @@ __device__ __forceinline__ void factor_tp_body(const LevelArgs& a, const long lo
             }
             thr = (T)a.tau * key_abs<T>(mk);
         }
-        rgj_inverse<T, M>(Dp, a.status, a.level, i, j, a.brk, thr);
+        const bool ok = rgj_inverse<T, M>(Dp, a.status, a.level, i, j, a.brk, thr, a.brk_cap);
         rst<T, M>(gDinv + j * MM, Dp);
         if (pt.hasL) {
             if (!first) {
@@ -162,6 +168,11 @@ __device__ __forceinline__ void factor_tp_body(const LevelArgs& a, const long lo
             T Cj[MM];
             rld<T, M>(Cj, a.C + (j - a.shift) * MM);
             rmm<T, M, false, false>(Yp, Dp, Cj);
+            if (!ok && a.brk != nullptr) {
+                // restart the local factorization at the next row after a breakdown
+#pragma unroll
+                for (int u = 0; u < MM; ++u) Yp[u] = T(0);
+            }
             rst<T, M>(gY + j * MM, Yp);
         }
         if (wchain) {

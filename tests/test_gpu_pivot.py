@@ -22,15 +22,18 @@ def _backward_error(s, X):
     return np.abs(R).max() / (rows.max() * np.abs(X).max() + np.abs(s.F).max())
 
 
-def _check(s, X):
-    """Normwise backward error within a few hundred units of rounding (local
-    multipliers are bounded by 1/tau = 1e3), forward error within kappa times
-    that, against the oracle's dense GEPP."""
+def _check(s, X, tau=1e-3):
+    """Normwise backward error within 4 (3m+1) u times the multiplier bound
+    1/tau of threshold pivoting (the local factorizations accept pivots down to
+    tau times the row's largest entry), forward error within kappa times that,
+    against the oracle's dense GEPP."""
+    m = s.D.shape[1]
     A = gen.btri_dense(s.B, s.D, s.C)
     ref = oracle.dense_solve(A, s.F)
     kappa = np.linalg.cond(A, 1)
-    assert _backward_error(s, X) <= 1e-12
-    assert oracle.rel_err(X, ref) <= 1e-11 + 1e-12 * kappa
+    eta = 4 * (3 * m + 1) * 2.0 ** -53 / max(tau, 1e-3)
+    assert _backward_error(s, X) <= eta
+    assert oracle.rel_err(X, ref) <= 1e-11 + eta * kappa
 
 
 @pytest.mark.parametrize("m", [1, 2, 4, 8, 16])
@@ -48,14 +51,22 @@ def test_pivoted_partitions_match_dense_gepp(cuda, m, N, p0):
 
 
 def test_plain_partitions_report_the_singular_block(cuda):
-    """The same kind of input without pivoting: a local block LU meets an
-    exactly singular pivot block and reports it."""
+    """Without pivoting, an exactly singular pivot block (D_j = 0 on the first
+    local row of a partition, where the pivot block is D_j itself) stops the
+    plain method with BT_ERR_SINGULAR; the pivoted plan solves the system."""
     import paper_0912_3678_gb300 as bt
-    s = gen.btri_nondominant(300, 4, 1, seed_rep=3, zero_frac=0.08)
-    with bt.BtPlan.tuned(300, 4, 1, "fp64", {"p0": 16}) as plan:
+    N, m = 300, 4
+    s = gen.btri_nondominant(N, m, 1, seed_rep=3, zero_frac=0.0)
+    s.D[19] = 0.0          # partitions of 18-19 rows: partition 1 starts at row 19
+    with bt.BtPlan.tuned(N, m, 1, "fp64", {"p0": 16}) as plan:
         plan.factor(*(to_dev(a, cuda) for a in (s.B, s.D, s.C)))
         code, lev, part, row = plan.info()
-    assert bt.BT_STATUS[code] == "BT_ERR_SINGULAR"
+    assert bt.BT_STATUS[code] == "BT_ERR_SINGULAR" and row == 19
+    with bt.BtPlan.tuned(N, m, 1, "fp64", {"p0": 16, "pivot": 1}) as plan:
+        plan.factor(*(to_dev(a, cuda) for a in (s.B, s.D, s.C)))
+        X = to_host(plan.solve(to_dev(s.F, cuda)))
+        plan.sync()
+    _check(s, X)
 
 
 @pytest.mark.parametrize("m", [1, 8])
