@@ -20,7 +20,7 @@ __all__ = ["BtPlan", "AbdPlan", "BtError", "BT_STATUS", "PREC", "load_library",
            "KERNEL_KINDS", "bt_solve_noalloc", "BT_NOALLOC_SCRATCH_BYTES", "bt_plan_create_tuned",
            "bt_batch_create", "bt_batch_run", "bt_batch_finish", "bt_batch_info", "bt_batch_destroy",
            "BtBatch", "BtTuning", "BtBatchDesc", "bt_refine_async", "bt_refine_result",
-           "bt_plan_workspace_size", "bt_plan_anorm", "bt_plan_set_pivot_tol", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay",
+           "bt_plan_workspace_size", "bt_plan_anorm", "bt_plan_set_pivot_tol", "ivp_parareal", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay",
            "bt_band_to_blocks", "band_to_blocks", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
            "abd_plan_create", "abd_factor", "abd_solve", "abd_residual", "abd_refine", "abd_sync",
            "abd_plan_destroy"]
@@ -176,6 +176,25 @@ def bt_refine_result(plan, tol=1e-12):
     rc = ctypes.c_double(0.0)
     code = _lib.load().bt_refine_result(plan, float(tol), ctypes.byref(rc))
     return code, rc.value
+
+
+def ivp_parareal(dl, d, du, g0, y0, T, p, nfine, ncoarse=1, kmax=None, tol=1e-12, g1=None, U=None,
+                 keep_history=False, stream=None, raise_on_error=True):
+    """Parareal for y' = L y + g0 + t g1 (L tridiagonal: dl, d, du; CUDA float64
+    vectors of length n) on [0, T] with p coarse intervals (see bt_ivp.h).
+    Returns (U [p+1, n], iterations, status code, history [(kmax+1), p+1, n] or None)."""
+    import torch
+    n = d.shape[0]
+    kmax = p if kmax is None else kmax
+    U = torch.empty((p + 1, n), dtype=torch.float64, device=d.device) if U is None else U
+    hist = torch.empty((kmax + 1, p + 1, n), dtype=torch.float64, device=d.device) if keep_history else None
+    it = ctypes.c_int(0)
+    code = _lib.load().ivp_parareal(int(n), _ptr(dl), _ptr(d), _ptr(du), _ptr(g0), _ptr(g1), _ptr(y0), float(T),
+                                    int(p), int(nfine), int(ncoarse), int(kmax), float(tol), _ptr(U), _ptr(hist),
+                                    ctypes.byref(it), _stream(stream))
+    if raise_on_error and code not in (0, 5):
+        _lib.check(code, "ivp_parareal")
+    return U, it.value, code, hist
 
 
 def bt_plan_set_pivot_tol(plan, tau: float):

@@ -75,6 +75,8 @@ SIGNATURES.update({
     "bt_plan_set_backward_tol": (_i32, [_vp, _f64]),
     "bt_plan_anorm": (_i32, [_vp, _vp]),
     "bt_plan_set_pivot_tol": (_i32, [_vp, _f64]),
+    "ivp_parareal": (_i32, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _f64, _i32, _i32, _i32, _i32, _f64, _vp, _vp,
+                            ctypes.POINTER(ctypes.c_int), _vp]),
     "bt_plan_workspace_size": (_i32, [_i32, _i64, _i32, _i32, _i32, ctypes.POINTER(BtTuning), _pi64]),
     "bt_plan_create_in": (_i32, [_pvp, _i32, _i64, _i32, _i32, _i32, ctypes.POINTER(BtTuning), _vp, _i64, _vp]),
 })

@@ -17,7 +17,7 @@ def _declared():
             continue
         text = open(os.path.join(ROOT, "include", hdr)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        names += re.findall(r"\b((?:bt|abd)_[a-z_0-9]+)\s*\(", text)
+        names += re.findall(r"\b((?:bt|abd|ivp)_[a-z_0-9]+)\s*\(", text)
     return sorted(set(names))
 
 
@@ -32,7 +32,7 @@ def lib():
 def test_header_declares_entry_points():
     names = _declared()
     for must in ("bt_plan_create", "bt_factor", "bt_solve", "bt_refine", "bt_residual", "bt_plan_destroy",
-                 "abd_plan_create", "abd_factor", "abd_solve", "abd_refine"):
+                 "abd_plan_create", "abd_factor", "abd_solve", "abd_refine", "ivp_parareal"):
         assert must in names
 
 
