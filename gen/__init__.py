@@ -163,6 +163,67 @@ def btri_nondominant(N: int, m: int, nrhs: int = 1, seed_rep: int = 0, zero_frac
     return BtriSystem(B, D, C, btri_matvec(B, D, C, Xs), Xs)
 
 
+# ----------------------------------------------------- circulant-like (cyclic) --
+
+@dataclass
+class CycSystem:
+    """S_j y_j + R_j y_{(j+1) mod N} = r_j, j = 0..N-1."""
+    S: np.ndarray
+    R: np.ndarray
+    RHS: np.ndarray
+    Ystar: np.ndarray
+
+
+def cyc_matvec(S, R, Y):
+    N, m = S.shape[0], S.shape[1]
+    Y3 = Y.reshape(N, m, -1)
+    out = np.einsum("jab,jbc->jac", S, Y3) + np.einsum("jab,jbc->jac", R, np.roll(Y3, -1, axis=0))
+    return out.reshape(N * m, -1)
+
+
+def cyc_dense(S, R):
+    N, m = S.shape[0], S.shape[1]
+    A = np.zeros((N * m, N * m))
+    for j in range(N):
+        A[j * m:(j + 1) * m, j * m:(j + 1) * m] += S[j]
+        k = (j + 1) % N
+        A[j * m:(j + 1) * m, k * m:(k + 1) * m] += R[j]
+    return A
+
+
+def cyc_random(N: int, m: int, nrhs: int = 1, seed_rep: int = 0, rng=None) -> CycSystem:
+    """A cyclic block bidiagonal system with R_j = 3 I + G/sqrt(m), S_j = G/sqrt(m)."""
+    rng = rng if rng is not None else rng_for(8, seed_rep)
+    s = 1.0 / math.sqrt(m)
+    S = rng.standard_normal((N, m, m)) * s
+    R = rng.standard_normal((N, m, m)) * s + 3.0 * np.eye(m)
+    Ys = rng.standard_normal((N * m, nrhs))
+    return CycSystem(S, R, cyc_matvec(S, R, Ys), Ys)
+
+
+def periodic_bvp(N: int, m: int, nrhs: int = 1, seed_rep: int = 0) -> CycSystem:
+    """Trapezoidal rule for the periodic linear BVP y' = L(t) y + q(t) on [0,1],
+    y(0) = y(1), with L(t) = S + cos(2 pi t) K (S, K as in the BVP workload) and
+    the periodic exact solution y(t) = exp(sin(2 pi t)) v: rows
+    S_j = -(I + h/2 L(t_j)), R_j = I - h/2 L(t_{j+1}), r_j = h/2 (q(t_j) + q(t_{j+1})),
+    j = 0..N-1, with y_N identified with y_0.  Ystar holds y(t_j), j < N."""
+    rng = rng_for(9, seed_rep)
+    Sm = stable_matrix(m, rng)
+    K = rng.standard_normal((m, m)) * 0.1
+    V = rng.standard_normal((m, nrhs))
+    h = 1.0 / N
+    t = np.arange(N + 1) * h
+    L = Sm[None] + np.cos(2 * np.pi * t)[:, None, None] * K[None]
+    ys = np.exp(np.sin(2 * np.pi * t))[:, None, None] * V[None]                  # [N+1][m][nrhs]
+    dys = (2 * np.pi * np.cos(2 * np.pi * t) * np.exp(np.sin(2 * np.pi * t)))[:, None, None] * V[None]
+    q = dys - np.einsum("jab,jbc->jac", L, ys)
+    I = np.eye(m)
+    S = -(I[None] + 0.5 * h * L[:-1])
+    R = I[None] - 0.5 * h * L[1:]
+    rhs = 0.5 * h * (q[:-1] + q[1:])
+    return CycSystem(S, R, rhs.reshape(N * m, nrhs), ys[:-1].reshape(N * m, nrhs))
+
+
 # --------------------------------------------------------------------- BABD --
 
 @dataclass

@@ -366,6 +366,25 @@ bt_status abd_refine(abd_plan plan, const double* RHS, double* Y, int nrhs, doub
 bt_status abd_sync(abd_plan plan);
 void abd_plan_destroy(abd_plan plan);
 
+/* ---------------------------------------------------------------------
+ * Circulant-like block systems (Sec. 2, Eq. (parpart1) and the remark after
+ * Eq. (redmatr1)): N >= 2 unknowns y_0..y_{N-1} (m each) with
+ *     S_j y_j + R_j y_{(j+1) mod N} = r_j,   j = 0..N-1,
+ * a block bidiagonal matrix closed into a cycle by its corner block (periodic
+ * one-step discretisations, circulant matrices with two block diagonals).
+ * Moving the last block row to the top gives the BABD form above with N-1
+ * steps, B0 = R_{N-1}, B1 = S_{N-1}; these calls are an abd plan on that
+ * permutation (the right-hand side is rotated by one block row into plan
+ * memory; the solution needs no permutation).  S, R: [N][m][m]; right-hand
+ * sides and solutions [N*m][nrhs].  Errors and refinement as for abd_*;
+ * cyc_residual returns the residual in the original row order. */
+bt_status cyc_plan_create(abd_plan* plan, int64_t N, int m, int nrhs_max, int prec, int64_t p, void* stream);
+bt_status cyc_factor(abd_plan plan, const double* S, const double* R);
+bt_status cyc_solve(abd_plan plan, const double* RHS, double* Y, int nrhs);
+bt_status cyc_residual(abd_plan plan, const double* RHS, const double* Y, double* Rout, int nrhs);
+bt_status cyc_refine(abd_plan plan, const double* RHS, double* Y, int nrhs, double tol, int maxit,
+                     int* iters_out, double* relcorr_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,8 @@ __all__ = ["BtPlan", "AbdPlan", "BtError", "BT_STATUS", "PREC", "load_library",
            "bt_plan_levels", "bt_plan_bytes", "bt_plan_trace", "bt_plan_trace_query", "bt_plan_launches",
            "KERNEL_KINDS", "bt_solve_noalloc", "BT_NOALLOC_SCRATCH_BYTES", "bt_plan_create_tuned",
            "bt_batch_create", "bt_batch_run", "bt_batch_finish", "bt_batch_info", "bt_batch_destroy",
-           "BtBatch", "BtTuning", "BtBatchDesc", "bt_refine_async", "bt_refine_result",
+           "BtBatch", "CycPlan", "cyc_plan_create", "cyc_factor", "cyc_solve", "cyc_residual", "cyc_refine",
+           "BtTuning", "BtBatchDesc", "bt_refine_async", "bt_refine_result",
            "bt_plan_workspace_size", "bt_plan_anorm", "bt_plan_set_pivot_tol", "ivp_parareal", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay",
            "bt_band_to_blocks", "band_to_blocks", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
            "abd_plan_create", "abd_factor", "abd_solve", "abd_residual", "abd_refine", "abd_sync",
@@ -166,6 +167,29 @@ def bt_refine(plan, F, X, nrhs, tol=1e-12, maxit=30, raise_on_error=True):
 
 def abd_refine(plan, RHS, Y, nrhs, tol=1e-12, maxit=30, raise_on_error=True):
     return _refine(_lib.load().abd_refine, "abd_refine", plan, RHS, Y, nrhs, tol, maxit, raise_on_error)
+
+
+def cyc_plan_create(N, m, nrhs_max=1, prec="fp64", p=0, stream=None):
+    h = ctypes.c_void_p()
+    _lib.check(_lib.load().cyc_plan_create(ctypes.byref(h), int(N), int(m), int(nrhs_max), _prec(prec),
+                                           int(p), _stream(stream)), "cyc_plan_create")
+    return h
+
+
+def cyc_factor(plan, S, R):
+    _lib.check(_lib.load().cyc_factor(plan, _ptr(S), _ptr(R)), "cyc_factor")
+
+
+def cyc_solve(plan, RHS, Y, nrhs):
+    _lib.check(_lib.load().cyc_solve(plan, _ptr(RHS), _ptr(Y), int(nrhs)), "cyc_solve")
+
+
+def cyc_residual(plan, RHS, Y, Rout, nrhs):
+    _lib.check(_lib.load().cyc_residual(plan, _ptr(RHS), _ptr(Y), _ptr(Rout), int(nrhs)), "cyc_residual")
+
+
+def cyc_refine(plan, RHS, Y, nrhs, tol=1e-12, maxit=30, raise_on_error=True):
+    return _refine(_lib.load().cyc_refine, "cyc_refine", plan, RHS, Y, nrhs, tol, maxit, raise_on_error)
 
 
 def bt_refine_async(plan, F, X, nrhs, sweeps=2):
@@ -522,6 +546,39 @@ class BtBatch:
 
     def __exit__(self, *a):
         self.close()
+
+
+class CycPlan(_PlanBase):
+    """Circulant-like plan: S_j y_j + R_j y_{(j+1) mod N} = r_j, j = 0..N-1
+    (a BABD plan on the rows rotated by one)."""
+    kind = 1
+
+    def __init__(self, n, m, nrhs_max=1, prec="fp64", p=0, stream=None):
+        import torch
+        self.m, self.n, self.nrhs_max, self.prec, self.stream = int(m), int(n), int(nrhs_max), prec, stream
+        self.rows = self.n
+        self.handle = cyc_plan_create(n, m, nrhs_max, prec, p, stream)
+        self._keep = ()
+        self._torch = torch
+
+    def factor(self, S, R):
+        self._keep = (S, R)
+        cyc_factor(self.handle, S, R)
+
+    def solve(self, RHS, Y=None):
+        Y = self._new_like_rhs(RHS) if Y is None else Y
+        cyc_solve(self.handle, RHS, Y, self._nrhs(RHS))
+        return Y
+
+    def residual(self, RHS, Y, Rout=None):
+        Rout = self._new_like_rhs(RHS) if Rout is None else Rout
+        cyc_residual(self.handle, RHS, Y, Rout, self._nrhs(RHS))
+        return Rout
+
+    def refine(self, RHS, Y=None, tol=1e-12, maxit=30, raise_on_error=True):
+        Y = self._new_like_rhs(RHS) if Y is None else Y
+        code, it, rc = cyc_refine(self.handle, RHS, Y, self._nrhs(RHS), tol, maxit, raise_on_error)
+        return Y, it, rc, code
 
 
 class AbdPlan(_PlanBase):

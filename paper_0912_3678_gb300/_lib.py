@@ -75,6 +75,12 @@ SIGNATURES.update({
     "bt_plan_set_backward_tol": (_i32, [_vp, _f64]),
     "bt_plan_anorm": (_i32, [_vp, _vp]),
     "bt_plan_set_pivot_tol": (_i32, [_vp, _f64]),
+    "cyc_plan_create": (_i32, [_pvp, _i64, _i32, _i32, _i32, _i64, _vp]),
+    "cyc_factor": (_i32, [_vp, _vp, _vp]),
+    "cyc_solve": (_i32, [_vp, _vp, _vp, _i32]),
+    "cyc_residual": (_i32, [_vp, _vp, _vp, _vp, _i32]),
+    "cyc_refine": (_i32, [_vp, _vp, _vp, _i32, _f64, _i32, ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(ctypes.c_double)]),
     "ivp_parareal": (_i32, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _f64, _i32, _i32, _i32, _i32, _f64, _vp, _vp,
                             ctypes.POINTER(ctypes.c_int), _vp]),
     "bt_plan_workspace_size": (_i32, [_i32, _i64, _i32, _i32, _i32, ctypes.POINTER(BtTuning), _pi64]),

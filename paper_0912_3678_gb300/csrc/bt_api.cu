@@ -78,6 +78,10 @@ struct bt_plan_s {
     long long* brk_dev = nullptr;       // [1 + brk_cap]: breakdown count and rows
     long long brk_cap = 0;
     std::vector<long long> starts_host, brk_host;
+    // circulant-like plans: a BABD plan of N-1 steps with the right-hand side rotated
+    bool cyclic = false;
+    double* rot = nullptr;              // [(N+1)*m][nrhs_max] rotated right-hand side
+    double* rot2 = nullptr;             // the same for residuals
     bool padded = false;                // caller blocks of order mu embedded in order m
     double* Ap[3] = {nullptr, nullptr, nullptr};   // padded matrices (B/S, D/R, C)
     double* Fp = nullptr;               // padded right-hand side / solution / residual
@@ -189,6 +193,11 @@ void layout(bt_plan_s* P, Arena& ar) {
         }
         if (top && P->kind == 1) P->keep = (double*)ar.take(sizeof(double) * v.a.N * m * (3 * m + nr) + 8);
         if (top && P->pivot) P->keep = (double*)ar.take(sizeof(double) * v.rows * m * (3 * m + nr) + 8);
+    }
+    if (P->kind == 1) {
+        // room for a rotated right-hand side (circulant-like plans)
+        P->rot = (double*)ar.take(sizeof(double) * rows0 * m * nr);
+        P->rot2 = (double*)ar.take(sizeof(double) * rows0 * m * nr);
     }
     if (P->pivot) {
         const long long pc = P->lv[0].pcap;
@@ -752,6 +761,61 @@ bt_status bt_plan_create_tuned(bt_plan* plan, int64_t nblk, int m, int nrhs_max,
 
 bt_status abd_plan_create(abd_plan* plan, int64_t N, int m, int nrhs_max, int prec, int64_t p, void* stream) {
     return plan_create(plan, 1, N, m, nrhs_max, prec, to_tuning(nullptr, p), stream);
+}
+
+bt_status cyc_plan_create(abd_plan* plan, int64_t N, int m, int nrhs_max, int prec, int64_t p, void* stream) {
+    if (!plan || N < 2) return BT_ERR_INVALID;
+    bt_status st = abd_plan_create(plan, N - 1, m, nrhs_max, prec, p, stream);
+    if (st == BT_OK) (*plan)->cyclic = true;
+    return st;
+}
+
+bt_status cyc_factor(abd_plan P, const double* S, const double* R) {
+    if (!P || !P->cyclic || !S || !R) return BT_ERR_INVALID;
+    // the last block row S_{N-1} y_{N-1} + R_{N-1} y_0 moves to the top
+    const size_t off = (size_t)P->N * P->mu * P->mu;
+    return abd_factor(P, S, R, R + off, S + off);
+}
+
+namespace {
+// dst = src rotated by one block row: dst[0] = src[N-1], dst[j+1] = src[j] (Nrows = N+1 of the abd plan)
+cudaError_t rotate_rhs(bt_plan_s* P, const double* src, double* dst, int nrhs, bool forward) {
+    const size_t blk = (size_t)P->mu * nrhs * sizeof(double);
+    const size_t rest = (size_t)P->N * blk;   // N = steps of the abd plan = cycle length - 1
+    cudaError_t e;
+    if (forward) {
+        e = cudaMemcpyAsync(dst, (const char*)src + rest, blk, cudaMemcpyDeviceToDevice, P->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync((char*)dst + blk, src, rest, cudaMemcpyDeviceToDevice, P->stream);
+    } else {
+        e = cudaMemcpyAsync((char*)dst + rest, src, blk, cudaMemcpyDeviceToDevice, P->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, (const char*)src + blk, rest, cudaMemcpyDeviceToDevice, P->stream);
+    }
+    return e;
+}
+}  // namespace
+
+bt_status cyc_solve(abd_plan P, const double* RHS, double* Y, int nrhs) {
+    if (!P || !P->cyclic || !RHS || !Y || nrhs < 1 || nrhs > P->nrhs_max) return BT_ERR_INVALID;
+    cudaError_t e = rotate_rhs(P, RHS, P->rot, nrhs, true);
+    if (e != cudaSuccess) return from_cuda(e);
+    return abd_solve(P, P->rot, Y, nrhs);
+}
+
+bt_status cyc_residual(abd_plan P, const double* RHS, const double* Y, double* Rout, int nrhs) {
+    if (!P || !P->cyclic || !RHS || !Y || !Rout || nrhs < 1 || nrhs > P->nrhs_max) return BT_ERR_INVALID;
+    cudaError_t e = rotate_rhs(P, RHS, P->rot, nrhs, true);
+    if (e != cudaSuccess) return from_cuda(e);
+    bt_status st = abd_residual(P, P->rot, Y, P->rot2, nrhs);
+    if (st != BT_OK) return st;
+    return from_cuda(rotate_rhs(P, P->rot2, Rout, nrhs, false));
+}
+
+bt_status cyc_refine(abd_plan P, const double* RHS, double* Y, int nrhs, double tol, int maxit, int* iters_out,
+                     double* relcorr_out) {
+    if (!P || !P->cyclic || !RHS || !Y || nrhs < 1 || nrhs > P->nrhs_max) return BT_ERR_INVALID;
+    cudaError_t e = rotate_rhs(P, RHS, P->rot, nrhs, true);
+    if (e != cudaSuccess) return from_cuda(e);
+    return abd_refine(P, P->rot, Y, nrhs, tol, maxit, iters_out, relcorr_out);
 }
 
 bt_status bt_factor(bt_plan P, const double* B, const double* D, const double* C) {

@@ -17,7 +17,7 @@ def _declared():
             continue
         text = open(os.path.join(ROOT, "include", hdr)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        names += re.findall(r"\b((?:bt|abd|ivp)_[a-z_0-9]+)\s*\(", text)
+        names += re.findall(r"\b((?:bt|abd|ivp|cyc)_[a-z_0-9]+)\s*\(", text)
     return sorted(set(names))
 
 
