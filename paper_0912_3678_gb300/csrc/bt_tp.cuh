@@ -3,6 +3,8 @@
 // the m x m blocks live in registers.  Same algorithm and outputs as the
 // CTA kernels in bt_cta.cuh.
 #pragma once
+#include <type_traits>
+
 #include "bt_device.cuh"
 #include "bt_level.h"
 
@@ -115,9 +117,273 @@ __device__ __forceinline__ bool rgj_inverse(T (&a)[M * M], long long* st, int le
     return ok;
 }
 
+// ------------------------------------------------------- scalar partitions --
+// m = 1, block tridiagonal levels: the recurrences of the bodies below with
+// the rows read and the factors written four at a time (one thread uses whole
+// 32-byte sectors, and the loads of the next four rows are issued before the
+// current four are processed).  Rows before the first multiple of 4 and after
+// the last one are taken one at a time.
+template <typename P, typename Q, typename R>
+__device__ __forceinline__ bool aligned16(const P* p, const Q* q, const R* r) {
+    return (((uintptr_t)p | (uintptr_t)q | (uintptr_t)r) & 15u) == 0;
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* g, const T (&v)[4]) {
+    if constexpr (std::is_same<T, double>::value) {
+        reinterpret_cast<double2*>(g)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2*>(g)[1] = make_double2(v[2], v[3]);
+    } else {
+        *reinterpret_cast<float4*>(g) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+template <typename T>
+__device__ __forceinline__ void ld4(T (&v)[4], const T* g) {
+    if constexpr (std::is_same<T, double>::value) {
+        const double2 p = reinterpret_cast<const double2*>(g)[0], q = reinterpret_cast<const double2*>(g)[1];
+        v[0] = p.x; v[1] = p.y; v[2] = q.x; v[3] = q.y;
+    } else {
+        const float4 p = *reinterpret_cast<const float4*>(g);
+        v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void factor_tp_scalar(const LevelArgs& a, const long long i) {
+    if (i >= a.p) return;
+    const Part pt = part_bounds(a, 0, i);
+    T* gDinv = reinterpret_cast<T*>(a.Dinv);
+    T* gY = reinterpret_cast<T*>(a.Y);
+    T* gZ = reinterpret_cast<T*>(a.Zc);
+    const double* gB = a.B - a.shift;
+    const double* gD = a.D - a.shift;
+    const double* gC = a.C - a.shift;
+    const long long s = pt.s, e = pt.e;
+    const bool hasL = pt.hasL, hasR = pt.hasR;
+    T yp = T(0), zp = T(0), cp = T(0);
+    T w = hasL ? (T)gC[s - 1] : T(0);   // W_s = C of the left separator row
+    const bool vec = aligned16(gB, gD, gC) && aligned16(gDinv, gY, gZ);
+    auto step = [&](long long j, double bj, double dj, double cj, T& dinv, T& z, T& y) {
+        const bool first = (j == s);
+        const bool needB = !first || hasL;
+        const bool needC = (j < e - 1) || hasR;
+        T u = (T)dj;
+        if (!first) u = fmaT<T>(-(T)bj, yp, u);
+        bool ok = true;
+        T pv = u;
+        T thr = T(0);
+        if (a.brk != nullptr) {
+            unsigned long long mk = abs_key(u);
+            if (needB) mk = max(mk, abs_key((T)bj));
+            if (needC) mk = max(mk, abs_key((T)cj));
+            thr = (T)a.tau * key_abs<T>(mk);
+        }
+        if (nonfinite(pv)) {
+            report(a.status, ST_NONFINITE, a.level, i, j);
+            pv = T(1);
+            ok = false;
+        } else if (a.brk != nullptr && !(abs_key(pv) > abs_key(thr))) {
+            record_breakdown(a.brk, a.brk_cap, j);
+            pv = T(1);
+            ok = false;
+        } else if (pv == T(0)) {
+            report(a.status, ST_SINGULAR, a.level, i, j);
+            pv = T(1);
+            ok = false;
+        }
+        const T r = rcp(pv);
+        dinv = r;
+        z = T(0);
+        if (hasL) z = first ? -r * (T)bj : -r * ((T)bj * zp);
+        y = T(0);
+        if (needC && (ok || a.brk == nullptr)) y = r * (T)cj;
+        if (hasL) {
+            cp = fmaT<T>(w, z, cp);
+            w = needC ? -w * y : T(0);
+        }
+        if (needC) yp = y;
+        zp = z;
+    };
+    long long j = s;
+    for (; j < e && ((j & 3) || !vec); ++j) {
+        T dv, zv, yv;
+        step(j, gB[j], gD[j], gC[j], dv, zv, yv);
+        gDinv[j] = dv;
+        gZ[j] = zv;
+        gY[j] = yv;
+    }
+    if (j + 4 <= e) {
+        double cb[4], cd[4], cc[4];
+        ld4<double>(cb, gB + j);
+        ld4<double>(cd, gD + j);
+        ld4<double>(cc, gC + j);
+        for (; j + 4 <= e; j += 4) {
+            const bool more = (j + 8 <= e);
+            double nb[4], nd[4], nc[4];
+            if (more) {
+                ld4<double>(nb, gB + j + 4);
+                ld4<double>(nd, gD + j + 4);
+                ld4<double>(nc, gC + j + 4);
+            }
+            T dv[4], zv[4], yv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) step(j + u, cb[u], cd[u], cc[u], dv[u], zv[u], yv[u]);
+            st4<T>(gDinv + j, dv);
+            st4<T>(gZ + j, zv);
+            st4<T>(gY + j, yv);
+            if (more) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    cb[u] = nb[u];
+                    cd[u] = nd[u];
+                    cc[u] = nc[u];
+                }
+            }
+        }
+    }
+    for (; j < e; ++j) {
+        T dv, zv, yv;
+        step(j, gB[j], gD[j], gC[j], dv, zv, yv);
+        gDinv[j] = dv;
+        gZ[j] = zv;
+        gY[j] = yv;
+    }
+    if (!hasL) return;
+    reinterpret_cast<T*>(a.Pf)[i] = cp;
+    reinterpret_cast<T*>(a.Qf)[i] = w;
+}
+
+// Forward substitution h_j = D'_j^{-1}(f_j - b_j h_{j-1}) for one right-hand
+// side; the top row's value after full elimination, H = sum_j w_j h_j with
+// w_s = 1, w_{j+1} = -w_j Y_j, is accumulated on the way (no backward pass).
+template <typename T>
+__device__ __forceinline__ void solve_fwd_tp_scalar(const LevelArgs& a, const long long i) {
+    if (i >= a.p) return;
+    const Part pt = part_bounds(a, 0, i);
+    const T* gDinv = reinterpret_cast<const T*>(a.Dinv);
+    const T* gY = reinterpret_cast<const T*>(a.Y);
+    const double* gB = a.B - a.shift;
+    const double* F = a.F;
+    double* X = a.X;
+    const long long s = pt.s, e = pt.e;
+    const bool hasL = pt.hasL;
+    T h = T(0), H = T(0), w = T(1);
+    const bool vec = aligned16(F, X, gB) && aligned16(gDinv, gY, gY);
+    auto step = [&](long long j, double fj, double bj, T dinv, T yj) -> T {
+        T v = (T)fj;
+        if (j != s) v = fmaT<T>(-(T)bj, h, v);
+        h = dinv * v;
+        if (hasL) {
+            H = fmaT<T>(w, h, H);
+            w = -w * yj;
+        }
+        return h;
+    };
+    long long j = s;
+    for (; j < e && ((j & 3) || !vec); ++j) X[j] = (double)step(j, F[j], gB[j], gDinv[j], hasL ? gY[j] : T(0));
+    if (j + 4 <= e) {
+        double cf[4], cb[4];
+        T cdv[4], cy[4];
+        ld4<double>(cf, F + j);
+        ld4<double>(cb, gB + j);
+        ld4<T>(cdv, gDinv + j);
+        if (hasL) ld4<T>(cy, gY + j);
+        for (; j + 4 <= e; j += 4) {
+            const bool more = (j + 8 <= e);
+            double nf[4], nb[4];
+            T ndv[4], ny[4];
+            if (more) {
+                ld4<double>(nf, F + j + 4);
+                ld4<double>(nb, gB + j + 4);
+                ld4<T>(ndv, gDinv + j + 4);
+                if (hasL) ld4<T>(ny, gY + j + 4);
+            }
+            double xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[u] = (double)step(j + u, cf[u], cb[u], cdv[u], hasL ? cy[u] : T(0));
+            st4<double>(X + j, xv);
+            if (more) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    cf[u] = nf[u];
+                    cb[u] = nb[u];
+                    cdv[u] = ndv[u];
+                    if (hasL) cy[u] = ny[u];
+                }
+            }
+        }
+    }
+    for (; j < e; ++j) X[j] = (double)step(j, F[j], gB[j], gDinv[j], hasL ? gY[j] : T(0));
+    if (hasL) reinterpret_cast<T*>(a.Hf)[i] = H;
+}
+
+// Back substitution x_j = h_j + Zc_j x_L - Y_j x_{j+1}, one right-hand side,
+// from the last local row up (chunks of four aligned rows, read backwards).
+template <typename T>
+__device__ __forceinline__ void solve_bwd_tp_scalar(const LevelArgs& a, const long long i) {
+    if (i >= a.p) return;
+    const Part pt = part_bounds(a, 0, i);
+    const T* gY = reinterpret_cast<const T*>(a.Y);
+    const T* gZ = reinterpret_cast<const T*>(a.Zc);
+    double* X = a.X;
+    const long long s = pt.s, e = pt.e;
+    const bool hasL = pt.hasL, hasR = pt.hasR;
+    T x = T(0), xl = T(0);
+    const bool vec = aligned16(X, gY, gZ);
+    if (hasR) {
+        const double xr = a.Xn[i];
+        X[e] = xr;
+        x = (T)xr;
+    }
+    if (hasL) xl = (T)a.Xn[i - 1];
+    auto step = [&](long long j, double hj, T yj, T zj) -> T {
+        T v = (T)hj;
+        if ((j < e - 1) || hasR) v = fmaT<T>(-yj, x, v);
+        if (hasL) v = fmaT<T>(zj, xl, v);
+        x = v;
+        return v;
+    };
+    long long j = e - 1;
+    for (; j >= s && (((j + 1) & 3) || !vec); --j) X[j] = (double)step(j, X[j], gY[j], hasL ? gZ[j] : T(0));
+    // j + 1 is now a multiple of 4: chunks [j-3, j]
+    if (j - 3 >= s) {
+        double ch[4];
+        T cy[4], cz[4];
+        ld4<double>(ch, X + j - 3);
+        ld4<T>(cy, gY + j - 3);
+        if (hasL) ld4<T>(cz, gZ + j - 3);
+        for (; j - 3 >= s; j -= 4) {
+            const bool more = (j - 7 >= s);
+            double nh[4];
+            T ny[4], nz[4];
+            if (more) {
+                ld4<double>(nh, X + j - 7);
+                ld4<T>(ny, gY + j - 7);
+                if (hasL) ld4<T>(nz, gZ + j - 7);
+            }
+            double xv[4];
+#pragma unroll
+            for (int u = 3; u >= 0; --u) xv[u] = (double)step(j - 3 + u, ch[u], cy[u], hasL ? cz[u] : T(0));
+            st4<double>(X + j - 3, xv);
+            if (more) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    ch[u] = nh[u];
+                    cy[u] = ny[u];
+                    if (hasL) cz[u] = nz[u];
+                }
+            }
+        }
+    }
+    for (; j >= s; --j) X[j] = (double)step(j, X[j], gY[j], hasL ? gZ[j] : T(0));
+}
+
 template <typename T, int M, int MODE>
 __device__ __forceinline__ void factor_tp_body(const LevelArgs& a, const long long i) {
     constexpr int MM = M * M;
+    if constexpr (M == 1 && MODE == 0) {
+        factor_tp_scalar<T>(a, i);
+        return;
+    }
     if (i >= a.p) return;
     const Part pt = part_bounds(a, MODE, i);
     T* gDinv = reinterpret_cast<T*>(a.Dinv);
@@ -273,6 +539,12 @@ __device__ __forceinline__ void vst(double* g, const T (&v)[M], int nr) {
 template <typename T, int M, int MODE>
 __device__ __forceinline__ void solve_fwd_tp_body(const LevelArgs& a, const long long tid) {
     constexpr int MM = M * M;
+    if constexpr (M == 1 && MODE == 0) {
+        if (a.nr == 1) {
+            solve_fwd_tp_scalar<T>(a, tid);
+            return;
+        }
+    }
     const int nr = a.nr;
     const long long i = tid / nr;
     const int c = (int)(tid % nr);
@@ -360,6 +632,12 @@ __device__ __forceinline__ void assemble_rhs_tp_body(const LevelArgs& a, const l
 template <typename T, int M, int MODE>
 __device__ __forceinline__ void solve_bwd_tp_body(const LevelArgs& a, const long long tid) {
     constexpr int MM = M * M;
+    if constexpr (M == 1 && MODE == 0) {
+        if (a.nr == 1) {
+            solve_bwd_tp_scalar<T>(a, tid);
+            return;
+        }
+    }
     const int nr = a.nr;
     const long long i = tid / nr;
     const int c = (int)(tid % nr);
