@@ -163,6 +163,23 @@ def btri_nondominant(N: int, m: int, nrhs: int = 1, seed_rep: int = 0, zero_frac
     return BtriSystem(B, D, C, btri_matvec(B, D, C, Xs), Xs)
 
 
+# ------------------------------------------------------------- heat equation --
+
+def heat_problem(n: int, nu: float = 0.5, seed_rep: int = 0):
+    """y' = L y + g0 + t g1 with L = nu/dx^2 tridiag(1, -2, 1) on n interior
+    points of [0, 1] (Dirichlet, dx = 1/(n+1)); y0, g0, g1 ~ N(0,1).
+    Returns (dl, d, du, y0, g0, g1) with dl[0] = du[n-1] = 0."""
+    dx = 1.0 / (n + 1)
+    c = nu / (dx * dx)
+    dl = np.full(n, c)
+    du = np.full(n, c)
+    d = np.full(n, -2.0 * c)
+    dl[0] = 0.0
+    du[-1] = 0.0
+    rng = rng_for(10, seed_rep)
+    return dl, d, du, rng.standard_normal(n), rng.standard_normal(n), rng.standard_normal(n)
+
+
 # ----------------------------------------------------- circulant-like (cyclic) --
 
 @dataclass
