@@ -165,9 +165,11 @@ def btri_nondominant(N: int, m: int, nrhs: int = 1, seed_rep: int = 0, zero_frac
 
 # ------------------------------------------------------------- heat equation --
 
-def heat_problem(n: int, nu: float = 0.5, seed_rep: int = 0):
+def heat_problem(n: int, nu: float = 0.5, seed_rep: int = 0, smooth: bool = False):
     """y' = L y + g0 + t g1 with L = nu/dx^2 tridiag(1, -2, 1) on n interior
-    points of [0, 1] (Dirichlet, dx = 1/(n+1)); y0, g0, g1 ~ N(0,1).
+    points of [0, 1] (Dirichlet, dx = 1/(n+1)).  Data: y0, g0, g1 ~ N(0,1), or
+    (smooth) a few low Fourier modes with N(0,1) amplitudes (the setting where
+    a coarse propagator resolves the solution and Parareal converges fast).
     Returns (dl, d, du, y0, g0, g1) with dl[0] = du[n-1] = 0."""
     dx = 1.0 / (n + 1)
     c = nu / (dx * dx)
@@ -177,7 +179,11 @@ def heat_problem(n: int, nu: float = 0.5, seed_rep: int = 0):
     dl[0] = 0.0
     du[-1] = 0.0
     rng = rng_for(10, seed_rep)
-    return dl, d, du, rng.standard_normal(n), rng.standard_normal(n), rng.standard_normal(n)
+    if not smooth:
+        return dl, d, du, rng.standard_normal(n), rng.standard_normal(n), rng.standard_normal(n)
+    x = np.arange(1, n + 1) * dx
+    modes = lambda: sum(rng.standard_normal() * np.sin(k * np.pi * x) for k in range(1, 5))
+    return dl, d, du, modes(), modes(), modes()
 
 
 # ----------------------------------------------------- circulant-like (cyclic) --

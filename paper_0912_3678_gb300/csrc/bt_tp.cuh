@@ -280,36 +280,36 @@ __device__ __forceinline__ void solve_fwd_tp_scalar(const LevelArgs& a, const lo
     };
     long long j = s;
     for (; j < e && ((j & 3) || !vec); ++j) X[j] = (double)step(j, F[j], gB[j], gDinv[j], hasL ? gY[j] : T(0));
-    if (j + 4 <= e) {
-        double cf[4], cb[4];
-        T cdv[4], cy[4];
-        ld4<double>(cf, F + j);
-        ld4<double>(cb, gB + j);
-        ld4<T>(cdv, gDinv + j);
-        if (hasL) ld4<T>(cy, gY + j);
-        for (; j + 4 <= e; j += 4) {
-            const bool more = (j + 8 <= e);
-            double nf[4], nb[4];
-            T ndv[4], ny[4];
-            if (more) {
-                ld4<double>(nf, F + j + 4);
-                ld4<double>(nb, gB + j + 4);
-                ld4<T>(ndv, gDinv + j + 4);
-                if (hasL) ld4<T>(ny, gY + j + 4);
-            }
-            double xv[4];
+    // chunks of four rows, two chunks loaded ahead of the one being processed
+    double cf[4], cb[4], nf[4], nb[4];
+    T cdv[4], cy[4], ndv[4], ny[4];
+    auto load = [&](long long r, double (&f)[4], double (&b)[4], T (&dv)[4], T (&y)[4]) {
+        ld4<double>(f, F + r);
+        ld4<double>(b, gB + r);
+        ld4<T>(dv, gDinv + r);
+        if (hasL) ld4<T>(y, gY + r);
+    };
+    if (j + 4 <= e) load(j, cf, cb, cdv, cy);
+    if (j + 8 <= e) load(j + 4, nf, nb, ndv, ny);
+    for (; j + 4 <= e; j += 4) {
+        double ff[4], fb[4];
+        T fdv[4], fy[4];
+        const bool far = (j + 12 <= e);
+        if (far) load(j + 8, ff, fb, fdv, fy);
+        double xv[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) xv[u] = (double)step(j + u, cf[u], cb[u], cdv[u], hasL ? cy[u] : T(0));
-            st4<double>(X + j, xv);
-            if (more) {
+        for (int u = 0; u < 4; ++u) xv[u] = (double)step(j + u, cf[u], cb[u], cdv[u], hasL ? cy[u] : T(0));
+        st4<double>(X + j, xv);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    cf[u] = nf[u];
-                    cb[u] = nb[u];
-                    cdv[u] = ndv[u];
-                    if (hasL) cy[u] = ny[u];
-                }
-            }
+        for (int u = 0; u < 4; ++u) {
+            cf[u] = nf[u];
+            cb[u] = nb[u];
+            cdv[u] = ndv[u];
+            cy[u] = ny[u];
+            nf[u] = ff[u];
+            nb[u] = fb[u];
+            ndv[u] = fdv[u];
+            ny[u] = fy[u];
         }
     }
     for (; j < e; ++j) X[j] = (double)step(j, F[j], gB[j], gDinv[j], hasL ? gY[j] : T(0));
@@ -344,34 +344,33 @@ __device__ __forceinline__ void solve_bwd_tp_scalar(const LevelArgs& a, const lo
     };
     long long j = e - 1;
     for (; j >= s && (((j + 1) & 3) || !vec); --j) X[j] = (double)step(j, X[j], gY[j], hasL ? gZ[j] : T(0));
-    // j + 1 is now a multiple of 4: chunks [j-3, j]
-    if (j - 3 >= s) {
-        double ch[4];
-        T cy[4], cz[4];
-        ld4<double>(ch, X + j - 3);
-        ld4<T>(cy, gY + j - 3);
-        if (hasL) ld4<T>(cz, gZ + j - 3);
-        for (; j - 3 >= s; j -= 4) {
-            const bool more = (j - 7 >= s);
-            double nh[4];
-            T ny[4], nz[4];
-            if (more) {
-                ld4<double>(nh, X + j - 7);
-                ld4<T>(ny, gY + j - 7);
-                if (hasL) ld4<T>(nz, gZ + j - 7);
-            }
-            double xv[4];
+    // j + 1 is now a multiple of 4: chunks [j-3, j], two loaded ahead
+    double ch[4], nh[4];
+    T cy[4], cz[4], ny[4], nz[4];
+    auto load = [&](long long r, double (&h)[4], T (&y)[4], T (&z)[4]) {
+        ld4<double>(h, X + r);
+        ld4<T>(y, gY + r);
+        if (hasL) ld4<T>(z, gZ + r);
+    };
+    if (j - 3 >= s) load(j - 3, ch, cy, cz);
+    if (j - 7 >= s) load(j - 7, nh, ny, nz);
+    for (; j - 3 >= s; j -= 4) {
+        double fh[4];
+        T fy[4], fz[4];
+        const bool far = (j - 11 >= s);
+        if (far) load(j - 11, fh, fy, fz);
+        double xv[4];
 #pragma unroll
-            for (int u = 3; u >= 0; --u) xv[u] = (double)step(j - 3 + u, ch[u], cy[u], hasL ? cz[u] : T(0));
-            st4<double>(X + j - 3, xv);
-            if (more) {
+        for (int u = 3; u >= 0; --u) xv[u] = (double)step(j - 3 + u, ch[u], cy[u], hasL ? cz[u] : T(0));
+        st4<double>(X + j - 3, xv);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    ch[u] = nh[u];
-                    cy[u] = ny[u];
-                    if (hasL) cz[u] = nz[u];
-                }
-            }
+        for (int u = 0; u < 4; ++u) {
+            ch[u] = nh[u];
+            cy[u] = ny[u];
+            cz[u] = nz[u];
+            nh[u] = fh[u];
+            ny[u] = fy[u];
+            nz[u] = fz[u];
         }
     }
     for (; j >= s; --j) X[j] = (double)step(j, X[j], gY[j], hasL ? gZ[j] : T(0));

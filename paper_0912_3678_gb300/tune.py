@@ -111,9 +111,15 @@ class Tuner:
 
     def candidates_k0(self, m, N):
         ks = [4, 8, 16, 32, 64, 128, 256] if m >= 8 else [8, 16, 32, 64, 128, 256, 512]
+        p0s = [max(1, min(N // k, (N + 1) // 2)) for k in ks]
+        if m <= 4:
+            # thread-per-partition kernels: whole waves of 128-thread CTAs on every SM
+            p0s += [self.sm_count() * 128 * c for c in (1, 2, 3, 4) if self.sm_count() * 128 * c <= (N + 1) // 2]
+        else:
+            # CTA per partition: whole waves of CTAs
+            p0s += [self.sm_count() * c for c in (2, 3, 4, 6) if self.sm_count() * c <= (N + 1) // 2]
         out = []
-        for k in ks:
-            p0 = max(1, min(N // k, (N + 1) // 2))
+        for p0 in p0s:
             if p0 not in [c["p0"] for c in out]:
                 out.append({"p0": p0, "ctas_per_sm": 0, "sub_rows": 0, "top_rows": 0, "reduced": 0, "tp_block": 0,
                             "local": 0})
