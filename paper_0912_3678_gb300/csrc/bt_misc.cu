@@ -591,10 +591,97 @@ cudaError_t launch_ir_update(long long n, double* X, const double* Dc, double* p
     k_reduce_pairs<<<1, 256, 0, s>>>(nb, partial, out);
     return cudaGetLastError();
 }
+// Scalar case (m = 1) of k_btri_direct: Gaussian elimination with partial
+// pivoting on a tridiagonal matrix (row interchanges between consecutive rows
+// fill in a second superdiagonal), one warp, lane c carrying right-hand side
+// c; every lane takes the same pivot decisions.  keep: [K][3] rows of U
+// (diagonal, first and second superdiagonal), then [K][nr] eliminated
+// right-hand sides.
+__global__ void __launch_bounds__(32) k_gtsv(int K, int nr, const double* __restrict__ B,
+                                             const double* __restrict__ D, const double* __restrict__ C,
+                                             const double* __restrict__ F, double* __restrict__ X,
+                                             double* __restrict__ keep, long long* status, int level) {
+    const int c = threadIdx.x;
+    const bool act = c < nr;
+    // working row i: [b (diag), cc (super), dd (second super)] and its right-hand side
+    double b = D[0], cc = (K > 1) ? C[0] : 0.0, f = act ? F[c] : 0.0;
+    double* U = keep;          // [K][3]
+    double* G = keep + 3 * (long long)K;   // [K][nr] eliminated right-hand sides
+    for (int i = 0; i < K; ++i) {
+        double dd = 0.0;
+        if (i + 1 < K) {
+            const double a1 = B[i + 1], b1 = D[i + 1], c1 = (i + 2 < K) ? C[i + 1] : 0.0;
+            double f1 = act ? F[(long long)(i + 1) * nr + c] : 0.0;
+            if (fabs(b) >= fabs(a1)) {
+                // pivot on row i: eliminate a1 from row i+1
+                double pv = b;
+                if (pv == 0.0 || nonfinite(pv)) {
+                    if (c == 0) report(status, pv == 0.0 ? ST_SINGULAR : ST_NONFINITE, level, -1, i);
+                    pv = 1.0;
+                    b = 1.0;
+                }
+                const double l = a1 * rcp(pv);
+                if (c == 0) {
+                    U[3 * i] = b;
+                    U[3 * i + 1] = cc;
+                    U[3 * i + 2] = 0.0;
+                }
+                if (act) G[(long long)i * nr + c] = f;
+                b = fma(-l, cc, b1);
+                cc = c1;
+                f = fma(-l, f, f1);
+            } else {
+                // interchange rows i and i+1, then eliminate
+                const double l = b * rcp(a1);
+                if (c == 0) {
+                    U[3 * i] = a1;
+                    U[3 * i + 1] = b1;
+                    U[3 * i + 2] = c1;
+                }
+                if (act) G[(long long)i * nr + c] = f1;
+                const double nb = fma(-l, b1, cc);
+                dd = -l * c1;
+                b = nb;
+                cc = dd;
+                f = fma(-l, f1, f);
+            }
+        } else {
+            double pv = b;
+            if (pv == 0.0 || nonfinite(pv)) {
+                if (c == 0) report(status, pv == 0.0 ? ST_SINGULAR : ST_NONFINITE, level, -1, i);
+                b = 1.0;
+            }
+            if (c == 0) {
+                U[3 * i] = b;
+                U[3 * i + 1] = 0.0;
+                U[3 * i + 2] = 0.0;
+            }
+            if (act) G[(long long)i * nr + c] = f;
+        }
+    }
+    __syncwarp();
+    // back substitution: x_i = (g_i - u1_i x_{i+1} - u2_i x_{i+2}) / u0_i
+    double x1 = 0.0, x2 = 0.0;
+    for (int i = K - 1; i >= 0; --i) {
+        const double u0 = U[3 * i], u1 = U[3 * i + 1], u2 = U[3 * i + 2];
+        double v = act ? G[(long long)i * nr + c] : 0.0;
+        v = fma(-u1, x1, v);
+        v = fma(-u2, x2, v);
+        const double xi = v * rcp(u0);
+        if (act) X[(long long)i * nr + c] = xi;
+        x2 = x1;
+        x1 = xi;
+    }
+}
+
 size_t btri_direct_smem(int m, int nr) { return sizeof(double) * ((size_t)(2 * m) * (3 * m + nr) + 2 * m); }
 cudaError_t launch_btri_direct(int K, int m, int nr, const double* B, const double* D, const double* C,
                                const double* F, double* X, double* keep, long long* status, int level,
                                cudaStream_t s) {
+    if (m == 1) {
+        k_gtsv<<<1, 32, 0, s>>>(K, nr, B, D, C, F, X, keep, status, level);
+        return cudaGetLastError();
+    }
     const size_t smem = btri_direct_smem(m, nr);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_btri_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
