@@ -118,6 +118,34 @@ def test_config2_full_size_fp64(cuda):
     assert oracle.rel_err(X, ref) <= TOL64
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32_ir"])
+def test_config2_in_the_bench_launch_configuration(cuda, prec):
+    """The block workload at full size (m = 16, N = 16384, 8 RHS) as the bench
+    runs it: the autotuner's partitioning for this shape (level-0 partitions
+    from the SM count, reduced system by cyclic reduction), one captured CUDA
+    graph per step (factor + solve, or factor + two corrections and the
+    checking residual), replayed; every entry against the oracle."""
+    import paper_0912_3678_gb300 as bt
+    N, m, nr = 16384, 16, 8
+    s = gen.btri_random(N, m, nr, seed_rep=0)
+    ref = oracle.btri_solve(s.B, s.D, s.C, s.F)
+    B, D, C, F = (to_dev(a, cuda) for a in (s.B, s.D, s.C, s.F))
+    with bt.BtPlan.tuned(N, m, nr, prec, {"reduced": 1}) as plan:
+        plan.factor(B, D, C)
+        X = plan.solve(F)
+        if prec == "fp64":
+            plan.capture("factor_solve", F, X)
+        else:
+            plan.capture("factor_refine", F, X, sweeps=2)
+        X.zero_()
+        plan.replay()
+        plan.sync()
+        if prec != "fp64":
+            code, rel = bt.bt_refine_result(plan.handle, 1e-12)
+            assert code == 0
+        assert oracle.rel_err(to_host(X), ref) <= (TOL64 if prec == "fp64" else TOLIR)
+
+
 @pytest.mark.parametrize("m,N", [(1, 5000), (4, 999), (8, 700), (16, 1024), (32, 130)])
 def test_mixed_precision_refinement(cuda, m, N):
     import paper_0912_3678_gb300 as bt
