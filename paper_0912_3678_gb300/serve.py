@@ -191,10 +191,14 @@ class Server:
         vecs = 6 * (N + 1) * m * r.nrhs * 8 + (N + 1) * m * m * 8   # rhs, solution, exact, build temporaries
         return ws, mats, vecs
 
-    def _evict_for(self, need):
+    def _evict_for(self, need, keep=None):
+        """Release idle cached factorizations (least recently used first) until
+        need bytes fit; never the one under `keep`, which the caller reuses."""
         for key in list(self.cache.keys()):
             if self.in_use + need <= self.cap:
                 break
+            if key == keep:
+                continue
             f = self.cache[key]
             if f.busy == 0:
                 f.destroy()
@@ -223,6 +227,15 @@ class Server:
                 f = None
         ws_b, mat_b, vec_b = self._footprint(r, _round_nrhs(r.nrhs))
         need = vec_b + (0 if f is not None else ws_b + mat_b)
+        if f is not None and self.in_use + need > self.cap and not self._evict_for(need, keep=key):
+            if f.busy:
+                return False        # requests in flight will release memory
+            # only the reused factorization itself is in the way: give up the reuse
+            f.destroy()
+            self.in_use -= f.nbytes
+            del self.cache[key]
+            f = None
+            need = vec_b + ws_b + mat_b
         if need > self.cap:
             # can never fit: fail it now instead of holding the queue
             r.status = 2            # BT_ERR_NOMEM
@@ -230,7 +243,7 @@ class Server:
             r.Y = None
             self.done.append(r)
             return True
-        if self.in_use + need > self.cap and not self._evict_for(need):
+        if self.in_use + need > self.cap and not self._evict_for(need, keep=key if f is not None else None):
             return False
         if f is not None:
             r.cache_hit = True
