@@ -75,7 +75,7 @@ MEASURED_TRAFFIC = {
 
 def _factor_flops_per_row(m: int) -> float:
     # algorithmic count per local block row: block-Thomas factorization
-    # (2/3 + 2 + 2) m^3 plus the left spike 4 m^3 (see DESIGN.md)
+    # (2/3 + 2 + 2) m^3 plus the left spike 4 m^3
     return (2.0 / 3.0 + 2.0 + 2.0 + 4.0) * m ** 3
 
 
@@ -170,7 +170,7 @@ def run_reference(args):
 
 
 def run_batch(args):
-    """Config 4: uneven independent systems (n log-uniform, m from {1,4,8,16,32},
+    """Batched workload: 4096 uneven independent systems (n log-uniform, m from {1,4,8,16,32},
     50/50 FP64 / BF16+refinement), generated on the device, one graph launch
     per step.  Accuracy: a sample of systems against the oracle."""
     import torch
@@ -405,7 +405,7 @@ def run_cyclic(args):
 
 
 def run_serve(args):
-    """Config 5: Poisson arrivals of BVP solves (m in {4,8,16}, N log-uniform
+    """Served workload: Poisson arrivals of BVP solves (m in {4,8,16}, N log-uniform
     [1e3, 5e5], 1-32 RHS, 30% factorization reuse) replayed in real time."""
     import torch
 

@@ -54,7 +54,7 @@ def test_babd_reduced_matrix(cuda):
     assert np.abs(b_ - be).max() <= 1e-13 * scale
 
 
-def test_config3_full_size(cuda):
+def test_babd_m8_n262144_full_size(cuda):
     """Trapezoidal BABD, m = 8, N = 2^18 steps: parity with the oracle and the
     O(h^2) error against the exact solution y(t) = exp(sin 3t) v."""
     N = 1 << 18
@@ -66,7 +66,7 @@ def test_config3_full_size(cuda):
     assert np.abs(Y - b.Yexact).max() <= 200 * h * h
 
 
-def test_config3_separated_bc_full_size(cuda):
+def test_babd_m8_n262144_separated_full_size(cuda):
     N = 1 << 18
     b = gen.babd_bvp(N, 8, 1, separated=True, seed_rep=1)
     Y, lev = _solve(cuda, b)

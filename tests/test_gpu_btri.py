@@ -1,6 +1,6 @@
 """GPU parity of the block tridiagonal partition solver (bt_*) against the
 oracle, element by element on the same seeded inputs.  FP64 path: normwise
-relative error <= 1e-11 (the configs here have kappa <= ~10); mixed precision
+relative error <= 1e-11 (the systems here have kappa <= ~10); mixed precision
 with FP64 refinement: <= 1e-10."""
 import numpy as np
 import pytest
@@ -79,7 +79,7 @@ def test_reduced_matrix_is_schur_complement(cuda, m, N, p):
     assert np.abs(g_ - ga).max() <= 1e-13 * scale
 
 
-def test_config1_scalar_p64(cuda):
+def test_scalar_n65536_p64(cuda):
     """Scalar tridiagonal n = 2^16, p = 64 partitions (the plain method)."""
     s = gen.tri_sdd(1 << 16, 1, seed_rep=0)
     sb = gen.BtriSystem(s.dl.reshape(-1, 1, 1), s.d.reshape(-1, 1, 1), s.du.reshape(-1, 1, 1), s.f, s.xstar)
@@ -110,7 +110,7 @@ def test_poisson_closed_form(cuda):
     assert np.linalg.norm(r) / (4 * np.linalg.norm(X) + np.linalg.norm(f)) <= 1e-14
 
 
-def test_config2_full_size_fp64(cuda):
+def test_block_m16_n16384_full_size_fp64(cuda):
     """Block tridiagonal m = 16, N = 16384 block rows, 8 right-hand sides."""
     s = gen.btri_random(16384, 16, 8, seed_rep=0)
     X, lev = _solve(cuda, s)
@@ -119,7 +119,7 @@ def test_config2_full_size_fp64(cuda):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_ir"])
-def test_config2_in_the_bench_launch_configuration(cuda, prec):
+def test_block_m16_n16384_in_the_bench_launch_configuration(cuda, prec):
     """The block workload at full size (m = 16, N = 16384, 8 RHS) as the bench
     runs it: the autotuner's partitioning for this shape (level-0 partitions
     from the SM count, reduced system by cyclic reduction), one captured CUDA
