@@ -96,27 +96,32 @@ def test_memory_admission_respects_cap(cuda):
 
 def test_cache_hit_under_memory_pressure_keeps_its_factorization(cuda):
     """A repeated problem arrives when the cache must shed memory: the eviction
-    releases another idle factorization, never the one the request reuses."""
+    releases another idle factorization, never the one the request reuses.
+    A (4 RHS) and C (1 RHS) stay cached; the cap leaves no room for B's vectors
+    (B repeats A with 4 RHS) unless one of them goes."""
     from paper_0912_3678_gb300 import serve
     rng = np.random.default_rng(5)
     pa = gen.bvp_problem(8, 1, seed_rep=501)
     pc = gen.bvp_problem(8, 1, seed_rep=502)
     sa = serve.BvpSpec(pa.Smat, pa.K, pa.B0, pa.B1)
     sc = serve.BvpSpec(pc.Smat, pc.K, pc.B0, pc.B1)
-    A = serve.Request(0, 0.0, 0, sa, 800, rng.standard_normal((8, 2)), "fp64")
-    C = serve.Request(1, 0.0, 1, sc, 800, rng.standard_normal((8, 2)), "fp64")
-    B = serve.Request(2, 0.0, 0, sa, 800, rng.standard_normal((8, 2)), "fp64")
+    A = serve.Request(0, 0.0, 0, sa, 800, rng.standard_normal((8, 4)), "fp64")
+    C = serve.Request(1, 0.0, 1, sc, 800, rng.standard_normal((8, 1)), "fp64")
+    B = serve.Request(2, 0.0, 0, sa, 800, rng.standard_normal((8, 4)), "fp64")
     probe = serve.Server(cuda, streams=1)
-    ws, mat, vec = probe._footprint(B, serve._round_nrhs(B.nrhs))
+    wsA, mat, vecB = probe._footprint(B, serve._round_nrhs(4))
+    wsC, _, _ = probe._footprint(C, serve._round_nrhs(1))
     probe.close()
-    cap = 2 * (ws + mat) + vec - 1          # A and C cached leave no room for B's vectors
+    cap = (wsA + mat) + (wsC + mat) + vecB - 1
     srv = serve.Server(cuda, mem_cap_bytes=cap, streams=1)
     for r in (A, C):
         srv.submit(r)
         srv.drain(timeout_s=60)
+    assert len(srv.cache) == 2
     srv.submit(B)
     srv.drain(timeout_s=60)
     assert B.status == 0 and B.cache_hit
+    assert len(srv.cache) == 1
     b = gen.trapezoidal_babd(gen.BvpProblem(sa.S, sa.K, sa.B0, sa.B1, B.V), B.N)
     ref = oracle.babd_solve(b.S, b.R, b.B0, b.B1, b.RHS)
     assert oracle.rel_err(to_host(B.Y), ref) <= 1e-11
