@@ -280,37 +280,34 @@ __device__ __forceinline__ void solve_fwd_tp_scalar(const LevelArgs& a, const lo
     };
     long long j = s;
     for (; j < e && ((j & 3) || !vec); ++j) X[j] = (double)step(j, F[j], gB[j], gDinv[j], hasL ? gY[j] : T(0));
-    // chunks of four rows, two chunks loaded ahead of the one being processed
-    double cf[4], cb[4], nf[4], nb[4];
-    T cdv[4], cy[4], ndv[4], ny[4];
-    auto load = [&](long long r, double (&f)[4], double (&b)[4], T (&dv)[4], T (&y)[4]) {
-        ld4<double>(f, F + r);
-        ld4<double>(b, gB + r);
-        ld4<T>(dv, gDinv + r);
-        if (hasL) ld4<T>(y, gY + r);
+    // chunks of four rows; the PD chunks after the one being processed are in flight
+    constexpr int PD = 3;
+    double qf[PD + 1][4], qb[PD + 1][4];
+    T qd[PD + 1][4], qy[PD + 1][4];
+    auto load = [&](long long r, int k) {
+        ld4<double>(qf[k], F + r);
+        ld4<double>(qb[k], gB + r);
+        ld4<T>(qd[k], gDinv + r);
+        if (hasL) ld4<T>(qy[k], gY + r);
     };
-    if (j + 4 <= e) load(j, cf, cb, cdv, cy);
-    if (j + 8 <= e) load(j + 4, nf, nb, ndv, ny);
+#pragma unroll
+    for (int k = 0; k < PD; ++k)
+        if (j + 4 * (k + 1) <= e) load(j + 4 * k, k);
     for (; j + 4 <= e; j += 4) {
-        double ff[4], fb[4];
-        T fdv[4], fy[4];
-        const bool far = (j + 12 <= e);
-        if (far) load(j + 8, ff, fb, fdv, fy);
+        if (j + 4 * (PD + 1) <= e) load(j + 4 * PD, PD);
         double xv[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) xv[u] = (double)step(j + u, cf[u], cb[u], cdv[u], hasL ? cy[u] : T(0));
+        for (int u = 0; u < 4; ++u) xv[u] = (double)step(j + u, qf[0][u], qb[0][u], qd[0][u], hasL ? qy[0][u] : T(0));
         st4<double>(X + j, xv);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            cf[u] = nf[u];
-            cb[u] = nb[u];
-            cdv[u] = ndv[u];
-            cy[u] = ny[u];
-            nf[u] = ff[u];
-            nb[u] = fb[u];
-            ndv[u] = fdv[u];
-            ny[u] = fy[u];
-        }
+        for (int k = 0; k < PD; ++k)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                qf[k][u] = qf[k + 1][u];
+                qb[k][u] = qb[k + 1][u];
+                qd[k][u] = qd[k + 1][u];
+                qy[k][u] = qy[k + 1][u];
+            }
     }
     for (; j < e; ++j) X[j] = (double)step(j, F[j], gB[j], gDinv[j], hasL ? gY[j] : T(0));
     if (hasL) reinterpret_cast<T*>(a.Hf)[i] = H;
@@ -344,34 +341,32 @@ __device__ __forceinline__ void solve_bwd_tp_scalar(const LevelArgs& a, const lo
     };
     long long j = e - 1;
     for (; j >= s && (((j + 1) & 3) || !vec); --j) X[j] = (double)step(j, X[j], gY[j], hasL ? gZ[j] : T(0));
-    // j + 1 is now a multiple of 4: chunks [j-3, j], two loaded ahead
-    double ch[4], nh[4];
-    T cy[4], cz[4], ny[4], nz[4];
-    auto load = [&](long long r, double (&h)[4], T (&y)[4], T (&z)[4]) {
-        ld4<double>(h, X + r);
-        ld4<T>(y, gY + r);
-        if (hasL) ld4<T>(z, gZ + r);
+    // j + 1 is now a multiple of 4: chunks [j-3, j]; PD chunks below it in flight
+    constexpr int PD = 3;
+    double qh[PD + 1][4];
+    T qy[PD + 1][4], qz[PD + 1][4];
+    auto load = [&](long long r, int k) {
+        ld4<double>(qh[k], X + r);
+        ld4<T>(qy[k], gY + r);
+        if (hasL) ld4<T>(qz[k], gZ + r);
     };
-    if (j - 3 >= s) load(j - 3, ch, cy, cz);
-    if (j - 7 >= s) load(j - 7, nh, ny, nz);
+#pragma unroll
+    for (int k = 0; k < PD; ++k)
+        if (j - 3 - 4 * k >= s) load(j - 3 - 4 * k, k);
     for (; j - 3 >= s; j -= 4) {
-        double fh[4];
-        T fy[4], fz[4];
-        const bool far = (j - 11 >= s);
-        if (far) load(j - 11, fh, fy, fz);
+        if (j - 3 - 4 * PD >= s) load(j - 3 - 4 * PD, PD);
         double xv[4];
 #pragma unroll
-        for (int u = 3; u >= 0; --u) xv[u] = (double)step(j - 3 + u, ch[u], cy[u], hasL ? cz[u] : T(0));
+        for (int u = 3; u >= 0; --u) xv[u] = (double)step(j - 3 + u, qh[0][u], qy[0][u], hasL ? qz[0][u] : T(0));
         st4<double>(X + j - 3, xv);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            ch[u] = nh[u];
-            cy[u] = ny[u];
-            cz[u] = nz[u];
-            nh[u] = fh[u];
-            ny[u] = fy[u];
-            nz[u] = fz[u];
-        }
+        for (int k = 0; k < PD; ++k)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                qh[k][u] = qh[k + 1][u];
+                qy[k][u] = qy[k + 1][u];
+                qz[k][u] = qz[k + 1][u];
+            }
     }
     for (; j >= s; --j) X[j] = (double)step(j, X[j], gY[j], hasL ? gZ[j] : T(0));
 }
