@@ -122,7 +122,15 @@ bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int p
  *                synchronises once per splitting pass; reduced and local are
  *                unused; graph capture only of solves (what = 2).  If more
  *                rows break down than the reduced system has room for,
- *                bt_factor returns BT_ERR_SINGULAR. */
+ *                bt_factor returns BT_ERR_SINGULAR.
+ *   serial       1 = captured sequences (bt_plan_capture with factor) run on
+ *                one stream.  0 (default): the factorization of the levels
+ *                above level 0 (and the reduced system's cyclic reduction)
+ *                runs on a second stream, concurrently with the level-0
+ *                forward substitution, which needs only the level-0 factors;
+ *                the streams join before the reduced system's right-hand side
+ *                is used.  Eager bt_factor / bt_solve calls always use the
+ *                plan's stream alone. */
 typedef struct {
     int64_t p0;
     int ctas_per_sm;
@@ -132,6 +140,7 @@ typedef struct {
     int tp_block;
     int local;
     int pivot;
+    int serial;
 } bt_tuning;
 
 /* bt_plan_create with explicit partitioning parameters (NULL = defaults). */

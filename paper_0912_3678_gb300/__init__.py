@@ -77,7 +77,7 @@ def _tuning(t):
         return t
     return BtTuning(int(t.get("p0", 0)), int(t.get("ctas_per_sm", 0)), int(t.get("sub_rows", 0)),
                     int(t.get("top_rows", 0)), int(t.get("reduced", 0)), int(t.get("tp_block", 0)),
-                    int(t.get("local", 0)), int(t.get("pivot", 0)))
+                    int(t.get("local", 0)), int(t.get("pivot", 0)), int(t.get("serial", 0)))
 
 
 def bt_plan_create_tuned(nblk, m, nrhs_max=1, prec="fp64", tuning=None, stream=None):

@@ -51,7 +51,8 @@ SIGNATURES = {
 class BtTuning(ctypes.Structure):
     _fields_ = [("p0", ctypes.c_int64), ("ctas_per_sm", ctypes.c_int), ("sub_rows", ctypes.c_int),
                 ("top_rows", ctypes.c_int), ("reduced", ctypes.c_int), ("tp_block", ctypes.c_int),
-                ("local", ctypes.c_int), ("pivot", ctypes.c_int)]
+                ("local", ctypes.c_int), ("pivot", ctypes.c_int),
+                ("serial", ctypes.c_int)]
 
 
 class BtBatchDesc(ctypes.Structure):

@@ -93,6 +93,14 @@ struct bt_plan_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     long long graph_launches = 0;
+    // captured factor+solve sequences: the factorization of levels >= 1 (and
+    // the reduced system's cyclic reduction) runs on a second stream, beside
+    // the level-0 forward substitution, which needs only the level-0 factors
+    bool serial = false;                // captured sequences on one stream
+    bool overlap = false;
+    bool join_pending = false;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // tracing
     bool trace = false;
     struct Rec { int key; cudaEvent_t a, b; };
@@ -274,6 +282,7 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
     const int sms = sm_count(P->device);
     std::vector<bt::LevelShape> shapes;
     P->pivot = (kind == 0 && tune.pivot > 0);
+    P->serial = tune.serial > 0;
     bt::Tuning tsh = tune;
     if (P->pivot) {
         tsh.reduced = 0;
@@ -504,8 +513,26 @@ bt_status run_factor_pivoted(bt_plan_s* P) {
 bt_status run_factor(bt_plan_s* P) {
     if (P->pivot) return run_factor_pivoted(P);
     const bt::Launchers* L = P->L;
+    const bool split = P->overlap && P->side && P->nlev >= 1;
+    cudaStream_t main_stream = P->stream;
+    // levels >= 1 on the side stream when split; rejoined by run_solve after level 0
+    auto rejoin = [&](bt_status st) {
+        if (P->stream != main_stream) {
+            cudaError_t e = cudaEventRecord(P->ev_join, P->stream);
+            P->stream = main_stream;
+            if (e != cudaSuccess) return from_cuda(e);
+            P->join_pending = true;
+        }
+        return st;
+    };
     for (int l = 0; l <= P->nlev; ++l) {
         Level& v = P->lv[l];
+        if (split && l == 1) {
+            cudaError_t e = cudaEventRecord(P->ev_fork, main_stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(P->side, P->ev_fork, 0);
+            if (e != cudaSuccess) return from_cuda(e);
+            P->stream = P->side;
+        }
         if (P->kind == 1 && l == P->nlev) break;   // BABD top: direct solve at solve time
         if (P->bcr && l == P->nlev) {
             // block cyclic reduction of the reduced system (or of the whole
@@ -520,16 +547,23 @@ bt_status run_factor(bt_plan_s* P) {
                 const long long ctas = (b.K == 1) ? 1 : (b.K + 1) / 2;
                 cudaError_t e =
                     launch(P, K_BCR_FACTOR, b.level, 1, [&] { return L->bcr_factor(b, ctas, P->stream); });
-                if (e != cudaSuccess) return from_cuda(e);
+                if (e != cudaSuccess) return rejoin(from_cuda(e));
             }
             break;
         }
         cudaError_t e = launch(P, K_FACTOR, l, 1, [&] { return L->factor(v.a, v.low, P->stream); });
         if (e == cudaSuccess && P->kind == 0 && l < P->nlev)
             e = launch(P, K_ASSEMBLE, l, 1, [&] { return L->assemble(v.a, v.low, P->stream); });
-        if (e != cudaSuccess) return from_cuda(e);
+        if (e != cudaSuccess) return rejoin(from_cuda(e));
     }
-    return BT_OK;
+    return rejoin(BT_OK);
+}
+
+// The main stream waits for a factorization left running on the side stream.
+cudaError_t join_factor(bt_plan_s* P) {
+    if (!P->join_pending) return cudaSuccess;
+    P->join_pending = false;
+    return cudaStreamWaitEvent(P->stream, P->ev_join, 0);
 }
 
 // Solve with the factors: F (level-0 rhs) -> X.
@@ -543,11 +577,13 @@ bt_status run_solve(bt_plan_s* P, const double* F, double* X, int nr) {
         cudaError_t e = launch(P, K_SOLVE_FWD, l, 1, [&] { return L->solve_fwd(v.a, v.low, P->stream); });
         if (e == cudaSuccess && P->kind == 0)
             e = launch(P, K_ASSEMBLE_RHS, l, 1, [&] { return L->assemble_rhs(v.a, v.low, P->stream); });
+        if (e == cudaSuccess && l == 0) e = join_factor(P);
         if (e != cudaSuccess) return from_cuda(e);
     }
     Level& t = P->lv[P->nlev];
     const int lt = P->nlev;
-    cudaError_t e;
+    cudaError_t e = join_factor(P);
+    if (e != cudaSuccess) return from_cuda(e);
     if (P->bcr) {
         e = cudaSuccess;
         if (P->nlev == 0) {
@@ -591,6 +627,10 @@ bt_status run_solve(bt_plan_s* P, const double* F, double* X, int nr) {
 
 bt_status run_residual(bt_plan_s* P, const double* F, const double* X, double* R, int nr,
                        unsigned long long* maxout = nullptr) {
+    if (P->join_pending) {
+        cudaError_t e = join_factor(P);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
     if (maxout) {
         cudaError_t e = cudaMemsetAsync(maxout, 0, kSlotWords * sizeof(unsigned long long), P->stream);
         if (e != cudaSuccess) return from_cuda(e);
@@ -740,6 +780,7 @@ static bt::Tuning to_tuning(const bt_tuning* t, int64_t p) {
         u.tp_block = t->tp_block;
         u.local = t->local;
         u.pivot = t->pivot;
+        u.serial = t->serial;
     }
     if (p > 0) u.p0 = p;
     return u;
@@ -753,6 +794,7 @@ bt_status bt_plan_create_tuned(bt_plan* plan, int64_t nblk, int m, int nrhs_max,
                                void* stream) {
     if (tuning && (tuning->p0 < 0 || tuning->ctas_per_sm < 0 || tuning->sub_rows < 0 || tuning->top_rows < 0 ||
                    tuning->reduced < 0 || tuning->reduced > 1 || tuning->local < 0 || tuning->local > 62 || tuning->pivot < 0 || tuning->pivot > 1 ||
+                   tuning->serial < 0 || tuning->serial > 1 ||
                    !(tuning->tp_block == 0 || tuning->tp_block == 64 || tuning->tp_block == 128 ||
                      tuning->tp_block == 256)))
         return BT_ERR_INVALID;
@@ -1043,6 +1085,12 @@ bt_status bt_plan_capture(bt_plan P, int what, const double* F, double* X, int n
     // kernels with large shared memory get their attribute before capture
     e = P->L->prepare();
     if (e != cudaSuccess) return from_cuda(e);
+    if (what != 2 && !P->pivot && !P->serial && P->nlev >= 1 && !P->side) {
+        e = cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
     cudaStream_t saved = P->stream, cap = nullptr;
     e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return from_cuda(e);
@@ -1072,13 +1120,19 @@ bt_status bt_plan_capture(bt_plan P, int what, const double* F, double* X, int n
                 e = cudaMemcpyAsync(P->B0, P->U[2], mm, cudaMemcpyDeviceToDevice, cap);
                 if (e == cudaSuccess) e = cudaMemcpyAsync(P->B1, P->U[3], mm, cudaMemcpyDeviceToDevice, cap);
             }
+            P->overlap = !P->serial;
             if (e == cudaSuccess) st = run_factor(P);
+            P->overlap = false;
             if (e == cudaSuccess && st == BT_OK && what == 3) st = ensure_anorm(P, true);
         }
         if (e == cudaSuccess && st == BT_OK) {
             st = padded_call(P, F, X, nrhs, [&](const double* f, double* x) {
                 return what == 3 ? run_refine_async(P, f, x, nrhs, sweeps) : run_solve(P, f, x, nrhs);
             });
+        }
+        if (P->join_pending) {
+            cudaError_t ej = join_factor(P);
+            if (e == cudaSuccess) e = ej;
         }
         cudaGraph_t g = nullptr;
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
@@ -1219,6 +1273,12 @@ void bt_plan_destroy(bt_plan P) {
     for (auto ev : P->pool) cudaEventDestroy(ev);
     if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
     if (P->graph) cudaGraphDestroy(P->graph);
+    if (P->side) {
+        cudaStreamSynchronize(P->side);
+        cudaStreamDestroy(P->side);
+    }
+    if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+    if (P->ev_join) cudaEventDestroy(P->ev_join);
     if (P->own_arena) cudaFree(P->arena);
     if (P->pinned) {
         if (P->status_host) cudaFreeHost(P->status_host);

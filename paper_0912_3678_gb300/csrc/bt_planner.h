@@ -13,6 +13,7 @@ struct Tuning {
     int tp_block = 0;        // threads per CTA of the thread-per-partition kernels (0: 128)
     int local = 0;           // level-0 local factorization: 0 block LU + spikes, L >= 1 cyclic reduction of 2^L rows
     int pivot = 0;           // 1: partitions split at breakdown rows, reduced system by banded GEPP
+    int serial = 0;          // 1: captured factor+solve sequences on one stream
 };
 
 struct LevelShape {

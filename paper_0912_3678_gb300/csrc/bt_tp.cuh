@@ -119,19 +119,19 @@ __device__ __forceinline__ bool rgj_inverse(T (&a)[M * M], long long* st, int le
 
 // ------------------------------------------------------- scalar partitions --
 // m = 1, block tridiagonal levels: the recurrences of the bodies below with
-// the rows read and the factors written four at a time (one thread uses whole
-// 32-byte sectors, and the loads of the next four rows are issued before the
-// current four are processed).  Rows before the first multiple of 4 and after
-// the last one are taken one at a time.
+// the rows read and the factors written four at a time (one 256-bit access
+// per thread and array: whole 32-byte sectors, half the load instructions of
+// 128-bit pairs), and the loads of the next chunks issued before the current
+// four rows are processed.  Rows before the first multiple of 4 and after the
+// last one, and arrays that are not 32-byte aligned, are taken one at a time.
 template <typename P, typename Q, typename R>
-__device__ __forceinline__ bool aligned16(const P* p, const Q* q, const R* r) {
-    return (((uintptr_t)p | (uintptr_t)q | (uintptr_t)r) & 15u) == 0;
+__device__ __forceinline__ bool aligned32(const P* p, const Q* q, const R* r) {
+    return (((uintptr_t)p | (uintptr_t)q | (uintptr_t)r) & 31u) == 0;
 }
 template <typename T>
 __device__ __forceinline__ void st4(T* g, const T (&v)[4]) {
     if constexpr (std::is_same<T, double>::value) {
-        reinterpret_cast<double2*>(g)[0] = make_double2(v[0], v[1]);
-        reinterpret_cast<double2*>(g)[1] = make_double2(v[2], v[3]);
+        *reinterpret_cast<double4_32a*>(g) = make_double4_32a(v[0], v[1], v[2], v[3]);
     } else {
         *reinterpret_cast<float4*>(g) = make_float4(v[0], v[1], v[2], v[3]);
     }
@@ -139,8 +139,8 @@ __device__ __forceinline__ void st4(T* g, const T (&v)[4]) {
 template <typename T>
 __device__ __forceinline__ void ld4(T (&v)[4], const T* g) {
     if constexpr (std::is_same<T, double>::value) {
-        const double2 p = reinterpret_cast<const double2*>(g)[0], q = reinterpret_cast<const double2*>(g)[1];
-        v[0] = p.x; v[1] = p.y; v[2] = q.x; v[3] = q.y;
+        const double4_32a p = *reinterpret_cast<const double4_32a*>(g);
+        v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w;
     } else {
         const float4 p = *reinterpret_cast<const float4*>(g);
         v[0] = p.x; v[1] = p.y; v[2] = p.z; v[3] = p.w;
@@ -161,7 +161,7 @@ __device__ __forceinline__ void factor_tp_scalar(const LevelArgs& a, const long 
     const bool hasL = pt.hasL, hasR = pt.hasR;
     T yp = T(0), zp = T(0), cp = T(0);
     T w = hasL ? (T)gC[s - 1] : T(0);   // W_s = C of the left separator row
-    const bool vec = aligned16(gB, gD, gC) && aligned16(gDinv, gY, gZ);
+    const bool vec = aligned32(gB, gD, gC) && aligned32(gDinv, gY, gZ);
     auto step = [&](long long j, double bj, double dj, double cj, T& dinv, T& z, T& y) {
         const bool first = (j == s);
         const bool needB = !first || hasL;
@@ -267,7 +267,7 @@ __device__ __forceinline__ void solve_fwd_tp_scalar(const LevelArgs& a, const lo
     const long long s = pt.s, e = pt.e;
     const bool hasL = pt.hasL;
     T h = T(0), H = T(0), w = T(1);
-    const bool vec = aligned16(F, X, gB) && aligned16(gDinv, gY, gY);
+    const bool vec = aligned32(F, X, gB) && aligned32(gDinv, gY, gY);
     auto step = [&](long long j, double fj, double bj, T dinv, T yj) -> T {
         T v = (T)fj;
         if (j != s) v = fmaT<T>(-(T)bj, h, v);
@@ -325,7 +325,7 @@ __device__ __forceinline__ void solve_bwd_tp_scalar(const LevelArgs& a, const lo
     const long long s = pt.s, e = pt.e;
     const bool hasL = pt.hasL, hasR = pt.hasR;
     T x = T(0), xl = T(0);
-    const bool vec = aligned16(X, gY, gZ);
+    const bool vec = aligned32(X, gY, gZ);
     if (hasR) {
         const double xr = a.Xn[i];
         X[e] = xr;

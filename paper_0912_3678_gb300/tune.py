@@ -109,6 +109,39 @@ class Tuner:
         times.sort()
         return times[len(times) // 2]
 
+    def time_captured(self, m, N, prec, nrhs, tuning, reps=5, data=None, sweeps=2) -> float:
+        """Median ms of one replay of the captured factor + solve graph (factor +
+        refinement with `sweeps` corrections for low precision), the way the
+        bench runs a step; decides whether the factorization of the reduced
+        systems runs on a second stream (it shares the SMs' FP64 pipes with the
+        level-0 forward substitution, which helps when that chain is latency-bound)."""
+        import torch
+
+        from . import BtPlan
+        dev = torch.device("cuda", torch.cuda.current_device())
+        B, D, C, F = data if data is not None else self._system(m, N, nrhs, dev)
+        X = torch.empty_like(F)
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+        times = []
+        with BtPlan.tuned(N, m, nrhs_max=nrhs, prec=prec, tuning=tuning) as plan:
+            plan.factor(B, D, C)
+            if prec == "fp64":
+                plan.capture("factor_solve", F, X)
+            else:
+                plan.capture("factor_refine", F, X, sweeps=sweeps)
+            for r in range(reps + 2):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                plan.replay()
+                e1.record()
+                torch.cuda.synchronize()
+                if r >= 2:
+                    times.append(e0.elapsed_time(e1))
+        times.sort()
+        return times[len(times) // 2]
+
     def candidates_k0(self, m, N):
         ks = [4, 8, 16, 32, 64, 128, 256] if m >= 8 else [8, 16, 32, 64, 128, 256, 512]
         p0s = [max(1, min(N // k, (N + 1) // 2)) for k in ks]
@@ -182,6 +215,13 @@ class Tuner:
             ms = run(t)
             if ms < 0.99 * best:
                 best, best_t = ms, t
+        if not best_t.get("local"):
+            # captured steps: second stream for the reduced systems or not
+            two = self.time_captured(m, N, prec, nrhs, dict(best_t, serial=0), reps, data)
+            one = self.time_captured(m, N, prec, nrhs, dict(best_t, serial=1), reps, data)
+            trials += [(two, dict(best_t, serial=0)), (one, dict(best_t, serial=1))]
+            if one < 0.99 * two:
+                best_t = dict(best_t, serial=1)
         self.cache[k] = {"tuning": best_t, "ms": best, "trials": len(trials)}
         self.save()
         return dict(best_t)

@@ -122,3 +122,28 @@ def test_babd_anorm_matches_numpy(cuda):
         plan.factor(*(to_dev(a, cuda) for a in (b.S, b.R, b.B0, b.B1)))
         got = plan.anorm()
     assert abs(got - exact) <= 1e-5 * exact
+
+
+@pytest.mark.parametrize("m,N", [(4, 5000), (8, 3000)])
+def test_babd_captured_step_refactors_new_matrices(cuda, m, N):
+    """Captured factor+solve of a BABD plan (reduced-system levels factored on a
+    second stream beside the level-0 forward substitution), replayed after the
+    blocks and right-hand side are overwritten in place: the new system's
+    solution."""
+    import paper_0912_3678_gb300 as bt
+    b0 = gen.babd_random(N, m, 2, seed_rep=5)
+    b1 = gen.babd_random(N, m, 2, seed_rep=6)
+    S, R, B0, B1, F = (to_dev(a, cuda) for a in (b0.S, b0.R, b0.B0, b0.B1, b0.RHS))
+    with bt.AbdPlan(N, m, nrhs_max=2) as plan:
+        assert len(plan.levels()) >= 2
+        plan.factor(S, R, B0, B1)
+        Y = plan.solve(F)
+        plan.capture("factor_solve", F, Y)
+        for b in (b1, b0):
+            for dev, host in zip((S, R, B0, B1, F), (b.S, b.R, b.B0, b.B1, b.RHS)):
+                dev.copy_(to_dev(host, cuda))
+            Y.zero_()
+            plan.replay()
+            plan.sync()
+            ref = oracle.babd_solve(b.S, b.R, b.B0, b.B1, b.RHS)
+            assert oracle.rel_err(to_host(Y), ref) <= 1e-11

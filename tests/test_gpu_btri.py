@@ -372,3 +372,36 @@ def test_anorm_matches_numpy(cuda, m):
         plan.factor(*(to_dev(a, cuda) for a in (s.B, s.D, s.C)))
         got = plan.anorm()
     assert abs(got - exact) <= 1e-5 * exact
+
+
+@pytest.mark.parametrize("m,N,tuning", [(1, 60000, {"p0": 2048}), (2, 30000, {}), (4, 20000, {}),
+                                        (8, 3000, {}), (16, 2000, {"reduced": 1}), (16, 2000, {"reduced": 0}),
+                                        (32, 400, {})])
+@pytest.mark.parametrize("prec", ["fp64", "fp32_ir"])
+def test_captured_step_refactors_new_matrices(cuda, m, N, tuning, prec):
+    """A captured factor+solve (or factor+refine) graph runs the factorization of
+    the reduced systems beside the level-0 forward substitution.  Replayed after
+    the matrices AND the right-hand side are overwritten in place, it must solve
+    the new system: a solve that read reduced-system factors before they were
+    rewritten would return the old system's answer."""
+    import paper_0912_3678_gb300 as bt
+    nr = 3
+    s0 = gen.btri_random(N, m, nr, seed_rep=41)
+    s1 = gen.btri_random(N, m, nr, seed_rep=42)
+    B, D, C, F = (to_dev(a, cuda) for a in (s0.B, s0.D, s0.C, s0.F))
+    with bt.BtPlan.tuned(N, m, nr, prec, tuning) as plan:
+        assert len(plan.levels()) >= 2
+        plan.factor(B, D, C)
+        X = plan.solve(F)
+        if prec == "fp64":
+            plan.capture("factor_solve", F, X)
+        else:
+            plan.capture("factor_refine", F, X, sweeps=3)
+        for s in (s1, s0, s1):
+            for dev, host in zip((B, D, C, F), (s.B, s.D, s.C, s.F)):
+                dev.copy_(to_dev(host, cuda))
+            X.zero_()
+            plan.replay()
+            plan.sync()
+            ref = oracle.btri_solve(s.B, s.D, s.C, s.F)
+            assert oracle.rel_err(to_host(X), ref) <= (TOL64 if prec == "fp64" else TOLIR)
