@@ -317,6 +317,10 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
         v.low = (l == 0) && (prec != BT_FP64);
         v.a.bf16 = (l == 0) && (prec == BT_BF16_IR) && (m >= 16) ? 1 : 0;
         v.a.tpb = tune.tp_block;
+        // m = 2, 4 FP64 levels with fewer partitions than lanes of a full thread-per-partition
+        // wave: one group of m*m lanes per partition (latency-bound levels)
+        v.a.group = ((m == 2 || m == 4) && !v.low && !(P->pivot && l == 0) &&
+                     v.a.p < (long long)sms * 128) ? 1 : 0;
         if (P->pivot && l == 0) v.pcap = pcap;
         P->lv.push_back(v);
     }

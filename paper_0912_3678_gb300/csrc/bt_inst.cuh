@@ -2,6 +2,7 @@
 #pragma once
 #include "bt_bcr.cuh"
 #include "bt_cta.cuh"
+#include "bt_gp.cuh"
 #include "bt_launch.h"
 #include "bt_tp.cuh"
 
@@ -15,6 +16,12 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 
 static inline unsigned grid_for(long long threads, int block) { return (unsigned)((threads + block - 1) / block); }
 static inline int tpb(const LevelArgs& a) { return (a.tpb == 64 || a.tpb == 256) ? a.tpb : 128; }
+// lane-group kernels (bt_gp.cuh): FP64 levels of block order 2 or 4 flagged by the planner
+template <typename T, int M>
+static inline bool use_gp(const LevelArgs& a) {
+    return (M == 2 || M == 4) && std::is_same<T, double>::value && a.group != 0;
+}
+static inline long long chunks(const LevelArgs& a, int m) { return (a.nr + m - 1) / m; }
 
 template <int M>
 struct Inst {
@@ -26,6 +33,8 @@ struct Inst {
             cudaError_t e = set_smem(k_factor_cta<T, M, MODE>, smem);
             if (e != cudaSuccess) return e;
             k_factor_cta<T, M, MODE><<<(unsigned)a.p, 8 * M, smem, s>>>(a);
+        } else if (use_gp<T, M>(a)) {
+            if constexpr (M == 2 || M == 4) k_factor_gp<M, MODE><<<grid_for(a.p * M * M, 128), 128, 0, s>>>(a);
         } else {
             k_factor_tp<T, M, MODE><<<grid_for(a.p, tpb(a)), tpb(a), 0, s>>>(a);
         }
@@ -43,6 +52,8 @@ struct Inst {
             cudaError_t e = set_smem(k_assemble_cta<T, M>, smem);
             if (e != cudaSuccess) return e;
             k_assemble_cta<T, M><<<(unsigned)(a.p - 1), 8 * M, smem, s>>>(a);
+        } else if (use_gp<T, M>(a)) {
+            if constexpr (M == 2 || M == 4) k_assemble_gp<M><<<grid_for((a.p - 1) * M * M, 128), 128, 0, s>>>(a);
         } else {
             k_assemble_tp<T, M><<<grid_for(a.p - 1, tpb(a)), tpb(a), 0, s>>>(a);
         }
@@ -59,6 +70,9 @@ struct Inst {
             cudaError_t e = set_smem(k_solve_fwd_cta<T, M, MODE>, smem);
             if (e != cudaSuccess) return e;
             k_solve_fwd_cta<T, M, MODE><<<(unsigned)a.p, 8 * M, smem, s>>>(a);
+        } else if (use_gp<T, M>(a)) {
+            if constexpr (M == 2 || M == 4)
+                k_solve_fwd_gp<M, MODE><<<grid_for(a.p * chunks(a, M) * M * M, 128), 128, 0, s>>>(a);
         } else {
             k_solve_fwd_tp<T, M, MODE><<<grid_for(a.p * a.nr, tpb(a)), tpb(a), 0, s>>>(a);
         }
@@ -76,6 +90,9 @@ struct Inst {
             cudaError_t e = set_smem(k_assemble_rhs_cta<T, M>, smem);
             if (e != cudaSuccess) return e;
             k_assemble_rhs_cta<T, M><<<(unsigned)(a.p - 1), 8 * M, smem, s>>>(a);
+        } else if (use_gp<T, M>(a)) {
+            if constexpr (M == 2 || M == 4)
+                k_assemble_rhs_gp<M><<<grid_for((a.p - 1) * chunks(a, M) * M * M, 128), 128, 0, s>>>(a);
         } else {
             k_assemble_rhs_tp<T, M><<<grid_for((a.p - 1) * a.nr, tpb(a)), tpb(a), 0, s>>>(a);
         }
@@ -92,6 +109,9 @@ struct Inst {
             cudaError_t e = set_smem(k_solve_bwd_cta<T, M, MODE>, smem);
             if (e != cudaSuccess) return e;
             k_solve_bwd_cta<T, M, MODE><<<(unsigned)a.p, 8 * M, smem, s>>>(a);
+        } else if (use_gp<T, M>(a)) {
+            if constexpr (M == 2 || M == 4)
+                k_solve_bwd_gp<M, MODE><<<grid_for(a.p * chunks(a, M) * M * M, 128), 128, 0, s>>>(a);
         } else {
             k_solve_bwd_tp<T, M, MODE><<<grid_for(a.p * a.nr, tpb(a)), tpb(a), 0, s>>>(a);
         }

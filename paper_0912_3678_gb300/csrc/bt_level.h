@@ -13,6 +13,7 @@ struct LevelArgs {
     int level;
     int tpb;           // threads per CTA of the thread-per-partition kernels (m <= 4): 64, 128 or 256
     int bf16;          // Schur product B_j Y_{j-1} with BF16 operands on the tensor cores (FP32 levels, m >= 16)
+    int group;         // m = 2, 4 FP64 levels: a group of m*m lanes per partition instead of one thread
     long long N, p, base, extra;
     const double* B;
     const double* D;

@@ -147,3 +147,15 @@ def test_babd_captured_step_refactors_new_matrices(cuda, m, N):
             plan.sync()
             ref = oracle.babd_solve(b.S, b.R, b.B0, b.B1, b.RHS)
             assert oracle.rel_err(to_host(Y), ref) <= 1e-11
+
+
+@pytest.mark.parametrize("m", [2, 4])
+@pytest.mark.parametrize("p", [19456, 0])
+def test_babd_thread_and_lane_group_kernels(cuda, m, p):
+    """BABD levels of block order 2 and 4: one thread per partition where the
+    partitions fill a whole wave (p = 128 per SM), a group of m*m lanes per
+    partition elsewhere (the recursion levels, and every level by default)."""
+    b = gen.babd_random(50000, m, 3, seed_rep=m)
+    Y, lev = _solve(cuda, b, p=p)
+    ref = oracle.babd_solve(b.S, b.R, b.B0, b.B1, b.RHS)
+    assert oracle.rel_err(Y, ref) <= 1e-11, lev

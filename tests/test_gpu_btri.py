@@ -405,3 +405,35 @@ def test_captured_step_refactors_new_matrices(cuda, m, N, tuning, prec):
             plan.sync()
             ref = oracle.btri_solve(s.B, s.D, s.C, s.F)
             assert oracle.rel_err(to_host(X), ref) <= (TOL64 if prec == "fp64" else TOLIR)
+
+
+@pytest.mark.parametrize("m", [2, 4])
+@pytest.mark.parametrize("p0,nr", [(19456, 3), (4096, 5), (1, 6)])
+def test_thread_and_lane_group_kernels(cuda, m, p0, nr):
+    """Block orders 2 and 4 in FP64: a level whose partitions fill a whole wave
+    of thread-per-partition CTAs (p0 = 128 per SM) runs one thread per
+    partition; levels with fewer partitions run a group of m*m lanes per
+    partition.  Both, mixed across levels and with right-hand-side counts that
+    are not multiples of m, against the oracle."""
+    import paper_0912_3678_gb300 as bt
+    N = 50000 if p0 > 1 else 300
+    s = gen.btri_random(N, m, nr, seed_rep=m + p0)
+    ref = oracle.btri_solve(s.B, s.D, s.C, s.F)
+    with bt.BtPlan.tuned(N, m, nr, "fp64", {"p0": p0}) as plan:
+        plan.factor(*(to_dev(a, cuda) for a in (s.B, s.D, s.C)))
+        X = to_host(plan.solve(to_dev(s.F, cuda)))
+        plan.sync()
+    assert oracle.rel_err(X, ref) <= TOL64
+
+
+def test_singular_block_in_a_thread_per_partition_level(cuda):
+    """A zero pivot block in a level run one thread per partition (m = 4,
+    128 partitions per SM) sets BT_ERR_SINGULAR with its block row."""
+    import paper_0912_3678_gb300 as bt
+    s = gen.btri_random(50000, 4, 1, seed_rep=8)
+    s.D[0] = 0.0
+    with bt.BtPlan.tuned(50000, 4, 1, "fp64", {"p0": 19456}) as plan:
+        plan.factor(*(to_dev(a, cuda) for a in (s.B, s.D, s.C)))
+        code, lev, part, row = plan.info()
+    assert bt.BT_STATUS[code] == "BT_ERR_SINGULAR"
+    assert (lev, row) == (0, 0)
