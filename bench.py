@@ -38,6 +38,18 @@ UNIT = "unknowns*rhs/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 
 
+def _hbm_peak_gbs():
+    """Measured device copy bandwidth of this GPU model (MEASURED_PEAKS.json), else 6800 GB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+HBM_PEAK_GBS = _hbm_peak_gbs()
+
+
 def _workload(name: str, m_opt=None, N_opt=None, nr_opt=None):
     import gen
     if name == "block":
@@ -180,7 +192,8 @@ def run_batch(args):
     from paper_0912_3678_gb300 import build as _build
     _build.build()
     dev = torch.device("cuda:0")
-    specs = gen.batch_specs(args.batch_count, nmax=args.batch_nmax)
+    scalar = args.workload == "scalar_batch"
+    specs = gen.scalar_batch_specs() if scalar else gen.batch_specs(args.batch_count, nmax=args.batch_nmax)
     systems, unknowns = [], 0
     gcpu = torch.Generator(device=dev).manual_seed(20091234 + 4000)
     for sp in specs:
@@ -242,16 +255,37 @@ def run_batch(args):
         t_or += time.perf_counter() - t1
         n_or += h["F"].size
         worst[sd["prec"]] = max(worst[sd["prec"]], oracle.rel_err(h["X"], ref))
+    if scalar:
+        desc = (f"{len(systems)} independent scalar tridiagonal systems, n=2^16 each, d~U[4,6], "
+                f"dl,du~U[-1,1], 1 RHS, FP64, one batch")
+        # Both rooflines of the one-shot scalar solve: 40 algorithmic bytes per unknown (read
+        # dl, d, du, f; write x) and 15 algorithmic FP64 flops per unknown (the partition
+        # method's LU 3, spikes 3, forward and back substitution 5, spike corrections 4).
+        # At about 0.4 flop per byte, far above the FP64/HBM balance of this GPU (about
+        # 0.18 flop per byte), the FP64 pipe binds.
+        per_s = unknowns / (ms / 1e3)
+        gbs = 40.0 * per_s / 1e9
+        ach = 15.0 * per_s / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "whole step (factor + solve, all levels), 15 FP64 flop per unknown",
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                "hbm": {"achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": gbs / HBM_PEAK_GBS,
+                        "bytes_per_unknown": 40}}
+    else:
+        desc = (f"{len(systems)} uneven block tridiagonal systems, n log-uniform "
+                f"[1e3,{args.batch_nmax:g}], m in {{1,4,8,16,32}}, 50/50 FP64 / BF16+IR, 1 RHS")
+        roof = None
     line = {"metric": METRIC, "value": unknowns / (ms / 1e3), "unit": "unknowns/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64 + bf16/f32+f64 refinement", "data": "synthetic",
-            "config": {"workload": f"{len(systems)} uneven block tridiagonal systems, n log-uniform "
-                                   f"[1e3,{args.batch_nmax:g}], m in {{1,4,8,16,32}}, 50/50 FP64 / BF16+IR, 1 RHS",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if scalar else "f64 + bf16/f32+f64 refinement", "data": "synthetic",
+            "config": {"workload": desc,
                        "graph_nodes": nodes, "waves": waves, "workspace_gb": nbytes / 2 ** 30,
                        "create_s": t_create, "partition_rows": k0,
                        "tuning_ms": {str(k): v for k, v in ktimes.items()}},
             "statuses_ok": sum(1 for x in status if x == 0), "systems": len(status),
-            "rel_err_sample_max": worst,
+            "rel_err_sample_max": worst, "roofline": roof,
             "cpu_baseline": {"value": n_or / t_or if t_or else None, "unit": "unknowns/s", "cores": 1,
                              "kind": "oracle", "sample": f"{len(sample)} systems of the batch"}}
     print(json.dumps(line))
@@ -441,7 +475,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="block16",
-                    choices=["block16", "block", "babd8", "scalar", "batch", "serve", "pivot", "parareal", "cyclic"])
+                    choices=["block16", "block", "babd8", "scalar", "scalar_batch", "batch", "serve", "pivot", "parareal",
+                             "cyclic"])
     ap.add_argument("--m", type=int, default=None, help="block order of --workload block")
     ap.add_argument("--N", type=int, default=None, help="block rows of --workload block")
     ap.add_argument("--nrhs", type=int, default=None, help="right-hand sides of --workload block")
@@ -464,7 +499,7 @@ def main():
         os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batch":
+    if args.workload in ("batch", "scalar_batch"):
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)

@@ -397,6 +397,12 @@ def batch_specs(count: int = 4096, nmin: float = 1e3, nmax: float = 1e6,
     return out
 
 
+def scalar_batch_specs(count: int = 1024, n: int = 1 << 16, rep: int = 0) -> list:
+    """The scalar tridiagonal throughput workload: `count` independent systems
+    of order n (the diagonally dominant scalar recipe, one seed each), all FP64."""
+    return [BatchSpec(n, 1, False, int(SEED_BASE + 1000 * 1 + 100000 * (rep + 1) + k)) for k in range(count)]
+
+
 def batch_system(spec: BatchSpec, nrhs: int = 1) -> BtriSystem:
     """Materialise one batched system: m = 1 follows the scalar recipe, m > 1
     the block recipe."""
