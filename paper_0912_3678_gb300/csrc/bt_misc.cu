@@ -595,82 +595,162 @@ cudaError_t launch_ir_update(long long n, double* X, const double* Dc, double* p
 // pivoting on a tridiagonal matrix (row interchanges between consecutive rows
 // fill in a second superdiagonal), one warp, lane c carrying right-hand side
 // c; every lane takes the same pivot decisions.  keep: [K][3] rows of U
-// (diagonal, first and second superdiagonal), then [K][nr] eliminated
-// right-hand sides.
+// (reciprocal of the diagonal, first and second superdiagonal), then [K][nr]
+// eliminated right-hand sides.
+//
+// The elimination is a chain of dependent FP64 operations (a reciprocal, a
+// multiplier and one update per row), so the loads are taken off it: the rows
+// are fetched 32 at a time one chunk ahead into registers (lane l: row
+// base + l of the matrix; every lane its own right-hand-side column of the 32
+// rows), parked in shared memory while the chain walks the current chunk from
+// there; the back substitution prefetches U and the eliminated right-hand
+// sides the same way, downwards.
+namespace {
+constexpr int kGtsvChunk = 32;
+struct GtsvRegs {
+    double a, b, c;                 // lane l: B, D, C of row base + l (C = 0 past the last coupling)
+    double f[kGtsvChunk];           // this lane's right-hand-side column of rows base .. base + 31
+};
+struct GtsvSmem {
+    double a[kGtsvChunk], b[kGtsvChunk], c[kGtsvChunk];
+    double f[kGtsvChunk][kGtsvChunk + 1];   // [row][column], padded
+};
+__device__ __forceinline__ void gtsv_fetch(GtsvRegs& q, long long base, long long K, int nr, bool act, int lane,
+                                           const double* __restrict__ B, const double* __restrict__ D,
+                                           const double* __restrict__ C, const double* __restrict__ F) {
+    const long long r = base + lane;
+    q.a = (r < K) ? B[r] : 0.0;
+    q.b = (r < K) ? D[r] : 0.0;
+    q.c = (r + 1 < K) ? C[r] : 0.0;
+#pragma unroll
+    for (int u = 0; u < kGtsvChunk; ++u) q.f[u] = (act && base + u < K) ? F[(base + u) * nr + lane] : 0.0;
+}
+__device__ __forceinline__ void gtsv_park(GtsvSmem& sm, const GtsvRegs& q, int lane) {
+    sm.a[lane] = q.a;
+    sm.b[lane] = q.b;
+    sm.c[lane] = q.c;
+#pragma unroll
+    for (int u = 0; u < kGtsvChunk; ++u) sm.f[u][lane] = q.f[u];
+}
+// back substitution: lane l holds row top - l of U; every lane its eliminated
+// right-hand-side column of rows top .. top - 31
+__device__ __forceinline__ void gtsv_fetch_back(GtsvRegs& q, long long top, int nr, bool act, int lane,
+                                                const double* U, const double* G) {
+    const long long r = top - lane;
+    q.a = (r >= 0) ? U[3 * r] : 0.0;
+    q.b = (r >= 0) ? U[3 * r + 1] : 0.0;
+    q.c = (r >= 0) ? U[3 * r + 2] : 0.0;
+#pragma unroll
+    for (int u = 0; u < kGtsvChunk; ++u) q.f[u] = (act && top - u >= 0) ? G[(top - u) * nr + lane] : 0.0;
+}
+}  // namespace
+
 __global__ void __launch_bounds__(32) k_gtsv(int K, int nr, const double* __restrict__ B,
                                              const double* __restrict__ D, const double* __restrict__ C,
                                              const double* __restrict__ F, double* __restrict__ X,
                                              double* __restrict__ keep, long long* status, int level) {
+    __shared__ GtsvSmem sm[2];
     const int c = threadIdx.x;
     const bool act = c < nr;
-    // working row i: [b (diag), cc (super), dd (second super)] and its right-hand side
-    double b = D[0], cc = (K > 1) ? C[0] : 0.0, f = act ? F[c] : 0.0;
-    double* U = keep;          // [K][3]
+    double* U = keep;                      // [K][3]
     double* G = keep + 3 * (long long)K;   // [K][nr] eliminated right-hand sides
-    for (int i = 0; i < K; ++i) {
-        double dd = 0.0;
-        if (i + 1 < K) {
-            const double a1 = B[i + 1], b1 = D[i + 1], c1 = (i + 2 < K) ? C[i + 1] : 0.0;
-            double f1 = act ? F[(long long)(i + 1) * nr + c] : 0.0;
-            if (fabs(b) >= fabs(a1)) {
-                // pivot on row i: eliminate a1 from row i+1
-                double pv = b;
-                if (pv == 0.0 || nonfinite(pv)) {
-                    if (c == 0) report(status, pv == 0.0 ? ST_SINGULAR : ST_NONFINITE, level, -1, i);
-                    pv = 1.0;
-                    b = 1.0;
+    // working row i: [b (diagonal), cc (super), dd (second super)] and its right-hand side
+    double b = D[0], cc = (K > 1) ? C[0] : 0.0, f = act ? F[c] : 0.0;
+    // chunk t holds rows i + 1 for i in [32 t, 32 t + 32)
+    GtsvRegs q;
+    gtsv_fetch(q, 1, K, nr, act, c, B, D, C, F);
+    gtsv_park(sm[0], q, c);
+    __syncwarp();
+    int cb = 0;
+    for (long long i0 = 0; i0 < K; i0 += kGtsvChunk) {
+        gtsv_fetch(q, i0 + 1 + kGtsvChunk, K, nr, act, c, B, D, C, F);   // in flight during the chain
+        const GtsvSmem& cur = sm[cb];
+        const int n = (int)((K - i0 < kGtsvChunk) ? (K - i0) : kGtsvChunk);
+#pragma unroll 1
+        for (int u = 0; u < n; ++u) {
+            const long long i = i0 + u;
+            const double a1 = cur.a[u], b1 = cur.b[u], c1 = cur.c[u], f1 = cur.f[u][c];
+            // magnitudes compared as integer keys: the FP64 pipe stays free for the chain
+            const unsigned long long kb = abs_key(b);
+            if (i + 1 < K) {
+                if (kb >= abs_key(a1)) {
+                    // pivot on row i: eliminate a1 from row i+1
+                    double pv = b;
+                    if (kb == 0ull || nonfinite(pv)) {
+                        if (c == 0) report(status, kb == 0ull ? ST_SINGULAR : ST_NONFINITE, level, -1, i);
+                        pv = 1.0;
+                    }
+                    const double rv = rcp(pv);
+                    const double l = a1 * rv;
+                    if (c == 0) {
+                        U[3 * i] = rv;
+                        U[3 * i + 1] = cc;
+                        U[3 * i + 2] = 0.0;
+                    }
+                    if (act) G[i * nr + c] = f;
+                    b = fma(-l, cc, b1);
+                    cc = c1;
+                    f = fma(-l, f, f1);
+                } else {
+                    // interchange rows i and i+1, then eliminate
+                    const double rv = rcp(a1);
+                    const double l = b * rv;
+                    if (c == 0) {
+                        U[3 * i] = rv;
+                        U[3 * i + 1] = b1;
+                        U[3 * i + 2] = c1;
+                    }
+                    if (act) G[i * nr + c] = f1;
+                    const double nb = fma(-l, b1, cc);
+                    cc = -l * c1;
+                    b = nb;
+                    f = fma(-l, f1, f);
                 }
-                const double l = a1 * rcp(pv);
+            } else {
+                double pv = b;
+                if (kb == 0ull || nonfinite(pv)) {
+                    if (c == 0) report(status, kb == 0ull ? ST_SINGULAR : ST_NONFINITE, level, -1, i);
+                    pv = 1.0;
+                }
                 if (c == 0) {
-                    U[3 * i] = b;
-                    U[3 * i + 1] = cc;
+                    U[3 * i] = rcp(pv);
+                    U[3 * i + 1] = 0.0;
                     U[3 * i + 2] = 0.0;
                 }
-                if (act) G[(long long)i * nr + c] = f;
-                b = fma(-l, cc, b1);
-                cc = c1;
-                f = fma(-l, f, f1);
-            } else {
-                // interchange rows i and i+1, then eliminate
-                const double l = b * rcp(a1);
-                if (c == 0) {
-                    U[3 * i] = a1;
-                    U[3 * i + 1] = b1;
-                    U[3 * i + 2] = c1;
-                }
-                if (act) G[(long long)i * nr + c] = f1;
-                const double nb = fma(-l, b1, cc);
-                dd = -l * c1;
-                b = nb;
-                cc = dd;
-                f = fma(-l, f1, f);
+                if (act) G[i * nr + c] = f;
             }
-        } else {
-            double pv = b;
-            if (pv == 0.0 || nonfinite(pv)) {
-                if (c == 0) report(status, pv == 0.0 ? ST_SINGULAR : ST_NONFINITE, level, -1, i);
-                b = 1.0;
-            }
-            if (c == 0) {
-                U[3 * i] = b;
-                U[3 * i + 1] = 0.0;
-                U[3 * i + 2] = 0.0;
-            }
-            if (act) G[(long long)i * nr + c] = f;
         }
+        cb ^= 1;
+        gtsv_park(sm[cb], q, c);
+        __syncwarp();
     }
+    // U and G come back from global memory: make this warp's stores visible to all its lanes
+    __threadfence_block();
     __syncwarp();
-    // back substitution: x_i = (g_i - u1_i x_{i+1} - u2_i x_{i+2}) / u0_i
+    // back substitution: x_i = (g_i - u1_i x_{i+1} - u2_i x_{i+2}) / u0_i  (U holds 1 / u0_i)
     double x1 = 0.0, x2 = 0.0;
-    for (int i = K - 1; i >= 0; --i) {
-        const double u0 = U[3 * i], u1 = U[3 * i + 1], u2 = U[3 * i + 2];
-        double v = act ? G[(long long)i * nr + c] : 0.0;
-        v = fma(-u1, x1, v);
-        v = fma(-u2, x2, v);
-        const double xi = v * rcp(u0);
-        if (act) X[(long long)i * nr + c] = xi;
-        x2 = x1;
-        x1 = xi;
+    gtsv_fetch_back(q, K - 1, nr, act, c, U, G);
+    gtsv_park(sm[0], q, c);
+    __syncwarp();
+    cb = 0;
+    for (long long top = K - 1; top >= 0; top -= kGtsvChunk) {
+        gtsv_fetch_back(q, top - kGtsvChunk, nr, act, c, U, G);
+        const GtsvSmem& cur = sm[cb];
+        const int n = (int)((top + 1 < kGtsvChunk) ? (top + 1) : kGtsvChunk);
+#pragma unroll 1
+        for (int u = 0; u < n; ++u) {
+            const long long i = top - u;
+            double v = cur.f[u][c];
+            v = fma(-cur.b[u], x1, v);
+            v = fma(-cur.c[u], x2, v);
+            const double xi = v * cur.a[u];
+            if (act) X[i * nr + c] = xi;
+            x2 = x1;
+            x1 = xi;
+        }
+        cb ^= 1;
+        gtsv_park(sm[cb], q, c);
+        __syncwarp();
     }
 }
 
