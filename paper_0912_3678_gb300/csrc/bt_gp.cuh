@@ -121,12 +121,24 @@ __device__ __forceinline__ void factor_gp_body(const LevelArgs& a, const long lo
     const bool wchain = (MODE == 0) && pt.hasL;
     double Yp = 0.0, Zp = 0.0, W = 0.0, CP = 0.0;
     if (wchain) W = a.C[(pt.s - 1 - a.shift) * MM + q];   // W_s = C of the left separator row
+    // the blocks of row j + 1 are loaded while row j is processed
+    auto needC_of = [&](long long j) { return (MODE == 0) && ((j < pt.e - 1) || pt.hasR); };
+    double nD = 0.0, nB = 0.0, nC = 0.0;
+    if (pt.s < pt.e) {
+        nD = a.D[(pt.s - a.shift) * MM + q];
+        nB = pt.hasL ? a.B[(pt.s - a.shift) * MM + q] : 0.0;
+        nC = needC_of(pt.s) ? a.C[(pt.s - a.shift) * MM + q] : 0.0;
+    }
     for (long long j = pt.s; j < pt.e; ++j) {
         const bool first = (j == pt.s);
-        const bool needB = !first || pt.hasL;
-        const bool needC = (MODE == 0) && ((j < pt.e - 1) || pt.hasR);
-        double Dp = a.D[(j - a.shift) * MM + q];
-        const double Bj = needB ? a.B[(j - a.shift) * MM + q] : 0.0;
+        const bool needC = needC_of(j);
+        double Dp = nD;
+        const double Bj = nB, Cj = nC;
+        if (j + 1 < pt.e) {
+            nD = a.D[(j + 1 - a.shift) * MM + q];
+            nB = a.B[(j + 1 - a.shift) * MM + q];
+            nC = needC_of(j + 1) ? a.C[(j + 1 - a.shift) * MM + q] : 0.0;
+        }
         if (MODE == 0 && !first) Dp = gmm<M, true, true>(g, Bj, Yp, Dp);
         ggj_inverse<M>(g, Dp, a.status, a.level, i, j);
         gDinv[j * MM + q] = Dp;
@@ -140,7 +152,6 @@ __device__ __forceinline__ void factor_gp_body(const LevelArgs& a, const long lo
             gZ[j * MM + q] = Zp;
         }
         if (needC) {
-            const double Cj = a.C[(j - a.shift) * MM + q];
             Yp = gmm<M, false, false>(g, Dp, Cj, 0.0);
             gY[j * MM + q] = Yp;
         }
@@ -221,10 +232,22 @@ __device__ __forceinline__ void solve_fwd_gp_body(const LevelArgs& a, const long
     const Part pt = part_bounds(a, MODE, i);
     const double* gDinv = reinterpret_cast<const double*>(a.Dinv);
     double hp = 0.0;
+    // row j + 1's data loaded while row j is processed
+    double nF = 0.0, nB = 0.0, nDi = 0.0;
+    if (pt.s < pt.e) {
+        nF = cl.live ? a.F[pt.s * E + o] : 0.0;
+        nDi = gDinv[pt.s * MM + q];
+    }
     for (long long j = pt.s; j < pt.e; ++j) {
-        double v = cl.live ? a.F[j * E + o] : 0.0;
-        if (j != pt.s) v = gmm<M, true, true>(g, a.B[(j - a.shift) * MM + q], hp, v);
-        hp = gmm<M, false, false>(g, gDinv[j * MM + q], v, 0.0);
+        double v = nF;
+        const double Bj = nB, Di = nDi;
+        if (j + 1 < pt.e) {
+            nF = cl.live ? a.F[(j + 1) * E + o] : 0.0;
+            nB = a.B[(j + 1 - a.shift) * MM + q];
+            nDi = gDinv[(j + 1) * MM + q];
+        }
+        if (j != pt.s) v = gmm<M, true, true>(g, Bj, hp, v);
+        hp = gmm<M, false, false>(g, Di, v, 0.0);
         if (cl.live) a.X[j * E + o] = hp;
     }
     if (MODE == 1) {
@@ -287,10 +310,25 @@ __device__ __forceinline__ void solve_bwd_gp_body(const LevelArgs& a, const long
     if (pt.hasL) xl = cl.live ? a.Xn[li * E + o] : 0.0;
     const double* gY = reinterpret_cast<const double*>(a.Y);
     const double* gZ = reinterpret_cast<const double*>(a.Zc);
+    auto useY = [&](long long j) { return MODE == 0 && ((j < pt.e - 1) || pt.hasR); };
+    // row j - 1's data loaded while row j is processed
+    double nH = 0.0, nY = 0.0, nZ = 0.0;
+    if (pt.e > pt.s) {
+        const long long j = pt.e - 1;
+        nH = cl.live ? a.X[j * E + o] : 0.0;
+        nY = useY(j) ? gY[j * MM + q] : 0.0;
+        nZ = pt.hasL ? gZ[j * MM + q] : 0.0;
+    }
     for (long long j = pt.e - 1; j >= pt.s; --j) {
-        double v = cl.live ? a.X[j * E + o] : 0.0;
-        if (MODE == 0 && ((j < pt.e - 1) || pt.hasR)) v = gmm<M, true, true>(g, gY[j * MM + q], x, v);
-        if (pt.hasL) v = gmm<M, false, true>(g, gZ[j * MM + q], xl, v);
+        double v = nH;
+        const double Yj = nY, Zj = nZ;
+        if (j - 1 >= pt.s) {
+            nH = cl.live ? a.X[(j - 1) * E + o] : 0.0;
+            nY = useY(j - 1) ? gY[(j - 1) * MM + q] : 0.0;
+            nZ = pt.hasL ? gZ[(j - 1) * MM + q] : 0.0;
+        }
+        if (useY(j)) v = gmm<M, true, true>(g, Yj, x, v);
+        if (pt.hasL) v = gmm<M, false, true>(g, Zj, xl, v);
         x = v;
         if (cl.live) a.X[j * E + o] = x;
     }
