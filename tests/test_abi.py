@@ -76,3 +76,30 @@ def test_missing_library_fails_loudly(tmp_path):
             _lib.load(str(tmp_path / "nope.so"))
     finally:
         _lib._lib = saved
+
+
+def _header_struct(name):
+    """Field (C type, name) pairs of `typedef struct { ... } name;` in include/bt.h."""
+    text = open(os.path.join(ROOT, "include", "bt.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    body = re.search(r"typedef struct\s*\{([^}]*)\}\s*" + name + r"\s*;", text).group(1)
+    return [tuple(f.rsplit(None, 1)) for f in (x.strip() for x in body.split(";")) if f]
+
+
+@pytest.mark.parametrize("cname,pyname", [("bt_tuning", "BtTuning"), ("bt_batch_desc", "BtBatchDesc")])
+def test_binding_structs_match_header(cname, pyname):
+    """The ctypes mirrors of the ABI's structs have the header's fields, in its
+    order, with the same C types."""
+    import ctypes
+
+    from paper_0912_3678_gb300 import _lib
+    ctype = {"int64_t": ctypes.c_int64, "int": ctypes.c_int, "double": ctypes.c_double,
+             "bt_tuning": _lib.BtTuning}
+    fields = _header_struct(cname)
+    py = getattr(_lib, pyname)._fields_
+    assert [f[1].lstrip("*") for f in fields] == [p[0] for p in py]
+    for (ct, nm), (pn, pt) in zip(fields, py):
+        if nm.startswith("*") or ct.endswith("*"):
+            assert pt is ctypes.c_void_p, nm
+        else:
+            assert pt is ctype[ct], nm

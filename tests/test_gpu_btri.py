@@ -437,3 +437,24 @@ def test_singular_block_in_a_thread_per_partition_level(cuda):
         code, lev, part, row = plan.info()
     assert bt.BT_STATUS[code] == "BT_ERR_SINGULAR"
     assert (lev, row) == (0, 0)
+
+
+@pytest.mark.parametrize("m,N,tuning", [(1, 60000, {"p0": 2048}), (4, 20000, {}), (16, 2000, {"reduced": 1})])
+def test_captured_step_same_with_one_or_two_streams(cuda, m, N, tuning):
+    """bt_tuning.serial only changes which stream the reduced systems are
+    factored on: the captured step gives bitwise the same solution both ways."""
+    import paper_0912_3678_gb300 as bt
+    s = gen.btri_random(N, m, 2, seed_rep=17)
+    B, D, C, F = (to_dev(a, cuda) for a in (s.B, s.D, s.C, s.F))
+    out = []
+    for serial in (0, 1):
+        with bt.BtPlan.tuned(N, m, 2, "fp64", dict(tuning, serial=serial)) as plan:
+            plan.factor(B, D, C)
+            X = plan.solve(F)
+            plan.capture("factor_solve", F, X)
+            X.zero_()
+            plan.replay()
+            plan.sync()
+            out.append(to_host(X))
+    assert np.array_equal(out[0], out[1])
+    assert oracle.rel_err(out[0], oracle.btri_solve(s.B, s.D, s.C, s.F)) <= TOL64
