@@ -55,6 +55,7 @@ class Request:
     status: int = -1
     relcorr: float = 0.0
     cache_hit: bool = False
+    fallback: bool = False     # refined path did not converge: solved again in FP64
     Y: object = None           # device solution [(N+1)*m, nrhs]
     Yexact_err: float = float("nan")
 
@@ -150,7 +151,7 @@ class _Factor:
 class Server:
     def __init__(self, device=None, mem_cap_bytes: float = 150e9, streams: int = 8, sweeps: int = 3,
                  tol: float = 1e-12, cache: bool = True, check_exact: bool = False, max_inflight: int = 0,
-                 keep_results: bool = True):
+                 keep_results: bool = True, fp64_fallback: bool = True):
         self.device = torch.device(device or "cuda")
         self.cap = int(mem_cap_bytes)
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
@@ -167,6 +168,10 @@ class Server:
         self._next_stream = 0
         self.max_inflight = max_inflight if max_inflight > 0 else 2 * streams
         self.keep_results = keep_results
+        # a refined request whose fixed sweeps end above the backward-error test
+        # (BT_ERR_NOT_CONVERGED) is queued again, first, as an FP64 request
+        self.fp64_fallback = fp64_fallback
+        self._not_converged = next(k for k, v in BT_STATUS.items() if v == "BT_ERR_NOT_CONVERGED")
         total = torch.cuda.get_device_properties(self.device).total_memory
         self.cap = min(self.cap, int(0.7 * total))      # headroom for the caching allocator
         self.peak_in_use = 0
@@ -218,6 +223,9 @@ class Server:
     def _launch(self, r: Request) -> bool:
         key = self._key(r)
         f = self.cache.get(key) if self.cache_enabled else None
+        if f is not None and f.busy and r.prec != "fp64":
+            # the refinement's norms live in the plan: one refined request per plan at a time
+            return False
         if f is not None and f.nrhs_max < r.nrhs:
             f = None if f.busy else f
             if f is not None:
@@ -285,6 +293,7 @@ class Server:
     def poll(self):
         """Retire finished requests, then admit queued ones (in arrival order)."""
         still = []
+        retry = []
         for item in self.running:
             r, ev, f, vec_b, rhs, yex = item
             if ev.query():
@@ -303,10 +312,18 @@ class Server:
                     if f.busy == 0:
                         f.destroy()
                         self.in_use -= f.nbytes
-                self.done.append(r)
+                if r.prec != "fp64" and r.status == self._not_converged and self.fp64_fallback:
+                    r.fallback = True
+                    r.prec = "fp64"
+                    r.status, r.relcorr, r.Y, r.cache_hit = -1, 0.0, None, False
+                    retry.append(r)
+                else:
+                    self.done.append(r)
             else:
                 still.append(item)
         self.running = still
+        for r in reversed(retry):
+            self.queue.appendleft(r)
         while self.queue and len(self.running) < self.max_inflight:
             if not self._launch(self.queue[0]):
                 break
@@ -359,6 +376,7 @@ class Server:
                 "mean_ms": 1e3 * sum(lat) / len(lat), "span_s": span,
                 "unknowns_per_s": unk / span if span > 0 else float("nan"),
                 "cache_hits": sum(r.cache_hit for r in self.done),
+                "fp64_fallbacks": sum(r.fallback for r in self.done),
                 "failed": sum(r.status != 0 for r in self.done)}
 
 

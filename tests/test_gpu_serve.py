@@ -137,3 +137,24 @@ def test_trace_replay_reports_latency(cuda):
     assert st["requests"] == len(reqs) and st["failed"] == 0
     assert 0 < st["p50_ms"] <= st["p99_ms"]
     srv.close()
+
+
+def test_refined_request_that_does_not_converge_falls_back_to_fp64(cuda):
+    """With no refinement sweep the FP32-factor solution fails the backward-error
+    test (BT_ERR_NOT_CONVERGED); the server queues the request again as FP64 and
+    returns that solution instead of a failure."""
+    from paper_0912_3678_gb300 import serve
+    reqs = _requests(count=6, seed=3, precs=("fp32_ir",))
+    srv = serve.Server(cuda, streams=2, sweeps=0)
+    for r in reqs:
+        srv.submit(r)
+    srv.drain()
+    st = srv.stats()
+    assert st["failed"] == 0
+    assert st["fp64_fallbacks"] == len(reqs)
+    for r in reqs:
+        assert r.fallback and r.prec == "fp64" and r.status == 0
+        b = gen.trapezoidal_babd(gen.BvpProblem(r.spec.S, r.spec.K, r.spec.B0, r.spec.B1, r.V), r.N)
+        ref = oracle.babd_solve(b.S, b.R, b.B0, b.B1, b.RHS)
+        assert oracle.rel_err(to_host(r.Y), ref) <= 1e-11, r.rid
+    srv.close()
