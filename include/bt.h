@@ -234,6 +234,26 @@ bt_status bt_plan_create_in(bt_plan* plan, int kind, int64_t n, int m, int nrhs_
  * plan's stream (new values in the same arrays are picked up).  Capture
  * synchronises the stream and replaces any earlier graph of the plan. */
 bt_status bt_plan_capture(bt_plan plan, int what, const double* F, double* X, int nrhs, int sweeps);
+
+/* Factor + solve (sweeps = -1, BT_FP64 plans) or factor + bt_refine_async
+ * with `sweeps` corrections (0..30, refined plans) from HOST arrays: B, D, C
+ * [N][m][m] and F [N*m][nrhs] are host memory read by the call, X
+ * [N*m][nrhs] host memory written by it.  Page-locked (pinned) host memory
+ * lets the copies run asynchronously; pageable memory works but the copies
+ * then synchronise.  The block rows are copied in chunks of level-0
+ * partitions on a copy stream of the plan, and each chunk's local
+ * factorizations (Eq. (parblock)) start on their own stream as soon as their
+ * rows have arrived, so the transfer overlaps the FP64 work; then the
+ * right-hand side, the reduced systems, the solve (or refinement) and the
+ * copy of X back, ordered on the plan's stream.  Asynchronous: bt_sync (or
+ * bt_refine_result) waits and returns the numerical status; the host arrays
+ * must stay valid until then.  The first call allocates device copies of the
+ * arrays (3 N m^2 + 2 N m nrhs_max doubles, cudaMalloc) owned by the plan;
+ * later factorizations of the plan (bt_factor) replace the bound matrices.
+ * Block tridiagonal plans without padding, pivoting or local cyclic
+ * reduction; BT_ERR_INVALID otherwise. */
+bt_status bt_factor_solve_host(bt_plan plan, const double* B, const double* D, const double* C, const double* F,
+                               double* X, int nrhs, int sweeps);
 bt_status bt_plan_replay(bt_plan plan);
 
 /* Wait for the plan's stream; return the recorded numerical status. */

@@ -21,7 +21,7 @@ __all__ = ["BtPlan", "AbdPlan", "BtError", "BT_STATUS", "PREC", "load_library",
            "bt_batch_create", "bt_batch_run", "bt_batch_finish", "bt_batch_info", "bt_batch_destroy",
            "BtBatch", "CycPlan", "cyc_plan_create", "cyc_factor", "cyc_solve", "cyc_residual", "cyc_refine",
            "BtTuning", "BtBatchDesc", "bt_refine_async", "bt_refine_result",
-           "bt_plan_workspace_size", "bt_plan_anorm", "bt_plan_set_pivot_tol", "ivp_parareal", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay",
+           "bt_plan_workspace_size", "bt_plan_anorm", "bt_plan_set_pivot_tol", "ivp_parareal", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay", "bt_factor_solve_host",
            "bt_band_to_blocks", "band_to_blocks", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
            "abd_plan_create", "abd_factor", "abd_solve", "abd_residual", "abd_refine", "abd_sync",
            "abd_plan_destroy"]
@@ -282,6 +282,27 @@ def band_to_blocks(band, s, r, m=None):
     return B, D, C
 
 
+def _host_ptr(t):
+    """Address of a host float64 array (a CPU torch tensor, pinned or not, or a numpy array)."""
+    import numpy as np
+    import torch
+    if isinstance(t, torch.Tensor):
+        if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+            raise TypeError("expected a contiguous CPU float64 tensor")
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        if t.dtype != np.float64 or not t.flags["C_CONTIGUOUS"]:
+            raise TypeError("expected a C-contiguous float64 array")
+        return t.ctypes.data
+    raise TypeError("expected a host array")
+
+
+def bt_factor_solve_host(plan, B, D, C, F, X, nrhs, sweeps=-1):
+    """Factor + solve (or + `sweeps` refinement corrections) from host arrays (see bt.h)."""
+    _lib.check(_lib.load().bt_factor_solve_host(plan, _host_ptr(B), _host_ptr(D), _host_ptr(C), _host_ptr(F),
+                                                _host_ptr(X), int(nrhs), int(sweeps)), "bt_factor_solve_host")
+
+
 def bt_plan_replay(plan):
     _lib.check(_lib.load().bt_plan_replay(plan), "bt_plan_replay")
 
@@ -435,6 +456,11 @@ class _PlanBase:
 
     def replay(self):
         bt_plan_replay(self.handle)
+
+    def factor_solve_host(self, B, D, C, F, X, sweeps=-1):
+        """bt_factor_solve_host: host (pinned) B, D, C, F in, host X out, asynchronous."""
+        nr = F.shape[1] if len(F.shape) == 2 else 1
+        bt_factor_solve_host(self.handle, B, D, C, F, X, nr, sweeps)
 
 
 class BtPlan(_PlanBase):

@@ -101,6 +101,15 @@ struct bt_plan_s {
     bool join_pending = false;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // host-buffer entry point: device copies of the caller's arrays, a copy
+    // stream and per-chunk streams on which the level-0 factorization of each
+    // chunk of partitions starts as soon as its rows have arrived
+    static constexpr int kChunks = 8;
+    double* hb = nullptr;               // B, D, C [N m m] each, then F, X [N m nrhs_max]
+    cudaStream_t copy_stream = nullptr;
+    cudaStream_t chunk_stream[kChunks] = {};
+    cudaEvent_t ev_in = nullptr, ev_rhs = nullptr;
+    cudaEvent_t ev_rows[kChunks] = {}, ev_part[kChunks] = {};
     // tracing
     bool trace = false;
     struct Rec { int key; cudaEvent_t a, b; };
@@ -514,7 +523,7 @@ bt_status run_factor_pivoted(bt_plan_s* P) {
     return from_cuda(e);
 }
 
-bt_status run_factor(bt_plan_s* P) {
+bt_status run_factor(bt_plan_s* P, bool level0_done = false) {
     if (P->pivot) return run_factor_pivoted(P);
     const bt::Launchers* L = P->L;
     const bool split = P->overlap && P->side && P->nlev >= 1;
@@ -555,12 +564,23 @@ bt_status run_factor(bt_plan_s* P) {
             }
             break;
         }
-        cudaError_t e = launch(P, K_FACTOR, l, 1, [&] { return L->factor(v.a, v.low, P->stream); });
+        cudaError_t e = cudaSuccess;
+        if (!(l == 0 && level0_done)) e = launch(P, K_FACTOR, l, 1, [&] { return L->factor(v.a, v.low, P->stream); });
         if (e == cudaSuccess && P->kind == 0 && l < P->nlev)
             e = launch(P, K_ASSEMBLE, l, 1, [&] { return L->assemble(v.a, v.low, P->stream); });
         if (e != cudaSuccess) return rejoin(from_cuda(e));
     }
     return rejoin(BT_OK);
+}
+
+// Second stream for the factorization of levels >= 1 (captured sequences and
+// the host-buffer entry point), created on first use.
+cudaError_t ensure_side(bt_plan_s* P) {
+    if (P->pivot || P->serial || P->nlev < 1 || P->side) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming);
+    return e;
 }
 
 // The main stream waits for a factorization left running on the side stream.
@@ -1089,10 +1109,8 @@ bt_status bt_plan_capture(bt_plan P, int what, const double* F, double* X, int n
     // kernels with large shared memory get their attribute before capture
     e = P->L->prepare();
     if (e != cudaSuccess) return from_cuda(e);
-    if (what != 2 && !P->pivot && !P->serial && P->nlev >= 1 && !P->side) {
-        e = cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming);
+    if (what != 2) {
+        e = ensure_side(P);
         if (e != cudaSuccess) return from_cuda(e);
     }
     cudaStream_t saved = P->stream, cap = nullptr;
@@ -1155,6 +1173,102 @@ bt_status bt_plan_capture(bt_plan P, int what, const double* F, double* X, int n
     }
     if (st == BT_OK && what != 2) P->factored = true;
     return st;
+}
+
+// Host-buffer factor + solve (or + refinement): the caller's arrays are host
+// memory.  The block rows are copied in chunks of level-0 partitions on a
+// copy stream, and each chunk's local factorizations start on their own
+// stream as soon as its rows (and the separator row before them) have
+// arrived, so the transfer overlaps the FP64 work; the right-hand side
+// follows, then the reduced systems, the solve and the copy of X back, all
+// ordered on the plan's stream.
+namespace {
+long long part_start(const LevelArgs& a, long long i) { return i * a.base + (i < a.extra ? i : a.extra); }
+
+cudaError_t ensure_host_path(bt_plan_s* P) {
+    cudaError_t e = cudaSuccess;
+    if (!P->hb) {
+        const size_t mm = (size_t)P->N * P->m * P->m, v = (size_t)P->N * P->m * P->nrhs_max;
+        e = cudaMalloc(&P->hb, sizeof(double) * (3 * mm + 2 * v));
+    }
+    if (e == cudaSuccess && !P->copy_stream) e = cudaStreamCreateWithFlags(&P->copy_stream, cudaStreamNonBlocking);
+    for (int k = 0; k < bt_plan_s::kChunks && e == cudaSuccess; ++k) {
+        if (!P->chunk_stream[k]) e = cudaStreamCreateWithFlags(&P->chunk_stream[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess && !P->ev_rows[k]) e = cudaEventCreateWithFlags(&P->ev_rows[k], cudaEventDisableTiming);
+        if (e == cudaSuccess && !P->ev_part[k]) e = cudaEventCreateWithFlags(&P->ev_part[k], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess && !P->ev_in) e = cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess && !P->ev_rhs) e = cudaEventCreateWithFlags(&P->ev_rhs, cudaEventDisableTiming);
+    return e;
+}
+}  // namespace
+
+bt_status bt_factor_solve_host(bt_plan P, const double* B, const double* D, const double* C, const double* F,
+                               double* X, int nrhs, int sweeps) {
+    if (!P || P->kind != 0 || !D || !F || !X || (P->N > 1 && (!B || !C)) || nrhs < 1 || nrhs > P->nrhs_max ||
+        sweeps < -1 || sweeps > 30 || P->padded || P->pivot || P->local > 0)
+        return BT_ERR_INVALID;
+    if (P->prec == BT_FP64 && sweeps >= 0) return BT_ERR_INVALID;
+    if (P->prec != BT_FP64 && sweeps < 0) return BT_ERR_INVALID;
+    cudaError_t e = ensure_host_path(P);
+    if (e == cudaSuccess) e = ensure_side(P);
+    if (e != cudaSuccess) return from_cuda(e);
+    const size_t mm = (size_t)P->m * P->m, bmm = sizeof(double) * mm;
+    double* dB = P->hb;
+    double* dD = dB + (size_t)P->N * mm;
+    double* dC = dD + (size_t)P->N * mm;
+    double* dF = dC + (size_t)P->N * mm;
+    double* dX = dF + (size_t)P->N * P->m * P->nrhs_max;
+    Level& v = P->lv[0];
+    P->A0 = dB;
+    P->A1 = dD;
+    P->A2 = dC;
+    v.a.B = dB;
+    v.a.D = dD;
+    v.a.C = dC;
+    v.a.shift = 0;
+    P->anorm_valid = false;
+    // the device copies may still be read by work queued earlier on the plan's stream
+    e = cudaEventRecord(P->ev_in, P->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->copy_stream, P->ev_in, 0);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->status, 0, 4 * sizeof(long long), P->stream);
+    const long long p = v.a.p;
+    const int K = (int)std::min<long long>(bt_plan_s::kChunks, std::max<long long>(p, 1));
+    for (int k = 0; k < K && e == cudaSuccess; ++k) {
+        const long long pb = p * k / K, pe = p * (k + 1) / K;
+        // rows of partitions [pb, pe) and the separator row before them (its C)
+        const long long r0 = std::max<long long>(part_start(v.a, pb) - 1, 0);
+        const long long r1 = (pe >= p) ? P->N : part_start(v.a, pe);
+        const size_t off = (size_t)r0 * mm, bytes = (size_t)(r1 - r0) * bmm;
+        e = cudaMemcpyAsync(dB + off, B + off, bytes, cudaMemcpyHostToDevice, P->copy_stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dD + off, D + off, bytes, cudaMemcpyHostToDevice, P->copy_stream);
+        if (e == cudaSuccess && C) e = cudaMemcpyAsync(dC + off, C + off, bytes, cudaMemcpyHostToDevice, P->copy_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(P->ev_rows[k], P->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(P->chunk_stream[k], P->ev_rows[k], 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(P->chunk_stream[k], P->ev_in, 0);
+        if (e == cudaSuccess)
+            e = launch(P, K_FACTOR, 0, 1,
+                       [&] { return P->L->factor_part(v.a, v.low, pb, pe, P->chunk_stream[k]); });
+        if (e == cudaSuccess) e = cudaEventRecord(P->ev_part[k], P->chunk_stream[k]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(P->stream, P->ev_part[k], 0);
+    }
+    const size_t fbytes = sizeof(double) * (size_t)P->N * P->m * nrhs;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dF, F, fbytes, cudaMemcpyHostToDevice, P->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(P->ev_rhs, P->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->stream, P->ev_rhs, 0);
+    if (e != cudaSuccess) return from_cuda(e);
+    P->overlap = !P->serial;
+    bt_status st = run_factor(P, true);
+    P->overlap = false;
+    P->factored = (st == BT_OK);
+    if (st == BT_OK) st = (sweeps < 0) ? run_solve(P, dF, dX, nrhs) : run_refine_async(P, dF, dX, nrhs, sweeps);
+    if (P->join_pending) {
+        cudaError_t ej = join_factor(P);
+        if (st == BT_OK && ej != cudaSuccess) st = from_cuda(ej);
+    }
+    if (st != BT_OK) return st;
+    e = cudaMemcpyAsync(X, dX, fbytes, cudaMemcpyDeviceToHost, P->stream);
+    return from_cuda(e);
 }
 
 bt_status bt_band_to_blocks(int64_t n, int s, int r, const double* band, int m, double* B, double* D, double* C,
@@ -1281,6 +1395,21 @@ void bt_plan_destroy(bt_plan P) {
         cudaStreamSynchronize(P->side);
         cudaStreamDestroy(P->side);
     }
+    if (P->copy_stream) {
+        cudaStreamSynchronize(P->copy_stream);
+        cudaStreamDestroy(P->copy_stream);
+    }
+    for (int k = 0; k < bt_plan_s::kChunks; ++k) {
+        if (P->chunk_stream[k]) {
+            cudaStreamSynchronize(P->chunk_stream[k]);
+            cudaStreamDestroy(P->chunk_stream[k]);
+        }
+        if (P->ev_rows[k]) cudaEventDestroy(P->ev_rows[k]);
+        if (P->ev_part[k]) cudaEventDestroy(P->ev_part[k]);
+    }
+    if (P->ev_in) cudaEventDestroy(P->ev_in);
+    if (P->ev_rhs) cudaEventDestroy(P->ev_rhs);
+    if (P->hb) cudaFree(P->hb);
     if (P->ev_fork) cudaEventDestroy(P->ev_fork);
     if (P->ev_join) cudaEventDestroy(P->ev_join);
     if (P->own_arena) cudaFree(P->arena);

@@ -783,7 +783,9 @@ __device__ __forceinline__ void solve_bwd_cta_body(const LevelArgs& a, const lon
     template <TPL>                                                                                     \
     __global__ void __launch_bounds__(8 * M) NAME(const LevelArgs a) {                                 \
         extern __shared__ __align__(16) unsigned char smem_raw[];                                      \
-        BODY<TARGS>(a, (long long)blockIdx.x, smem_raw);                                                \
+        const long long u = a.unit0 + (long long)blockIdx.x;                                           \
+        if (a.unit_end > 0 && u >= a.unit_end) return;                                                 \
+        BODY<TARGS>(a, u, smem_raw);                                                                   \
     }                                                                                                  \
     template <TPL>                                                                                     \
     __global__ void __launch_bounds__(8 * M)                                                           \

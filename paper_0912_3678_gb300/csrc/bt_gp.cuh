@@ -334,25 +334,35 @@ __device__ __forceinline__ void solve_bwd_gp_body(const LevelArgs& a, const long
     }
 }
 
+// Units [unit0, unit_end) of the launch (whole groups: both are multiples of M*M).
+__device__ __forceinline__ bool gp_unit(const LevelArgs& a, long long& u) {
+    u = a.unit0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    return !(a.unit_end > 0 && u >= a.unit_end);
+}
 template <int M, int MODE>
 __global__ void __launch_bounds__(128) k_factor_gp(const LevelArgs a) {
-    factor_gp_body<M, MODE>(a, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    long long u;
+    if (gp_unit(a, u)) factor_gp_body<M, MODE>(a, u);
 }
 template <int M>
 __global__ void __launch_bounds__(128) k_assemble_gp(const LevelArgs a) {
-    assemble_gp_body<M>(a, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    long long u;
+    if (gp_unit(a, u)) assemble_gp_body<M>(a, u);
 }
 template <int M, int MODE>
 __global__ void __launch_bounds__(128) k_solve_fwd_gp(const LevelArgs a) {
-    solve_fwd_gp_body<M, MODE>(a, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    long long u;
+    if (gp_unit(a, u)) solve_fwd_gp_body<M, MODE>(a, u);
 }
 template <int M>
 __global__ void __launch_bounds__(128) k_assemble_rhs_gp(const LevelArgs a) {
-    assemble_rhs_gp_body<M>(a, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    long long u;
+    if (gp_unit(a, u)) assemble_rhs_gp_body<M>(a, u);
 }
 template <int M, int MODE>
 __global__ void __launch_bounds__(128) k_solve_bwd_gp(const LevelArgs a) {
-    solve_bwd_gp_body<M, MODE>(a, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    long long u;
+    if (gp_unit(a, u)) solve_bwd_gp_body<M, MODE>(a, u);
 }
 
 }  // namespace bt

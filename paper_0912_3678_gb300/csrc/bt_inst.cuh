@@ -44,6 +44,35 @@ struct Inst {
         if (a.mode == 0) return low ? factor_t<float, 0>(a, s) : factor_t<double, 0>(a, s);
         return low ? factor_t<float, 1>(a, s) : factor_t<double, 1>(a, s);
     }
+    template <typename T, int MODE>
+    static cudaError_t factor_part_t(const LevelArgs& a0, long long pb, long long pe, cudaStream_t s) {
+        if (pe > a0.p) pe = a0.p;
+        if (pb < 0 || pe <= pb) return cudaSuccess;
+        LevelArgs a = a0;
+        if constexpr (M >= 8) {
+            const size_t smem = factor_smem_bytes<T, M>();
+            cudaError_t e = set_smem(k_factor_cta<T, M, MODE>, smem);
+            if (e != cudaSuccess) return e;
+            a.unit0 = pb;
+            a.unit_end = pe;
+            k_factor_cta<T, M, MODE><<<(unsigned)(pe - pb), 8 * M, smem, s>>>(a);
+        } else if (use_gp<T, M>(a)) {
+            if constexpr (M == 2 || M == 4) {
+                a.unit0 = pb * M * M;
+                a.unit_end = pe * M * M;
+                k_factor_gp<M, MODE><<<grid_for((pe - pb) * M * M, 128), 128, 0, s>>>(a);
+            }
+        } else {
+            a.unit0 = pb;
+            a.unit_end = pe;
+            k_factor_tp<T, M, MODE><<<grid_for(pe - pb, tpb(a)), tpb(a), 0, s>>>(a);
+        }
+        return cudaGetLastError();
+    }
+    static cudaError_t factor_part(const LevelArgs& a, bool low, long long pb, long long pe, cudaStream_t s) {
+        if (a.mode == 0) return low ? factor_part_t<float, 0>(a, pb, pe, s) : factor_part_t<double, 0>(a, pb, pe, s);
+        return low ? factor_part_t<float, 1>(a, pb, pe, s) : factor_part_t<double, 1>(a, pb, pe, s);
+    }
     template <typename T>
     static cudaError_t assemble_t(const LevelArgs& a, cudaStream_t s) {
         if (a.p <= 1) return cudaSuccess;
@@ -267,7 +296,7 @@ struct Inst {
         return cudaErrorNotSupported;
     }
     static const Launchers* table() {
-        static const Launchers L = {factor, assemble, solve_fwd, assemble_rhs, solve_bwd,
+        static const Launchers L = {factor, factor_part, assemble, solve_fwd, assemble_rhs, solve_bwd,
                                     factor_b, assemble_b, solve_fwd_b, assemble_rhs_b, solve_bwd_b,
                                     M >= 8,
                                     M >= 8 ? factor_smem_bytes<double, M>() : 0,

@@ -12,6 +12,8 @@ namespace bt {
 struct Launchers {
     // low = true: local factors of this level in FP32 (the level's T is float)
     cudaError_t (*factor)(const LevelArgs&, bool low, cudaStream_t);
+    // the factorization of partitions [p_begin, p_end) of a level only
+    cudaError_t (*factor_part)(const LevelArgs&, bool low, long long p_begin, long long p_end, cudaStream_t);
     cudaError_t (*assemble)(const LevelArgs&, bool low, cudaStream_t);
     cudaError_t (*solve_fwd)(const LevelArgs&, bool low, cudaStream_t);
     cudaError_t (*assemble_rhs)(const LevelArgs&, bool low, cudaStream_t);

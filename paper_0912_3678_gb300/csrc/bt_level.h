@@ -42,6 +42,8 @@ struct LevelArgs {
     long long* brk;            // breakdown list: [0] count, [1..brk_cap] block rows (null: report singular)
     long long brk_cap;
     double tau;                // breakdown: |pivot| <= tau * largest entry of the row's blocks
+    // a launch over part of the level: units [unit0, unit_end) (unit_end = 0: the whole level)
+    long long unit0, unit_end;
 };
 
 }  // namespace bt

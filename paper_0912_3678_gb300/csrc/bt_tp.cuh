@@ -686,7 +686,9 @@ __device__ __forceinline__ void solve_bwd_tp_body(const LevelArgs& a, const long
 #define BT_TP_KERNELS(NAME, BODY, TPL, TARGS)                                                           \
     template <TPL>                                                                                     \
     __global__ void __launch_bounds__(256) NAME(const LevelArgs a) {                                   \
-        BODY<TARGS>(a, (long long)blockIdx.x * blockDim.x + threadIdx.x);                               \
+        const long long u = a.unit0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;               \
+        if (a.unit_end > 0 && u >= a.unit_end) return;                                                 \
+        BODY<TARGS>(a, u);                                                                             \
     }                                                                                                  \
     template <TPL>                                                                                     \
     __global__ void __launch_bounds__(256)                                                             \

@@ -458,3 +458,60 @@ def test_captured_step_same_with_one_or_two_streams(cuda, m, N, tuning):
             out.append(to_host(X))
     assert np.array_equal(out[0], out[1])
     assert oracle.rel_err(out[0], oracle.btri_solve(s.B, s.D, s.C, s.F)) <= TOL64
+
+
+@pytest.mark.parametrize("m,N,tuning", [(1, 60000, {"p0": 2048}), (4, 20000, {}), (8, 3000, {}),
+                                        (16, 2000, {"reduced": 1}), (16, 999, {"reduced": 0}), (2, 40, {"p0": 3})])
+@pytest.mark.parametrize("pinned", [True, False])
+def test_factor_solve_host_matches_oracle(cuda, m, N, tuning, pinned):
+    """bt_factor_solve_host: host arrays in and out, block rows copied in chunks
+    of partitions whose factorizations start as their rows arrive; twice on
+    the same plan with different systems."""
+    import torch
+
+    import paper_0912_3678_gb300 as bt
+    nr = 3
+    with bt.BtPlan.tuned(N, m, nr, "fp64", tuning) as plan:
+        for rep in range(2):
+            s = gen.btri_random(N, m, nr, seed_rep=60 + rep)
+            host = [torch.from_numpy(np.ascontiguousarray(a)) for a in (s.B, s.D, s.C, s.F)]
+            if pinned:
+                host = [h.pin_memory() for h in host]
+            X = torch.empty(host[3].shape, dtype=torch.float64)
+            X = X.pin_memory() if pinned else X.numpy()
+            plan.factor_solve_host(*host, X)
+            plan.sync()
+            Xh = X.numpy() if pinned else X
+            assert oracle.rel_err(Xh, oracle.btri_solve(s.B, s.D, s.C, s.F)) <= TOL64
+
+
+@pytest.mark.parametrize("m,N", [(4, 20000), (16, 2000)])
+def test_factor_refine_host_matches_oracle(cuda, m, N):
+    """The refined variant of the host entry point (FP32 local factors, FP64
+    corrections) reaches the refinement tolerance."""
+    import torch
+
+    import paper_0912_3678_gb300 as bt
+    s = gen.btri_random(N, m, 2, seed_rep=71)
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (s.B, s.D, s.C, s.F)]
+    X = torch.empty(host[3].shape, dtype=torch.float64).pin_memory()
+    with bt.BtPlan.tuned(N, m, 2, "fp32_ir", {}) as plan:
+        plan.factor_solve_host(*host, X, sweeps=3)
+        code, rel = bt.bt_refine_result(plan.handle, 1e-12)
+        assert code == 0
+    assert oracle.rel_err(X.numpy(), oracle.btri_solve(s.B, s.D, s.C, s.F)) <= TOLIR
+
+
+def test_factor_solve_host_refuses_other_plans(cuda):
+    import torch
+
+    import paper_0912_3678_gb300 as bt
+    s = gen.btri_random(100, 4, 1, seed_rep=1)
+    host = [torch.from_numpy(np.ascontiguousarray(a)) for a in (s.B, s.D, s.C, s.F)]
+    X = torch.empty(host[3].shape, dtype=torch.float64)
+    with bt.BtPlan.tuned(100, 4, 1, "fp64", {"pivot": 1}) as plan:
+        with pytest.raises(bt.BtError):
+            plan.factor_solve_host(*host, X)
+    with bt.BtPlan.tuned(100, 4, 1, "fp64", {}) as plan:
+        with pytest.raises(bt.BtError):
+            plan.factor_solve_host(*host, X, sweeps=2)      # sweeps only for refined plans
