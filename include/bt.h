@@ -254,6 +254,15 @@ bt_status bt_plan_capture(bt_plan plan, int what, const double* F, double* X, in
  * reduction; BT_ERR_INVALID otherwise. */
 bt_status bt_factor_solve_host(bt_plan plan, const double* B, const double* D, const double* C, const double* F,
                                double* X, int nrhs, int sweeps);
+
+/* bt_factor_solve_host recorded into the plan's CUDA graph (as bt_plan_capture
+ * does for device arrays): bt_plan_replay then re-runs the copies in, the
+ * factorization, the solve (or refinement) and the copy of X out as one graph
+ * launch, reading the same host arrays.  The host arrays must be page-locked
+ * (BT_ERR_CUDA otherwise); synchronises the stream and replaces any earlier
+ * graph of the plan. */
+bt_status bt_plan_capture_host(bt_plan plan, const double* B, const double* D, const double* C, const double* F,
+                               double* X, int nrhs, int sweeps);
 bt_status bt_plan_replay(bt_plan plan);
 
 /* Wait for the plan's stream; return the recorded numerical status. */

@@ -21,7 +21,7 @@ __all__ = ["BtPlan", "AbdPlan", "BtError", "BT_STATUS", "PREC", "load_library",
            "bt_batch_create", "bt_batch_run", "bt_batch_finish", "bt_batch_info", "bt_batch_destroy",
            "BtBatch", "CycPlan", "cyc_plan_create", "cyc_factor", "cyc_solve", "cyc_residual", "cyc_refine",
            "BtTuning", "BtBatchDesc", "bt_refine_async", "bt_refine_result",
-           "bt_plan_workspace_size", "bt_plan_anorm", "bt_plan_set_pivot_tol", "ivp_parareal", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay", "bt_factor_solve_host",
+           "bt_plan_workspace_size", "bt_plan_anorm", "bt_plan_set_pivot_tol", "ivp_parareal", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay", "bt_factor_solve_host", "bt_plan_capture_host",
            "bt_band_to_blocks", "band_to_blocks", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
            "abd_plan_create", "abd_factor", "abd_solve", "abd_residual", "abd_refine", "abd_sync",
            "abd_plan_destroy"]
@@ -303,6 +303,12 @@ def bt_factor_solve_host(plan, B, D, C, F, X, nrhs, sweeps=-1):
                                                 _host_ptr(X), int(nrhs), int(sweeps)), "bt_factor_solve_host")
 
 
+def bt_plan_capture_host(plan, B, D, C, F, X, nrhs, sweeps=-1):
+    """Record bt_factor_solve_host (pinned host arrays) into the plan's graph; replay() re-runs it."""
+    _lib.check(_lib.load().bt_plan_capture_host(plan, _host_ptr(B), _host_ptr(D), _host_ptr(C), _host_ptr(F),
+                                                _host_ptr(X), int(nrhs), int(sweeps)), "bt_plan_capture_host")
+
+
 def bt_plan_replay(plan):
     _lib.check(_lib.load().bt_plan_replay(plan), "bt_plan_replay")
 
@@ -461,6 +467,11 @@ class _PlanBase:
         """bt_factor_solve_host: host (pinned) B, D, C, F in, host X out, asynchronous."""
         nr = F.shape[1] if len(F.shape) == 2 else 1
         bt_factor_solve_host(self.handle, B, D, C, F, X, nr, sweeps)
+
+    def capture_host(self, B, D, C, F, X, sweeps=-1):
+        """bt_plan_capture_host: the host-array call as one graph; replay() re-runs it."""
+        nr = F.shape[1] if len(F.shape) == 2 else 1
+        bt_plan_capture_host(self.handle, B, D, C, F, X, nr, sweeps)
 
 
 class BtPlan(_PlanBase):

@@ -72,6 +72,7 @@ SIGNATURES.update({
     "bt_plan_capture": (_i32, [_vp, _i32, _vp, _vp, _i32, _i32]),
     "bt_plan_replay": (_i32, [_vp]),
     "bt_factor_solve_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32]),
+    "bt_plan_capture_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32]),
     "bt_band_to_blocks": (_i32, [_i64, _i32, _i32, _vp, _i32, _vp, _vp, _vp, _vp]),
     "bt_refine_result": (_i32, [_vp, _f64, _pf64]),
     "bt_plan_set_backward_tol": (_i32, [_vp, _f64]),

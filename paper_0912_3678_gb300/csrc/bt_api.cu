@@ -105,6 +105,7 @@ struct bt_plan_s {
     // stream and per-chunk streams on which the level-0 factorization of each
     // chunk of partitions starts as soon as its rows have arrived
     static constexpr int kChunks = 8;
+    static constexpr int kPhases = 4;   // row slabs of the block kernels' host path
     double* hb = nullptr;               // B, D, C [N m m] each, then F, X [N m nrhs_max]
     cudaStream_t copy_stream = nullptr;
     cudaStream_t chunk_stream[kChunks] = {};
@@ -1203,16 +1204,20 @@ cudaError_t ensure_host_path(bt_plan_s* P) {
 }
 }  // namespace
 
-bt_status bt_factor_solve_host(bt_plan P, const double* B, const double* D, const double* C, const double* F,
-                               double* X, int nrhs, int sweeps) {
+namespace {
+bt_status check_host_call(bt_plan P, const double* B, const double* D, const double* C, const double* F,
+                          const double* X, int nrhs, int sweeps) {
     if (!P || P->kind != 0 || !D || !F || !X || (P->N > 1 && (!B || !C)) || nrhs < 1 || nrhs > P->nrhs_max ||
         sweeps < -1 || sweeps > 30 || P->padded || P->pivot || P->local > 0)
         return BT_ERR_INVALID;
     if (P->prec == BT_FP64 && sweeps >= 0) return BT_ERR_INVALID;
     if (P->prec != BT_FP64 && sweeps < 0) return BT_ERR_INVALID;
-    cudaError_t e = ensure_host_path(P);
-    if (e == cudaSuccess) e = ensure_side(P);
-    if (e != cudaSuccess) return from_cuda(e);
+    return BT_OK;
+}
+
+bt_status enqueue_host(bt_plan P, const double* B, const double* D, const double* C, const double* F, double* X,
+                       int nrhs, int sweeps) {
+    cudaError_t e = cudaSuccess;
     const size_t mm = (size_t)P->m * P->m, bmm = sizeof(double) * mm;
     double* dB = P->hb;
     double* dD = dB + (size_t)P->N * mm;
@@ -1234,7 +1239,50 @@ bt_status bt_factor_solve_host(bt_plan P, const double* B, const double* D, cons
     if (e == cudaSuccess) e = cudaMemsetAsync(P->status, 0, 4 * sizeof(long long), P->stream);
     const long long p = v.a.p;
     const int K = (int)std::min<long long>(bt_plan_s::kChunks, std::max<long long>(p, 1));
-    for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    // CTA kernels (m >= 8): row slabs of every partition in turn, the factorization in as
+    // many phases, so every partition starts as soon as the first slab is in (strided
+    // copies: one per array for each class of partitions with the same row count)
+    const long long base = v.a.base, extra = v.a.extra;
+    const bool slabs = P->L->factor_phase != nullptr && p >= 2 && base >= 1 &&
+                       (size_t)(base + 1) * bmm < ((size_t)1 << 30);
+    const int KP = bt_plan_s::kPhases;
+    if (slabs && e == cudaSuccess) {
+        struct Cls { long long first, count, stride, local; };
+        Cls cls[3];
+        int nc = 0;
+        const long long nA = std::min<long long>(extra, p - 1);
+        if (nA > 0) cls[nc++] = {0, nA, base + 1, base};                       // base+1 rows, last is the separator
+        if (p - 1 - nA > 0) cls[nc++] = {nA, p - 1 - nA, base, base - 1};      // base rows, last is the separator
+        const long long lastcnt = base + ((p - 1) < extra ? 1 : 0);
+        cls[nc++] = {p - 1, 1, lastcnt, lastcnt};                              // the last partition: no separator
+        auto copy2d = [&](long long row0, long long stride, long long rows, long long count) {
+            if (rows <= 0 || count <= 0) return cudaSuccess;
+            const size_t off = (size_t)row0 * mm, pitch = (size_t)stride * bmm, width = (size_t)rows * bmm;
+            cudaError_t r = cudaMemcpy2DAsync(dB + off, pitch, B + off, pitch, width, count, cudaMemcpyHostToDevice,
+                                              P->copy_stream);
+            if (r == cudaSuccess)
+                r = cudaMemcpy2DAsync(dD + off, pitch, D + off, pitch, width, count, cudaMemcpyHostToDevice,
+                                      P->copy_stream);
+            if (r == cudaSuccess && C)
+                r = cudaMemcpy2DAsync(dC + off, pitch, C + off, pitch, width, count, cudaMemcpyHostToDevice,
+                                      P->copy_stream);
+            return r;
+        };
+        // the separator rows first: the first phase reads the left separator's C
+        for (int c = 0; c < nc && e == cudaSuccess; ++c)
+            if (cls[c].local < cls[c].stride) e = copy2d(part_start(v.a, cls[c].first) + cls[c].local, cls[c].stride, 1, cls[c].count);
+        for (int k = 0; k < KP && e == cudaSuccess; ++k) {
+            for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+                const long long l0 = cls[c].local * k / KP, l1 = cls[c].local * (k + 1) / KP;
+                e = copy2d(part_start(v.a, cls[c].first) + l0, cls[c].stride, l1 - l0, cls[c].count);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(P->ev_rows[k], P->copy_stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(P->stream, P->ev_rows[k], 0);
+            if (e == cudaSuccess)
+                e = launch(P, K_FACTOR, 0, 1, [&] { return P->L->factor_phase(v.a, v.low, k, KP, P->stream); });
+        }
+    }
+    for (int k = 0; k < K && e == cudaSuccess && !slabs; ++k) {
         const long long pb = p * k / K, pe = p * (k + 1) / K;
         // rows of partitions [pb, pe) and the separator row before them (its C)
         const long long r0 = std::max<long long>(part_start(v.a, pb) - 1, 0);
@@ -1269,6 +1317,62 @@ bt_status bt_factor_solve_host(bt_plan P, const double* B, const double* D, cons
     if (st != BT_OK) return st;
     e = cudaMemcpyAsync(X, dX, fbytes, cudaMemcpyDeviceToHost, P->stream);
     return from_cuda(e);
+}
+}  // namespace
+
+bt_status bt_factor_solve_host(bt_plan P, const double* B, const double* D, const double* C, const double* F,
+                               double* X, int nrhs, int sweeps) {
+    bt_status st = check_host_call(P, B, D, C, F, X, nrhs, sweeps);
+    if (st != BT_OK) return st;
+    cudaError_t e = ensure_host_path(P);
+    if (e == cudaSuccess) e = ensure_side(P);
+    if (e != cudaSuccess) return from_cuda(e);
+    return enqueue_host(P, B, D, C, F, X, nrhs, sweeps);
+}
+
+bt_status bt_plan_capture_host(bt_plan P, const double* B, const double* D, const double* C, const double* F,
+                               double* X, int nrhs, int sweeps) {
+    bt_status st = check_host_call(P, B, D, C, F, X, nrhs, sweeps);
+    if (st != BT_OK) return st;
+    cudaError_t e = ensure_host_path(P);
+    if (e == cudaSuccess) e = ensure_side(P);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+    if (e == cudaSuccess) e = P->L->prepare();
+    if (e != cudaSuccess) return from_cuda(e);
+    if (P->graph_exec) {
+        cudaGraphExecDestroy(P->graph_exec);
+        P->graph_exec = nullptr;
+    }
+    if (P->graph) {
+        cudaGraphDestroy(P->graph);
+        P->graph = nullptr;
+    }
+    cudaStream_t saved = P->stream, cap = nullptr;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return from_cuda(e);
+    const bool saved_trace = P->trace;
+    const long long l0 = P->launches;
+    P->trace = false;
+    P->stream = cap;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        st = enqueue_host(P, B, D, C, F, X, nrhs, sweeps);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (e == cudaSuccess) e = e2;
+        P->graph = g;
+        if (e == cudaSuccess && st == BT_OK) e = cudaGraphInstantiate(&P->graph_exec, g, 0);
+    }
+    P->stream = saved;
+    P->trace = saved_trace;
+    P->graph_launches = P->launches - l0;
+    P->launches = l0;
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return from_cuda(e);
+    }
+    return st;
 }
 
 bt_status bt_band_to_blocks(int64_t n, int s, int r, const double* band, int m, double* B, double* D, double* C,

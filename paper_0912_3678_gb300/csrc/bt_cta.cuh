@@ -304,19 +304,42 @@ __device__ __forceinline__ void factor_cta_body(const LevelArgs& a, const long l
 
     auto needB = [&](long long j) { return j > pt.s || pt.hasL; };
     auto needC = [&](long long j) { return (MODE == 0) && ((j < pt.e - 1) || pt.hasR); };
-    if (pt.s < pt.e) {
-        RowPrefetch<T, M> pf;
-        pf.load(needB(pt.s) ? a.B + (pt.s - a.shift) * MM : nullptr, a.D + (pt.s - a.shift) * MM,
-                needC(pt.s) ? a.C + (pt.s - a.shift) * MM : nullptr);
-        pf.store(sB, sD, sC, needB(pt.s), needC(pt.s));
+    // rows of this launch: the whole partition, or one phase of it (the rows of every
+    // partition arriving in slabs); a later phase resumes from the state the previous
+    // one left in Y, Zc (rows already stored) and Pf, Qf (the running sum and W)
+    long long jb = pt.s, je = pt.e;
+    const bool phased = (MODE == 0) && a.phases > 1;
+    if (phased) {
+        const long long cnt = pt.e - pt.s;
+        jb = pt.s + cnt * a.phase / a.phases;
+        je = pt.s + cnt * (a.phase + 1) / a.phases;
     }
-    if (wchain) load_blk<T, M>(sW, a.C + (pt.s - 1 - a.shift) * MM);   // W_s = C of the left separator row
+    if (jb < je) {
+        RowPrefetch<T, M> pf;
+        pf.load(needB(jb) ? a.B + (jb - a.shift) * MM : nullptr, a.D + (jb - a.shift) * MM,
+                needC(jb) ? a.C + (jb - a.shift) * MM : nullptr);
+        pf.store(sB, sD, sC, needB(jb), needC(jb));
+    }
+    if (jb > pt.s) {
+        if (jb < je) {
+            load_blkT<T, M>(sY, gY + (jb - 1) * MM);
+            if (pt.hasL) load_blkT<T, M>(sZ, gZ + (jb - 1) * MM);
+        }
+        if (wchain) {
+            load_blkT<T, M>(sW, reinterpret_cast<const T*>(a.Qf) + i * MM);
+            const T* gP = reinterpret_cast<const T*>(a.Pf) + i * MM;
+#pragma unroll
+            for (int q = 0; q < S::R; ++q) cp[q] = gP[(o.r0 + q) * M + o.c];
+        }
+    } else if (wchain) {
+        load_blk<T, M>(sW, a.C + (pt.s - 1 - a.shift) * MM);   // W_s = C of the left separator row
+    }
     __syncthreads();
 
-    for (long long j = pt.s; j < pt.e; ++j) {
+    for (long long j = jb; j < je; ++j) {
         const bool first = (j == pt.s);
         const bool nC = needC(j);
-        const bool more = (j + 1 < pt.e);
+        const bool more = (j + 1 < je);
         RowPrefetch<T, M> pf;
         if (more)
             pf.load(needB(j + 1) ? a.B + (j + 1 - a.shift) * MM : nullptr, a.D + (j + 1 - a.shift) * MM,
@@ -413,6 +436,7 @@ __device__ __forceinline__ void factor_cta_body(const LevelArgs& a, const long l
 
     if (MODE == 0) {
         if (!pt.hasL) return;
+        // final: C_sep P_first and W_e; between phases: the running sum and W
         store_own<T, M>(reinterpret_cast<T*>(a.Pf) + i * MM, cp, o);
         store_blk<T, M>(reinterpret_cast<T*>(a.Qf) + i * MM, sW);   // W_e (zero when there is no x_R)
     } else {

@@ -69,6 +69,13 @@ struct Inst {
         }
         return cudaGetLastError();
     }
+    static cudaError_t factor_phase(const LevelArgs& a0, bool low, int k, int phases, cudaStream_t s) {
+        if (a0.mode != 0 || k < 0 || k >= phases) return cudaErrorInvalidValue;
+        LevelArgs a = a0;
+        a.phase = k;
+        a.phases = phases;
+        return low ? factor_t<float, 0>(a, s) : factor_t<double, 0>(a, s);
+    }
     static cudaError_t factor_part(const LevelArgs& a, bool low, long long pb, long long pe, cudaStream_t s) {
         if (a.mode == 0) return low ? factor_part_t<float, 0>(a, pb, pe, s) : factor_part_t<double, 0>(a, pb, pe, s);
         return low ? factor_part_t<float, 1>(a, pb, pe, s) : factor_part_t<double, 1>(a, pb, pe, s);
@@ -296,7 +303,8 @@ struct Inst {
         return cudaErrorNotSupported;
     }
     static const Launchers* table() {
-        static const Launchers L = {factor, factor_part, assemble, solve_fwd, assemble_rhs, solve_bwd,
+        static const Launchers L = {factor, factor_part, M >= 8 ? factor_phase : nullptr, assemble, solve_fwd,
+                                    assemble_rhs, solve_bwd,
                                     factor_b, assemble_b, solve_fwd_b, assemble_rhs_b, solve_bwd_b,
                                     M >= 8,
                                     M >= 8 ? factor_smem_bytes<double, M>() : 0,

@@ -14,6 +14,8 @@ struct Launchers {
     cudaError_t (*factor)(const LevelArgs&, bool low, cudaStream_t);
     // the factorization of partitions [p_begin, p_end) of a level only
     cudaError_t (*factor_part)(const LevelArgs&, bool low, long long p_begin, long long p_end, cudaStream_t);
+    // phase k of `phases` of a block tridiagonal level's factorization (CTA kernels; null for m <= 4)
+    cudaError_t (*factor_phase)(const LevelArgs&, bool low, int k, int phases, cudaStream_t);
     cudaError_t (*assemble)(const LevelArgs&, bool low, cudaStream_t);
     cudaError_t (*solve_fwd)(const LevelArgs&, bool low, cudaStream_t);
     cudaError_t (*assemble_rhs)(const LevelArgs&, bool low, cudaStream_t);

@@ -44,6 +44,9 @@ struct LevelArgs {
     double tau;                // breakdown: |pivot| <= tau * largest entry of the row's blocks
     // a launch over part of the level: units [unit0, unit_end) (unit_end = 0: the whole level)
     long long unit0, unit_end;
+    // factorization in phases (CTA kernels, mode 0): phase k of `phases` takes local rows
+    // [s + L k / phases, s + L (k+1) / phases) of every partition (L = e - s); phases <= 1: all
+    int phase, phases;
 };
 
 }  // namespace bt

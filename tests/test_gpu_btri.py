@@ -515,3 +515,26 @@ def test_factor_solve_host_refuses_other_plans(cuda):
     with bt.BtPlan.tuned(100, 4, 1, "fp64", {}) as plan:
         with pytest.raises(bt.BtError):
             plan.factor_solve_host(*host, X, sweeps=2)      # sweeps only for refined plans
+
+
+@pytest.mark.parametrize("m,N,tuning", [(16, 2000, {"reduced": 1}), (8, 3000, {}), (4, 20000, {})])
+def test_captured_host_call_reads_new_host_data(cuda, m, N, tuning):
+    """bt_plan_capture_host: the host-array call as one graph; replayed after the
+    pinned host arrays are overwritten with another system, it solves that one."""
+    import torch
+
+    import paper_0912_3678_gb300 as bt
+    nr = 2
+    s0 = gen.btri_random(N, m, nr, seed_rep=80)
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (s0.B, s0.D, s0.C, s0.F)]
+    X = torch.empty(host[3].shape, dtype=torch.float64).pin_memory()
+    with bt.BtPlan.tuned(N, m, nr, "fp64", tuning) as plan:
+        plan.capture_host(*host, X)
+        for rep in (81, 82):
+            s = gen.btri_random(N, m, nr, seed_rep=rep)
+            for h, a in zip(host, (s.B, s.D, s.C, s.F)):
+                h.copy_(torch.from_numpy(np.ascontiguousarray(a)))
+            X.zero_()
+            plan.replay()
+            plan.sync()
+            assert oracle.rel_err(X.numpy(), oracle.btri_solve(s.B, s.D, s.C, s.F)) <= TOL64
