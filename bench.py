@@ -566,7 +566,13 @@ def main():
     results = {}
     paths = [p for p in args.paths.split(",") if p]
     tunings = {}
-    if w["kind"] == "btri" and args.tuning:
+    if w["kind"] == "babd" and args.tuning:
+        # BABD plans: {"reduced": 1} = cyclic reduction of the whole system (FP64 only)
+        fixed = {k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(",") if kv)}
+        paths = [p for p in paths if p == "fp64"] if fixed.get("reduced") else paths
+        for prec in paths:
+            tunings[prec] = dict(fixed)
+    elif w["kind"] == "btri" and args.tuning:
         fixed = {k: int(v) for k, v in (kv.split("=") for kv in args.tuning.split(",") if kv)}
         for prec in paths:
             tunings[prec] = dict(fixed)
@@ -577,7 +583,7 @@ def main():
             tunings[prec] = tuner.tune(m, N, prec, nrhs=nr)
     for prec in paths:
         if prec in tunings:
-            plan = bt.BtPlan.tuned(N, m, nrhs_max=nr, prec=prec, tuning=tunings[prec])
+            plan = Plan.tuned(N, m, nrhs_max=nr, prec=prec, tuning=tunings[prec])
         else:
             plan = Plan(N, m, nrhs_max=nr, prec=prec)
 
@@ -766,6 +772,14 @@ def main():
             "solve_fwd": 6.0 * m * m * nr * local_rows,                # 2 matvecs + top-row sweep per row
             "solve_bwd": 4.0 * m * m * nr * local_rows,                # 2 matvecs per row
             "residual": 6.0 * m * m * nr * N,                          # 3 m^2 nrhs FMA per block row, FP64
+        }
+    elif (tunings.get(head) or {}).get("reduced"):
+        pairs = N // 2                                                  # first cyclic-reduction level
+        flops_per = {
+            "factor": (2.0 / 3.0 + 2.0 + 2.0) * m ** 3 * pairs,        # LU of R_2k, R^-1 S_2k, S_2k+1 T
+            "solve_fwd": 4.0 * m * m * nr * pairs,                     # R^-1 r_2k, S_2k+1 u
+            "solve_bwd": 2.0 * m * m * nr * pairs,                     # T y_2k
+            "residual": 4.0 * m * m * nr * (N + 1),
         }
     else:
         flops_per = {

@@ -393,6 +393,19 @@ void bt_batch_destroy(bt_batch batch);
 
 bt_status abd_plan_create(abd_plan* plan, int64_t N, int m, int nrhs_max, int prec, int64_t p,
                           void* stream);
+
+/* abd_plan_create with explicit parameters (bt_tuning; NULL = defaults):
+ * p0, sub_rows, top_rows and serial as for bt_plan_create_tuned; local and
+ * pivot must be 0.  reduced = 1: cyclic reduction of the whole BABD system
+ * instead of partitions (the method Sec. 2 recommends for ABD/BABD matrices):
+ * rows 2k and 2k+1 of every level eliminate y_{2k+1} (one inverse of R_{2k} by
+ * Gauss-Jordan with partial pivoting and two block products per pair, one
+ * launch per level and phase), down to one row, which with the boundary row
+ * is a 2m x 2m system solved by elimination with partial pivoting; about
+ * log2 N levels.  Blocks of order 8, 16 or 32 and BT_FP64 only
+ * (BT_ERR_INVALID otherwise). */
+bt_status abd_plan_create_tuned(abd_plan* plan, int64_t N, int m, int nrhs_max, int prec, const bt_tuning* tuning,
+                                void* stream);
 /* Reads S, R, B0, B1 (kept by reference like bt_factor; B0 and B1 are also
  * copied into the plan). */
 bt_status abd_factor(abd_plan plan, const double* S, const double* R, const double* B0,

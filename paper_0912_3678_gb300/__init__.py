@@ -22,6 +22,7 @@ __all__ = ["BtPlan", "AbdPlan", "BtError", "BT_STATUS", "PREC", "load_library",
            "BtBatch", "CycPlan", "cyc_plan_create", "cyc_factor", "cyc_solve", "cyc_residual", "cyc_refine",
            "BtTuning", "BtBatchDesc", "bt_refine_async", "bt_refine_result",
            "bt_plan_workspace_size", "bt_plan_anorm", "bt_plan_set_pivot_tol", "ivp_parareal", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay", "bt_factor_solve_host", "bt_plan_capture_host",
+           "abd_plan_create_tuned",
            "bt_band_to_blocks", "band_to_blocks", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
            "abd_plan_create", "abd_factor", "abd_solve", "abd_residual", "abd_refine", "abd_sync",
            "abd_plan_destroy"]
@@ -125,6 +126,15 @@ def abd_plan_create(N, m, nrhs_max=1, prec="fp64", p=0, stream=None):
     h = ctypes.c_void_p()
     _lib.check(_lib.load().abd_plan_create(ctypes.byref(h), int(N), int(m), int(nrhs_max), _prec(prec),
                                            int(p), _stream(stream)), "abd_plan_create")
+    return h
+
+
+def abd_plan_create_tuned(N, m, nrhs_max=1, prec="fp64", tuning=None, stream=None):
+    h = ctypes.c_void_p()
+    t = _tuning(tuning)
+    _lib.check(_lib.load().abd_plan_create_tuned(ctypes.byref(h), int(N), int(m), int(nrhs_max), _prec(prec),
+                                                 ctypes.byref(t) if t is not None else None, _stream(stream)),
+               "abd_plan_create_tuned")
     return h
 
 
@@ -621,6 +631,19 @@ class CycPlan(_PlanBase):
 class AbdPlan(_PlanBase):
     """BABD plan: B0 y_0 + B1 y_N = beta;  S_j y_j + R_j y_{j+1} = r_j."""
     kind = 1
+
+    @classmethod
+    def tuned(cls, N, m, nrhs_max=1, prec="fp64", tuning=None, stream=None):
+        """A plan with explicit parameters; tuning {"reduced": 1}: cyclic reduction
+        of the whole system (abd_plan_create_tuned)."""
+        import torch
+        self = cls.__new__(cls)
+        self.m, self.n, self.nrhs_max, self.prec, self.stream = int(m), int(N), int(nrhs_max), prec, stream
+        self.rows = self.n + 1
+        self.handle = abd_plan_create_tuned(N, m, nrhs_max, prec, tuning, stream)
+        self._keep = ()
+        self._torch = torch
+        return self
 
     def factor(self, S, R, B0, B1):
         self._keep = (S, R, B0, B1)

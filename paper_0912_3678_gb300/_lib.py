@@ -40,6 +40,7 @@ SIGNATURES = {
     "bt_plan_destroy": (None, [_vp]),
     "bt_solve_noalloc": (_i32, [_i64, _i32, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _pi64]),
     "abd_plan_create": (_i32, [_pvp, _i64, _i32, _i32, _i32, _i64, _vp]),
+    "abd_plan_create_tuned": (_i32, [_pvp, _i64, _i32, _i32, _i32, _vp, _vp]),
     "abd_factor": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "abd_solve": (_i32, [_vp, _vp, _vp, _i32]),
     "abd_residual": (_i32, [_vp, _vp, _vp, _vp, _i32]),

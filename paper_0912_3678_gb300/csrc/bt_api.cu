@@ -13,6 +13,7 @@
 #include "bt_misc.h"
 #include "bt_planner.h"
 #include "bt_bcr.cuh"
+#include "bt_crb.cuh"
 
 namespace {
 
@@ -89,6 +90,11 @@ struct bt_plan_s {
     double* Rp = nullptr;
     const double* U[4] = {nullptr, nullptr, nullptr, nullptr};   // caller matrices of a padded plan
     std::vector<bt::BcrArgs> bl;        // its levels
+    // BABD plans solved by cyclic reduction of the whole system (no partitions)
+    bool crb = false;
+    std::vector<bt::CrbArgs> cl;        // its levels (N_q rows each, down to one row)
+    const double* crb_top[4] = {nullptr, nullptr, nullptr, nullptr};   // S, R, F, X of the last row
+    double* crb_topx = nullptr;
     // captured call sequence
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -209,8 +215,35 @@ void layout(bt_plan_s* P, Arena& ar) {
             v.a.F = Fn;
             v.a.X = Xn;
         }
-        if (top && P->kind == 1) P->keep = (double*)ar.take(sizeof(double) * v.a.N * m * (3 * m + nr) + 8);
+        if (top && P->kind == 1)
+            P->keep = (double*)ar.take(sizeof(double) * (P->crb ? 1 : v.a.N) * m * (3 * m + nr) + 8);
         if (top && P->pivot) P->keep = (double*)ar.take(sizeof(double) * v.rows * m * (3 * m + nr) + 8);
+    }
+    if (P->crb) {
+        const long long vb = (long long)m * nr;
+        for (size_t q = 0; q < P->cl.size(); ++q) {
+            bt::CrbArgs& c = P->cl[q];
+            const long long pairs = c.N / 2, nn = c.N - pairs;
+            c.Rinv = (double*)ar.take(sizeof(double) * pairs * mm);
+            c.T = (double*)ar.take(sizeof(double) * pairs * mm);
+            c.Sn = (double*)ar.take(sizeof(double) * nn * mm);
+            c.Rn = (double*)ar.take(sizeof(double) * nn * mm);
+            c.U = (double*)ar.take(sizeof(double) * pairs * vb);
+            c.Fn = (double*)ar.take(sizeof(double) * (nn + 1) * vb);
+            double* xn = (double*)ar.take(sizeof(double) * (nn + 1) * vb);
+            c.Xn = xn;
+            if (q + 1 < P->cl.size()) {
+                P->cl[q + 1].S = c.Sn;
+                P->cl[q + 1].R = c.Rn;
+                P->cl[q + 1].F = c.Fn;
+                P->cl[q + 1].X = xn;
+            } else {
+                P->crb_top[0] = c.Sn;
+                P->crb_top[1] = c.Rn;
+                P->crb_top[2] = c.Fn;
+                P->crb_topx = xn;
+            }
+        }
     }
     if (P->kind == 1) {
         // room for a rotated right-hand side (circulant-like plans)
@@ -298,7 +331,23 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
         tsh.reduced = 0;
         tsh.local = 0;
     }
-    if (!bt::plan_shapes(kind, N, m, sms, tsh, shapes)) {
+    P->crb = (kind == 1 && tune.reduced == 1);
+    if (P->crb) {
+        // cyclic reduction of the whole BABD system: blocks of order 8, 16 or 32, FP64
+        if (mu != m || m < 8 || prec != BT_FP64) {
+            delete P;
+            return BT_ERR_INVALID;
+        }
+        shapes.assign(1, bt::LevelShape{N, 0, 0, 0, N + 1});
+        long long n = N;
+        while (n > 1) {
+            bt::CrbArgs c{};
+            c.N = n;
+            c.level = (int)P->cl.size();
+            P->cl.push_back(c);
+            n -= n / 2;
+        }
+    } else if (!bt::plan_shapes(kind, N, m, sms, tsh, shapes)) {
         delete P;
         return BT_ERR_INVALID;
     }
@@ -392,6 +441,7 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
     layout(P, real);
     for (auto& v : P->lv) v.a.status = P->status;
     for (auto& b : P->bl) b.status = P->status;
+    for (auto& c : P->cl) c.status = P->status;
     if (P->pinned) {
         e = cudaMallocHost((void**)&P->status_host, 4 * sizeof(long long));
         if (e == cudaSuccess) e = cudaMallocHost((void**)&P->norms_host, kHostNorms * sizeof(double));
@@ -526,6 +576,18 @@ bt_status run_factor_pivoted(bt_plan_s* P) {
 
 bt_status run_factor(bt_plan_s* P, bool level0_done = false) {
     if (P->pivot) return run_factor_pivoted(P);
+    if (P->crb) {
+        // cyclic reduction of the whole BABD system, level by level
+        if (!P->cl.empty()) {
+            P->cl[0].S = P->A0;
+            P->cl[0].R = P->A1;
+        }
+        for (auto& c : P->cl) {
+            cudaError_t e = launch(P, K_FACTOR, c.level, 1, [&] { return P->L->crb_factor(c, P->stream); });
+            if (e != cudaSuccess) return from_cuda(e);
+        }
+        return BT_OK;
+    }
     const bt::Launchers* L = P->L;
     const bool split = P->overlap && P->side && P->nlev >= 1;
     cudaStream_t main_stream = P->stream;
@@ -594,6 +656,33 @@ cudaError_t join_factor(bt_plan_s* P) {
 // Solve with the factors: F (level-0 rhs) -> X.
 bt_status run_solve(bt_plan_s* P, const double* F, double* X, int nr) {
     const bt::Launchers* L = P->L;
+    if (P->crb) {
+        cudaError_t e = cudaSuccess;
+        if (!P->cl.empty()) {
+            P->cl[0].F = F;
+            P->cl[0].X = X;
+        }
+        for (auto& c : P->cl) {
+            c.nr = nr;
+            if (e == cudaSuccess) e = launch(P, K_SOLVE_FWD, c.level, 1, [&] { return L->crb_rhs(c, P->stream); });
+        }
+        // one row left: with the boundary row, a 2m x 2m system
+        const double* tS = P->cl.empty() ? P->A0 : P->crb_top[0];
+        const double* tR = P->cl.empty() ? P->A1 : P->crb_top[1];
+        const double* tF = P->cl.empty() ? F : P->crb_top[2];
+        double* tX = P->cl.empty() ? X : P->crb_topx;
+        const int lt = (int)P->cl.size();
+        if (e == cudaSuccess)
+            e = launch(P, K_DIRECT, lt, 1, [&] {
+                return bt::launch_babd_direct(1, P->m, nr, tS, tR, P->B0, P->B1, tF, tX, P->keep, P->status, lt,
+                                              P->stream);
+            });
+        for (int q = (int)P->cl.size() - 1; q >= 0 && e == cudaSuccess; --q) {
+            bt::CrbArgs& c = P->cl[q];
+            e = launch(P, K_SOLVE_BWD, c.level, 1, [&] { return L->crb_back(c, P->stream); });
+        }
+        return from_cuda(e);
+    }
     P->lv[0].a.F = F;
     P->lv[0].a.X = X;
     for (auto& v : P->lv) v.a.nr = nr;
@@ -824,6 +913,15 @@ bt_status bt_plan_create_tuned(bt_plan* plan, int64_t nblk, int m, int nrhs_max,
                      tuning->tp_block == 256)))
         return BT_ERR_INVALID;
     return plan_create(plan, 0, nblk, m, nrhs_max, prec, to_tuning(tuning, 0), stream);
+}
+
+bt_status abd_plan_create_tuned(abd_plan* plan, int64_t N, int m, int nrhs_max, int prec, const bt_tuning* tuning,
+                                void* stream) {
+    if (tuning && (tuning->p0 < 0 || tuning->ctas_per_sm < 0 || tuning->sub_rows < 0 || tuning->top_rows < 0 ||
+                   tuning->reduced < 0 || tuning->reduced > 1 || tuning->local != 0 || tuning->pivot != 0 ||
+                   tuning->serial < 0 || tuning->serial > 1))
+        return BT_ERR_INVALID;
+    return plan_create(plan, 1, N, m, nrhs_max, prec, to_tuning(tuning, 0), stream);
 }
 
 bt_status abd_plan_create(abd_plan* plan, int64_t N, int m, int nrhs_max, int prec, int64_t p, void* stream) {

@@ -1,6 +1,7 @@
 // Instantiates the launchers of one block order M (included by bt_inst_m*.cu).
 #pragma once
 #include "bt_bcr.cuh"
+#include "bt_crb.cuh"
 #include "bt_cta.cuh"
 #include "bt_gp.cuh"
 #include "bt_launch.h"
@@ -302,6 +303,37 @@ struct Inst {
         }
         return cudaErrorNotSupported;
     }
+    // ------------------------------------------------ BABD cyclic reduction --
+    static cudaError_t crb_factor(const CrbArgs& a, cudaStream_t s) {
+        if constexpr (M >= 8) {
+            constexpr size_t smem = crb_factor_smem_bytes<M>();
+            cudaError_t e = set_smem(k_crb_factor<M>, smem);
+            if (e != cudaSuccess) return e;
+            k_crb_factor<M><<<(unsigned)(a.N - a.N / 2), 8 * M, smem, s>>>(a);
+            return cudaGetLastError();
+        }
+        return cudaErrorNotSupported;
+    }
+    static cudaError_t crb_rhs(const CrbArgs& a, cudaStream_t s) {
+        if constexpr (M >= 8) {
+            constexpr size_t smem = crb_vec_smem_bytes<M>();
+            cudaError_t e = set_smem(k_crb_rhs<M>, smem);
+            if (e != cudaSuccess) return e;
+            k_crb_rhs<M><<<(unsigned)(a.N - a.N / 2), 8 * M, smem, s>>>(a);
+            return cudaGetLastError();
+        }
+        return cudaErrorNotSupported;
+    }
+    static cudaError_t crb_back(const CrbArgs& a, cudaStream_t s) {
+        if constexpr (M >= 8) {
+            constexpr size_t smem = crb_vec_smem_bytes<M>();
+            cudaError_t e = set_smem(k_crb_back<M>, smem);
+            if (e != cudaSuccess) return e;
+            k_crb_back<M><<<(unsigned)(a.N / 2 + 1), 8 * M, smem, s>>>(a);
+            return cudaGetLastError();
+        }
+        return cudaErrorNotSupported;
+    }
     static const Launchers* table() {
         static const Launchers L = {factor, factor_part, M >= 8 ? factor_phase : nullptr, assemble, solve_fwd,
                                     assemble_rhs, solve_bwd,
@@ -316,7 +348,10 @@ struct Inst {
                                     prepare,
                                     M >= 8 ? bcr_factor : nullptr,
                                     M >= 8 ? bcr_rhs : nullptr,
-                                    M >= 8 ? bcr_back : nullptr};
+                                    M >= 8 ? bcr_back : nullptr,
+                                    M >= 8 ? crb_factor : nullptr,
+                                    M >= 8 ? crb_rhs : nullptr,
+                                    M >= 8 ? crb_back : nullptr};
         return &L;
     }
 };

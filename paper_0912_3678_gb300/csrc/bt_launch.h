@@ -5,6 +5,7 @@
 
 namespace bt {
 struct BcrArgs;
+struct CrbArgs;
 }
 
 namespace bt {
@@ -42,6 +43,11 @@ struct Launchers {
     cudaError_t (*bcr_factor)(const BcrArgs&, long long ctas, cudaStream_t);   // one reduction step
     cudaError_t (*bcr_rhs)(const BcrArgs&, long long ctas, cudaStream_t);
     cudaError_t (*bcr_back)(const BcrArgs&, long long ctas, cudaStream_t);
+    // cyclic reduction of a whole BABD system: one level's factor, right-hand side and back
+    // substitution (m >= 8; null otherwise)
+    cudaError_t (*crb_factor)(const CrbArgs&, cudaStream_t);
+    cudaError_t (*crb_rhs)(const CrbArgs&, cudaStream_t);
+    cudaError_t (*crb_back)(const CrbArgs&, cudaStream_t);
 };
 
 const Launchers* launchers_m1();

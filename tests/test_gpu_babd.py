@@ -159,3 +159,53 @@ def test_babd_thread_and_lane_group_kernels(cuda, m, p):
     Y, lev = _solve(cuda, b, p=p)
     ref = oracle.babd_solve(b.S, b.R, b.B0, b.B1, b.RHS)
     assert oracle.rel_err(Y, ref) <= 1e-11, lev
+
+
+@pytest.mark.parametrize("m", [8, 16, 32])
+@pytest.mark.parametrize("N,nrhs,sep", [(1, 1, False), (2, 2, True), (3, 1, False), (7, 3, True), (100, 2, False),
+                                        (777, 1, True), (4099, 3, False)])
+def test_babd_cyclic_reduction_matches_oracle(cuda, m, N, nrhs, sep):
+    """Cyclic reduction of the whole BABD system (abd tuning reduced = 1): odd
+    and even level sizes, separated and general boundary conditions."""
+    import paper_0912_3678_gb300 as bt
+    b = gen.babd_bvp(N, m, nrhs, separated=sep, seed_rep=3 * N + m)
+    with bt.AbdPlan.tuned(N, m, nrhs, "fp64", {"reduced": 1}) as plan:
+        plan.factor(*(to_dev(a, cuda) for a in (b.S, b.R, b.B0, b.B1)))
+        Y = to_host(plan.solve(to_dev(b.RHS, cuda)))
+        plan.sync()
+    ref = oracle.babd_solve(b.S, b.R, b.B0, b.B1, b.RHS)
+    assert oracle.rel_err(Y, ref) <= 1e-11
+
+
+def test_babd_cyclic_reduction_trapezoidal_bvp_order(cuda):
+    """On the manufactured trapezoidal BVP the cyclic-reduction solution meets
+    the exact y(t) to second order, like the partition solution."""
+    import paper_0912_3678_gb300 as bt
+    errs = []
+    for N in (256, 512, 1024):
+        b = gen.babd_bvp(N, 8, 1, seed_rep=0)
+        with bt.AbdPlan.tuned(N, 8, 1, "fp64", {"reduced": 1}) as plan:
+            plan.factor(*(to_dev(a, cuda) for a in (b.S, b.R, b.B0, b.B1)))
+            Y = to_host(plan.solve(to_dev(b.RHS, cuda)))
+        errs.append(np.abs(Y - b.Yexact).max())
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def test_babd_cyclic_reduction_reports_a_singular_block(cuda):
+    """A zero R_{2k} (host-made fault in the input) is a singular pivot block at
+    row 2k of the first level."""
+    import paper_0912_3678_gb300 as bt
+    b = gen.babd_random(64, 8, 1, seed_rep=2)
+    b.R[10] = 0.0
+    with bt.AbdPlan.tuned(64, 8, 1, "fp64", {"reduced": 1}) as plan:
+        plan.factor(*(to_dev(a, cuda) for a in (b.S, b.R, b.B0, b.B1)))
+        code, lev, part, row = plan.info()
+    assert bt.BT_STATUS[code] == "BT_ERR_SINGULAR"
+    assert (lev, row) == (0, 10)
+
+
+def test_babd_cyclic_reduction_refuses_unsupported_plans(cuda):
+    import paper_0912_3678_gb300 as bt
+    for m, prec in ((4, "fp64"), (8, "fp32_ir"), (12, "fp64")):
+        with pytest.raises(bt.BtError):
+            bt.AbdPlan.tuned(100, m, 1, prec, {"reduced": 1})
