@@ -93,7 +93,9 @@ bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int p
  *   reduced      solver of the top-level reduced system of a block tridiagonal
  *                plan with m >= 8: 0 = partitioned again recursively (default),
  *                1 = block cyclic reduction (the cyclic-reduction variant of
- *                Sec. 2 with one synchronisation per reduction step)
+ *                Sec. 2 with one synchronisation per reduction step).  BABD
+ *                plans (abd_plan_create_tuned): 1 = cyclic reduction of the
+ *                whole system instead of partitions
  *   tp_block     CTA shape of the thread-per-partition kernels used for m <= 4:
  *                threads per CTA, 64, 128 or 256 (0: 128)
  *   local        local factorization of a block tridiagonal plan with m >= 8:
