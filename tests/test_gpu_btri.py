@@ -461,7 +461,9 @@ def test_captured_step_same_with_one_or_two_streams(cuda, m, N, tuning):
 
 
 @pytest.mark.parametrize("m,N,tuning", [(1, 60000, {"p0": 2048}), (4, 20000, {}), (8, 3000, {}),
-                                        (16, 2000, {"reduced": 1}), (16, 999, {"reduced": 0}), (2, 40, {"p0": 3})])
+                                        (16, 2000, {"reduced": 1}), (16, 999, {"reduced": 0}), (2, 40, {"p0": 3}),
+                                        (16, 1216, {"p0": 608, "reduced": 1}), (8, 1199, {"p0": 600}),
+                                        (32, 9, {"p0": 2})])
 @pytest.mark.parametrize("pinned", [True, False])
 def test_factor_solve_host_matches_oracle(cuda, m, N, tuning, pinned):
     """bt_factor_solve_host: host arrays in and out, block rows copied in chunks
