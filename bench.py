@@ -10,11 +10,18 @@ the faster path whose normwise relative error against the FP64 oracle is
 <= 1e-10.  Metric: unknowns x right-hand sides solved per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload block16|babd8|scalar]
+                  [--workload block16|block|babd8|scalar|scalar_batch|batch|serve|pivot|parareal|cyclic]
+                  [--tuning key=value,...]
 
---impl reference times the FP64 CPU oracle on the same workload (the
-baseline of this project).  With N > 1 (torchrun), every rank solves its own
-replica (replicas only, weak scaling); timings are max over ranks.
+The device figure (`value`) times one captured CUDA graph per step with the
+inputs already in device memory and L2 flushed between steps; `e2e` times the
+same step from pinned host arrays through the library's host-array entry
+point (bt_plan_capture_host + replay: block rows copied in slabs while the
+level-0 factorization runs, X copied back) for block tridiagonal workloads,
+otherwise host copies around the captured step.  --impl reference times the
+FP64 CPU oracle on the same workload (the baseline of this project).  With
+N > 1 (torchrun), every rank solves its own replica (replicas only, weak
+scaling); timings are max over ranks.
 """
 from __future__ import annotations
 
