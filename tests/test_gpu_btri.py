@@ -540,3 +540,24 @@ def test_captured_host_call_reads_new_host_data(cuda, m, N, tuning):
             plan.replay()
             plan.sync()
             assert oracle.rel_err(X.numpy(), oracle.btri_solve(s.B, s.D, s.C, s.F)) <= TOL64
+
+
+def test_host_path_block_m16_n16384_full_size(cuda):
+    """The end-to-end path the bench times, at the full block workload size
+    (m = 16, N = 16384, 8 RHS, the autotuner's plan shape): the captured
+    host-array call, replayed; every entry against the oracle."""
+    import torch
+
+    import paper_0912_3678_gb300 as bt
+    N, m, nr = 16384, 16, 8
+    s = gen.btri_random(N, m, nr, seed_rep=0)
+    ref = oracle.btri_solve(s.B, s.D, s.C, s.F)
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (s.B, s.D, s.C, s.F)]
+    X = torch.empty(host[3].shape, dtype=torch.float64).pin_memory()
+    with bt.BtPlan.tuned(N, m, nr, "fp64", {"p0": 608, "reduced": 1, "serial": 1}) as plan:
+        plan.capture_host(*host, X)
+        for _ in range(2):
+            X.zero_()
+            plan.replay()
+            plan.sync()
+            assert oracle.rel_err(X.numpy(), ref) <= TOL64
