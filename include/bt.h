@@ -172,6 +172,15 @@ bt_status bt_solve(bt_plan plan, const double* F, double* X, int nrhs);
 bt_status bt_band_to_blocks(int64_t n, int s, int r, const double* band, int m, double* B, double* D, double* C,
                             void* stream);
 
+/* y[i] = 1/x[i] for n FP64 values (device arrays, asynchronous on `stream`)
+ * with the reciprocal that every FP64 pivot step of the factorizations uses
+ * instead of a division: the hardware seed rcp.approx.ftz.f64 refined by one
+ * third-order Newton step, r = r0 (1 + e + e^2) with e = 1 - x r0 (within one
+ * unit in the last place of 1/x); zero, subnormal, huge (|x| >= 2^1022) and
+ * non-finite x take the IEEE division.  Exposed so that its accuracy can be
+ * checked against IEEE 1/x.  BT_ERR_INVALID on n < 0 or null arrays. */
+bt_status bt_device_rcp(int64_t n, const double* x, double* y, void* stream);
+
 /* R = F - A X in FP64 with the matrices given to the last bt_factor. */
 bt_status bt_residual(bt_plan plan, const double* F, const double* X, double* R, int nrhs);
 
@@ -332,8 +341,9 @@ void bt_plan_destroy(bt_plan plan);
  * The first call on a device looks up the array's device address (with
  * cudaGetSymbolAddress); make that first call before any stream capture.
  * All calls share the array: calls whose GPU work overlaps race, so callers
- * must serialise them.  The call synchronises `stream` before returning and
- * returns the numerical status (BT_ERR_SINGULAR / BT_ERR_NONFINITE). */
+ * must serialise them.  Every call ends by copying the device status word to
+ * host memory and synchronising `stream`, then returns the numerical status
+ * (BT_ERR_SINGULAR / BT_ERR_NONFINITE). */
 #define BT_NOALLOC_SCRATCH_BYTES (8u << 20)
 bt_status bt_solve_noalloc(int64_t nblk, int m, const double* B, const double* D, const double* C,
                            const double* F, double* X, int nrhs, void* stream, int64_t* required_bytes);

@@ -23,7 +23,7 @@ __all__ = ["BtPlan", "AbdPlan", "BtError", "BT_STATUS", "PREC", "load_library",
            "BtTuning", "BtBatchDesc", "bt_refine_async", "bt_refine_result",
            "bt_plan_workspace_size", "bt_plan_anorm", "bt_plan_set_pivot_tol", "ivp_parareal", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay", "bt_factor_solve_host", "bt_plan_capture_host",
            "abd_plan_create_tuned",
-           "bt_band_to_blocks", "band_to_blocks", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
+           "bt_band_to_blocks", "band_to_blocks", "bt_device_rcp", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
            "abd_plan_create", "abd_factor", "abd_solve", "abd_residual", "abd_refine", "abd_sync",
            "abd_plan_destroy"]
 
@@ -271,6 +271,15 @@ CAPTURE = {"factor_solve": 1, "solve": 2, "factor_refine": 3}
 def bt_plan_capture(plan, what, F, X, nrhs, sweeps=0):
     w = CAPTURE[what] if isinstance(what, str) else int(what)
     _lib.check(_lib.load().bt_plan_capture(plan, w, _ptr(F), _ptr(X), int(nrhs), int(sweeps)), "bt_plan_capture")
+
+
+def bt_device_rcp(x, y=None, stream=None):
+    """y = 1/x elementwise with the device FP64 reciprocal of the pivot steps."""
+    import torch
+    if y is None:
+        y = torch.empty_like(x)
+    _lib.check(_lib.load().bt_device_rcp(int(x.numel()), _ptr(x), _ptr(y), _stream(stream)), "bt_device_rcp")
+    return y
 
 
 def bt_band_to_blocks(n, s, r, band, m, B, D, C, stream=None):

@@ -75,6 +75,7 @@ SIGNATURES.update({
     "bt_factor_solve_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32]),
     "bt_plan_capture_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32]),
     "bt_band_to_blocks": (_i32, [_i64, _i32, _i32, _vp, _i32, _vp, _vp, _vp, _vp]),
+    "bt_device_rcp": (_i32, [_i64, _vp, _vp, _vp]),
     "bt_refine_result": (_i32, [_vp, _f64, _pf64]),
     "bt_plan_set_backward_tol": (_i32, [_vp, _f64]),
     "bt_plan_anorm": (_i32, [_vp, _vp]),

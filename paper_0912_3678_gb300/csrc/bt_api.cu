@@ -14,6 +14,7 @@
 #include "bt_planner.h"
 #include "bt_bcr.cuh"
 #include "bt_crb.cuh"
+#include "bt_rsolve.h"
 
 namespace {
 
@@ -90,6 +91,14 @@ struct bt_plan_s {
     double* Rp = nullptr;
     const double* U[4] = {nullptr, nullptr, nullptr, nullptr};   // caller matrices of a padded plan
     std::vector<bt::BcrArgs> bl;        // its levels
+    // refined plans: the reduced system's cyclic-reduction factors are also kept
+    // in FP32 and the correction solves apply them in one cluster launch
+    bool rs32 = false;
+    // refined plans of order 16: level-0 factors and solves on the warp-per-partition
+    // kernels (when the matrices start on 16-byte boundaries; bt_warp.cuh)
+    bool warp = false;
+    bt::RsolveArgs rsa{};
+    bt::CvtArgs cva{};
     // BABD plans solved by cyclic reduction of the whole system (no partitions)
     bool crb = false;
     std::vector<bt::CrbArgs> cl;        // its levels (N_q rows each, down to one row)
@@ -173,6 +182,14 @@ void layout(bt_plan_s* P, Arena& ar) {
         P->Fp = (double*)ar.take(sizeof(double) * rows0 * m * nr);
         P->Xp = (double*)ar.take(sizeof(double) * rows0 * m * nr);
         P->Rp = (double*)ar.take(sizeof(double) * rows0 * m * nr);
+    }
+    if (P->warp) {
+        // warp-per-partition FP32 kernels at level 0: W chain, h_j and sum_j W_j h_j
+        Level& v0 = P->lv[0];
+        const long long pa = std::max(v0.a.p, v0.pcap);
+        v0.a.W = ar.take(sizeof(float) * rows0 * mm);
+        v0.a.Hv = ar.take(sizeof(float) * rows0 * m * nr);
+        v0.a.Hw = ar.take(sizeof(float) * pa * m * nr);
     }
     for (int l = 0; l <= P->nlev; ++l) {
         Level& v = P->lv[l];
@@ -291,6 +308,38 @@ void layout(bt_plan_s* P, Arena& ar) {
             K = keep;
         }
     }
+    if (P->rs32) {
+        bt::RsolveArgs& r = P->rsa;
+        bt::CvtArgs& c = P->cva;
+        r.nlev = (int)P->bl.size();
+        r.m = m;
+        r.nr = nr;
+        c.nseg = 0;
+        auto seg = [&](const void* src, long long n) {
+            float* d = (float*)ar.take(sizeof(float) * n);
+            if (c.nseg < bt::kCvtSegs) {
+                c.src[c.nseg] = (const double*)src;
+                c.dst[c.nseg] = d;
+                c.n[c.nseg] = n;
+                ++c.nseg;
+            }
+            return (const float*)d;
+        };
+        for (size_t q = 0; q < P->bl.size(); ++q) {
+            const bt::BcrArgs& b = P->bl[q];
+            const long long K = b.K, kept = (K + 1) / 2, odd = (K == 1) ? 1 : K / 2;
+            r.K[q] = K;
+            r.al[q] = (K > 1) ? seg(b.al, kept * mm) : nullptr;
+            r.ga[q] = (K > 1) ? seg(b.ga, kept * mm) : nullptr;
+            r.Dinv[q] = seg(b.Dinv, odd * mm);
+            r.B[q] = (K > 1) ? seg(b.B, K * mm) : nullptr;
+            r.C[q] = (K > 1) ? seg(b.C, K * mm) : nullptr;
+            r.f[q] = (float*)ar.take(sizeof(float) * K * m * nr);
+            r.x[q] = (float*)ar.take(sizeof(float) * K * m * nr);
+        }
+        r.F0 = P->bl[0].F;
+        r.X0 = P->bl[0].X;
+    }
 }
 
 bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, int prec, const bt::Tuning& tune,
@@ -384,6 +433,7 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
         P->lv.push_back(v);
     }
     P->nlev = (int)P->lv.size() - 1;
+    P->warp = (kind == 0) && (m == 16) && (prec == BT_FP32_IR) && !P->pivot && tune.local == 0 && P->lv[0].low;
     P->bcr = !P->pivot && (kind == 0 && P->lv[P->nlev].a.p == 0 && (P->nlev >= 1 || tune.local > 0));
     if (P->bcr) {
         long long K = P->lv[P->nlev].a.N;
@@ -406,6 +456,8 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
             }
             P->bl[q].mode = mode;
         }
+        P->rs32 = (prec != BT_FP64) && P->local == 0 && P->nlev >= 1 && m >= 8 &&
+                  (int)P->bl.size() <= bt::kRsMaxLevels && 5 * (int)P->bl.size() <= bt::kCvtSegs;
     }
     if (kind == 0) {
         // the top level is a single partition; levels below it have >= 2
@@ -625,6 +677,10 @@ bt_status run_factor(bt_plan_s* P, bool level0_done = false) {
                     launch(P, K_BCR_FACTOR, b.level, 1, [&] { return L->bcr_factor(b, ctas, P->stream); });
                 if (e != cudaSuccess) return rejoin(from_cuda(e));
             }
+            if (P->rs32) {
+                cudaError_t e = launch(P, K_BCR_FACTOR, P->nlev, 1, [&] { return bt::launch_cvt_f32(P->cva, P->stream); });
+                if (e != cudaSuccess) return rejoin(from_cuda(e));
+            }
             break;
         }
         cudaError_t e = cudaSuccess;
@@ -686,11 +742,17 @@ bt_status run_solve(bt_plan_s* P, const double* F, double* X, int nr) {
     P->lv[0].a.F = F;
     P->lv[0].a.X = X;
     for (auto& v : P->lv) v.a.nr = nr;
+    const bool w0 = P->warp && L->warp_ok && L->warp_ok(P->lv[0].a, P->lv[0].low);
     for (int l = 0; l < P->nlev; ++l) {
         Level& v = P->lv[l];
-        cudaError_t e = launch(P, K_SOLVE_FWD, l, 1, [&] { return L->solve_fwd(v.a, v.low, P->stream); });
+        const bool w = (l == 0) && w0;
+        cudaError_t e = launch(P, K_SOLVE_FWD, l, 1, [&] {
+            return w ? L->solve_fwd_w(v.a, P->stream) : L->solve_fwd(v.a, v.low, P->stream);
+        });
         if (e == cudaSuccess && P->kind == 0)
-            e = launch(P, K_ASSEMBLE_RHS, l, 1, [&] { return L->assemble_rhs(v.a, v.low, P->stream); });
+            e = launch(P, K_ASSEMBLE_RHS, l, 1, [&] {
+                return w ? L->sep_rhs_w(v.a, P->stream) : L->assemble_rhs(v.a, v.low, P->stream);
+            });
         if (e == cudaSuccess && l == 0) e = join_factor(P);
         if (e != cudaSuccess) return from_cuda(e);
     }
@@ -698,7 +760,10 @@ bt_status run_solve(bt_plan_s* P, const double* F, double* X, int nr) {
     const int lt = P->nlev;
     cudaError_t e = join_factor(P);
     if (e != cudaSuccess) return from_cuda(e);
-    if (P->bcr) {
+    if (P->bcr && P->rs32) {
+        P->rsa.nr = nr;
+        e = launch(P, K_BCR_SOLVE, P->nlev, 1, [&] { return bt::launch_rsolve_f32(P->rsa, P->stream); });
+    } else if (P->bcr) {
         e = cudaSuccess;
         if (P->nlev == 0) {
             P->bl[0].F = F;
@@ -733,14 +798,19 @@ bt_status run_solve(bt_plan_s* P, const double* F, double* X, int nr) {
     if (e != cudaSuccess) return from_cuda(e);
     for (int l = P->nlev - 1; l >= 0; --l) {
         Level& v = P->lv[l];
-        e = launch(P, K_SOLVE_BWD, l, 1, [&] { return L->solve_bwd(v.a, v.low, P->stream); });
+        const bool w = (l == 0) && w0;
+        e = launch(P, K_SOLVE_BWD, l, 1, [&] {
+            return w ? L->solve_bwd_w(v.a, P->stream) : L->solve_bwd(v.a, v.low, P->stream);
+        });
         if (e != cudaSuccess) return from_cuda(e);
     }
     return BT_OK;
 }
 
+// df: the refinement residual of a refined plan, in double-float arithmetic on
+// the FP32 pipe (bt_resid_df.cu); otherwise plain FP64.
 bt_status run_residual(bt_plan_s* P, const double* F, const double* X, double* R, int nr,
-                       unsigned long long* maxout = nullptr) {
+                       unsigned long long* maxout = nullptr, bool df = false) {
     if (P->join_pending) {
         cudaError_t e = join_factor(P);
         if (e != cudaSuccess) return from_cuda(e);
@@ -751,8 +821,10 @@ bt_status run_residual(bt_plan_s* P, const double* F, const double* X, double* R
     }
     cudaError_t e = launch(P, K_RESID, 0, 1, [&] {
         if (P->kind == 0)
-            return bt::launch_resid_btri(P->N, P->m, nr, P->A0, P->A1, P->A2, X, F, R, P->stream, maxout);
-        return bt::launch_resid_babd(P->N, P->m, nr, P->A0, P->A1, P->B0, P->B1, X, F, R, P->stream, maxout);
+            return df ? bt::launch_resid_btri_df(P->N, P->m, nr, P->A0, P->A1, P->A2, X, F, R, P->stream, maxout)
+                      : bt::launch_resid_btri(P->N, P->m, nr, P->A0, P->A1, P->A2, X, F, R, P->stream, maxout);
+        return df ? bt::launch_resid_babd_df(P->N, P->m, nr, P->A0, P->A1, P->B0, P->B1, X, F, R, P->stream, maxout)
+                  : bt::launch_resid_babd(P->N, P->m, nr, P->A0, P->A1, P->B0, P->B1, X, F, R, P->stream, maxout);
     });
     return from_cuda(e);
 }
@@ -819,7 +891,7 @@ bt_status run_refine(bt_plan_s* P, const double* F, double* X, int nr, double to
     cudaError_t e = cudaMemsetAsync(P->norms, 0, 2 * sizeof(double), P->stream);
     if (e != cudaSuccess) return from_cuda(e);
     for (int it = 0;; ++it) {
-        st = run_residual(P, F, X, P->Rbuf, nr, P->rmax);
+        st = run_residual(P, F, X, P->Rbuf, nr, P->rmax, P->prec != BT_FP64);
         if (st != BT_OK) return st;
         e = fetch_norms(P);
         if (e != cudaSuccess) return from_cuda(e);
@@ -848,7 +920,7 @@ bt_status run_refine_async(bt_plan_s* P, const double* F, double* X, int nr, int
     if (st == BT_OK) st = run_solve(P, F, X, nr);
     const long long n = P->lv[0].rows * P->m * nr;
     for (int it = 0; it < sweeps && st == BT_OK; ++it) {
-        st = run_residual(P, F, X, P->Rbuf, nr);
+        st = run_residual(P, F, X, P->Rbuf, nr, nullptr, P->prec != BT_FP64);
         if (st == BT_OK) st = run_solve(P, P->Rbuf, P->Dbuf, nr);
         if (st != BT_OK) return st;
         cudaError_t e = launch(P, K_IR, 0, 2,
@@ -860,7 +932,7 @@ bt_status run_refine_async(bt_plan_s* P, const double* F, double* X, int nr, int
         if (e != cudaSuccess) return from_cuda(e);
     }
     // final residual of the result: its backward error decides convergence
-    if (st == BT_OK) st = run_residual(P, F, X, P->Rbuf, nr, P->rmax);
+    if (st == BT_OK) st = run_residual(P, F, X, P->Rbuf, nr, P->rmax, P->prec != BT_FP64);
     P->async_sweeps = sweeps;
     return st;
 }

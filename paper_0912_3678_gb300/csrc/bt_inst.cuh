@@ -6,6 +6,7 @@
 #include "bt_gp.cuh"
 #include "bt_launch.h"
 #include "bt_tp.cuh"
+#include "bt_warp.cuh"
 
 namespace bt {
 
@@ -26,9 +27,23 @@ static inline long long chunks(const LevelArgs& a, int m) { return (a.nr + m - 1
 
 template <int M>
 struct Inst {
+    // FP32 block tridiagonal levels of order 16: one warp per partition (bt_warp.cuh)
+    template <typename T, int MODE>
+    static bool warp_factor(const LevelArgs& a) {
+        if constexpr (M == 16 && MODE == 0 && std::is_same<T, float>::value) return use_factor_w16(a);
+        return false;
+    }
+    static cudaError_t launch_w16(const LevelArgs& a, long long units, cudaStream_t s) {
+        const size_t smem = factor_w16_smem_bytes();
+        cudaError_t e = set_smem(k_factor_w16<0>, smem);
+        if (e != cudaSuccess) return e;
+        k_factor_w16<0><<<grid_for(units, WarpF16::WARPS), 32 * WarpF16::WARPS, smem, s>>>(a);
+        return cudaGetLastError();
+    }
     template <typename T, int MODE>
     static cudaError_t factor_t(const LevelArgs& a, cudaStream_t s) {
         if (a.p <= 0) return cudaSuccess;
+        if (warp_factor<T, MODE>(a)) return launch_w16(a, a.p, s);
         if constexpr (M >= 8) {
             const size_t smem = factor_smem_bytes<T, M>();
             cudaError_t e = set_smem(k_factor_cta<T, M, MODE>, smem);
@@ -50,6 +65,11 @@ struct Inst {
         if (pe > a0.p) pe = a0.p;
         if (pb < 0 || pe <= pb) return cudaSuccess;
         LevelArgs a = a0;
+        if (warp_factor<T, MODE>(a)) {
+            a.unit0 = pb;
+            a.unit_end = pe;
+            return launch_w16(a, pe - pb, s);
+        }
         if constexpr (M >= 8) {
             const size_t smem = factor_smem_bytes<T, M>();
             cudaError_t e = set_smem(k_factor_cta<T, M, MODE>, smem);
@@ -245,6 +265,42 @@ struct Inst {
         return low ? solve_bwd_bt<float, 1>(args, work, nwork, grid, s)
                    : solve_bwd_bt<double, 1>(args, work, nwork, grid, s);
     }
+    static bool warp_ok(const LevelArgs& a, bool low) {
+        if constexpr (M == 16) return low && use_factor_w16(a);
+        return false;
+    }
+    template <int NH>
+    static cudaError_t launch_sw(void (*k)(const LevelArgs), const LevelArgs& a, cudaStream_t s) {
+        const size_t smem = sizeof(typename WarpS16<NH>::Smem) * WarpS16<NH>::WARPS;
+        cudaError_t e = set_smem(k, smem);
+        if (e != cudaSuccess) return e;
+        k<<<grid_for(a.p, WarpS16<NH>::WARPS), 32 * WarpS16<NH>::WARPS, smem, s>>>(a);
+        return cudaGetLastError();
+    }
+    static cudaError_t solve_fwd_w(const LevelArgs& a, cudaStream_t s) {
+        if (a.p <= 0) return cudaSuccess;
+        if constexpr (M == 16) {
+            if (a.nr <= 8) return launch_sw<4>(k_solve_fwd_w16<4>, a, s);
+            return launch_sw<16>(k_solve_fwd_w16<16>, a, s);
+        }
+        return cudaErrorInvalidValue;
+    }
+    static cudaError_t solve_bwd_w(const LevelArgs& a, cudaStream_t s) {
+        if (a.p <= 0) return cudaSuccess;
+        if constexpr (M == 16) {
+            if (a.nr <= 8) return launch_sw<4>(k_solve_bwd_w16<4>, a, s);
+            return launch_sw<16>(k_solve_bwd_w16<16>, a, s);
+        }
+        return cudaErrorInvalidValue;
+    }
+    static cudaError_t sep_rhs_w(const LevelArgs& a, cudaStream_t s) {
+        if (a.p <= 1) return cudaSuccess;
+        const long long n = (a.p - 1) * 16LL * a.nr;
+        long long blocks = (n + 255) / 256;
+        if (blocks > 4096) blocks = 4096;
+        k_sep_rhs_w16<0><<<(unsigned)blocks, 256, 0, s>>>(a);
+        return cudaGetLastError();
+    }
     static cudaError_t prepare() {
         if constexpr (M >= 8) {
             const size_t f64 = factor_smem_bytes<double, M>(), f32 = factor_smem_bytes<float, M>();
@@ -259,6 +315,13 @@ struct Inst {
             if (e == cudaSuccess) e = set_smem(k_bcr_factor<double, double, double, M>, bcr_factor_smem_bytes<double, M>());
             if (e == cudaSuccess) e = set_smem(k_bcr_rhs<double, M>, bcr_vec_smem_bytes<double, M>());
             if (e == cudaSuccess) e = set_smem(k_bcr_back<double, double, M>, bcr_vec_smem_bytes<double, M>());
+            if constexpr (M == 16) {
+                if (e == cudaSuccess) e = set_smem(k_factor_w16<0>, factor_w16_smem_bytes());
+                if (e == cudaSuccess)
+                    e = set_smem(k_solve_fwd_w16<16>, sizeof(WarpS16<16>::Smem) * WarpS16<16>::WARPS);
+                if (e == cudaSuccess)
+                    e = set_smem(k_solve_bwd_w16<16>, sizeof(WarpS16<16>::Smem) * WarpS16<16>::WARPS);
+            }
             return e;
         }
         return cudaSuccess;
@@ -351,7 +414,11 @@ struct Inst {
                                     M >= 8 ? bcr_back : nullptr,
                                     M >= 8 ? crb_factor : nullptr,
                                     M >= 8 ? crb_rhs : nullptr,
-                                    M >= 8 ? crb_back : nullptr};
+                                    M >= 8 ? crb_back : nullptr,
+                                    warp_ok,
+                                    M == 16 ? solve_fwd_w : nullptr,
+                                    M == 16 ? sep_rhs_w : nullptr,
+                                    M == 16 ? solve_bwd_w : nullptr};
         return &L;
     }
 };

@@ -48,6 +48,13 @@ struct Launchers {
     cudaError_t (*crb_factor)(const CrbArgs&, cudaStream_t);
     cudaError_t (*crb_rhs)(const CrbArgs&, cudaStream_t);
     cudaError_t (*crb_back)(const CrbArgs&, cudaStream_t);
+    // warp-per-partition FP32 kernels (order 16; null otherwise): whether the level's
+    // factorization runs on them, and their forward solve, separator right-hand side and
+    // back substitution (they need the level's W, Hv and Hw buffers)
+    bool (*warp_ok)(const LevelArgs&, bool low);
+    cudaError_t (*solve_fwd_w)(const LevelArgs&, cudaStream_t);
+    cudaError_t (*sep_rhs_w)(const LevelArgs&, cudaStream_t);
+    cudaError_t (*solve_bwd_w)(const LevelArgs&, cudaStream_t);
 };
 
 const Launchers* launchers_m1();

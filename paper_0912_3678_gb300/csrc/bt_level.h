@@ -47,6 +47,13 @@ struct LevelArgs {
     // factorization in phases (CTA kernels, mode 0): phase k of `phases` takes local rows
     // [s + L k / phases, s + L (k+1) / phases) of every partition (L = e - s); phases <= 1: all
     int phase, phases;
+    // warp-per-partition FP32 kernels (order 16, bt_warp.cuh): the left separator's
+    // chain W_j = -W_{j-1} Y_{j-1} per block row ([rows][m][m], null: not stored), the
+    // forward-solve vectors h_j ([rows][m][nr], FP32) and sum_j W_j h_j per partition
+    // ([p][m][nr], FP32)
+    void* W;
+    void* Hv;
+    void* Hw;
 };
 
 }  // namespace bt

@@ -1,6 +1,7 @@
 // FP64 residuals, the refinement update with deterministic norms, and the
 // direct solver for the small BABD system at the top of the recursion.
 #include <cuda_runtime.h>
+#include "../../include/bt.h"
 #include "bt_device.cuh"
 #include "bt_misc.h"
 
@@ -876,3 +877,22 @@ cudaError_t launch_band_to_blocks(long long n, int s_, int r, const double* band
 }
 
 }  // namespace bt
+
+namespace bt {
+namespace {
+// y = rcp(x) elementwise: the FP64 reciprocal every FP64 pivot step uses.
+__global__ void __launch_bounds__(256) k_rcp(long long n, const double* __restrict__ x, double* __restrict__ y) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        y[e] = rcp(x[e]);
+}
+}  // namespace
+}  // namespace bt
+
+extern "C" bt_status bt_device_rcp(int64_t n, const double* x, double* y, void* stream) {
+    if (n < 0 || (n > 0 && (x == nullptr || y == nullptr))) return BT_ERR_INVALID;
+    if (n == 0) return BT_OK;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    bt::k_rcp<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(n, x, y);
+    return cudaGetLastError() == cudaSuccess ? BT_OK : BT_ERR_CUDA;
+}

@@ -40,3 +40,17 @@ cudaError_t launch_unpad_rhs(long long rows, int m, int M, int nr, const double*
 cudaError_t launch_band_to_blocks(long long n, int s, int r, const double* band, long long N, int m, double* B,
                                   double* D, double* C, cudaStream_t stream);
 }  // namespace bt
+
+namespace bt {
+// Refinement residuals in double-float arithmetic on the FP32 pipe (compensated
+// dot products, bt_resid_df.cu): entries accurate to a few units of 2^-48 of
+// sum |a||x| + |f|, returned rounded to FP32 precision in FP64 storage; same
+// arguments and maxima slots as launch_resid_btri / launch_resid_babd.
+size_t resid_df_smem(int kind, int m, int nr);
+cudaError_t launch_resid_btri_df(long long N, int m, int nr, const double* B, const double* D, const double* C,
+                                 const double* X, const double* F, double* R, cudaStream_t s,
+                                 unsigned long long* maxout = nullptr);
+cudaError_t launch_resid_babd_df(long long N, int m, int nr, const double* S, const double* Rm, const double* B0,
+                                 const double* B1, const double* Y, const double* F, double* Rout, cudaStream_t s,
+                                 unsigned long long* maxout = nullptr);
+}  // namespace bt

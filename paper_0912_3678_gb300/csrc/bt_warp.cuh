@@ -1,0 +1,580 @@
+// Warp-per-partition local factorization in FP32 for blocks of order 16 (the
+// low-precision local factors of the refined paths, Sec. 2 LU variant,
+// Eqs. (parfact)-(parblock), with each pivot block inverted by Gauss-Jordan
+// elimination with partial pivoting inside the block).
+//
+// One warp owns one partition.  Every block row j applies Gauss-Jordan
+// elimination to the augmented 16 x 64 matrix
+//     [ D'_j | C_j | T_j | I ]  ->  [ I | Y_j | Zc_j | D'_j^{-1} ],
+//     D'_j = D_j - B_j Y_{j-1},   T_j = -B_j Zc_{j-1}  (T_s = -B_s),
+// so the upper factor Y_j = D'_j^{-1} C_j, the left spike Zc_j and the
+// inverse come out of one elimination.  Lane r (r < 16) holds row r of
+// [D'|C], lane 16 + r row r of [T|I]; a column of D' lies across lanes 0-15,
+// so the pivot of step k is one redux over 32-bit magnitude keys, and rows
+// are never swapped: the pivot row of step k is only broadcast (through
+// shared memory) and every other row eliminates against it.  Row r ends as
+// the pivot row of some step k_r with pivot d_r, which makes it row k_r of
+// the result after division by d_r.  No CTA barrier is involved: the warp
+// synchronises with __syncwarp only.
+//
+// The left separator's coupling to the top row (needed by its reduced row,
+// Eq. (parblock)) runs as the forward chain W_s = C_{s-1},
+// Pf = sum_j W_j Zc_j, W_{j+1} = -W_j Y_j, Qf = W_e, fused with the next
+// row's Schur product (both read the rows of Y_{j-1} and Zc_{j-1} once).
+// Input block rows (FP64) are staged into shared memory with cp.async,
+// one row ahead, and converted to FP32 by integer operations.
+#pragma once
+#include "bt_bcr.cuh"
+
+namespace bt {
+
+struct WarpF16 {
+    static constexpr int M = 16;
+    static constexpr int WARPS = 4;    // partitions (warps) per CTA
+    static constexpr int SR = 18;      // row stride of the FP64 staging blocks (doubles, 144 bytes)
+    static constexpr int FR = 20;      // row stride of the FP32 blocks (floats, 80 bytes)
+    struct Smem {
+        double stage[2][3][M * SR];    // B, D, C of two block rows (FP64)
+        float cv[3][M * FR];           // B, D, C of the current row (FP32)
+        float ex[2][M * FR];           // rows of Y_{j-1} (0) and Zc_{j-1} (1), by row index
+        float prow[2][2][2 * M + 4];   // pivot row of step k (parity k & 1), both halves
+    };
+};
+
+// 1/x from the hardware approximation (relative error below 2^-22): the
+// local factors are FP32 approximations that refinement corrects.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Stage one 16 x 16 FP64 block (2 KB, 16-byte aligned) into a padded shared block:
+// 4 copies of 16 bytes per lane, each instruction covering 512 contiguous bytes.
+__device__ __forceinline__ void stage_blk16(double* dst, const double* src, int lane) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int g = q * 32 + lane, rr = g >> 3, cc = (g & 7) * 2;
+        cp_async16(dst + rr * WarpF16::SR + cc, src + rr * 16 + cc);
+    }
+}
+
+// FP64 staging block -> FP32 block (zeros when absent): lane l converts row
+// l / 2, columns (l % 2) * 8 .. + 7.
+__device__ __forceinline__ void convert_blk16(float* dst, const double* src, bool present, int lane) {
+    const int rr = lane >> 1, c0 = (lane & 1) * 8;
+    float o[8];
+    if (present) {
+        const double2* s = reinterpret_cast<const double2*>(src + rr * WarpF16::SR + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double2 v = s[q];
+            o[2 * q] = trunc_f32(v.x);
+            o[2 * q + 1] = trunc_f32(v.y);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) o[q] = 0.f;
+    }
+    float4* d = reinterpret_cast<float4*>(dst + rr * WarpF16::FR + c0);
+    d[0] = make_float4(o[0], o[1], o[2], o[3]);
+    d[1] = make_float4(o[4], o[5], o[6], o[7]);
+}
+
+__device__ __forceinline__ void read_row16(float (&v)[16], const float* s) {
+    const float4* p = reinterpret_cast<const float4*>(s);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 t = p[q];
+        v[4 * q] = t.x;
+        v[4 * q + 1] = t.y;
+        v[4 * q + 2] = t.z;
+        v[4 * q + 3] = t.w;
+    }
+}
+__device__ __forceinline__ void write_row16(float* s, const float* v) {
+    float4* p = reinterpret_cast<float4*>(s);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) p[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+// Block tridiagonal level (mode 0), FP32 factors: partition i of the level.
+__device__ __forceinline__ void factor_warp16_body(const LevelArgs& a, const long long i, WarpF16::Smem& sm) {
+    constexpr int M = 16;
+    constexpr int FR = WarpF16::FR;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, h = lane >> 4, r = lane & 15;
+    const Part pt = part_bounds(a, 0, i);
+    const long long MM = M * M;
+    float* gDinv = reinterpret_cast<float*>(a.Dinv);
+    float* gY = reinterpret_cast<float*>(a.Y);
+    float* gZ = reinterpret_cast<float*>(a.Zc);
+    const bool hasL = pt.hasL;
+    auto needB = [&](long long j) { return j > pt.s || hasL; };
+    auto needC = [&](long long j) { return (j < pt.e - 1) || pt.hasR; };
+    long long jb = pt.s, je = pt.e;
+    if (a.phases > 1) {
+        const long long cnt = pt.e - pt.s;
+        jb = pt.s + cnt * a.phase / a.phases;
+        je = pt.s + cnt * (a.phase + 1) / a.phases;
+    }
+    auto issue = [&](long long j, int buf) {
+        const long long o = (j - a.shift) * MM;
+        if (needB(j)) stage_blk16(sm.stage[buf][0], a.B + o, lane);
+        stage_blk16(sm.stage[buf][1], a.D + o, lane);
+        if (needC(j)) stage_blk16(sm.stage[buf][2], a.C + o, lane);
+        cp_async_commit();
+    };
+
+    float w[16], cp[16];   // W_j row r (both halves); sum_j W_j Zc_j row r (upper half)
+#pragma unroll
+    for (int c = 0; c < 16; ++c) cp[c] = 0.f;
+    bool wpend = false;    // the W step of the previous row is still to be taken
+    if (jb < je) issue(jb, 0);
+    if (jb > pt.s) {
+        // a later phase: resume from the stored Y_{jb-1}, Zc_{jb-1} and the running W, Pf
+        const float* yb = gY + (jb - 1) * MM;
+        const float* zb = gZ + (jb - 1) * MM;
+        float v[16];
+        read_row16(v, (h == 0) ? yb + r * M : zb + r * M);
+        if (h == 1 && !hasL) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) v[c] = 0.f;
+        }
+        write_row16(&sm.ex[h][r * FR], v);
+        if (hasL) {
+            read_row16(w, reinterpret_cast<const float*>(a.Qf) + i * MM + r * M);
+            read_row16(cp, reinterpret_cast<const float*>(a.Pf) + i * MM + r * M);
+        }
+    } else if (hasL) {
+        // W_s = C of the left separator row
+        const double* cs = a.C + (pt.s - 1 - a.shift) * MM + r * M;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) w[c] = trunc_f32(cs[c]);
+    }
+    if (!hasL) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) w[c] = 0.f;
+    }
+
+    for (long long j = jb; j < je; ++j) {
+        const int buf = (int)((j - jb) & 1);
+        if (j + 1 < je) issue(j + 1, buf ^ 1);
+        else cp_async_commit();
+        cp_async_wait<1>();
+        __syncwarp();
+        const bool hB = needB(j), hC = needC(j);
+        convert_blk16(sm.cv[0], sm.stage[buf][0], hB, lane);
+        convert_blk16(sm.cv[1], sm.stage[buf][1], true, lane);
+        convert_blk16(sm.cv[2], sm.stage[buf][2], hC, lane);
+        __syncwarp();
+        float bro[16], a32[32];
+        read_row16(bro, &sm.cv[0][r * FR]);
+        if (h == 0) {
+            float t[16];
+            read_row16(t, &sm.cv[1][r * FR]);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) a32[c] = t[c];
+            read_row16(t, &sm.cv[2][r * FR]);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) a32[16 + c] = t[c];
+        } else {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                a32[c] = 0.f;
+                a32[16 + c] = (c == r) ? 1.f : 0.f;
+            }
+        }
+        if (j > pt.s) {
+            // D'_j = D_j - B_j Y_{j-1} (lower half), T_j = -B_j Zc_{j-1} (upper half), and the
+            // pending W step: W_j = -W_{j-1} Y_{j-1}, Pf += W_{j-1} Zc_{j-1}
+            float acc[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[c] = 0.f;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                float srow[16];
+                read_row16(srow, &sm.ex[h][k * FR]);
+                const float bk = bro[k], wk = w[k];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    a32[c] = fmaf(-bk, srow[c], a32[c]);
+                    acc[c] = fmaf(wk, srow[c], acc[c]);
+                }
+            }
+            if (wpend) {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const float wn = __shfl_sync(FULL, -acc[c], r);
+                    if (h == 1) cp[c] += acc[c];
+                    w[c] = wn;
+                }
+            }
+        } else if (h == 1 && hasL) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) a32[c] = -bro[c];   // T_s = -B_s
+        }
+        if (hasL && h == 0 && a.W != nullptr) write_row16(reinterpret_cast<float*>(a.W) + j * MM + r * M, w);
+        __syncwarp();   // every lane has read ex before it is rewritten below
+
+        // Gauss-Jordan elimination without row interchanges
+        int bad = 0;
+        bool used = false;
+        float dsave = 1.f;
+        int kpos = 0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const unsigned key = (h == 0 && !used) ? ((mag_key<float>(a32[k]) << 5) | (unsigned)(31 - lane)) : 0u;
+            const unsigned best = __reduce_max_sync(FULL, key);
+            const int p = 31 - (int)(best & 31u);
+            float piv = __shfl_sync(FULL, a32[k], p);
+            const float colk = __shfl_sync(FULL, a32[k], r);
+            // a zero (or subnormal: its reciprocal overflows FP32) or non-finite
+            // pivot is reported after the elimination (the first such step wins)
+            // and replaced by 1 to keep going
+            const unsigned pe = (__float_as_uint(piv) >> 23) & 0xffu;
+            const int flag = (pe == 0xffu) ? ST_NONFINITE : (pe == 0u ? ST_SINGULAR : 0);
+            bad = bad ? bad : flag;
+            piv = flag ? 1.f : piv;
+            const float rp = rcp_approx(piv);
+            const bool mine = (r == p);
+            const float l = mine ? 0.f : colk * rp;
+            float* pb = sm.prow[k & 1][h];
+            if (mine) {
+                float4* d = reinterpret_cast<float4*>(pb);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) d[q] = make_float4(a32[4 * q], a32[4 * q + 1], a32[4 * q + 2], a32[4 * q + 3]);
+            }
+            __syncwarp();
+            const float4* s = reinterpret_cast<const float4*>(pb);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float4 t = s[q];
+                a32[4 * q] = fmaf(-l, t.x, a32[4 * q]);
+                a32[4 * q + 1] = fmaf(-l, t.y, a32[4 * q + 1]);
+                a32[4 * q + 2] = fmaf(-l, t.z, a32[4 * q + 2]);
+                a32[4 * q + 3] = fmaf(-l, t.w, a32[4 * q + 3]);
+            }
+            if (mine) {
+                used = true;
+                dsave = piv;
+                kpos = k;
+            }
+        }
+        if (bad && lane == 0) report(a.status, bad, a.level, i, j);
+        // row r is row kpos of [I | Y | Zc | D'^{-1}] after division by its pivot
+        const float sc = rcp_approx(dsave);
+        if (h == 0) {
+            float y[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) y[c] = a32[16 + c] * sc;
+            if (hC) write_row16(gY + j * MM + kpos * M, y);
+            write_row16(&sm.ex[0][kpos * FR], y);
+        } else {
+            float z[16], di[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                z[c] = a32[c] * sc;
+                di[c] = a32[16 + c] * sc;
+            }
+            write_row16(gDinv + j * MM + kpos * M, di);
+            if (hasL) write_row16(gZ + j * MM + kpos * M, z);
+            write_row16(&sm.ex[1][kpos * FR], z);
+        }
+        wpend = hasL;
+        __syncwarp();
+    }
+    cp_async_wait<0>();
+    if (!hasL) return;
+    if (wpend) {
+        // the W step of the last row: Pf += W Zc_{je-1}, W_{je} = -W Y_{je-1}
+        float acc[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            float srow[16];
+            read_row16(srow, &sm.ex[h][k * FR]);
+            const float wk = w[k];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[c] = fmaf(wk, srow[c], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const float wn = __shfl_sync(FULL, -acc[c], r);
+            if (h == 1) cp[c] += acc[c];
+            w[c] = wn;
+        }
+    }
+    // final: C_sep P_first (Pf) and W_e (Qf); between phases: the running sum and W
+    if (h == 1) write_row16(reinterpret_cast<float*>(a.Pf) + i * MM + r * M, cp);
+    else write_row16(reinterpret_cast<float*>(a.Qf) + i * MM + r * M, w);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(32 * WarpF16::WARPS) k_factor_w16(const LevelArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    WarpF16::Smem& sm = reinterpret_cast<WarpF16::Smem*>(smem_raw)[warp];
+    const long long u = a.unit0 + (long long)blockIdx.x * WarpF16::WARPS + warp;
+    const long long end = (a.unit_end > 0) ? a.unit_end : a.p;
+    if (u >= end) return;
+    factor_warp16_body(a, u, sm);
+}
+
+constexpr size_t factor_w16_smem_bytes() { return sizeof(WarpF16::Smem) * WarpF16::WARPS; }
+
+// ---------------------------------------------------------------- solves --
+// Forward and back substitution with the warp kernel's FP32 factors, one warp
+// per partition (block tridiagonal, order 16).  Lane (r, hc) holds entry r of
+// right-hand-side columns hc*NH .. hc*NH + NH - 1 of each block row; block
+// products take the other rows from a shared exchange row (broadcast loads).
+//   forward   h_s = D'^{-1}_s f_s,  h_j = D'^{-1}_j (f_j - B_j h_{j-1}),
+//             Hw  = sum_j W_j h_j              (the left separator's coupling),
+//             g_e = f_e - B_e h_{e-1}          (right separator, partial:
+//                                               k_sep_rhs_w16 subtracts Hw of the next partition)
+//   backward  x_j = h_j + Zc_j x_L - Y_j x_{j+1}.
+template <int NH>
+struct WarpS16 {
+    static constexpr int M = 16;
+    static constexpr int WARPS = 4;
+    static constexpr int SW = 2 * NH + 4;   // exchange row stride (floats)
+    struct Smem {
+        double stage[2][M * WarpF16::SR];    // B_j of two block rows (FP64)
+        float xa[M * SW];                    // exchange row: h_{j-1}, t_j, or x_{j+1}
+        float xb[M * SW];                    // exchange row: h_j, or x_L
+    };
+};
+
+template <int NH>
+__device__ __forceinline__ void load_vec(float (&v)[NH], const double* g, int cbase, int nr) {
+#pragma unroll
+    for (int q = 0; q < NH; ++q) v[q] = (cbase + q < nr) ? trunc_f32(g[cbase + q]) : 0.f;
+}
+template <int NH>
+__device__ __forceinline__ void put_vec(float* s, const float (&v)[NH]) {
+#pragma unroll
+    for (int q = 0; q < NH; q += 4) *reinterpret_cast<float4*>(s + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+}
+// acc[q] += sgn * sum_k A[k] X[k][q]  (A: 16 coefficients in registers; X rows in shared memory)
+template <int NH, bool NEG>
+__device__ __forceinline__ void gemv_acc(float (&acc)[NH], const float (&A)[16], const float* X, int stride) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const float ak = NEG ? -A[k] : A[k];
+#pragma unroll
+        for (int q = 0; q < NH; q += 4) {
+            const float4 x = *reinterpret_cast<const float4*>(X + k * stride + q);
+            acc[q] = fmaf(ak, x.x, acc[q]);
+            acc[q + 1] = fmaf(ak, x.y, acc[q + 1]);
+            acc[q + 2] = fmaf(ak, x.z, acc[q + 2]);
+            acc[q + 3] = fmaf(ak, x.w, acc[q + 3]);
+        }
+    }
+}
+__device__ __forceinline__ void load_row16(float (&v)[16], const float* g) { read_row16(v, g); }
+
+template <int NH>
+__device__ __forceinline__ void solve_fwd_w16_body(const LevelArgs& a, const long long i,
+                                                   typename WarpS16<NH>::Smem& sm) {
+    constexpr int M = 16, SW = WarpS16<NH>::SW;
+    const int lane = threadIdx.x & 31, r = lane & 15, hc = lane >> 4;
+    const int nr = a.nr, E = M * nr, cb = hc * NH;
+    const Part pt = part_bounds(a, 0, i);
+    const long long MM = M * M;
+    const float* gDi = reinterpret_cast<const float*>(a.Dinv);
+    const float* gW = reinterpret_cast<const float*>(a.W);
+    float* gH = reinterpret_cast<float*>(a.Hv);
+    float* xa = sm.xa + r * SW + cb;
+    float* xb = sm.xb + r * SW + cb;
+    float acc[NH];
+#pragma unroll
+    for (int q = 0; q < NH; ++q) acc[q] = 0.f;
+    // prefetch of the next row: D'^{-1} row r, W row r, f entries
+    float pDi[16], pW[16], pf[NH];
+    auto fetch = [&](long long j) {
+        load_row16(pDi, gDi + j * MM + r * M);
+        if (pt.hasL) load_row16(pW, gW + j * MM + r * M);
+        load_vec<NH>(pf, a.F + (j * M + r) * nr, cb, nr);
+    };
+    if (pt.s < pt.e) {
+        fetch(pt.s);
+        if (pt.s + 1 < pt.e) stage_blk16(sm.stage[1], a.B + (pt.s + 1 - a.shift) * MM, lane);
+        cp_async_commit();
+    }
+    for (long long j = pt.s; j < pt.e; ++j) {
+        const int buf = (int)((j - pt.s) & 1);
+        float Di[16], Wr[16], t[NH];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            Di[k] = pDi[k];
+            Wr[k] = pW[k];
+        }
+#pragma unroll
+        for (int q = 0; q < NH; ++q) t[q] = pf[q];
+        if (j + 1 < pt.e) fetch(j + 1);
+        // B_j sits in stage[(j - s) & 1]; B_{s+1} was issued before the loop
+        if (j > pt.s && j + 1 < pt.e) stage_blk16(sm.stage[buf ^ 1], a.B + (j + 1 - a.shift) * MM, lane);
+        cp_async_commit();
+        if (j > pt.s) {
+            // t = f_j - B_j h_{j-1}  (h_{j-1} in xb)
+            cp_async_wait<1>();
+            __syncwarp();
+            float Br[16];
+            const double* sb = sm.stage[buf] + r * WarpF16::SR;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) Br[k] = trunc_f32(sb[k]);
+            gemv_acc<NH, true>(t, Br, sm.xb + cb, SW);
+        }
+        put_vec<NH>(xa, t);
+        __syncwarp();
+        float h[NH];
+#pragma unroll
+        for (int q = 0; q < NH; ++q) h[q] = 0.f;
+        gemv_acc<NH, false>(h, Di, sm.xa + cb, SW);
+        __syncwarp();          // xb (h_{j-1}) and xa (t) fully read
+        put_vec<NH>(xb, h);
+#pragma unroll
+        for (int q = 0; q < NH; ++q)
+            if (cb + q < nr) gH[j * E + r * nr + cb + q] = h[q];
+        __syncwarp();
+        if (pt.hasL) gemv_acc<NH, false>(acc, Wr, sm.xb + cb, SW);
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+    if (pt.hasL) {
+        float* hw = reinterpret_cast<float*>(a.Hw) + i * E + r * nr;
+#pragma unroll
+        for (int q = 0; q < NH; ++q)
+            if (cb + q < nr) hw[cb + q] = acc[q];
+    }
+    if (pt.hasR) {
+        // partial reduced right-hand side of the right separator e: f_e - B_e h_{e-1}
+        const long long e = pt.e;
+        float g[NH], Br[16];
+        load_vec<NH>(g, a.F + (e * M + r) * nr, cb, nr);
+        if (pt.e > pt.s) {
+            const double* be = a.B + (e - a.shift) * MM + r * M;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) Br[k] = trunc_f32(be[k]);
+            gemv_acc<NH, true>(g, Br, sm.xb + cb, SW);
+        }
+        double* fn = a.Fn + i * E + r * nr;
+#pragma unroll
+        for (int q = 0; q < NH; ++q)
+            if (cb + q < nr) fn[cb + q] = (double)g[q];
+    }
+}
+
+template <int NH>
+__device__ __forceinline__ void solve_bwd_w16_body(const LevelArgs& a, const long long i,
+                                                   typename WarpS16<NH>::Smem& sm) {
+    constexpr int M = 16, SW = WarpS16<NH>::SW;
+    const int lane = threadIdx.x & 31, r = lane & 15, hc = lane >> 4;
+    const int nr = a.nr, E = M * nr, cb = hc * NH;
+    const Part pt = part_bounds(a, 0, i);
+    const long long MM = M * M;
+    const float* gY = reinterpret_cast<const float*>(a.Y);
+    const float* gZ = reinterpret_cast<const float*>(a.Zc);
+    const float* gH = reinterpret_cast<const float*>(a.Hv);
+    float* xa = sm.xa + r * SW + cb;   // x_{j+1}
+    float* xb = sm.xb + r * SW + cb;   // x_L
+    float v[NH];
+    if (pt.hasR) {
+        const double* xr = a.Xn + i * E + r * nr;
+        double* xo = a.X + pt.e * E + r * nr;
+#pragma unroll
+        for (int q = 0; q < NH; ++q) {
+            const double d = (cb + q < nr) ? xr[cb + q] : 0.0;
+            v[q] = trunc_f32(d);
+            if (cb + q < nr) xo[cb + q] = d;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < NH; ++q) v[q] = 0.f;
+    }
+    put_vec<NH>(xa, v);
+    if (pt.hasL) {
+        load_vec<NH>(v, a.Xn + (i - 1) * E + r * nr, cb, nr);
+        put_vec<NH>(xb, v);
+    }
+    __syncwarp();
+    auto useY = [&](long long j) { return (j < pt.e - 1) || pt.hasR; };
+    float pY[16], pZ[16], ph[NH];
+    auto fetch = [&](long long j) {
+        if (useY(j)) load_row16(pY, gY + j * MM + r * M);
+        if (pt.hasL) load_row16(pZ, gZ + j * MM + r * M);
+#pragma unroll
+        for (int q = 0; q < NH; ++q) ph[q] = (cb + q < nr) ? gH[j * E + r * nr + cb + q] : 0.f;
+    };
+    if (pt.e > pt.s) fetch(pt.e - 1);
+    for (long long j = pt.e - 1; j >= pt.s; --j) {
+        float Yr[16], Zr[16], x[NH];
+        const bool uY = useY(j);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            Yr[k] = pY[k];
+            Zr[k] = pZ[k];
+        }
+#pragma unroll
+        for (int q = 0; q < NH; ++q) x[q] = ph[q];
+        if (j - 1 >= pt.s) fetch(j - 1);
+        if (uY) gemv_acc<NH, true>(x, Yr, sm.xa + cb, SW);
+        if (pt.hasL) gemv_acc<NH, false>(x, Zr, sm.xb + cb, SW);
+        __syncwarp();          // x_{j+1} fully read
+        put_vec<NH>(xa, x);
+        double* xo = a.X + j * E + r * nr;
+#pragma unroll
+        for (int q = 0; q < NH; ++q)
+            if (cb + q < nr) xo[cb + q] = (double)x[q];
+        __syncwarp();
+    }
+}
+
+template <int NH>
+__global__ void __launch_bounds__(32 * WarpS16<NH>::WARPS) k_solve_fwd_w16(const LevelArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    auto& sm = reinterpret_cast<typename WarpS16<NH>::Smem*>(smem_raw)[warp];
+    const long long u = (long long)blockIdx.x * WarpS16<NH>::WARPS + warp;
+    if (u >= a.p) return;
+    solve_fwd_w16_body<NH>(a, u, sm);
+}
+template <int NH>
+__global__ void __launch_bounds__(32 * WarpS16<NH>::WARPS) k_solve_bwd_w16(const LevelArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    auto& sm = reinterpret_cast<typename WarpS16<NH>::Smem*>(smem_raw)[warp];
+    const long long u = (long long)blockIdx.x * WarpS16<NH>::WARPS + warp;
+    if (u >= a.p) return;
+    solve_bwd_w16_body<NH>(a, u, sm);
+}
+// Reduced right-hand side of separator s: g_s -= Hw of partition s + 1.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_sep_rhs_w16(const LevelArgs a) {
+    const long long E = 16LL * a.nr;
+    const long long n = (a.p - 1) * E;
+    const float* hw = reinterpret_cast<const float*>(a.Hw);
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        a.Fn[e] -= (double)hw[e + E];
+}
+
+// The warp kernel serves FP32 block tridiagonal levels of order 16 without the
+// BF16 tensor-core products and without breakdown detection (pivoted plans),
+// whose matrices start on 16-byte boundaries (the staging copies are 16 bytes).
+inline bool use_factor_w16(const LevelArgs& a) {
+    const uintptr_t al = (uintptr_t)a.B | (uintptr_t)a.D | (uintptr_t)a.C;
+    return a.mode == 0 && !a.bf16 && a.brk == nullptr && a.starts == nullptr && (al & 15u) == 0;
+}
+
+}  // namespace bt

@@ -1,9 +1,9 @@
 """bt_solve_noalloc: the solve for callers that may not allocate device
 memory (a host application that owns all device memory through its own pool,
 or a hot loop that cannot accept cudaMalloc's implicit synchronisation).  It
-must give the same answer as the plan-based entry points, on consecutive
-calls that share its static scratch array, and refuse problems larger than
-that array without touching the GPU.  This file sorts last so that a run
+must give the FP64 oracle's answer and the same answer as the plan-based
+entry points, on consecutive calls that share its static scratch array, and
+refuse problems larger than that array.  This file sorts last so that a run
 stopping at the first failure has already run every other test."""
 import ctypes
 
@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import gen
+import oracle
 from conftest import to_dev, to_host
 
 pytestmark = pytest.mark.gpu
@@ -49,6 +50,7 @@ def test_noalloc_matches_plan_on_consecutive_calls(cuda):
         code, req, X = _noalloc_solve(lib, s, cuda)
         assert code == 0, bt.bt_status_string(code)
         assert 0 < req <= bt.BT_NOALLOC_SCRATCH_BYTES
+        assert oracle.rel_err(X, oracle.btri_solve(s.B, s.D, s.C, s.F)) <= TOL64
         ref = _plan_solve(bt, s, cuda)
         err = np.linalg.norm(X - ref) / np.linalg.norm(ref)
         assert err <= TOL64
@@ -62,6 +64,7 @@ def test_noalloc_scalar_and_singular_status(cuda):
     s = gen.BtriSystem(t.dl.reshape(-1, 1, 1), t.d.reshape(-1, 1, 1), t.du.reshape(-1, 1, 1), t.f, t.xstar)
     code, req, X = _noalloc_solve(lib, s, cuda)
     assert code == 0
+    assert oracle.rel_err(X, oracle.tri_solve(t.dl, t.d, t.du, t.f)) <= TOL64
     ref = _plan_solve(bt, s, cuda)
     assert np.linalg.norm(X - ref) / np.linalg.norm(ref) <= TOL64
     bad = gen.btri_random(40, 4, 1, seed_rep=6)
@@ -77,9 +80,17 @@ def test_noalloc_scalar_and_singular_status(cuda):
 def test_noalloc_rejects_problems_beyond_the_scratch(cuda):
     import paper_0912_3678_gb300 as bt
     from paper_0912_3678_gb300 import _lib
+    import torch
     lib = _lib.load()
     req = ctypes.c_int64(0)
-    one = ctypes.c_void_p(16)   # never dereferenced: the size check comes first
-    code = lib.bt_solve_noalloc(100000, 32, one, one, one, one, ctypes.c_void_p(32), 1, None, ctypes.byref(req))
+    # real (small) device buffers: the call must refuse on size alone, but if
+    # that check ever moved behind a launch, the kernels would read valid memory
+    a = torch.zeros(32 * 32, dtype=torch.float64, device=cuda)
+    f = torch.zeros(32, dtype=torch.float64, device=cuda)
+    x = torch.full_like(f, 7.0)
+    code = lib.bt_solve_noalloc(100000, 32, a.data_ptr(), a.data_ptr(), a.data_ptr(), f.data_ptr(), x.data_ptr(), 1,
+                                torch.cuda.current_stream().cuda_stream, ctypes.byref(req))
+    torch.cuda.synchronize()
     assert bt.BT_STATUS[code] == "BT_ERR_INVALID"
     assert req.value > bt.BT_NOALLOC_SCRATCH_BYTES
+    assert bool((x == 7.0).all())          # nothing was written
