@@ -190,6 +190,7 @@ void layout(bt_plan_s* P, Arena& ar) {
         v0.a.W = ar.take(sizeof(float) * rows0 * mm);
         v0.a.Hv = ar.take(sizeof(float) * rows0 * m * nr);
         v0.a.Hw = ar.take(sizeof(float) * pa * m * nr);
+        v0.a.As = ar.take(2 * sizeof(float) * 3 * rows0 * mm);
     }
     for (int l = 0; l <= P->nlev; ++l) {
         Level& v = P->lv[l];
@@ -503,6 +504,9 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
         if (!P->status_host || !P->norms_host) e = cudaErrorMemoryAllocation;
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(P->status, 0, 4 * sizeof(long long), P->stream);
+    // the split copy of the matrix: blocks B_0 and C_{N-1} are never written and stay zero
+    if (e == cudaSuccess && P->warp && P->lv[0].a.As)
+        e = cudaMemsetAsync(P->lv[0].a.As, 0, 2 * sizeof(float) * 3 * P->lv[0].rows * (size_t)m * m, P->stream);
     if (e != cudaSuccess) {
         if (P->own_arena) cudaFree(P->arena);
         if (P->pinned) {
@@ -820,6 +824,10 @@ bt_status run_residual(bt_plan_s* P, const double* F, const double* X, double* R
         if (e != cudaSuccess) return from_cuda(e);
     }
     cudaError_t e = launch(P, K_RESID, 0, 1, [&] {
+        if (P->kind == 0 && df && P->warp && P->L->warp_ok && P->L->warp_ok(P->lv[0].a, P->lv[0].low) &&
+            ((((uintptr_t)X) | ((uintptr_t)F)) & 15u) == 0)
+            return bt::launch_resid_btri_dfs(P->N, P->m, nr, reinterpret_cast<const float2*>(P->lv[0].a.As), X, F,
+                                             R, P->stream, maxout);
         if (P->kind == 0)
             return df ? bt::launch_resid_btri_df(P->N, P->m, nr, P->A0, P->A1, P->A2, X, F, R, P->stream, maxout)
                       : bt::launch_resid_btri(P->N, P->m, nr, P->A0, P->A1, P->A2, X, F, R, P->stream, maxout);

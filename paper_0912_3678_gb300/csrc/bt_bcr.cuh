@@ -67,6 +67,30 @@ __device__ __forceinline__ float trunc_f32(double v) {
     }
     return __uint_as_float(sign | ((unsigned)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
 }
+// v = hi + lo: hi = v truncated to FP32, lo = the remaining 29 mantissa
+// bits, rounded to FP32.  Integer and FP32 operations only (the FP64 pipe,
+// which also executes integer-to-float conversions on this GPU, is not used):
+// hi is assembled from the exponent and the top 23 fraction bits; the
+// remainder L < 2^29 is converted as L = 64 L1 + L0 with each part read off
+// 2^23 + L_i (the magic-number conversion), scaled by the weight of its last
+// bit.  Magnitudes outside the FP32 range give hi = 0 (below) or infinity
+// (above, also NaN); lo is 0 below 2^-74.
+__device__ __forceinline__ float2 split_f64(double v) {
+    const unsigned hw = (unsigned)__double2hiint(v), lw = (unsigned)__double2loint(v);
+    const unsigned sign = hw & 0x80000000u;
+    const unsigned e = (hw >> 20) & 0x7ffu;
+    const unsigned mant = __funnelshift_l(lw, hw, 3) & 0x7fffffu;
+    unsigned hb = sign | ((e - 896u) << 23) | mant;
+    if (e - 897u >= 254u) hb = (e < 897u) ? sign : (sign | 0x7f800000u | (((hw & 0xfffffu) | lw) ? 0x400000u : 0u));
+    const unsigned L = lw & 0x1fffffffu;
+    const float l1 = __fsub_rn(__uint_as_float(0x4b000000u | (L >> 6)), 8388608.f);
+    const float l0 = __fsub_rn(__uint_as_float(0x4b000000u | (L & 63u)), 8388608.f);
+    const unsigned se = e - 948u;   // FP32 exponent field of 2^(e - 1075), the weight of bit 0
+    float lo = __fmul_rn(fmaf(l1, 64.f, l0), __uint_as_float((se << 23) | sign));
+    if (se - 1u >= 254u) lo = 0.f;
+    return make_float2(__uint_as_float(hb), lo);
+}
+
 template <typename T, typename G>
 __device__ __forceinline__ T cvt_in(G v) {
     if constexpr (std::is_same<T, G>::value) return v;

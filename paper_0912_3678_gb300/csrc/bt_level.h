@@ -54,6 +54,9 @@ struct LevelArgs {
     void* W;
     void* Hv;
     void* Hw;
+    // the level matrix split into FP32 pairs (hi, lo) for the double-float
+    // refinement residual: float2 [3][rows][m][m] (B, D, C); null: not kept
+    void* As;
 };
 
 }  // namespace bt

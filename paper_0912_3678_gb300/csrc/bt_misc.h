@@ -50,6 +50,10 @@ size_t resid_df_smem(int kind, int m, int nr);
 cudaError_t launch_resid_btri_df(long long N, int m, int nr, const double* B, const double* D, const double* C,
                                  const double* X, const double* F, double* R, cudaStream_t s,
                                  unsigned long long* maxout = nullptr);
+// The same residual for order 16 with the matrix kept as FP32 pairs float2 [3][N][16][16]
+// (B, D, C; written by the warp-per-partition factorization).
+cudaError_t launch_resid_btri_dfs(long long N, int m, int nr, const float2* As, const double* X, const double* F,
+                                  double* R, cudaStream_t s, unsigned long long* maxout = nullptr);
 cudaError_t launch_resid_babd_df(long long N, int m, int nr, const double* S, const double* Rm, const double* B0,
                                  const double* B1, const double* Y, const double* F, double* Rout, cudaStream_t s,
                                  unsigned long long* maxout = nullptr);

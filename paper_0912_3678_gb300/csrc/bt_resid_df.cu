@@ -20,36 +20,13 @@
 // error 2^-24 on those terms); the refined paths need entries inside the
 // FP32 range in any case (their local factors are FP32).
 #include <cuda_runtime.h>
+#include <cstdint>
 
 #include "bt_bcr.cuh"
 #include "bt_misc.h"
 
 namespace bt {
 namespace {
-
-// v = hi + lo: hi = v truncated to FP32, lo = the remaining 29 mantissa
-// bits, rounded to FP32.  Integer and FP32 operations only (the FP64 pipe,
-// which also executes integer-to-float conversions on this GPU, is not used):
-// hi is assembled from the exponent and the top 23 fraction bits; the
-// remainder L < 2^29 is converted as L = 64 L1 + L0 with each part read off
-// 2^23 + L_i (the magic-number conversion), scaled by the weight of its last
-// bit.  Magnitudes outside the FP32 range give hi = 0 (below) or infinity
-// (above, also NaN); lo is 0 below 2^-74.
-__device__ __forceinline__ float2 split_f64(double v) {
-    const unsigned hw = (unsigned)__double2hiint(v), lw = (unsigned)__double2loint(v);
-    const unsigned sign = hw & 0x80000000u;
-    const unsigned e = (hw >> 20) & 0x7ffu;
-    const unsigned mant = __funnelshift_l(lw, hw, 3) & 0x7fffffu;
-    unsigned hb = sign | ((e - 896u) << 23) | mant;
-    if (e - 897u >= 254u) hb = (e < 897u) ? sign : (sign | 0x7f800000u | (((hw & 0xfffffu) | lw) ? 0x400000u : 0u));
-    const unsigned L = lw & 0x1fffffffu;
-    const float l1 = __fsub_rn(__uint_as_float(0x4b000000u | (L >> 6)), 8388608.f);
-    const float l0 = __fsub_rn(__uint_as_float(0x4b000000u | (L & 63u)), 8388608.f);
-    const unsigned se = e - 948u;   // FP32 exponent field of 2^(e - 1075), the weight of bit 0
-    float lo = __fmul_rn(fmaf(l1, 64.f, l0), __uint_as_float((se << 23) | sign));
-    if (se - 1u >= 254u) lo = 0.f;
-    return make_float2(__uint_as_float(hb), lo);
-}
 
 // Exact FP32 -> FP64 by integer operations (FP32 subnormals become zero).
 __device__ __forceinline__ double f32_to_f64(float f) {
@@ -235,8 +212,8 @@ __global__ void __launch_bounds__(kDfThreads) k_resid_btri_df(long long N, int n
             for (int k = 0; k < M; ++k) {
                 const float2 ak = Ar[k];
                 const float4 xk = xq[k * pcp];
-                a[(blk * M + k) & 3].sub(ak, make_float2(xk.x, xk.y));
-                b[(blk * M + k) & 3].sub(ak, make_float2(xk.z, xk.w));
+                a[k & 3].sub(ak, make_float2(xk.x, xk.y));
+                b[k & 3].sub(ak, make_float2(xk.z, xk.w));
             }
         }
         DF& a0 = a[0];
@@ -315,8 +292,8 @@ __global__ void __launch_bounds__(kDfThreads) k_resid_babd_df(long long N, int n
             for (int k = 0; k < M; ++k) {
                 const float2 ak = Ar[k];
                 const float4 xk = xq[k * pcp];
-                a[(blk * M + k) & 3].sub(ak, make_float2(xk.x, xk.y));
-                b[(blk * M + k) & 3].sub(ak, make_float2(xk.z, xk.w));
+                a[k & 3].sub(ak, make_float2(xk.x, xk.y));
+                b[k & 3].sub(ak, make_float2(xk.z, xk.w));
             }
         }
         DF& a0 = a[0];
@@ -339,6 +316,260 @@ __global__ void __launch_bounds__(kDfThreads) k_resid_babd_df(long long N, int n
     if (maxout) block_max3_df(mr, mx, mf, maxout);
 }
 
+__device__ __forceinline__ void df_cp16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void df_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void df_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Persistent, pipelined form of k_resid_btri_df: each CTA strides over tiles
+// of G block rows; the FP64 blocks, x rows and f rows of the next tile are
+// copied into a second shared buffer (cp.async, 16-byte pieces) while the
+// current tile is split into double-float form and reduced.  Needs 16-byte
+// aligned arrays and an even number of entries per block row of x (m nr).
+template <int M>
+__global__ void __launch_bounds__(kDfThreads) k_resid_btri_df2(long long N, int nr, int G, long long ntiles,
+                                                               const double* __restrict__ B,
+                                                               const double* __restrict__ D,
+                                                               const double* __restrict__ C,
+                                                               const double* __restrict__ X,
+                                                               const double* __restrict__ F, double* __restrict__ R,
+                                                               unsigned long long* maxout) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int MM = M * M;
+    const int ncp = (nr + 1) / 2, cs = df_pair_shift(nr), pcp = 1 << cs;
+    const int V = M * nr;                                  // doubles per block row of x or f
+    const int nA = G * 3 * MM, nX = (G + 2) * V, nF = G * V;
+    const int nraw = nA + nX + nF;
+    double* raw0 = reinterpret_cast<double*>(smem);
+    double* raw1 = raw0 + nraw;
+    float2* sA = reinterpret_cast<float2*>(raw1 + nraw);   // [G][3][M][M]
+    float4* sX = reinterpret_cast<float4*>(sA + nA);       // [G + 2][M][pcp]
+    const double* arr[3] = {B, D, C};
+    auto issue = [&](long long t, double* raw) {
+        if (t < ntiles) {
+            const long long j0 = t * G;
+            const int g = (int)((N - j0) < G ? (N - j0) : G);
+            for (int w = 0; w < 3; ++w) {
+                const double* src = arr[w] + j0 * MM;
+                double* dst = raw + w * G * MM;
+                for (int c = threadIdx.x; c < g * MM / 2; c += blockDim.x) df_cp16(dst + 2 * c, src + 2 * c);
+            }
+            const long long lo = (j0 - 1 > 0) ? j0 - 1 : 0, hi = (j0 + g + 1 < N) ? j0 + g + 1 : N;
+            double* dx = raw + nA + (lo - (j0 - 1)) * V;
+            const double* sx = X + lo * V;
+            for (int c = threadIdx.x; c < (int)(hi - lo) * V / 2; c += blockDim.x) df_cp16(dx + 2 * c, sx + 2 * c);
+            const double* sf = F + j0 * V;
+            for (int c = threadIdx.x; c < g * V / 2; c += blockDim.x) df_cp16(raw + nA + nX + 2 * c, sf + 2 * c);
+        }
+        df_commit();
+    };
+    unsigned long long mr = 0ull, mx = 0ull, mf = 0ull;
+    int buf = 0;
+    issue(blockIdx.x, raw0);
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
+        double* raw = buf ? raw1 : raw0;
+        issue(t + gridDim.x, buf ? raw0 : raw1);
+        df_wait<1>();
+        __syncthreads();
+        const long long j0 = t * G;
+        const int g = (int)((N - j0) < G ? (N - j0) : G);
+        for (int idx = threadIdx.x; idx < g * 3 * MM; idx += blockDim.x) {
+            const int gj = idx / (3 * MM), rem = idx % (3 * MM), w = rem / MM, e = rem % MM;
+            const long long j = j0 + gj;
+            const bool present = (w == 1) || (w == 0 && j > 0) || (w == 2 && j + 1 < N);
+            sA[idx] = present ? split_f64(raw[w * G * MM + gj * MM + e]) : make_float2(0.f, 0.f);
+        }
+        for (int idx = threadIdx.x; idx < ((g + 2) * M) << cs; idx += blockDim.x) {
+            const int cp = idx & (pcp - 1), qk = idx >> cs, q = qk / M, k = qk % M;
+            const long long row = j0 - 1 + q;
+            float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+            if (cp < ncp && row >= 0 && row < N) {
+                const double* src = raw + nA + q * V + k * nr + 2 * cp;
+                const double v0 = src[0];
+                a = split_f64(v0);
+                unsigned long long m0 = abs_bits64(v0);
+                if (2 * cp + 1 < nr) {
+                    const double v1 = src[1];
+                    b = split_f64(v1);
+                    m0 = umax_(m0, abs_bits64(v1));
+                }
+                if (q >= 1 && q <= g) mx = umax_(mx, m0);
+            }
+            sX[idx] = make_float4(a.x, a.y, b.x, b.y);
+        }
+        __syncthreads();
+        const double* rf = raw + nA + nX;
+        for (int u = threadIdx.x; u < ((g * M) << cs); u += blockDim.x) {
+            const int cp = u & (pcp - 1), gr = u >> cs, gj = gr / M, r = gr % M;
+            if (cp >= ncp) continue;
+            const long long row = (j0 + gj) * M + r;
+            const int c0 = 2 * cp;
+            const bool two = c0 + 1 < nr;
+            const double f0 = rf[(gj * M + r) * nr + c0], f1 = two ? rf[(gj * M + r) * nr + c0 + 1] : 0.0;
+            mf = umax_(mf, umax_(abs_bits64(f0), abs_bits64(f1)));
+            DF a[4], b[4];
+            a[0].init(split_f64(f0));
+            b[0].init(split_f64(f1));
+#pragma unroll
+            for (int qq = 1; qq < 4; ++qq) {
+                a[qq].init(make_float2(0.f, 0.f));
+                b[qq].init(make_float2(0.f, 0.f));
+            }
+#pragma unroll
+            for (int blk = 0; blk < 3; ++blk) {
+                const float2* Ar = sA + ((gj * 3 + blk) * M + r) * M;
+                const float4* xq = sX + (gj + blk) * M * pcp + cp;
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    const float2 ak = Ar[k];
+                    const float4 xk = xq[k * pcp];
+                    a[k & 3].sub(ak, make_float2(xk.x, xk.y));
+                    b[k & 3].sub(ak, make_float2(xk.z, xk.w));
+                }
+            }
+            a[0].merge(a[1]);
+            a[2].merge(a[3]);
+            a[0].merge(a[2]);
+            b[0].merge(b[1]);
+            b[2].merge(b[3]);
+            b[0].merge(b[2]);
+            const double r0 = f32_to_f64(a[0].value());
+            R[row * nr + c0] = r0;
+            mr = umax_(mr, abs_bits64(r0));
+            if (two) {
+                const double r1 = f32_to_f64(b[0].value());
+                R[row * nr + c0 + 1] = r1;
+                mr = umax_(mr, abs_bits64(r1));
+            }
+        }
+        __syncthreads();
+    }
+    df_wait<0>();
+    if (maxout) block_max3_df(mr, mx, mf, maxout);
+}
+
+// Variant of k_resid_btri_df2 for matrices kept as FP32 pairs (hi, lo) by the
+// warp-per-partition factorization (float2 [3][N][M][M]): the pairs are
+// copied straight into a double-buffered shared array, so only x and f are
+// split per call.
+template <int M>
+__global__ void __launch_bounds__(kDfThreads) k_resid_btri_dfs(long long N, int nr, int G, long long ntiles,
+                                                               const float2* __restrict__ As,
+                                                               const double* __restrict__ X,
+                                                               const double* __restrict__ F, double* __restrict__ R,
+                                                               unsigned long long* maxout) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int MM = M * M;
+    const int ncp = (nr + 1) / 2, cs = df_pair_shift(nr), pcp = 1 << cs;
+    const int V = M * nr;
+    const int nA = G * 3 * MM, nX = (G + 2) * V, nF = G * V;
+    float2* sA0 = reinterpret_cast<float2*>(smem);          // [G][3][M][M], two buffers
+    float2* sA1 = sA0 + nA;
+    double* raw0 = reinterpret_cast<double*>(sA1 + nA);     // x, f rows, two buffers
+    double* raw1 = raw0 + (nX + nF);
+    float4* sX = reinterpret_cast<float4*>(raw1 + (nX + nF));   // [G + 2][M][pcp]
+    auto issue = [&](long long t, float2* sA, double* raw) {
+        if (t < ntiles) {
+            const long long j0 = t * G;
+            const int g = (int)((N - j0) < G ? (N - j0) : G);
+            for (int c = threadIdx.x; c < g * 3 * (MM / 2); c += blockDim.x) {
+                const int blk = c / (MM / 2), piece = c % (MM / 2), gj = blk / 3, w = blk % 3;
+                df_cp16(sA + (gj * 3 + w) * MM + 2 * piece, As + (w * N + j0 + gj) * MM + 2 * piece);
+            }
+            const long long lo = (j0 - 1 > 0) ? j0 - 1 : 0, hi = (j0 + g + 1 < N) ? j0 + g + 1 : N;
+            double* dx = raw + (lo - (j0 - 1)) * V;
+            const double* sx = X + lo * V;
+            for (int c = threadIdx.x; c < (int)(hi - lo) * V / 2; c += blockDim.x) df_cp16(dx + 2 * c, sx + 2 * c);
+            const double* sf = F + j0 * V;
+            for (int c = threadIdx.x; c < g * V / 2; c += blockDim.x) df_cp16(raw + nX + 2 * c, sf + 2 * c);
+        }
+        df_commit();
+    };
+    unsigned long long mr = 0ull, mx = 0ull, mf = 0ull;
+    int buf = 0;
+    issue(blockIdx.x, sA0, raw0);
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, buf ^= 1) {
+        float2* sA = buf ? sA1 : sA0;
+        double* raw = buf ? raw1 : raw0;
+        issue(t + gridDim.x, buf ? sA0 : sA1, buf ? raw0 : raw1);
+        df_wait<1>();
+        __syncthreads();
+        const long long j0 = t * G;
+        const int g = (int)((N - j0) < G ? (N - j0) : G);
+        for (int idx = threadIdx.x; idx < ((g + 2) * M) << cs; idx += blockDim.x) {
+            const int cp = idx & (pcp - 1), qk = idx >> cs, q = qk / M, k = qk % M;
+            const long long row = j0 - 1 + q;
+            float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+            if (cp < ncp && row >= 0 && row < N) {
+                const double* src = raw + q * V + k * nr + 2 * cp;
+                const double v0 = src[0];
+                a = split_f64(v0);
+                unsigned long long m0 = abs_bits64(v0);
+                if (2 * cp + 1 < nr) {
+                    const double v1 = src[1];
+                    b = split_f64(v1);
+                    m0 = umax_(m0, abs_bits64(v1));
+                }
+                if (q >= 1 && q <= g) mx = umax_(mx, m0);
+            }
+            sX[idx] = make_float4(a.x, a.y, b.x, b.y);
+        }
+        __syncthreads();
+        const double* rf = raw + nX;
+        for (int u = threadIdx.x; u < ((g * M) << cs); u += blockDim.x) {
+            const int cp = u & (pcp - 1), gr = u >> cs, gj = gr / M, r = gr % M;
+            if (cp >= ncp) continue;
+            const long long row = (j0 + gj) * M + r;
+            const int c0 = 2 * cp;
+            const bool two = c0 + 1 < nr;
+            const double f0 = rf[(gj * M + r) * nr + c0], f1 = two ? rf[(gj * M + r) * nr + c0 + 1] : 0.0;
+            mf = umax_(mf, umax_(abs_bits64(f0), abs_bits64(f1)));
+            DF a[4], b[4];
+            a[0].init(split_f64(f0));
+            b[0].init(split_f64(f1));
+#pragma unroll
+            for (int qq = 1; qq < 4; ++qq) {
+                a[qq].init(make_float2(0.f, 0.f));
+                b[qq].init(make_float2(0.f, 0.f));
+            }
+#pragma unroll
+            for (int blk = 0; blk < 3; ++blk) {
+                const float2* Ar = sA + ((gj * 3 + blk) * M + r) * M;
+                const float4* xq = sX + (gj + blk) * M * pcp + cp;
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    const float2 ak = Ar[k];
+                    const float4 xk = xq[k * pcp];
+                    a[k & 3].sub(ak, make_float2(xk.x, xk.y));
+                    b[k & 3].sub(ak, make_float2(xk.z, xk.w));
+                }
+            }
+            a[0].merge(a[1]);
+            a[2].merge(a[3]);
+            a[0].merge(a[2]);
+            b[0].merge(b[1]);
+            b[2].merge(b[3]);
+            b[0].merge(b[2]);
+            const double r0 = f32_to_f64(a[0].value());
+            R[row * nr + c0] = r0;
+            mr = umax_(mr, abs_bits64(r0));
+            if (two) {
+                const double r1 = f32_to_f64(b[0].value());
+                R[row * nr + c0 + 1] = r1;
+                mr = umax_(mr, abs_bits64(r1));
+            }
+        }
+        __syncthreads();
+    }
+    df_wait<0>();
+    if (maxout) block_max3_df(mr, mx, mf, maxout);
+}
+
 template <typename K>
 cudaError_t launch_df(K kernel, size_t smem, long long ctas, cudaStream_t s) {
     if (smem > 48 * 1024) {
@@ -351,16 +582,87 @@ cudaError_t launch_df(K kernel, size_t smem, long long ctas, cudaStream_t s) {
 
 }  // namespace
 
+static size_t resid_dfs_smem(int m, int nr, int G) {
+    const int pcp = 1 << df_pair_shift(nr), V = m * nr;
+    const size_t nA = (size_t)G * 3 * m * m, nX = (size_t)(G + 2) * V, nF = (size_t)G * V;
+    return 2 * nA * sizeof(float2) + 2 * (nX + nF) * sizeof(double) + (size_t)(G + 2) * m * pcp * sizeof(float4);
+}
+
+cudaError_t launch_resid_btri_dfs(long long N, int m, int nr, const float2* As, const double* X, const double* F,
+                                  double* R, cudaStream_t s, unsigned long long* maxout) {
+    if (N <= 0) return cudaSuccess;
+    if (m != 16 || ((uintptr_t)As | (uintptr_t)X | (uintptr_t)F) & 15u) return cudaErrorInvalidValue;
+    int G = df_rows_per_cta(m, nr);
+    while (G > 1 && resid_dfs_smem(m, nr, G) > 180 * 1024) --G;
+    const long long ntiles = (N + G - 1) / G;
+    const size_t smem = resid_dfs_smem(m, nr, G);
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long per_sm = (long long)(200 * 1024) / (long long)smem;
+    if (per_sm > 8) per_sm = 8;
+    if (per_sm < 1) per_sm = 1;
+    long long grid = per_sm * sms;
+    if (grid > ntiles) grid = ntiles;
+    cudaError_t e = launch_df(k_resid_btri_dfs<16>, smem, grid, s);
+    if (e != cudaSuccess) return e;
+    k_resid_btri_dfs<16><<<(unsigned)grid, kDfThreads, smem, s>>>(N, nr, G, ntiles, As, X, F, R, maxout);
+    return cudaGetLastError();
+}
+
 size_t resid_df_smem(int kind, int m, int nr) {
     const int G = df_rows_per_cta(m, nr), pcp = 1 << df_pair_shift(nr);
     const size_t a = (size_t)G * (kind == 0 ? 3 : 2) * m * m * sizeof(float2);
     return a + (size_t)(G + 2) * m * pcp * sizeof(float4);
 }
 
+static size_t resid_df2_smem(int m, int nr, int G) {
+    const int pcp = 1 << df_pair_shift(nr), V = m * nr;
+    const size_t nA = (size_t)G * 3 * m * m, nX = (size_t)(G + 2) * V, nF = (size_t)G * V;
+    return 2 * (nA + nX + nF) * sizeof(double) + nA * sizeof(float2) + (size_t)(G + 2) * m * pcp * sizeof(float4);
+}
+
 cudaError_t launch_resid_btri_df(long long N, int m, int nr, const double* B, const double* D, const double* C,
                                  const double* X, const double* F, double* R, cudaStream_t s,
                                  unsigned long long* maxout) {
     if (N <= 0) return cudaSuccess;
+    const uintptr_t al = (uintptr_t)B | (uintptr_t)D | (uintptr_t)C | (uintptr_t)X | (uintptr_t)F;
+    if (m >= 8 && ((m * nr) % 2) == 0 && (al & 15u) == 0) {
+        // persistent pipelined kernel: a few CTAs per SM stride over tiles
+        // block rows per tile: enough units for the threads, within 180 KB of shared memory
+        int G = df_rows_per_cta(m, nr);
+        while (G > 1 && resid_df2_smem(m, nr, G) > 180 * 1024) --G;
+        const long long ntiles = (N + G - 1) / G;
+        const size_t smem = resid_df2_smem(m, nr, G);
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        long long per_sm = (long long)(200 * 1024) / (long long)smem;
+        if (per_sm > 8) per_sm = 8;
+        if (per_sm < 1) per_sm = 1;
+        long long grid = per_sm * sms;
+        if (grid > ntiles) grid = ntiles;
+        cudaError_t e = cudaSuccess;
+        switch (m) {
+            case 8:
+                e = launch_df(k_resid_btri_df2<8>, smem, grid, s);
+                if (e == cudaSuccess)
+                    k_resid_btri_df2<8><<<(unsigned)grid, kDfThreads, smem, s>>>(N, nr, G, ntiles, B, D, C, X, F, R, maxout);
+                break;
+            case 16:
+                e = launch_df(k_resid_btri_df2<16>, smem, grid, s);
+                if (e == cudaSuccess)
+                    k_resid_btri_df2<16><<<(unsigned)grid, kDfThreads, smem, s>>>(N, nr, G, ntiles, B, D, C, X, F, R, maxout);
+                break;
+            default:
+                e = launch_df(k_resid_btri_df2<32>, smem, grid, s);
+                if (e == cudaSuccess)
+                    k_resid_btri_df2<32><<<(unsigned)grid, kDfThreads, smem, s>>>(N, nr, G, ntiles, B, D, C, X, F, R, maxout);
+                break;
+        }
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
     const int G = df_rows_per_cta(m, nr);
     const long long ctas = (N + G - 1) / G;
     const size_t smem = resid_df_smem(0, m, nr);

@@ -70,17 +70,27 @@ __device__ __forceinline__ void stage_blk16(double* dst, const double* src, int 
 }
 
 // FP64 staging block -> FP32 block (zeros when absent): lane l converts row
-// l / 2, columns (l % 2) * 8 .. + 7.
-__device__ __forceinline__ void convert_blk16(float* dst, const double* src, bool present, int lane) {
+// l / 2, columns (l % 2) * 8 .. + 7.  With gs (the block's place in the split
+// copy of the matrix) the (hi, lo) pairs of the present entries are stored too.
+__device__ __forceinline__ void convert_blk16(float* dst, const double* src, bool present, int lane,
+                                              float2* gs = nullptr) {
     const int rr = lane >> 1, c0 = (lane & 1) * 8;
     float o[8];
     if (present) {
         const double2* s = reinterpret_cast<const double2*>(src + rr * WarpF16::SR + c0);
+        float2 sp[8];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const double2 v = s[q];
-            o[2 * q] = trunc_f32(v.x);
-            o[2 * q + 1] = trunc_f32(v.y);
+            sp[2 * q] = split_f64(v.x);
+            sp[2 * q + 1] = split_f64(v.y);
+            o[2 * q] = sp[2 * q].x;
+            o[2 * q + 1] = sp[2 * q + 1].x;
+        }
+        if (gs != nullptr) {
+            float4* g4 = reinterpret_cast<float4*>(gs + rr * 16 + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) g4[q] = make_float4(sp[2 * q].x, sp[2 * q].y, sp[2 * q + 1].x, sp[2 * q + 1].y);
         }
     } else {
 #pragma unroll
@@ -174,9 +184,11 @@ __device__ __forceinline__ void factor_warp16_body(const LevelArgs& a, const lon
         cp_async_wait<1>();
         __syncwarp();
         const bool hB = needB(j), hC = needC(j);
-        convert_blk16(sm.cv[0], sm.stage[buf][0], hB, lane);
-        convert_blk16(sm.cv[1], sm.stage[buf][1], true, lane);
-        convert_blk16(sm.cv[2], sm.stage[buf][2], hC, lane);
+        float2* gsp = reinterpret_cast<float2*>(a.As);
+        const long long rows = a.N;
+        convert_blk16(sm.cv[0], sm.stage[buf][0], hB, lane, gsp ? gsp + (0 * rows + j) * MM : nullptr);
+        convert_blk16(sm.cv[1], sm.stage[buf][1], true, lane, gsp ? gsp + (1 * rows + j) * MM : nullptr);
+        convert_blk16(sm.cv[2], sm.stage[buf][2], hC, lane, gsp ? gsp + (2 * rows + j) * MM : nullptr);
         __syncwarp();
         float bro[16], a32[32];
         read_row16(bro, &sm.cv[0][r * FR]);
@@ -295,6 +307,20 @@ __device__ __forceinline__ void factor_warp16_body(const LevelArgs& a, const lon
         __syncwarp();
     }
     cp_async_wait<0>();
+    if (a.As != nullptr && pt.hasR && (a.phases <= 1 || a.phase == a.phases - 1)) {
+        // the split copy also holds the right separator row e (read only by the residual)
+        const long long e = pt.e, o = (e - a.shift) * MM;
+        __syncwarp();
+        stage_blk16(sm.stage[0][0], a.B + o, lane);
+        stage_blk16(sm.stage[0][1], a.D + o, lane);
+        stage_blk16(sm.stage[0][2], a.C + o, lane);
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncwarp();
+        float2* gsp = reinterpret_cast<float2*>(a.As);
+        for (int w = 0; w < 3; ++w) convert_blk16(sm.cv[w], sm.stage[0][w], true, lane, gsp + (w * a.N + e) * MM);
+        __syncwarp();
+    }
     if (!hasL) return;
     if (wpend) {
         // the W step of the last row: Pf += W Zc_{je-1}, W_{je} = -W Y_{je-1}
