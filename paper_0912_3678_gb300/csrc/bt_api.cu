@@ -62,6 +62,7 @@ struct bt_plan_s {
     unsigned long long* rmax = nullptr; // [kMaxSlots][3] max |r|, |x|, |f| of the last residual (bit patterns)
     unsigned long long* amax = nullptr; // [kMaxSlots][3] ||A||_inf (bit pattern) in word 0
     bool anorm_valid = false;
+    bool anorm_fac = false;             // ||A||_inf was taken by the last level-0 factorization
     int async_sweeps = 0;
     double eta_tol = -1.0;              // backward-error stopping threshold (< 0: default)
     double* partial = nullptr;          // [2*1024]
@@ -191,6 +192,7 @@ void layout(bt_plan_s* P, Arena& ar) {
         v0.a.Hv = ar.take(sizeof(float) * rows0 * m * nr);
         v0.a.Hw = ar.take(sizeof(float) * pa * m * nr);
         v0.a.As = ar.take(2 * sizeof(float) * 3 * rows0 * mm);
+        v0.a.nrm = (double*)ar.take(sizeof(double) * 2 * pa);
     }
     for (int l = 0; l <= P->nlev; ++l) {
         Level& v = P->lv[l];
@@ -688,7 +690,20 @@ bt_status run_factor(bt_plan_s* P, bool level0_done = false) {
             break;
         }
         cudaError_t e = cudaSuccess;
-        if (!(l == 0 && level0_done)) e = launch(P, K_FACTOR, l, 1, [&] { return L->factor(v.a, v.low, P->stream); });
+        // warp kernels at level 0 take ||A||_inf while they convert the rows
+        const bool wn = (l == 0) && !level0_done && P->warp && L->warp_ok && L->warp_ok(v.a, v.low);
+        P->anorm_fac = false;
+        if (wn) {
+            e = cudaMemsetAsync(P->amax, 0, kSlotWords * sizeof(unsigned long long), P->stream);
+            v.a.amax = P->amax;
+        }
+        if (e == cudaSuccess && !(l == 0 && level0_done))
+            e = launch(P, K_FACTOR, l, 1, [&] { return L->factor(v.a, v.low, P->stream); });
+        v.a.amax = nullptr;
+        if (wn && e == cudaSuccess) {
+            P->anorm_valid = true;
+            P->anorm_fac = true;
+        }
         if (e == cudaSuccess && P->kind == 0 && l < P->nlev)
             e = launch(P, K_ASSEMBLE, l, 1, [&] { return L->assemble(v.a, v.low, P->stream); });
         if (e != cudaSuccess) return rejoin(from_cuda(e));
@@ -839,7 +854,7 @@ bt_status run_residual(bt_plan_s* P, const double* F, const double* X, double* R
 
 // ||A||_inf of the factored matrices (once per factorization).
 bt_status ensure_anorm(bt_plan_s* P, bool force) {
-    if (P->anorm_valid && !force) return BT_OK;
+    if (P->anorm_valid && (!force || P->anorm_fac)) return BT_OK;
     cudaError_t e = cudaMemsetAsync(P->amax, 0, kSlotWords * sizeof(unsigned long long), P->stream);
     if (e == cudaSuccess)
         e = launch(P, K_NORM, 0, 1, [&] {
@@ -884,6 +899,29 @@ double backward_error(const bt_plan_s* P) {
     return den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
 }
 
+// One refinement correction from the residual in Rbuf: d = solve(r), X += d,
+// and (||d||^2, ||x||^2) in P->norms.  With the warp kernels at level 0 the
+// back substitution applies the update itself and leaves per-partition norm
+// partials; otherwise d goes through Dbuf and the update kernel.
+bt_status run_correction(bt_plan_s* P, double* X, int nr, long long n) {
+    Level& v0 = P->lv[0];
+    const bool w = P->warp && P->nlev >= 1 && P->L->warp_ok && P->L->warp_ok(v0.a, v0.low) && v0.a.nrm;
+    if (w) {
+        v0.a.accum = 1;
+        bt_status st = run_solve(P, P->Rbuf, X, nr);
+        v0.a.accum = 0;
+        if (st != BT_OK) return st;
+        cudaError_t e = launch(P, K_IR, 0, 1,
+                               [&] { return bt::launch_reduce_pairs((int)v0.a.p, v0.a.nrm, P->norms, P->stream); });
+        return from_cuda(e);
+    }
+    bt_status st = run_solve(P, P->Rbuf, P->Dbuf, nr);
+    if (st != BT_OK) return st;
+    cudaError_t e = launch(P, K_IR, 0, 2,
+                           [&] { return bt::launch_ir_update(n, X, P->Dbuf, P->partial, P->norms, P->stream); });
+    return from_cuda(e);
+}
+
 bt_status run_refine(bt_plan_s* P, const double* F, double* X, int nr, double tol, int maxit, int* iters,
                      double* relcorr) {
     // x = solve(f); then repeat: r = f - A x (FP64); stop when the normwise
@@ -914,11 +952,8 @@ bt_status run_refine(bt_plan_s* P, const double* F, double* X, int nr, double to
         if (eta <= eta_tol) return BT_OK;
         if (it > 0 && rel <= tol) return BT_OK;
         if (it == maxit) return BT_ERR_NOT_CONVERGED;
-        st = run_solve(P, P->Rbuf, P->Dbuf, nr);
+        st = run_correction(P, X, nr, n);
         if (st != BT_OK) return st;
-        e = launch(P, K_IR, 0, 2,
-                   [&] { return bt::launch_ir_update(n, X, P->Dbuf, P->partial, P->norms, P->stream); });
-        if (e != cudaSuccess) return from_cuda(e);
     }
 }
 
@@ -929,11 +964,8 @@ bt_status run_refine_async(bt_plan_s* P, const double* F, double* X, int nr, int
     const long long n = P->lv[0].rows * P->m * nr;
     for (int it = 0; it < sweeps && st == BT_OK; ++it) {
         st = run_residual(P, F, X, P->Rbuf, nr, nullptr, P->prec != BT_FP64);
-        if (st == BT_OK) st = run_solve(P, P->Rbuf, P->Dbuf, nr);
+        if (st == BT_OK) st = run_correction(P, X, nr, n);
         if (st != BT_OK) return st;
-        cudaError_t e = launch(P, K_IR, 0, 2,
-                               [&] { return bt::launch_ir_update(n, X, P->Dbuf, P->partial, P->norms, P->stream); });
-        if (e != cudaSuccess) return from_cuda(e);
     }
     if (sweeps == 0) {
         cudaError_t e = cudaMemsetAsync(P->norms, 0, 2 * sizeof(double), P->stream);

@@ -57,6 +57,12 @@ struct LevelArgs {
     // the level matrix split into FP32 pairs (hi, lo) for the double-float
     // refinement residual: float2 [3][rows][m][m] (B, D, C); null: not kept
     void* As;
+    // warp kernels: ||A||_inf maxima slots filled by the factorization (null: not
+    // computed there); back substitution in update form X += d with per-partition
+    // (||d||^2, ||x||^2) partials in nrm[2 i] (accum != 0)
+    unsigned long long* amax;
+    int accum;
+    double* nrm;
 };
 
 }  // namespace bt

@@ -585,6 +585,11 @@ int ir_update_blocks(long long n) {
     if (b < 1) b = 1;
     return (int)b;
 }
+cudaError_t launch_reduce_pairs(int n, const double* partial, double* out, cudaStream_t s) {
+    k_reduce_pairs<<<1, 256, 0, s>>>(n, partial, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ir_update(long long n, double* X, const double* Dc, double* partial, double* out,
                              cudaStream_t s) {
     const int nb = ir_update_blocks(n);

@@ -18,6 +18,8 @@ cudaError_t launch_resid_babd(long long N, int m, int nr, const double* S, const
 cudaError_t launch_norm_inf(int kind, long long N, int m, const double* A0, const double* A1, const double* A2,
                             const double* B0, const double* B1, unsigned long long* out, cudaStream_t s);
 int ir_update_blocks(long long n);
+// out[0..1] = sums over the n pairs partial[2i], partial[2i+1] (one CTA, fixed order)
+cudaError_t launch_reduce_pairs(int n, const double* partial, double* out, cudaStream_t s);
 cudaError_t launch_ir_update(long long n, double* X, const double* Dc, double* partial, double* out,
                              cudaStream_t s);
 size_t babd_direct_smem(int m, int nr);

@@ -25,6 +25,7 @@
 // one row ahead, and converted to FP32 by integer operations.
 #pragma once
 #include "bt_bcr.cuh"
+#include "bt_misc.h"
 
 namespace bt {
 
@@ -150,6 +151,7 @@ __device__ __forceinline__ void factor_warp16_body(const LevelArgs& a, const lon
 #pragma unroll
     for (int c = 0; c < 16; ++c) cp[c] = 0.f;
     bool wpend = false;    // the W step of the previous row is still to be taken
+    float amax_run = 0.f;  // largest row sum of |A| over this partition's rows (lanes 0-15)
     if (jb < je) issue(jb, 0);
     if (jb > pt.s) {
         // a later phase: resume from the stored Y_{jb-1}, Zc_{jb-1} and the running W, Pf
@@ -200,6 +202,13 @@ __device__ __forceinline__ void factor_warp16_body(const LevelArgs& a, const lon
             read_row16(t, &sm.cv[2][r * FR]);
 #pragma unroll
             for (int c = 0; c < 16; ++c) a32[16 + c] = t[c];
+            if (a.amax != nullptr) {
+                // row r of block row j of A (entries truncated toward zero): |B| + |D| + |C|
+                float rs = 0.f;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) rs += fabsf(bro[c]) + fabsf(a32[c]) + fabsf(a32[16 + c]);
+                amax_run = fmaxf(amax_run, rs);
+            }
         } else {
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
@@ -320,6 +329,29 @@ __device__ __forceinline__ void factor_warp16_body(const LevelArgs& a, const lon
         float2* gsp = reinterpret_cast<float2*>(a.As);
         for (int w = 0; w < 3; ++w) convert_blk16(sm.cv[w], sm.stage[0][w], true, lane, gsp + (w * a.N + e) * MM);
         __syncwarp();
+        if (a.amax != nullptr && h == 0) {
+            float t0[16], t1[16], t2[16];
+            read_row16(t0, &sm.cv[0][r * FR]);
+            read_row16(t1, &sm.cv[1][r * FR]);
+            read_row16(t2, &sm.cv[2][r * FR]);
+            float rs = 0.f;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) rs += fabsf(t0[c]) + fabsf(t1[c]) + fabsf(t2[c]);
+            amax_run = fmaxf(amax_run, rs);
+        }
+        __syncwarp();
+    }
+    if (a.amax != nullptr) {
+        // as a double bit pattern, like the residual maxima slots
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) amax_run = fmaxf(amax_run, __shfl_xor_sync(FULL, amax_run, off));
+        if (lane == 0) {
+            const unsigned u = __float_as_uint(amax_run);
+            const unsigned e8 = (u >> 23) & 0xffu;
+            const unsigned long long bits =
+                (e8 == 0u) ? 0ull : (((unsigned long long)(e8 + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29));
+            atomicMax(a.amax + 3 * ((blockIdx.x * WarpF16::WARPS + (threadIdx.x >> 5)) % kMaxSlots), bits);
+        }
     }
     if (!hasL) return;
     if (wpend) {
@@ -516,6 +548,7 @@ __device__ __forceinline__ void solve_bwd_w16_body(const LevelArgs& a, const lon
     float* xa = sm.xa + r * SW + cb;   // x_{j+1}
     float* xb = sm.xb + r * SW + cb;   // x_L
     float v[NH];
+    float dd = 0.f, xx = 0.f;   // update form: sums of d^2 and of the updated x^2
     if (pt.hasR) {
         const double* xr = a.Xn + i * E + r * nr;
         double* xo = a.X + pt.e * E + r * nr;
@@ -523,7 +556,17 @@ __device__ __forceinline__ void solve_bwd_w16_body(const LevelArgs& a, const lon
         for (int q = 0; q < NH; ++q) {
             const double d = (cb + q < nr) ? xr[cb + q] : 0.0;
             v[q] = trunc_f32(d);
-            if (cb + q < nr) xo[cb + q] = d;
+            if (cb + q < nr) {
+                if (a.accum) {
+                    const double xn = xo[cb + q] + d;
+                    xo[cb + q] = xn;
+                    const float xf = trunc_f32(xn);
+                    dd = fmaf(v[q], v[q], dd);
+                    xx = fmaf(xf, xf, xx);
+                } else {
+                    xo[cb + q] = d;
+                }
+            }
         }
     } else {
 #pragma unroll
@@ -560,10 +603,33 @@ __device__ __forceinline__ void solve_bwd_w16_body(const LevelArgs& a, const lon
         __syncwarp();          // x_{j+1} fully read
         put_vec<NH>(xa, x);
         double* xo = a.X + j * E + r * nr;
+        if (a.accum) {
 #pragma unroll
-        for (int q = 0; q < NH; ++q)
-            if (cb + q < nr) xo[cb + q] = (double)x[q];
+            for (int q = 0; q < NH; ++q)
+                if (cb + q < nr) {
+                    const double xn = xo[cb + q] + (double)x[q];
+                    xo[cb + q] = xn;
+                    const float xf = trunc_f32(xn);
+                    dd = fmaf(x[q], x[q], dd);
+                    xx = fmaf(xf, xf, xx);
+                }
+        } else {
+#pragma unroll
+            for (int q = 0; q < NH; ++q)
+                if (cb + q < nr) xo[cb + q] = (double)x[q];
+        }
         __syncwarp();
+    }
+    if (a.accum) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            dd += __shfl_xor_sync(0xffffffffu, dd, off);
+            xx += __shfl_xor_sync(0xffffffffu, xx, off);
+        }
+        if (lane == 0) {
+            a.nrm[2 * i] = (double)dd;
+            a.nrm[2 * i + 1] = (double)xx;
+        }
     }
 }
 
