@@ -4,10 +4,15 @@ Default workload: block tridiagonal A x = f with m = 16 blocks, N = 16384 block
 rows (n = 262144 unknowns) and 8 right-hand sides; D_j = 4I + G/4, B_j, C_j =
 G/4 (seeded synthetic data).  One step = the whole hot path on one system:
 factor (local block LU with spikes, reduced systems, recursion) + solve, for
-two paths: "fp64" (every step in FP64) and "fp32_ir" (FP32 local factors, FP64
-reduced systems, FP64-residual iterative refinement).  The headline value is
-the faster path whose normwise relative error against the FP64 oracle is
-<= 1e-10.  Metric: unknowns x right-hand sides solved per second.
+three paths: "fp64" (every step in FP64), "fp32_ir" (FP32 local factors, FP64
+reduced-system factorization, refinement with a double-float residual) and
+"bf16_ir" (as fp32_ir with BF16 tensor-core Schur products).  The headline
+value is the faster path whose normwise relative error against the FP64
+oracle is <= 1e-10.  Metric: unknowns x right-hand sides solved per second.
+The same JSON line carries, under "configs", short runs of the other
+workloads (1024 scalar systems of n = 2^16, the BABD boundary value problem,
+the 4096 uneven systems and the served stream with p50/p99 latency);
+--no-configs leaves them out.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload block16|block|babd8|scalar|scalar_batch|batch|serve|pivot|parareal|cyclic]
@@ -89,7 +94,49 @@ def _workload(name: str, m_opt=None, N_opt=None, nr_opt=None):
 # configuration reports null; an entry is dropped when its kernel changes.
 MEASURED_TRAFFIC = {
     ("block16", "fp64", "factor", 608): 150.0e6,
+    ("block16", "fp32_ir", "residual", 608): 141.5e6,
 }
+
+
+def _cpu_info():
+    """Host CPU model and the cores this process may use."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                k = ln.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "processor name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+            for ln in out.splitlines():
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    try:
+        ncpu = len(os.sched_getaffinity(0))
+    except AttributeError:
+        ncpu = os.cpu_count()
+    return {"cpu_model": model, "nproc": ncpu}
+
+
+def _derived_peaks(dev, sm_mhz):
+    """FP64 and FP32 FMA peaks (TFLOP/s) from this device's SM count and the SM
+    clock sampled during the timed region (2 FP64 and 128 FP32 FMA per clock
+    per SM on this GPU; one FMA = 2 flop)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    ghz = (sm_mhz or 2070.0) / 1e3
+    return {"sms": sms, "sm_ghz": ghz, "fp64": sms * 2 * 2 * ghz / 1e3, "fp32": sms * 128 * 2 * ghz / 1e3}
 
 
 def _factor_flops_per_row(m: int) -> float:
@@ -181,14 +228,14 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w["desc"], "path": "sequential FP64 oracle (block Thomas / BABD GEPP), 1 core"},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"the full workload, {args.steps} timed solves"},
+                         "sample": f"the full workload, {args.steps} timed solves", **_cpu_info()},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
 
 
-def run_batch(args):
+def run_batch(args, emit=True):
     """Batched workload: 4096 uneven independent systems (n log-uniform, m from {1,4,8,16,32},
     50/50 FP64 / BF16+refinement), generated on the device, one graph launch
     per step.  Accuracy: a sample of systems against the oracle."""
@@ -273,10 +320,11 @@ def run_batch(args):
         per_s = unknowns / (ms / 1e3)
         gbs = 40.0 * per_s / 1e9
         ach = 15.0 * per_s / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+        pk = _derived_peaks(dev, None)
+        roof = {"bound": "alu", "achieved": ach, "peak": pk["fp64"], "unit": "TFLOP/s",
+                "frac": ach / pk["fp64"], "traffic": None,
                 "kernel": "whole step (factor + solve, all levels), 15 FP64 flop per unknown",
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                "peak_source": f"derived: {pk['sms']} SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (maximum clock)",
                 "hbm": {"achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": gbs / HBM_PEAK_GBS,
                         "bytes_per_unknown": 40}}
     else:
@@ -294,10 +342,13 @@ def run_batch(args):
             "statuses_ok": sum(1 for x in status if x == 0), "systems": len(status),
             "rel_err_sample_max": worst, "roofline": roof,
             "cpu_baseline": {"value": n_or / t_or if t_or else None, "unit": "unknowns/s", "cores": 1,
-                             "kind": "oracle", "sample": f"{len(sample)} systems of the batch"}}
-    print(json.dumps(line))
+                             "kind": "oracle", "sample": f"{len(sample)} systems of the batch", **_cpu_info()}}
+    if emit:
+        print(json.dumps(line))
     b.close()
-    return 0
+    del b, systems
+    torch.cuda.empty_cache()
+    return line
 
 
 def _timed(step, warmup, steps):
@@ -459,7 +510,7 @@ def run_cyclic(args):
     return 0
 
 
-def run_serve(args):
+def run_serve(args, emit=True):
     """Served workload: Poisson arrivals of BVP solves (m in {4,8,16}, N log-uniform
     [1e3, 5e5], 1-32 RHS, 30% factorization reuse) replayed in real time."""
     import torch
@@ -485,8 +536,10 @@ def run_serve(args):
                                    f"{args.serve_seconds:g} s, m in {{4,8,16}}, N log-uniform [1e3,5e5], "
                                    "1-32 RHS, 30% reuse, 150 GB cap, 8 streams"},
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "served": st}
-    print(json.dumps(line))
-    return 0
+    if emit:
+        print(json.dumps(line))
+    torch.cuda.empty_cache()
+    return line
 
 
 def main():
@@ -507,7 +560,9 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-prec", default="fp64")
-    ap.add_argument("--paths", default="fp64,fp32_ir")
+    ap.add_argument("--paths", default="fp64,fp32_ir,bf16_ir")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="headline only: skip the other workloads' summary in the JSON line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="use the built-in partitioning instead of the autotuner")
     ap.add_argument("--tuning", default=None,
@@ -521,9 +576,11 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.workload in ("batch", "scalar_batch"):
-        return run_batch(args)
+        run_batch(args)
+        return 0
     if args.workload == "serve":
-        return run_serve(args)
+        run_serve(args)
+        return 0
     if args.workload == "pivot":
         return run_pivot(args)
     if args.workload == "parareal":
@@ -546,6 +603,81 @@ def main():
         _build.build()
     if dist is not None:
         dist.barrier()
+    line = _measure(args, dist, ws, rank, local)
+    if rank == 0:
+        if args.workload == "block16" and not args.no_configs:
+            line["configs"] = _other_configs(args)
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def _other_configs(args):
+    """The other workloads, each measured briefly after the headline on the
+    same GPU (fewer steps, built-in partitioning for the batches): the scalar
+    throughput batch, the BABD boundary value problem, the uneven batch and
+    the served stream.  One summary per workload: its metric, error against
+    the oracle, roofline, and p50/p99 where it has latencies."""
+    import copy
+
+    import torch
+    keys = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "dtype", "rel_err_vs_oracle",
+            "rel_err_sample_max", "backward_error", "roofline", "cpu_baseline", "p50_ms", "p99_ms", "statuses_ok",
+            "systems", "e2e")
+    out = {}
+
+    def summary(line, extra=None):
+        d = {k: line[k] for k in keys if k in line and line[k] is not None}
+        d["workload"] = line.get("config", {}).get("workload")
+        if "paths" in line:
+            d["paths"] = {p: {k: v for k, v in q.items() if k in ("ms_per_step", "value", "rel_err_vs_oracle")}
+                          for p, q in line["paths"].items()}
+            d["path"] = line.get("config", {}).get("path")
+        if extra:
+            d.update(extra)
+        return d
+
+    def run(name, fn):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as exc:            # a failed extra leaves the headline intact
+            out[name] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+        out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+        torch.cuda.empty_cache()
+
+    def babd():
+        a = copy.copy(args)
+        a.workload, a.paths, a.tuning, a.cpu_seconds = "babd8", "fp64,fp32_ir", None, 3.0
+        return summary(_measure(a, None, 1, 0, int(os.environ.get("LOCAL_RANK", "0"))))
+
+    def batch(scalar):
+        a = copy.copy(args)
+        a.workload = "scalar_batch" if scalar else "batch"
+        a.steps, a.warmup, a.no_tune = 3, 2, True
+        return summary(run_batch(a, emit=False), {"tuning": "built-in"})
+
+    def serve(rate, seconds):
+        a = copy.copy(args)
+        a.serve_rate, a.serve_seconds, a.serve_prec = rate, seconds, "fp64"
+        return summary(run_serve(a, emit=False))
+
+    run("scalar_batch_1024x65536", lambda: batch(True))
+    run("babd_m8_N262144", babd)
+    run("batch_4096_uneven", lambda: batch(False))
+    run("serve_2000rps", lambda: serve(2000.0, 1.0))
+    run("serve_200rps", lambda: serve(200.0, 2.0))
+    return out
+
+
+def _measure(args, dist, ws, rank, local):
+    """One workload, every path of --paths: the timed captured step, the
+    end-to-end host-array step, per-kernel times, the roofline of the
+    dominant level-0 kernel and (rank 0) the oracle baseline and errors.
+    Returns the JSON line (None on ranks other than 0)."""
+    import torch
+    dev = torch.device(f"cuda:{local}")
     import paper_0912_3678_gb300 as bt
     from paper_0912_3678_gb300 import dist as bdist
 
@@ -729,9 +861,7 @@ def main():
         plan.close()
 
     if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
-        return 0
+        return None
 
     # ---- CPU baseline: the oracle on the host cores, bounded sample; its
     # solution also gives each path's error against plain FP64.
@@ -746,14 +876,14 @@ def main():
         t0 = time.perf_counter()
         ref = oracle_solve()
         first = time.perf_counter() - t0
-        reps = max(1, min(50, int(10.0 / max(first, 1e-3))))
+        reps = max(1, min(50, int(getattr(args, "cpu_seconds", 10.0) / max(first, 1e-3))))
         t0 = time.perf_counter()
         for _ in range(reps):
             oracle_solve()
         per = (time.perf_counter() - t0) / reps
         cpu = {"value": w["unknowns"] / per, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"the full workload solved {reps + 1} times (about {per * (reps + 1):.1f} s), "
-                         "single-threaded C, FP64"}
+                         "single-threaded C, FP64", **_cpu_info()}
 
     import oracle as _o
     for prec, r in results.items():
@@ -767,53 +897,69 @@ def main():
     # roofline of the dominant level-0 kernel of the headline path (largest
     # time per step among factor / forward solve / back substitution / FP64
     # residual), on its algorithmic flop count and the peak of its arithmetic
-    fp64_peak = FP64_PEAK_TFLOPS
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    pk = _derived_peaks(dev, (r["clocks"] or {}).get("sm_mhz"))
+    fp64_peak, fp32_peak = pk["fp64"], pk["fp32"]
     if w["kind"] == "btri":
         local_rows = N - (r["levels"][0][1] - 1)
     else:
         local_rows = N - r["levels"][0][1]
+    refined = head != "fp64"
     if w["kind"] == "btri":
         flops_per = {
             "factor": _factor_flops_per_row(m) * local_rows,          # (2/3+2+2) m^3 + 4 m^3 per local row
             "solve_fwd": 6.0 * m * m * nr * local_rows,                # 2 matvecs + top-row sweep per row
             "solve_bwd": 4.0 * m * m * nr * local_rows,                # 2 matvecs per row
-            "residual": 6.0 * m * m * nr * N,                          # 3 m^2 nrhs FMA per block row, FP64
+            # FP64 residual: 3 m^2 nrhs FMA per block row.  Refined paths: the same terms in
+            # double-float arithmetic on the FP32 pipe, 15 FP32 flop per term (TwoProduct
+            # 1 FMUL + 1 FMA, two cross-term FMAs, TwoSum 6 FADD, 2 FADD into the second sum)
+            "residual": (15.0 if refined else 2.0) * 3 * m * m * nr * N,
         }
+        bytes_per = {"residual": 8.0 * (3 * m * m * N + 3 * N * m * nr)}   # A, x, f read; r written
     elif (tunings.get(head) or {}).get("reduced"):
         pairs = N // 2                                                  # first cyclic-reduction level
         flops_per = {
             "factor": (2.0 / 3.0 + 2.0 + 2.0) * m ** 3 * pairs,        # LU of R_2k, R^-1 S_2k, S_2k+1 T
             "solve_fwd": 4.0 * m * m * nr * pairs,                     # R^-1 r_2k, S_2k+1 u
             "solve_bwd": 2.0 * m * m * nr * pairs,                     # T y_2k
-            "residual": 4.0 * m * m * nr * (N + 1),
+            "residual": (15.0 if refined else 2.0) * 2 * m * m * nr * (N + 1),
         }
+        bytes_per = {"residual": 8.0 * (2 * m * m * N + 3 * (N + 1) * m * nr)}
     else:
         flops_per = {
             "factor": (2.0 / 3.0 + 4.0) * m ** 3 * local_rows,         # LU of R_j, propagator, spike product
             "solve_fwd": 4.0 * m * m * nr * local_rows,                # 2 matvecs per step
             "solve_bwd": 2.0 * m * m * nr * local_rows,                # 1 matvec per step
-            "residual": 4.0 * m * m * nr * (N + 1),                    # 2 m^2 nrhs FMA per block row, FP64
+            "residual": (15.0 if refined else 2.0) * 2 * m * m * nr * (N + 1),
         }
+        bytes_per = {"residual": 8.0 * (2 * m * m * N + 3 * (N + 1) * m * nr)}
     cand = {k: v for k, v in r["lvl0"].items() if v[1] > 0}
     roof = None
     if cand:
         dom = max(cand, key=lambda k: cand[k][0])
         t_launch = cand[dom][0] / cand[dom][1] / 1e3
-        is64 = head == "fp64" or dom == "residual"
+        is64 = not refined
         peak = fp64_peak if is64 else fp32_peak
         ach = flops_per[dom] / t_launch / 1e12
+        what = ("FP64" if is64 else ("FP32 double-float" if dom == "residual" else "FP32"))
         roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": MEASURED_TRAFFIC.get((args.workload, head, dom, r["levels"][0][1])),
-                "kernel": f"level-0 {dom} ({'FP64' if is64 else 'FP32'})",
-                "peak_source": ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (probe measured 1.20)"
-                                if is64 else "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz"),
+                "kernel": f"level-0 {dom} ({what})",
+                "peak_source": (f"derived: {pk['sms']} SMs x {2 if is64 else 128} {'FP64' if is64 else 'FP32'} "
+                                f"FMA/clk x 2 flop x {pk['sm_ghz']:.3f} GHz (median SM clock sampled during "
+                                f"the timed steps)"),
                 "launch_ms": t_launch * 1e3}
+        if dom in bytes_per:
+            gbs = bytes_per[dom] / t_launch / 1e9
+            roof["hbm"] = {"achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": gbs / HBM_PEAK_GBS,
+                           "bytes_per_launch": bytes_per[dom], "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    st = sorted(r["ms_steps"])
+    p50 = float(np.percentile(st, 50)) if st else None
+    p99 = float(np.percentile(st, 99)) if st else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if head == "fp64" else "f32+f64",
-        "data": "synthetic",
+        "data": "synthetic", "p50_ms": p50, "p99_ms": p99,
         "config": {"workload": w["desc"], "path": head, "l2": "flushed (256 MB write) between timed steps",
                    "parallelism": f"replicas x{ws}", "levels": r["levels"],
                    "tuning": tunings.get(head, "built-in"),
@@ -833,10 +979,7 @@ def main():
                       "graph": q["graph"], "converged": q["converged"],
                       "launches_per_step": q["launches"]} for p, q in results.items()},
     }
-    print(json.dumps(line))
-    if dist is not None:
-        dist.destroy_process_group()
-    return 0
+    return line
 
 
 if __name__ == "__main__":
