@@ -22,6 +22,10 @@ with a coarse mesh of p equal intervals tau_i = i T / p (Eq. (coarse)).
               reduced system (redsys) iteratively and returns every iterate.
 * ``laplacian`` / ``eig_*``: the 1-D Dirichlet heat operator and its closed
               form eigenpairs, for the pins.
+* ``gam3_coefficients``, ``bvm_blocks``, ``bvm_rhs``, ``bvm_sequential``:
+              the parallel IVP solver of Sec. 3 with a block Boundary Value
+              Method as the local solver (general block tridiagonal M_i):
+              the discrete problem (My) solved by its sequential recursion.
 """
 from __future__ import annotations
 
@@ -115,3 +119,93 @@ def parareal(dl, d, du, y0, g0, g1, T: float, p: int, nfine: int, ncoarse: int, 
             Un.append(Gi(i, Un[i]) + Fv[i] - Gv[i])
         iters.append(np.array(Un))
     return np.array(iters)
+
+
+# --------------------------------------------------------------------------
+# Parallel IVP solver with a block Boundary Value Method (Sec. 3, Eqs.
+# (M_iy_i), (My)) for y' = L y + g(t), L a constant m x m matrix, y(0) = y0.
+# Coarse mesh of p equal intervals, N steps of h = T / (p N) in each.
+#
+# Method: the generalized Adams BVM with k = 2 steps (nu = 1 initial value)
+# as main formula,
+#     y_n - y_{n-1} = h (b0 f_{n-1} + b1 f_n + b2 f_{n+1}),  n = 1..N-1,
+# its coefficients fixed by exactness on polynomials of degree <= 3 (order
+# 3), and the trapezoidal rule as the final additional formula
+#     y_N - y_{N-1} = h/2 (f_{N-1} + f_N),
+# which keeps M_i block tridiagonal.  With f = L y + g, block row n of M_i is
+#     B_n y_{n-1} + D_n y_n + C_n y_{n+1} = r_n,
+# and the row n = 1 term B_1 y_0 is moved to the right: v_i = -B_1.
+# --------------------------------------------------------------------------
+def gam3_coefficients():
+    """(b0, b1, b2) as exact fractions: exactness of the main formula on
+    y = t^q, q = 1..3, with the nodes t_{n-1} = 0, t_n = 1, t_{n+1} = 2 (h = 1),
+    i.e. y(1) - y(0) = 1 = sum_j b_j q j^(q-1) (with 0^0 = 1), solved by
+    Gauss-Jordan elimination in rational arithmetic."""
+    from fractions import Fraction
+    rows = [[Fraction(q) * Fraction(j) ** (q - 1) for j in (0, 1, 2)] + [Fraction(1)] for q in (1, 2, 3)]
+    for c in range(3):
+        piv = next(r for r in range(c, 3) if rows[r][c] != 0)
+        rows[c], rows[piv] = rows[piv], rows[c]
+        pv = rows[c][c]
+        rows[c] = [v / pv for v in rows[c]]
+        for r in range(3):
+            if r != c and rows[r][c] != 0:
+                f = rows[r][c]
+                rows[r] = [a - f * b for a, b in zip(rows[r], rows[c])]
+    return tuple(rows[c][3] for c in range(3))
+
+
+def bvm_blocks(L, h: float, N: int):
+    """Block rows of the local matrix M_i (identical for every interval):
+    B, D, C of shape [N][m][m] (B[0] and C[N-1] unused) and the coupling of
+    row 1 to the interval's initial value, v = -B_1, shape [m][m]."""
+    L = np.asarray(L, dtype=np.float64)
+    m = L.shape[0]
+    b0, b1, b2 = (float(c) for c in gam3_coefficients())
+    I = np.eye(m)
+    B = np.zeros((N, m, m))
+    D = np.zeros((N, m, m))
+    C = np.zeros((N, m, m))
+    for n in range(N):                       # row n + 1 of the interval
+        if n < N - 1:                        # main formula
+            B[n] = -(I + h * b0 * L)
+            D[n] = I - h * b1 * L
+            C[n] = -h * b2 * L
+        else:                                # final formula (trapezoidal rule)
+            B[n] = -(I + 0.5 * h * L)
+            D[n] = I - 0.5 * h * L
+    return B, D, C, -B[0].copy()
+
+
+def bvm_rhs(Gi, h: float, N: int):
+    """Right-hand sides r_n (n = 1..N) of one interval from the samples
+    Gi[k] = g(tau_{i-1} + k h), k = 0..N; shape [N][m]."""
+    b0, b1, b2 = (float(c) for c in gam3_coefficients())
+    Gi = np.asarray(Gi, dtype=np.float64)
+    r = np.zeros((N, Gi.shape[1]))
+    for n in range(1, N + 1):
+        if n < N:
+            r[n - 1] = h * (b0 * Gi[n - 1] + b1 * Gi[n] + b2 * Gi[n + 1])
+        else:
+            r[n - 1] = 0.5 * h * (Gi[n - 1] + Gi[n])
+    return r
+
+
+def bvm_sequential(L, y0, G, T: float, p: int, N: int):
+    """The discrete solution of (My) by its sequential recursion,
+    y_{N0} = y0,  M_i y_i = g_i + v_i y_{N,i-1},  i = 1..p,
+    each M_i solved by the oracle's block Thomas algorithm.  G holds g at
+    the p N + 1 fine grid points; returns Y with Y[k] ~ y(k h)."""
+    from . import btri_solve
+    h = T / (p * N)
+    B, D, C, v = bvm_blocks(L, h, N)
+    G = np.asarray(G, dtype=np.float64)
+    m = B.shape[1]
+    Y = np.zeros((p * N + 1, m))
+    Y[0] = np.asarray(y0, dtype=np.float64)
+    for i in range(p):
+        r = bvm_rhs(G[i * N:(i + 1) * N + 1], h, N)
+        r[0] += v @ Y[i * N]
+        y = btri_solve(B, D, C, r.reshape(N * m, 1)).reshape(N, m)
+        Y[i * N + 1:(i + 1) * N + 1] = y
+    return Y

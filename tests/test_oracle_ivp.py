@@ -84,3 +84,50 @@ def test_parareal_properties():
     # and the iteration contracts for this dissipative problem
     errs = [np.abs(U[k] - ref).max() for k in range(p + 1)]
     assert errs[2] < 0.1 * errs[0]
+
+
+# ---------------------------------------------------------------- block BVM --
+def _stable_L(m, seed):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    return Q @ np.diag(-rng.uniform(0.5, 3.0, m)) @ Q.T + 0.1 * rng.standard_normal((m, m))
+
+
+def _forcing(L, y, dy, T, p, N):
+    """g(t) = y'(t) - L y(t) at the p N + 1 fine grid points."""
+    t = np.arange(p * N + 1) * (T / (p * N))
+    return np.array([dy(tk) - L @ y(tk) for tk in t]), t
+
+
+def test_bvm_exact_on_quadratic_solutions():
+    """Both formulas (the order-3 main formula and the trapezoidal final one)
+    are exact for polynomials of degree <= 2, so with g = y' - L y the
+    discrete solution of (My) equals y(t) at every grid point, across the
+    interval boundaries (y_{0i} = y_{N,i-1})."""
+    m, p, N, T = 3, 4, 6, 1.3
+    L = _stable_L(m, 1)
+    c = np.random.default_rng(2).standard_normal((3, m))
+    y = lambda t: c[0] + c[1] * t + c[2] * t * t
+    dy = lambda t: c[1] + 2 * c[2] * t
+    G, t = _forcing(L, y, dy, T, p, N)
+    Y = ivp.bvm_sequential(L, y(0.0), G, T, p, N)
+    ref = np.array([y(tk) for tk in t])
+    assert np.abs(Y - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_bvm_third_order_convergence():
+    """On a smooth manufactured solution the error at the grid points falls by
+    about 8 per halving of h (order 3; the lower-order final formula at the
+    end of each interval does not reduce it)."""
+    m, p, T = 4, 2, 1.0
+    L = _stable_L(m, 3)
+    v = np.random.default_rng(4).standard_normal(m)
+    y = lambda t: np.exp(np.sin(3 * t)) * v
+    dy = lambda t: 3 * np.cos(3 * t) * np.exp(np.sin(3 * t)) * v
+    errs = []
+    for N in (16, 32, 64):
+        G, t = _forcing(L, y, dy, T, p, N)
+        Y = ivp.bvm_sequential(L, y(0.0), G, T, p, N)
+        errs.append(np.abs(Y - np.array([y(tk) for tk in t])).max())
+    for a, b in zip(errs, errs[1:]):
+        assert 7.0 < a / b < 9.0, errs
