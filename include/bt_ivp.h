@@ -43,6 +43,30 @@ bt_status ivp_parareal(int64_t n, const double* dl, const double* d, const doubl
                        const double* g1, const double* y0, double T, int p, int nfine, int ncoarse, int kmax,
                        double tol, double* U, double* hist, int* iters_out, void* stream);
 
+/* Parallel IVP solver with a block Boundary Value Method as the local method
+ * (Sec. 3, Eqs. (M_iy_i), (My), (D), (redsys), (pups)).
+ *
+ * Problem: y' = L y + g(t), y(0) = y0, t in [0, T], L a constant m x m matrix.
+ * Coarse mesh of p equal intervals (Eq. (coarse)), N steps of h = T / (p N) in
+ * each (Eq. (hi)).  Local method: the order-3 generalized Adams BVM with
+ * k = 2, y_n - y_{n-1} = h (5/12 f_{n-1} + 2/3 f_n - 1/12 f_{n+1}) for
+ * n = 1..N-1 (coefficients from the order conditions), and the trapezoidal
+ * rule y_N - y_{N-1} = h/2 (f_{N-1} + f_N) as final formula, so that every
+ * M_i is block tridiagonal (and, with constant L, the same matrix M).
+ * Steps: (D) M z_i = g_i for every interval and the propagator
+ * w = M^{-1} v, one partition-method factorization of M (bt_plan, FP64) and
+ * its solves; (redsys) y_{0,1} = y0, y_{0,i+1} = z_{N,i} + w_N y_{0,i};
+ * (pups) y_i = z_i + w y_{0,i}.
+ *
+ * Arguments (device pointers): L [m][m] row-major; y0 [m]; G [p N + 1][m]
+ * with G[k] = g(k h) on the fine grid; Y [p N + 1][m] output, Y[k] ~ y(k h)
+ * (Y[0] = y0).  1 <= m <= 32, p >= 1, N >= 1, T > 0.  Allocates its workspace
+ * (cudaMalloc), runs on `stream` and synchronises it.  Errors:
+ * BT_ERR_INVALID for bad arguments, BT_ERR_NOMEM, BT_ERR_SINGULAR /
+ * BT_ERR_NONFINITE from the factorization of M. */
+bt_status ivp_bvm(int m, int64_t p, int64_t N, double T, const double* L, const double* y0, const double* G,
+                  double* Y, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

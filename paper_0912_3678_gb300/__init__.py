@@ -21,7 +21,7 @@ __all__ = ["BtPlan", "AbdPlan", "BtError", "BT_STATUS", "PREC", "load_library",
            "bt_batch_create", "bt_batch_run", "bt_batch_finish", "bt_batch_info", "bt_batch_destroy",
            "BtBatch", "CycPlan", "cyc_plan_create", "cyc_factor", "cyc_solve", "cyc_residual", "cyc_refine",
            "BtTuning", "BtBatchDesc", "bt_refine_async", "bt_refine_result",
-           "bt_plan_workspace_size", "bt_plan_anorm", "bt_plan_set_pivot_tol", "ivp_parareal", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay", "bt_factor_solve_host", "bt_plan_capture_host",
+           "bt_plan_workspace_size", "bt_plan_anorm", "bt_plan_set_pivot_tol", "ivp_parareal", "ivp_bvm", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay", "bt_factor_solve_host", "bt_plan_capture_host",
            "abd_plan_create_tuned",
            "bt_band_to_blocks", "band_to_blocks", "bt_device_rcp", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
            "abd_plan_create", "abd_factor", "abd_solve", "abd_residual", "abd_refine", "abd_sync",
@@ -229,6 +229,18 @@ def ivp_parareal(dl, d, du, g0, y0, T, p, nfine, ncoarse=1, kmax=None, tol=1e-12
     if raise_on_error and code not in (0, 5):
         _lib.check(code, "ivp_parareal")
     return U, it.value, code, hist
+
+
+def ivp_bvm(L, y0, G, T, p, N, Y=None, stream=None):
+    """Parallel IVP solver with the order-3 block BVM (see bt_ivp.h) for
+    y' = L y + g(t): L [m, m], y0 [m], G [p N + 1, m] = g on the fine grid
+    (CUDA float64).  Returns Y [p N + 1, m], Y[k] ~ y(k T / (p N))."""
+    import torch
+    m = L.shape[0]
+    Y = torch.empty((p * N + 1, m), dtype=torch.float64, device=L.device) if Y is None else Y
+    _lib.check(_lib.load().ivp_bvm(int(m), int(p), int(N), float(T), _ptr(L), _ptr(y0), _ptr(G), _ptr(Y),
+                                   _stream(stream)), "ivp_bvm")
+    return Y
 
 
 def bt_plan_set_pivot_tol(plan, tau: float):

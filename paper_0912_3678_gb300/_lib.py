@@ -88,6 +88,7 @@ SIGNATURES.update({
                           ctypes.POINTER(ctypes.c_double)]),
     "ivp_parareal": (_i32, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _f64, _i32, _i32, _i32, _i32, _f64, _vp, _vp,
                             ctypes.POINTER(ctypes.c_int), _vp]),
+    "ivp_bvm": (_i32, [_i32, _i64, _i64, _f64, _vp, _vp, _vp, _vp, _vp]),
     "bt_plan_workspace_size": (_i32, [_i32, _i64, _i32, _i32, _i32, ctypes.POINTER(BtTuning), _pi64]),
     "bt_plan_create_in": (_i32, [_pvp, _i32, _i64, _i32, _i32, _i32, ctypes.POINTER(BtTuning), _vp, _i64, _vp]),
 })

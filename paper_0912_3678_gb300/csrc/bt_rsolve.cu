@@ -295,26 +295,26 @@ __global__ void __cluster_dims__(kRsCtas, 1, 1) __launch_bounds__(kRsThreads) k_
     for (long long e = t0; e < a.K[0] * E; e += T) a.X0[e] = widen(__ldcg(a.x[0] + e));
 }
 
+// One grid row per segment (blockIdx.y), grid-stride within it.
 __global__ void __launch_bounds__(256) k_cvt_f32(const CvtArgs a) {
-    for (int sgi = 0; sgi < a.nseg; ++sgi) {
-        const double* s = a.src[sgi];
-        float* d = a.dst[sgi];
-        const long long n = a.n[sgi];
-        for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-            d[e] = trunc_f32(s[e]);
-    }
+    const int sgi = blockIdx.y;
+    const double* s = a.src[sgi];
+    float* d = a.dst[sgi];
+    const long long n = a.n[sgi];
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        d[e] = trunc_f32(s[e]);
 }
 
 }  // namespace
 
 cudaError_t launch_cvt_f32(const CvtArgs& a, cudaStream_t s) {
     if (a.nseg <= 0) return cudaSuccess;
-    long long tot = 0;
-    for (int i = 0; i < a.nseg; ++i) tot += a.n[i];
-    long long blocks = (tot / a.nseg + 255) / 256;
-    if (blocks < 1) blocks = 1;
-    if (blocks > 1184) blocks = 1184;
-    k_cvt_f32<<<(unsigned)blocks, 256, 0, s>>>(a);
+    long long mx = 0;
+    for (int i = 0; i < a.nseg; ++i) mx = a.n[i] > mx ? a.n[i] : mx;
+    long long bx = (mx + 255) / 256;
+    if (bx < 1) bx = 1;
+    if (bx > 256) bx = 256;
+    k_cvt_f32<<<dim3((unsigned)bx, (unsigned)a.nseg), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

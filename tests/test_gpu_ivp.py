@@ -74,3 +74,54 @@ def test_parareal_invalid_arguments(cuda):
             bt.ivp_parareal(*args, 0.1, bad["p"], bad["nfine"], 1)
     with pytest.raises(bt.BtError):
         bt.ivp_parareal(*args, -1.0, 4, 2, 1)
+
+
+# ------------------------------------------------------------------ block BVM --
+def _bvm_problem(m, p, N, T, seed):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    L = Q @ np.diag(-rng.uniform(0.5, 3.0, m)) @ Q.T + 0.1 * rng.standard_normal((m, m))
+    v = rng.standard_normal(m)
+    y = lambda t: np.exp(np.sin(3 * t)) * v
+    dy = lambda t: 3 * np.cos(3 * t) * np.exp(np.sin(3 * t)) * v
+    t = np.arange(p * N + 1) * (T / (p * N))
+    G = np.array([dy(tk) - L @ y(tk) for tk in t])
+    return L, y(0.0), G, np.array([y(tk) for tk in t])
+
+
+@pytest.mark.parametrize("m,p,N", [(1, 1, 1), (1, 3, 2), (3, 4, 7), (8, 16, 64), (16, 40, 50), (5, 33, 9)])
+def test_ivp_bvm_matches_sequential_oracle(cuda, m, p, N):
+    """The parallel solver (one factorization of M, the local solves (D),
+    the reduced recurrence and the parallel updates) against the oracle's
+    sequential recursion M_i y_i = g_i + v_i y_{N,i-1}, entry by entry; more
+    than 32 intervals take several solves of at most 32 right-hand sides."""
+    import paper_0912_3678_gb300 as bt
+    T = 1.0
+    L, y0, G, _ = _bvm_problem(m, p, N, T, seed=m + p + N)
+    ref = ivp.bvm_sequential(L, y0, G, T, p, N)
+    Y = bt.ivp_bvm(to_dev(L, cuda), to_dev(y0, cuda), to_dev(G, cuda), T, p, N)
+    Yh = to_host(Y)
+    assert np.abs(Yh - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_ivp_bvm_third_order_on_the_gpu(cuda):
+    """The GPU solution converges to the exact y(t) with order 3."""
+    import paper_0912_3678_gb300 as bt
+    m, p, T = 6, 8, 1.0
+    errs = []
+    for N in (16, 32, 64):
+        L, y0, G, exact = _bvm_problem(m, p, N, T, seed=11)
+        Y = to_host(bt.ivp_bvm(to_dev(L, cuda), to_dev(y0, cuda), to_dev(G, cuda), T, p, N))
+        errs.append(np.abs(Y - exact).max())
+    for a, b in zip(errs, errs[1:]):
+        assert 7.0 < a / b < 9.0, errs
+
+
+def test_ivp_bvm_rejects_bad_arguments(cuda):
+    import paper_0912_3678_gb300 as bt
+    L, y0, G, _ = _bvm_problem(2, 2, 3, 1.0, seed=1)
+    Ld, yd, Gd = (to_dev(a, cuda) for a in (L, y0, G))
+    with pytest.raises(bt.BtError):
+        bt.ivp_bvm(Ld, yd, Gd, -1.0, 2, 3)
+    with pytest.raises(bt.BtError):
+        bt.ivp_bvm(Ld, yd, Gd, 1.0, 0, 3)
