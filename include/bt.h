@@ -125,6 +125,17 @@ bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int p
  *                unused; graph capture only of solves (what = 2).  If more
  *                rows break down than the reduced system has room for,
  *                bt_factor returns BT_ERR_SINGULAR.
+ *                2 = partitions factored by local QR (the variant of Sec. 2
+ *                with N^(i) = Q^(i), S^(i) = R^(i)): every partition's local
+ *                block is reduced by block Householder steps (one CTA per
+ *                partition, FP64), so singular or ill-conditioned diagonal
+ *                blocks need neither splits nor host synchronisation; the
+ *                reduced system keeps p - 1 block rows and is solved by
+ *                Gaussian elimination with partial pivoting.  BT_FP64 only
+ *                (other precisions: BT_ERR_INVALID); reduced and local are
+ *                unused; factor and solve may be captured.  A singular local
+ *                block (an exactly zero R diagonal entry) is reported as
+ *                BT_ERR_SINGULAR.
  *   serial       1 = captured sequences (bt_plan_capture with factor) run on
  *                one stream.  0 (default): the factorization of the levels
  *                above level 0 (and the reduced system's cyclic reduction)

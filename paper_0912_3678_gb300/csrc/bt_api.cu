@@ -14,6 +14,7 @@
 #include "bt_planner.h"
 #include "bt_bcr.cuh"
 #include "bt_crb.cuh"
+#include "bt_qr.h"
 #include "bt_rsolve.h"
 
 namespace {
@@ -76,6 +77,9 @@ struct bt_plan_s {
     // pivoted partitions: level 0 split at breakdown rows, reduced system by banded GEPP
     bool pivot = false;
     double pivot_tau = 1e-3;
+    // partitions factored by local QR (pivot = 2): no splits, reduced system by banded GEPP
+    bool qr = false;
+    bt::QrArgs qa{};
     long long p_init = 0, base_init = 0, extra_init = 0;
     long long* starts_dev = nullptr;    // [pcap+1]
     long long* brk_dev = nullptr;       // [1 + brk_cap]: breakdown count and rows
@@ -199,7 +203,18 @@ void layout(bt_plan_s* P, Arena& ar) {
         const size_t ts = v.low ? sizeof(float) : sizeof(double);
         const bool top = (l == P->nlev);
         const bool holder = top && (P->bcr || P->pivot);
-        if (!(top && P->kind == 1) && !holder) {
+        if (l == 0 && P->qr) {
+            // local QR factors (bt_qr.h)
+            bt::QrArgs& q = P->qa;
+            const long long pa = v.a.p;
+            q.Qt = (double*)ar.take(sizeof(double) * v.rows * 4 * mm);
+            q.R = (double*)ar.take(sizeof(double) * v.rows * 3 * mm);
+            q.Z = (double*)ar.take(sizeof(double) * v.rows * mm);
+            q.W = (double*)ar.take(sizeof(double) * v.rows * mm);
+            q.Vb = (double*)ar.take(sizeof(double) * pa * mm);
+            q.Ta = (double*)ar.take(sizeof(double) * pa * mm);
+            q.Tf = (double*)ar.take(sizeof(double) * pa * m * nr);
+        } else if (!(top && P->kind == 1) && !holder) {
             const long long pa = std::max(v.a.p, v.pcap);
             v.a.Dinv = ar.take(ts * v.rows * mm);
             if (P->kind == 0) v.a.Y = ar.take(ts * v.rows * mm);
@@ -270,7 +285,7 @@ void layout(bt_plan_s* P, Arena& ar) {
         P->rot = (double*)ar.take(sizeof(double) * rows0 * m * nr);
         P->rot2 = (double*)ar.take(sizeof(double) * rows0 * m * nr);
     }
-    if (P->pivot) {
+    if (P->pivot && !P->qr) {
         const long long pc = P->lv[0].pcap;
         P->starts_dev = (long long*)ar.take(sizeof(long long) * (pc + 1));
         P->brk_cap = 4 * pc;
@@ -377,7 +392,12 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
     const int sms = sm_count(P->device);
     std::vector<bt::LevelShape> shapes;
     P->pivot = (kind == 0 && tune.pivot > 0);
+    P->qr = P->pivot && tune.pivot == 2;
     P->serial = tune.serial > 0;
+    if (P->qr && prec != BT_FP64) {
+        delete P;
+        return BT_ERR_INVALID;
+    }
     bt::Tuning tsh = tune;
     if (P->pivot) {
         tsh.reduced = 0;
@@ -409,7 +429,7 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
         // enlarge up to pcap - 1 block rows) by the pivoted direct solver
         const bt::LevelShape s0 = shapes[0];
         shapes.resize(1);
-        pcap = std::min<long long>(N + 1, std::max<long long>(2 * s0.p, N / 16) + 16);
+        pcap = P->qr ? s0.p : std::min<long long>(N + 1, std::max<long long>(2 * s0.p, N / 16) + 16);
         shapes.push_back(bt::LevelShape{s0.p - 1, 0, 0, 0, std::max<long long>(pcap - 1, 1)});
         P->p_init = s0.p;
         P->base_init = s0.base;
@@ -506,6 +526,7 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
         if (!P->status_host || !P->norms_host) e = cudaErrorMemoryAllocation;
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(P->status, 0, 4 * sizeof(long long), P->stream);
+    if (e == cudaSuccess && P->qr) e = bt::qr_prepare(m);
     // the split copy of the matrix: blocks B_0 and C_{N-1} are never written and stay zero
     if (e == cudaSuccess && P->warp && P->lv[0].a.As)
         e = cudaMemsetAsync(P->lv[0].a.As, 0, 2 * sizeof(float) * 3 * P->lv[0].rows * (size_t)m * m, P->stream);
@@ -632,7 +653,41 @@ bt_status run_factor_pivoted(bt_plan_s* P) {
     return from_cuda(e);
 }
 
+// The QR arguments of level 0 and its reduced system for nr right-hand sides.
+bt::QrArgs& qr_args(bt_plan_s* P, int nr) {
+    bt::QrArgs& q = P->qa;
+    const Level& v = P->lv[0];
+    const Level& t = P->lv[1];
+    q.N = v.a.N;
+    q.p = v.a.p;
+    q.base = v.a.base;
+    q.extra = v.a.extra;
+    q.m = P->m;
+    q.nr = nr;
+    q.B = v.a.B;
+    q.D = v.a.D;
+    q.C = v.a.C;
+    q.Bn = v.a.Bn;
+    q.Dn = v.a.Dn;
+    q.Cn = v.a.Cn;
+    q.F = v.a.F;
+    q.X = v.a.X;
+    q.Fn = v.a.Fn;
+    q.Xn = t.a.X;
+    q.status = P->status;
+    return q;
+}
+
+// Partitions factored by local QR: one launch for every partition, one that
+// completes the reduced diagonal; no host synchronisation.
+bt_status run_factor_qr(bt_plan_s* P) {
+    bt::QrArgs& q = qr_args(P, 1);
+    cudaError_t e = launch(P, K_FACTOR, 0, 2, [&] { return bt::launch_qr_factor(q, P->stream); });
+    return from_cuda(e);
+}
+
 bt_status run_factor(bt_plan_s* P, bool level0_done = false) {
+    if (P->qr) return run_factor_qr(P);
     if (P->pivot) return run_factor_pivoted(P);
     if (P->crb) {
         // cyclic reduction of the whole BABD system, level by level
@@ -765,6 +820,12 @@ bt_status run_solve(bt_plan_s* P, const double* F, double* X, int nr) {
     for (int l = 0; l < P->nlev; ++l) {
         Level& v = P->lv[l];
         const bool w = (l == 0) && w0;
+        if (l == 0 && P->qr) {
+            bt::QrArgs& q = qr_args(P, nr);
+            cudaError_t e = launch(P, K_SOLVE_FWD, 0, 2, [&] { return bt::launch_qr_solve_fwd(q, P->stream); });
+            if (e != cudaSuccess) return from_cuda(e);
+            continue;
+        }
         cudaError_t e = launch(P, K_SOLVE_FWD, l, 1, [&] {
             return w ? L->solve_fwd_w(v.a, P->stream) : L->solve_fwd(v.a, v.low, P->stream);
         });
@@ -819,6 +880,7 @@ bt_status run_solve(bt_plan_s* P, const double* F, double* X, int nr) {
         Level& v = P->lv[l];
         const bool w = (l == 0) && w0;
         e = launch(P, K_SOLVE_BWD, l, 1, [&] {
+            if (l == 0 && P->qr) return bt::launch_qr_solve_bwd(qr_args(P, nr), P->stream);
             return w ? L->solve_bwd_w(v.a, P->stream) : L->solve_bwd(v.a, v.low, P->stream);
         });
         if (e != cudaSuccess) return from_cuda(e);
@@ -1019,7 +1081,7 @@ bt_status bt_plan_create(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int p
 bt_status bt_plan_create_tuned(bt_plan* plan, int64_t nblk, int m, int nrhs_max, int prec, const bt_tuning* tuning,
                                void* stream) {
     if (tuning && (tuning->p0 < 0 || tuning->ctas_per_sm < 0 || tuning->sub_rows < 0 || tuning->top_rows < 0 ||
-                   tuning->reduced < 0 || tuning->reduced > 1 || tuning->local < 0 || tuning->local > 62 || tuning->pivot < 0 || tuning->pivot > 1 ||
+                   tuning->reduced < 0 || tuning->reduced > 1 || tuning->local < 0 || tuning->local > 62 || tuning->pivot < 0 || tuning->pivot > 2 ||
                    tuning->serial < 0 || tuning->serial > 1 ||
                    !(tuning->tp_block == 0 || tuning->tp_block == 64 || tuning->tp_block == 128 ||
                      tuning->tp_block == 256)))
@@ -1303,7 +1365,7 @@ bt_status bt_plan_create_in(bt_plan* plan, int kind, int64_t n, int m, int nrhs_
 
 bt_status bt_plan_capture(bt_plan P, int what, const double* F, double* X, int nrhs, int sweeps) {
     if (!P || what < 1 || what > 3) return BT_ERR_INVALID;
-    if (P->pivot && what != 2) return BT_ERR_INVALID;   // the pivoted factorization synchronises
+    if (P->pivot && !P->qr && what != 2) return BT_ERR_INVALID;   // the pivoted factorization synchronises
     bt_status st = check_solve(P, P->kind, F, X, nrhs);
     if (st != BT_OK) return st;
     if (what == 3 && (sweeps < 0 || sweeps > 30)) return BT_ERR_INVALID;

@@ -44,6 +44,83 @@ def test_lu_variant_sparsity():
     assert np.count_nonzero(np.abs(mid["wT"]) > 1e-300) > 0.8 * mid["wT"].size
 
 
+@pytest.mark.parametrize("n,zero_col", [(1, False), (2, False), (5, False), (12, False), (6, True)])
+def test_householder_qr(n, zero_col):
+    """Q orthogonal, R upper triangular, Q R = a; R equals LAPACK's R
+    (numpy.linalg.qr) up to the signs of its rows; a zero column is skipped."""
+    rng = np.random.default_rng(n)
+    a = rng.standard_normal((n, n))
+    if zero_col:
+        a[:, 2] = 0.0
+    Q, R = P.householder_qr(a)
+    assert np.abs(Q.T @ Q - np.eye(n)).max() <= 4e-15 * n
+    assert np.all(np.tril(R, -1) == 0)
+    assert np.abs(Q @ R - a).max() <= 4e-15 * n * np.abs(a).max()
+    assert np.allclose(np.abs(R), np.abs(np.linalg.qr(a, mode="r")), atol=1e-13)
+
+
+@pytest.mark.parametrize("N,m,p", [(11, 2, 3), (13, 3, 5), (15, 2, 7), (9, 1, 4), (12, 4, 1)])
+def test_qr_variant_F_T_G(N, m, p):
+    """The QR variant (N^(i) = Q^(i), S^(i) = R^(i)) also gives A = F T G, on
+    matrices with singular diagonal blocks (where every local block A^(i)
+    spans at least two block rows, so that A^(i) stays nonsingular), and its
+    separator rows of T are the same Schur complement as the LU variant's."""
+    zf = 0.3 if N // p >= 3 else 0.0
+    s = gen.btri_nondominant(N, m, 1, seed_rep=3 * N + m, zero_frac=zf)
+    A = gen.btri_dense(s.B, s.D, s.C)
+    F, T, G, parts = P.parallel_factors_qr(A, m, N, p)
+    assert np.abs(F @ T @ G - A).max() <= 1e-12 * np.abs(A).max()
+    for d in parts:
+        k = d["Q"].shape[0]
+        assert np.abs(d["Q"].T @ d["Q"] - np.eye(k)).max() <= 1e-14 * k
+        assert np.all(np.tril(d["R"], -1) == 0)
+    al, be, ga, g, Tp = P.btri_reduced_blocks(A, s.F, m, N, p)
+    local, seps = P.btri_bounds(N, p)
+    scale = np.abs(Tp).max() if Tp.size else 1.0
+    for k, sidx in enumerate(seps):
+        rows = slice(sidx * m, (sidx + 1) * m)
+        assert np.abs(T[rows, rows] - al[k]).max() <= 1e-12 * scale
+        if k >= 1:
+            assert np.abs(T[rows, seps[k - 1] * m:(seps[k - 1] + 1) * m] - be[k]).max() <= 1e-12 * scale
+        if k + 1 < len(seps):
+            assert np.abs(T[rows, seps[k + 1] * m:(seps[k + 1] + 1) * m] - ga[k]).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("N,m,p,nr", [(11, 2, 3, 1), (40, 3, 6, 2), (9, 1, 5, 1), (30, 4, 1, 3), (64, 2, 32, 1)])
+def test_partition_solve_matches_dense(N, m, p, nr):
+    """The partition method by its definition (Schur complement, banded
+    reduced solve, local back substitution) gives the dense solution."""
+    s = gen.btri_random(N, m, nr, seed_rep=N * p + m)
+    A = gen.btri_dense(s.B, s.D, s.C)
+    x = P.partition_solve(s.B, s.D, s.C, s.F, p)
+    ref = np.linalg.solve(A, s.F.reshape(N * m, -1))
+    assert np.abs(x - ref).max() <= 1e-12 * np.abs(ref).max() * np.linalg.cond(A, 1)
+    # its reduced system is the one of btri_reduced_blocks: x on the separators solves it
+    al, be, ga, g, T = P.btri_reduced_blocks(A, s.F, m, N, p)
+    _, seps = P.btri_bounds(N, p)
+    if seps:
+        xs = np.concatenate([x[j * m:(j + 1) * m] for j in seps])
+        assert np.abs(T @ xs - g.reshape(len(seps) * m, -1)).max() <= 1e-12 * (np.abs(T).max() * np.abs(xs).max())
+
+
+def test_qr_variant_sparsity():
+    """QR variant: v^T keeps the sparsity of b1^T (last block column), y = Q^T c1
+    is confined to the last two block rows (R has two block superdiagonals),
+    z = Q^T b0 and w^T = c0^T R^{-1} are fill-in."""
+    N, m, p = 17, 2, 3
+    s = gen.btri_random(N, m, 1, seed_rep=5)
+    A = gen.btri_dense(s.B, s.D, s.C)
+    _, _, _, parts = P.parallel_factors_qr(A, m, N, p)
+    mid = parts[1]
+    k = mid["Q"].shape[0]
+    assert np.all(mid["vT"][:, :k - m] == 0) and np.abs(mid["vT"][:, k - m:]).max() > 0
+    assert np.all(mid["y"][:k - 2 * m] == 0) and np.abs(mid["y"][k - 2 * m:k - m]).max() > 0
+    R = mid["R"]
+    assert all(np.all(R[r * m:(r + 1) * m, (r + 3) * m:] == 0) for r in range(k // m))
+    assert np.count_nonzero(np.abs(mid["z"]) > 1e-300) > 0.8 * mid["z"].size
+    assert np.count_nonzero(np.abs(mid["wT"]) > 1e-300) > 0.8 * mid["wT"].size
+
+
 @pytest.mark.parametrize("N", [40, 80, 400])
 def test_reduced_size_depends_on_p_only(N):
     p, m = 6, 2
