@@ -104,6 +104,10 @@ struct bt_plan_s {
     bool warp = false;
     bt::RsolveArgs rsa{};
     bt::CvtArgs cva{};
+    // refined plans of order 8 or 16: the reduced system's FP32 cyclic
+    // reduction in one cluster launch
+    bool rf = false;
+    bt::RfactorArgs rfa{};
     // BABD plans solved by cyclic reduction of the whole system (no partitions)
     bool crb = false;
     std::vector<bt::CrbArgs> cl;        // its levels (N_q rows each, down to one row)
@@ -347,16 +351,47 @@ void layout(bt_plan_s* P, Arena& ar) {
             const bt::BcrArgs& b = P->bl[q];
             const long long K = b.K, kept = (K + 1) / 2, odd = (K == 1) ? 1 : K / 2;
             r.K[q] = K;
-            r.al[q] = (K > 1) ? seg(b.al, kept * mm) : nullptr;
-            r.ga[q] = (K > 1) ? seg(b.ga, kept * mm) : nullptr;
-            r.Dinv[q] = seg(b.Dinv, odd * mm);
-            r.B[q] = (K > 1) ? seg(b.B, K * mm) : nullptr;
-            r.C[q] = (K > 1) ? seg(b.C, K * mm) : nullptr;
+            if (b.mode == bt::BCR_F64) {
+                r.al[q] = (K > 1) ? seg(b.al, kept * mm) : nullptr;
+                r.ga[q] = (K > 1) ? seg(b.ga, kept * mm) : nullptr;
+                r.Dinv[q] = seg(b.Dinv, odd * mm);
+            } else {
+                // FP32 factors, used as they are
+                r.al[q] = (const float*)b.al;
+                r.ga[q] = (const float*)b.ga;
+                r.Dinv[q] = (const float*)b.Dinv;
+            }
+            // the level matrix: FP64 at the first level (the partition level's
+            // output), FP32 above it when the levels are FP32
+            const bool in64 = (b.mode == bt::BCR_F64) || q == 0;
+            r.B[q] = (K > 1) ? (in64 ? seg(b.B, K * mm) : (const float*)b.B) : nullptr;
+            r.C[q] = (K > 1) ? (in64 ? seg(b.C, K * mm) : (const float*)b.C) : nullptr;
             r.f[q] = (float*)ar.take(sizeof(float) * K * m * nr);
             r.x[q] = (float*)ar.take(sizeof(float) * K * m * nr);
         }
         r.F0 = P->bl[0].F;
         r.X0 = P->bl[0].X;
+        if (P->rf) {
+            bt::RfactorArgs& f = P->rfa;
+            f.nlev = (int)P->bl.size();
+            f.m = m;
+            f.level0 = P->nlev;
+            f.B0 = (const double*)P->bl[0].B;
+            f.D0 = (const double*)P->bl[0].D;
+            f.C0 = (const double*)P->bl[0].C;
+            for (size_t q = 0; q < P->bl.size(); ++q) {
+                const bt::BcrArgs& b = P->bl[q];
+                f.K[q] = b.K;
+                f.B[q] = q ? (float*)b.B : nullptr;
+                f.D[q] = q ? (float*)b.D : nullptr;
+                f.C[q] = q ? (float*)b.C : nullptr;
+                f.al[q] = (float*)b.al;
+                f.ga[q] = (float*)b.ga;
+                f.Dinv[q] = (float*)b.Dinv;
+            }
+            f.B0f = const_cast<float*>(r.B[0]);
+            f.C0f = const_cast<float*>(r.C[0]);
+        }
     }
 }
 
@@ -481,6 +516,13 @@ bt_status plan_create(bt_plan* out, int kind, int64_t N, int m, int nrhs_max, in
         }
         P->rs32 = (prec != BT_FP64) && P->local == 0 && P->nlev >= 1 && m >= 8 &&
                   (int)P->bl.size() <= bt::kRsMaxLevels && 5 * (int)P->bl.size() <= bt::kCvtSegs;
+        if (P->rs32) {
+            // the reduced system of a refined plan is factored in FP32 too: its
+            // factors only enter the FP32 correction solves
+            for (int q = 0; q < n; ++q)
+                P->bl[q].mode = (q > 0) ? bt::BCR_F32 : (n == 1 ? bt::BCR_F32_ONLY : bt::BCR_F32_FIRST);
+            P->rf = (m == 8 || m == 16) && n >= 2;
+        }
     }
     if (kind == 0) {
         // the top level is a single partition; levels below it have >= 2
@@ -730,6 +772,13 @@ bt_status run_factor(bt_plan_s* P, bool level0_done = false) {
                 P->bl[0].B = v.a.B;
                 P->bl[0].D = v.a.D;
                 P->bl[0].C = v.a.C;
+            }
+            if (P->rf) {
+                P->rfa.status = P->status;
+                cudaError_t e = launch(P, K_BCR_FACTOR, P->nlev, 1,
+                                       [&] { return bt::launch_rfactor_f32(P->rfa, P->stream); });
+                if (e != cudaSuccess) return rejoin(from_cuda(e));
+                break;
             }
             for (size_t q = 0; q < P->bl.size(); ++q) {
                 bt::BcrArgs& b = P->bl[q];

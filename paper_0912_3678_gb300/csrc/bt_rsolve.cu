@@ -1,8 +1,9 @@
 // Solve of the reduced system (Eq. (redmatr)) by block cyclic reduction in one
-// launch, for the refined paths: the FP64 cyclic-reduction factors (computed
-// by k_bcr_factor, Sec. 2 cyclic-reduction variant) are applied as FP32
-// copies, inside the FP32 correction solve that the FP64 refinement
-// corrects.  One thread-block cluster of kRsCtas CTAs runs every level:
+// launch, for the refined paths: the cyclic-reduction factors (computed by
+// k_bcr_factor, Sec. 2 cyclic-reduction variant) are applied in FP32 inside
+// the FP32 correction solve that the FP64 refinement corrects.  One
+// thread-block cluster (16 CTAs where the device can place such a cluster,
+// else 8) runs every level:
 //   forward   f^{q+1}_i = f^q_{2i} + alpha_i f^q_{2i-1} + gamma_i f^q_{2i+1},
 //   top       x = D^{-1} f                     (the single remaining row),
 //   backward  x^q_{2i} = x^{q+1}_i,
@@ -10,7 +11,10 @@
 // with a hardware cluster barrier between levels (no spin loops, no
 // grid-wide dependency); levels with at most kRsCluster rows are finished by
 // one CTA between __syncthreads.  The level vectors live in global memory (L2)
-// and are read past L1 (ld.global.cg).
+// and are read past L1 (ld.global.cg); the first level reads the FP64
+// right-hand side and writes the FP64 solution directly, converting as it
+// goes.  The factors come from an FP32 cyclic reduction (or FP32 copies of an
+// FP64 one).
 #include <cuda_runtime.h>
 
 #include "bt_bcr.cuh"
@@ -19,7 +23,8 @@
 namespace bt {
 namespace {
 
-constexpr int kRsCtas = 8;
+constexpr int kRsCtasMax = 16;   // non-portable cluster size, where it can be scheduled
+constexpr int kRsCtasPortable = 8;
 constexpr int kRsThreads = 512;
 
 // Release/acquire at cluster scope orders every CTA's global-memory writes
@@ -35,6 +40,11 @@ __device__ __forceinline__ void cluster_barrier() {
 __device__ __forceinline__ unsigned cluster_rank() {
     unsigned r;
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
     return r;
 }
 
@@ -68,6 +78,36 @@ __device__ __forceinline__ void zero_f4(float* dst, long long n) {
     for (int e = threadIdx.x; e < (int)(n / 4); e += blockDim.x) d4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// The first level's right-hand side is the FP64 F0 and its solution the
+// FP64 X0: they are converted where they are read and written (no separate
+// conversion passes).  idx4 counts float4 units of the level vector.
+__device__ __forceinline__ float4 get_f4(const RsolveArgs& a, int q, long long idx4) {
+    if (q == 0) {
+        const double2* s2 = reinterpret_cast<const double2*>(a.F0) + 2 * idx4;
+        const double2 u = __ldcg(s2), w = __ldcg(s2 + 1);
+        return make_float4(trunc_f32(u.x), trunc_f32(u.y), trunc_f32(w.x), trunc_f32(w.y));
+    }
+    return __ldcg(reinterpret_cast<const float4*>(a.f[q]) + idx4);
+}
+__device__ __forceinline__ void put_x4(const RsolveArgs& a, int q, long long idx4, float4 v) {
+    if (q == 0) {
+        double2* d2 = reinterpret_cast<double2*>(a.X0) + 2 * idx4;
+        d2[0] = make_double2(widen(v.x), widen(v.y));
+        d2[1] = make_double2(widen(v.z), widen(v.w));
+    } else {
+        reinterpret_cast<float4*>(a.x[q])[idx4] = v;
+    }
+}
+__device__ __forceinline__ void put_x1(const RsolveArgs& a, int q, long long idx, float v) {
+    if (q == 0) a.X0[idx] = widen(v);
+    else a.x[q][idx] = v;
+}
+// dst <- f[q] entries [e0, e0 + n) (n and e0 multiples of 4)
+__device__ __forceinline__ void stage_fq(const RsolveArgs& a, int q, float* dst, long long e0, long long n) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (int e = threadIdx.x; e < (int)(n / 4); e += blockDim.x) d4[e] = get_f4(a, q, e0 / 4 + e);
+}
+
 constexpr int kRsSmemFloats = 24 * 1024;   // 96 KB of shared memory per CTA
 constexpr long long kRsCluster = 64;       // levels with more rows run on the whole cluster
 
@@ -91,9 +131,9 @@ __device__ void rs_forward(const RsolveArgs& a, int q, long long lo, long long h
         const long long f0 = 2 * c0 - 1, f1 = (2 * c1 < K) ? 2 * c1 : K;   // rows [f0, f1)
         if (f0 < 0) {
             zero_f4(sf, E);
-            stage_f4(sf + E, a.f[q], f1 * E);
+            stage_fq(a, q, sf + E, 0, f1 * E);
         } else {
-            stage_f4(sf, a.f[q] + f0 * E, (f1 - f0) * E);
+            stage_fq(a, q, sf, f0 * E, (f1 - f0) * E);
         }
         const long long nf = f1 - f0;
         if (nf < 2 * n + 1) zero_f4(sf + nf * E, (2 * n + 1 - nf) * E);
@@ -163,8 +203,7 @@ __device__ void rs_backward(const RsolveArgs& a, int q, long long lo, long long 
         }
         for (int e = threadIdx.x; e < (int)nodd * (E / 4); e += blockDim.x) {
             const int il = e / (E / 4), w = e - il * (E / 4);
-            reinterpret_cast<float4*>(sf)[e] =
-                __ldcg(reinterpret_cast<const float4*>(a.f[q] + (2 * (c0 + il) + 1) * E) + w);
+            reinterpret_cast<float4*>(sf)[e] = get_f4(a, q, (2 * (c0 + il) + 1) * (E / 4) + w);
         }
         stage_f4(sD, a.Dinv[q] + c0 * MM, nodd * MM);
         const long long xend = (c1 + 1 <= kept) ? c1 + 1 : kept;   // x^{q+1} rows [c0, xend)
@@ -174,7 +213,7 @@ __device__ void rs_backward(const RsolveArgs& a, int q, long long lo, long long 
         for (int u = threadIdx.x; u < (int)n * (E / 4); u += blockDim.x) {
             const int il = u / (E / 4);
             const int w = u - il * (E / 4);
-            reinterpret_cast<float4*>(a.x[q])[(2 * (c0 + il)) * (E / 4) + w] = reinterpret_cast<const float4*>(sx)[il * (E / 4) + w];
+            put_x4(a, q, (2 * (c0 + il)) * (E / 4) + w, reinterpret_cast<const float4*>(sx)[il * (E / 4) + w]);
         }
         // pass 1: t = f - B x_l - C x_r in place of f; pass 2: x = D^{-1} t
         if (v4) {
@@ -214,7 +253,7 @@ __device__ void rs_backward(const RsolveArgs& a, int q, long long lo, long long 
                     x.z = fmaf(d, t.z, x.z);
                     x.w = fmaf(d, t.w, x.w);
                 }
-                reinterpret_cast<float4*>(a.x[q])[rw * E4 + e4] = x;
+                put_x4(a, q, rw * E4 + e4, x);
             }
         } else {
             for (int u = threadIdx.x; u < (int)nodd * E; u += blockDim.x) {
@@ -244,7 +283,7 @@ __device__ void rs_backward(const RsolveArgs& a, int q, long long lo, long long 
                     s0 = fmaf(Di[k], sf[il * E + k * nr + c], s0);
                     s1 = fmaf(Di[k + 1], sf[il * E + (k + 1) * nr + c], s1);
                 }
-                a.x[q][rw * E + el] = s0 + s1;
+                put_x1(a, q, rw * E + el, s0 + s1);
             }
         }
         __syncthreads();
@@ -252,22 +291,19 @@ __device__ void rs_backward(const RsolveArgs& a, int q, long long lo, long long 
 }
 
 template <int M>
-__global__ void __cluster_dims__(kRsCtas, 1, 1) __launch_bounds__(kRsThreads) k_rsolve_f32(const RsolveArgs a) {
+__global__ void __launch_bounds__(kRsThreads) k_rsolve_f32(const RsolveArgs a) {
     extern __shared__ __align__(16) float sm[];
     const int nr = a.nr;
     const int E = M * nr;   // multiple of 4 (M >= 8)
     const int rank = (int)cluster_rank();
-    const long long T = (long long)kRsCtas * kRsThreads;
-    const long long t0 = (long long)rank * kRsThreads + threadIdx.x;
+    const long long nct = (long long)cluster_size();
     const int top = a.nlev - 1;
     // levels 0 .. big-1 run on the whole cluster, the rest on CTA 0 alone
     int big = 0;
     while (big < top && a.K[big] > kRsCluster) ++big;
-    for (long long e = t0; e < a.K[0] * E; e += T) a.f[0][e] = trunc_f32(a.F0[e]);
-    cluster_barrier();
     for (int q = 0; q < big; ++q) {
         const long long kept = (a.K[q] + 1) / 2;
-        rs_forward<M>(a, q, kept * rank / kRsCtas, kept * (rank + 1) / kRsCtas, sm);
+        rs_forward<M>(a, q, kept * rank / nct, kept * (rank + 1) / nct, sm);
         cluster_barrier();
     }
     if (rank == 0) {
@@ -275,13 +311,15 @@ __global__ void __cluster_dims__(kRsCtas, 1, 1) __launch_bounds__(kRsThreads) k_
             rs_forward<M>(a, q, 0, (a.K[q] + 1) / 2, sm);   // ends with __syncthreads
         }
         const float* Di = a.Dinv[top];
-        const float* f = a.f[top];
+        if (top == 0) stage_fq(a, 0, sm, 0, E);
+        else stage_f4(sm, a.f[top], E);
+        __syncthreads();
         for (int u = threadIdx.x; u < E; u += blockDim.x) {
             const int r = u / nr, c = u % nr;
             float s = 0.f;
 #pragma unroll
-            for (int k = 0; k < M; ++k) s = fmaf(Di[r * M + k], __ldcg(f + k * nr + c), s);
-            a.x[top][u] = s;
+            for (int k = 0; k < M; ++k) s = fmaf(Di[r * M + k], sm[k * nr + c], s);
+            put_x1(a, top, u, s);
         }
         __syncthreads();
         for (int q = top - 1; q >= big; --q) rs_backward<M>(a, q, 0, (a.K[q] + 1) / 2, sm);
@@ -289,10 +327,9 @@ __global__ void __cluster_dims__(kRsCtas, 1, 1) __launch_bounds__(kRsThreads) k_
     cluster_barrier();
     for (int q = big - 1; q >= 0; --q) {
         const long long kept = (a.K[q] + 1) / 2;
-        rs_backward<M>(a, q, kept * rank / kRsCtas, kept * (rank + 1) / kRsCtas, sm);
-        cluster_barrier();
+        rs_backward<M>(a, q, kept * rank / nct, kept * (rank + 1) / nct, sm);
+        if (q > 0) cluster_barrier();
     }
-    for (long long e = t0; e < a.K[0] * E; e += T) a.X0[e] = widen(__ldcg(a.x[0] + e));
 }
 
 // One grid row per segment (blockIdx.y), grid-stride within it.
@@ -303,6 +340,291 @@ __global__ void __launch_bounds__(256) k_cvt_f32(const CvtArgs a) {
     const long long n = a.n[sgi];
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
         d[e] = trunc_f32(s[e]);
+}
+
+
+// ---------------------------------------------------------------------------
+// One-launch FP32 factorization of the reduced system by cyclic reduction
+// (the refined paths, m = 8, 16): every level in one thread-block cluster,
+// a cluster barrier between levels.  A kept row r = 2q of a level is handled
+// by a pair of warps, one per side: side 0 inverts the left odd neighbour
+// D_{r-1} and forms alpha_q = -B_r D_{r-1}^{-1}, alpha C_{r-1} and
+// B'_q = alpha B_{r-1}; side 1 inverts D_{r+1} (stored as Dinv[q]) and forms
+// gamma_q = -C_r D_{r+1}^{-1}, gamma B_{r+1} and C'_q = gamma C_{r+1}; side 0
+// then writes D'_q = D_r + alpha C_{r-1} + gamma B_{r+1} (the pair meets at a
+// named barrier).  In a warp, lane l holds columns [W h, W h + W) of row
+// r = l mod m of a block (h = l / m, W = m^2 / 32).  The inverses are
+// Gauss-Jordan eliminations with partial pivoting: the pivot of column k is
+// found by a warp max-reduction over the rows not used yet, rows are not
+// interchanged, the pivot row passes through shared memory and each row's
+// multiplier through a shuffle.
+
+constexpr int kRfThreads = 256;   // the cluster launch: 4 warp pairs per CTA, so that a CTA of
+                                  // the level-0 forward solve still fits beside it on its SM
+constexpr int kRfThreads0 = 64;   // the first level: one CTA (one warp pair) per kept row
+
+template <int N>
+__device__ __forceinline__ void rf_lds(float (&v)[N], const float* s) {
+    if constexpr (N % 4 == 0) {
+        const float4* p = reinterpret_cast<const float4*>(s);
+#pragma unroll
+        for (int u = 0; u < N / 4; ++u) {
+            const float4 t = p[u];
+            v[4 * u] = t.x;
+            v[4 * u + 1] = t.y;
+            v[4 * u + 2] = t.z;
+            v[4 * u + 3] = t.w;
+        }
+    } else {
+        const float2* p = reinterpret_cast<const float2*>(s);
+#pragma unroll
+        for (int u = 0; u < N / 2; ++u) {
+            const float2 t = p[u];
+            v[2 * u] = t.x;
+            v[2 * u + 1] = t.y;
+        }
+    }
+}
+template <int N>
+__device__ __forceinline__ void rf_sts(float* s, const float (&v)[N]) {
+    if constexpr (N % 4 == 0) {
+        float4* p = reinterpret_cast<float4*>(s);
+#pragma unroll
+        for (int u = 0; u < N / 4; ++u) p[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+    } else {
+        float2* p = reinterpret_cast<float2*>(s);
+#pragma unroll
+        for (int u = 0; u < N / 2; ++u) p[u] = make_float2(v[2 * u], v[2 * u + 1]);
+    }
+}
+// N consecutive floats of global memory (L2), from FP32 or FP64 (truncated)
+template <int N>
+__device__ __forceinline__ void rf_ldg(float (&v)[N], const float* g) {
+    if constexpr (N % 4 == 0) {
+        const float4* p = reinterpret_cast<const float4*>(g);
+#pragma unroll
+        for (int u = 0; u < N / 4; ++u) {
+            const float4 t = __ldcg(p + u);
+            v[4 * u] = t.x;
+            v[4 * u + 1] = t.y;
+            v[4 * u + 2] = t.z;
+            v[4 * u + 3] = t.w;
+        }
+    } else {
+        const float2* p = reinterpret_cast<const float2*>(g);
+#pragma unroll
+        for (int u = 0; u < N / 2; ++u) {
+            const float2 t = __ldcg(p + u);
+            v[2 * u] = t.x;
+            v[2 * u + 1] = t.y;
+        }
+    }
+}
+template <int N>
+__device__ __forceinline__ void rf_ldg(float (&v)[N], const double* g) {
+    const double2* p = reinterpret_cast<const double2*>(g);
+#pragma unroll
+    for (int u = 0; u < N / 2; ++u) {
+        const double2 t = __ldcg(p + u);
+        v[2 * u] = trunc_f32(t.x);
+        v[2 * u + 1] = trunc_f32(t.y);
+    }
+}
+template <int N>
+__device__ __forceinline__ void rf_stg(float* g, const float (&v)[N]) { rf_sts<N>(g, v); }
+
+// Gauss-Jordan inverse of an M x M block by one warp; lane (r, h) holds
+// columns [W h, W h + W) of row r in a[] and of the identity in b[].  Column
+// k's pivot is the unused row of largest magnitude (ties to the lowest row);
+// no interchanges, so the lanes of the row that was column k's pivot end with
+// their part of row k of the inverse in b[] and slot = k.  Returns false when
+// a pivot column is zero (the result is then inf/nan).
+template <int M>
+__device__ __forceinline__ bool rf_inverse(float (&a)[M * M / 32], float (&b)[M * M / 32], int& slot, float* prow,
+                                           int r, int h) {
+    constexpr int W = M * M / 32;
+    bool used = false, ok = true;
+    slot = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) b[w] = (W * h + w == r) ? 1.f : 0.f;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        const int hk = k / W, kk = k % W;
+        const float ak = a[kk];
+        const unsigned key = (!used && h == hk) ? (__float_as_uint(ak) & 0x7fffffffu) + 1u : 0u;
+        const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+        const unsigned win = __ballot_sync(0xffffffffu, key == kmax);
+        if (kmax <= 1u) ok = false;
+        const int pr = (__ffs(win) - 1) % M;
+        const float ark = __shfl_sync(0xffffffffu, ak, r + M * hk);   // this row's entry in column k
+        const bool me = (r == pr);
+        if (me) {
+            used = true;
+            slot = k;
+            rf_sts<W>(prow + W * h, a);
+            rf_sts<W>(prow + M + W * h, b);
+        }
+        __syncwarp();
+        float pa[W], pb[W];
+        rf_lds<W>(pa, prow + W * h);
+        rf_lds<W>(pb, prow + M + W * h);
+        const float inv = __frcp_rn(prow[k]);
+        if (me) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                a[w] *= inv;
+                b[w] *= inv;
+            }
+        } else {
+            const float f = ark * inv;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                a[w] = fmaf(-f, pa[w], a[w]);
+                b[w] = fmaf(-f, pb[w], b[w]);
+            }
+        }
+        __syncwarp();
+    }
+    return ok;
+}
+
+// Columns [W h, W h + W) of row r of (sgn x S): x the full row in registers,
+// S an M x M block in shared memory.
+template <int M>
+__device__ __forceinline__ void rf_row_part(float (&out)[M * M / 32], const float (&x)[M], const float* S, int h,
+                                            float sgn) {
+    constexpr int W = M * M / 32;
+    float acc[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) acc[w] = 0.f;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+        float srow[W];
+        rf_lds<W>(srow, S + k * M + W * h);
+#pragma unroll
+        for (int w = 0; w < W; ++w) acc[w] = fmaf(x[k], srow[w], acc[w]);
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) out[w] = sgn * acc[w];
+}
+
+template <int M, int NT>
+constexpr size_t rf_smem_floats() {
+    // per warp: inverse, two coupling blocks, the multiplier, pivot row; per pair: side 1's share of D'
+    return (size_t)(NT / 32) * (4 * M * M + 2 * M) + (size_t)(NT / 64) * M * M;
+}
+
+__device__ __forceinline__ void pair_sync(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+
+// Levels [q0, q1).  CLUSTER: one thread-block cluster takes every level in
+// turn (rows split over its CTAs, a cluster barrier between levels); else a
+// plain grid takes the single level q0 (rows split over the CTAs) and also
+// makes the FP32 copies of the first level's B and C.
+template <int M, int NT, bool CLUSTER>
+__global__ void __launch_bounds__(NT) k_rfactor_f32(const RfactorArgs a, int q0, int q1) {
+    constexpr int W = M * M / 32;
+    constexpr int MM = M * M;
+    constexpr int NP = NT / 64;   // warp pairs per CTA
+    extern __shared__ __align__(16) float sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = lane % M, h = lane / M;
+    const int side = warp & 1, pair = warp >> 1;
+    float* ws = sm + warp * (4 * MM + 2 * M);
+    float* Dv = ws;             // the inverse
+    float* Y1 = ws + MM;        // the coupling blocks of the products
+    float* Y2 = ws + 2 * MM;
+    float* Mt = ws + 3 * MM;    // the multiplier
+    float* prow = ws + 4 * MM;  // pivot row
+    float* Ex = sm + (NT / 32) * (4 * MM + 2 * M) + pair * MM;   // side 1's share of D'
+    const int rank = CLUSTER ? (int)cluster_rank() : (int)blockIdx.x;
+    const long long nct = CLUSTER ? (long long)cluster_size() : (long long)gridDim.x;
+    // the first level's side-1 tasks also leave FP32 copies of the odd rows'
+    // B and C (all the solves read of that level's matrix)
+    const bool copy0 = !CLUSTER && q0 == 0;
+    for (int q = q0; q < q1; ++q) {
+        const long long K = a.K[q];
+        // row rr of block `which` (0 B, 1 D, 2 C) of this level: the whole row or this lane's part
+        auto ldrow = [&](float (&v)[M], int which, long long rr) {
+            if (q == 0) rf_ldg<M>(v, (which == 0 ? a.B0 : which == 1 ? a.D0 : a.C0) + rr * MM + r * M);
+            else rf_ldg<M>(v, (which == 0 ? a.B[q] : which == 1 ? a.D[q] : a.C[q]) + rr * MM + r * M);
+        };
+        auto ldpart = [&](float (&v)[W], int which, long long rr) {
+            if (q == 0) rf_ldg<W>(v, (which == 0 ? a.B0 : which == 1 ? a.D0 : a.C0) + rr * MM + r * M + W * h);
+            else rf_ldg<W>(v, (which == 0 ? a.B[q] : which == 1 ? a.D[q] : a.C[q]) + rr * MM + r * M + W * h);
+        };
+        if (K == 1) {
+            if (rank == 0 && warp == 0) {
+                float x[W], inv[W];
+                int slot;
+                ldpart(x, 1, 0);
+                if (!rf_inverse<M>(x, inv, slot, prow, r, h) && lane == 0)
+                    report(a.status, ST_SINGULAR, a.level0 + q, -2, 0);
+                rf_stg<W>(a.Dinv[q] + slot * M + W * h, inv);
+            }
+            break;
+        }
+        const long long kept = (K + 1) / 2;
+        const long long lo = kept * rank / nct, hi = kept * (rank + 1) / nct;
+        for (long long qq = lo + pair; qq < hi; qq += NP) {
+            const long long rw = 2 * qq;
+            const bool has = (side == 0) ? (qq >= 1) : (rw + 1 < K);
+            const long long nb = (side == 0) ? rw - 1 : rw + 1;
+            const bool far = (side == 0) ? (rw - 1 >= 1) : (rw + 2 < K);
+            float* multo = ((side == 0) ? a.al[q] : a.ga[q]) + qq * MM + r * M + W * h;
+            float* fout = ((side == 0) ? a.B[q + 1] : a.C[q + 1]) + qq * MM + r * M + W * h;
+            float p1[W], p2[W], mlt[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) p1[w] = p2[w] = mlt[w] = 0.f;
+            if (has) {
+                // every block of the task is requested before the inverse starts
+                float x[W], inv[W], c[M];
+                int slot;
+                ldpart(x, 1, nb);
+                ldrow(c, side == 0 ? 0 : 2, rw);
+                {
+                    float y[W];
+                    const long long o = nb * MM + r * M + W * h;
+                    ldpart(y, side == 0 ? 2 : 0, nb);
+                    rf_sts<W>(Y1 + r * M + W * h, y);
+                    if (copy0 && q == 0 && side == 1) rf_stg<W>(a.B0f + o, y);
+                    if (far) {
+                        ldpart(y, side == 0 ? 0 : 2, nb);
+                        rf_sts<W>(Y2 + r * M + W * h, y);
+                    } else {
+#pragma unroll
+                        for (int w = 0; w < W; ++w) y[w] = 0.f;
+                    }
+                    if (copy0 && q == 0 && side == 1) rf_stg<W>(a.C0f + o, y);
+                }
+                if (!rf_inverse<M>(x, inv, slot, prow, r, h) && lane == 0)
+                    report(a.status, ST_SINGULAR, a.level0 + q, -2, nb);
+                rf_sts<W>(Dv + slot * M + W * h, inv);
+                if (side == 1) rf_stg<W>(a.Dinv[q] + qq * MM + slot * M + W * h, inv);
+                __syncwarp();
+                rf_row_part<M>(mlt, c, Dv, h, -1.f);
+                rf_sts<W>(Mt + r * M + W * h, mlt);
+                __syncwarp();
+                float mr[M];
+                rf_lds<M>(mr, Mt + r * M);
+                rf_row_part<M>(p1, mr, Y1, h, 1.f);
+                if (far) rf_row_part<M>(p2, mr, Y2, h, 1.f);
+            }
+            rf_stg<W>(multo, mlt);
+            rf_stg<W>(fout, p2);
+            if (side == 1) rf_sts<W>(Ex + r * M + W * h, p1);
+            pair_sync(1 + pair);
+            if (side == 0) {
+                float d[W], ex[W];
+                ldpart(d, 1, rw);
+                rf_lds<W>(ex, Ex + r * M + W * h);
+#pragma unroll
+                for (int w = 0; w < W; ++w) d[w] = (d[w] + p1[w]) + ex[w];
+                rf_stg<W>(a.D[q + 1] + qq * MM + r * M + W * h, d);
+            }
+            pair_sync(1 + pair);
+        }
+        if (CLUSTER) cluster_barrier();
+    }
 }
 
 }  // namespace
@@ -318,21 +640,102 @@ cudaError_t launch_cvt_f32(const CvtArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// The cluster size is chosen once per kernel (and device): 16 CTAs if the
+// occupancy query places at least one such cluster, else 8.
+template <typename K, typename Args>
+static cudaError_t launch_cluster(K kernel, const Args& a, int threads, size_t smem, cudaStream_t s, int& ctas) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (ctas == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        ctas = kRsCtasPortable;
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+            cfg.gridDim = dim3(kRsCtasMax);
+            at[0].val.clusterDim.x = kRsCtasMax;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) == cudaSuccess && n >= 1) ctas = kRsCtasMax;
+        }
+        cudaGetLastError();   // a refused query leaves no error behind
+    }
+    cfg.gridDim = dim3(ctas);
+    at[0].val.clusterDim.x = ctas;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 template <typename K>
-static cudaError_t launch_rs(K kernel, const RsolveArgs& a, cudaStream_t s) {
-    const size_t smem = sizeof(float) * kRsSmemFloats;
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kernel<<<kRsCtas, kRsThreads, smem, s>>>(a);
-    return cudaGetLastError();
+static cudaError_t launch_rs(K kernel, const RsolveArgs& a, cudaStream_t s, int& ctas) {
+    return launch_cluster(kernel, a, kRsThreads, sizeof(float) * kRsSmemFloats, s, ctas);
+}
+
+// The first level (the widest) as a plain launch of one CTA per kept row, the
+// others in one cluster launch.
+template <int M>
+static cudaError_t launch_rf(const RfactorArgs& a, cudaStream_t s, int& ctas) {
+    const long long kept0 = (a.K[0] + 1) / 2;
+    int q0 = 0;
+    if (a.K[0] > 1) {
+        const size_t smem0 = sizeof(float) * rf_smem_floats<M, kRfThreads0>();
+        k_rfactor_f32<M, kRfThreads0, false><<<(unsigned)kept0, kRfThreads0, smem0, s>>>(a, 0, 1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        q0 = 1;
+    }
+    if (q0 >= a.nlev) return cudaSuccess;
+    const size_t smem = sizeof(float) * rf_smem_floats<M, kRfThreads>();
+    auto kernel = k_rfactor_f32<M, kRfThreads, true>;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kRfThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (ctas == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        ctas = kRsCtasPortable;
+        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+            cfg.gridDim = dim3(kRsCtasMax);
+            at[0].val.clusterDim.x = kRsCtasMax;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, kernel, &cfg) == cudaSuccess && n >= 1) ctas = kRsCtasMax;
+        }
+        cudaGetLastError();
+    }
+    cfg.gridDim = dim3(ctas);
+    at[0].val.clusterDim.x = ctas;
+    return cudaLaunchKernelEx(&cfg, kernel, a, q0, a.nlev);
+}
+
+cudaError_t launch_rfactor_f32(const RfactorArgs& a, cudaStream_t s) {
+    if (a.nlev < 1 || a.nlev > kRsMaxLevels) return cudaErrorInvalidValue;
+    static int ctas[2] = {0, 0};
+    switch (a.m) {
+        case 8: return launch_rf<8>(a, s, ctas[0]);
+        case 16: return launch_rf<16>(a, s, ctas[1]);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_rsolve_f32(const RsolveArgs& a, cudaStream_t s) {
     if (a.nlev < 1 || a.nlev > kRsMaxLevels || a.nr < 1 || a.nr > 32) return cudaErrorInvalidValue;
+    static int ctas[3] = {0, 0, 0};
     switch (a.m) {
-        case 8: return launch_rs(k_rsolve_f32<8>, a, s);
-        case 16: return launch_rs(k_rsolve_f32<16>, a, s);
-        case 32: return launch_rs(k_rsolve_f32<32>, a, s);
+        case 8: return launch_rs(k_rsolve_f32<8>, a, s, ctas[0]);
+        case 16: return launch_rs(k_rsolve_f32<16>, a, s, ctas[1]);
+        case 32: return launch_rs(k_rsolve_f32<32>, a, s, ctas[2]);
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -33,7 +33,31 @@ struct CvtArgs {
     long long n[kCvtSegs];
 };
 
+// One-launch FP32 cyclic-reduction factorization of the reduced system (the
+// refined paths, block orders 8 and 16): level q has K[q] rows; its matrix is
+// the FP64 B0, D0, C0 for q = 0 and the FP32 B[q], D[q], C[q] above; it
+// writes al[q], ga[q] ((K+1)/2 blocks), Dinv[q] (K/2 blocks, 1 when K == 1)
+// and the next level's matrix B[q+1], D[q+1], C[q+1].
+struct RfactorArgs {
+    int nlev, m, level0;   // level0: the plan level number of q = 0 (status reports)
+    long long K[kRsMaxLevels];
+    const double* B0;
+    const double* D0;
+    const double* C0;
+    float* B[kRsMaxLevels];
+    float* D[kRsMaxLevels];
+    float* C[kRsMaxLevels];
+    float* al[kRsMaxLevels];
+    float* ga[kRsMaxLevels];
+    float* Dinv[kRsMaxLevels];
+    float* B0f;            // FP32 copies of B0 and C0 for the solves ([K[0]][m][m]; the odd
+    float* C0f;            // rows, the only ones the solves read, are written)
+    long long* status;
+};
+
 cudaError_t launch_cvt_f32(const CvtArgs& a, cudaStream_t s);
+// m in {8, 16}
+cudaError_t launch_rfactor_f32(const RfactorArgs& a, cudaStream_t s);
 // m in {8, 16, 32}
 cudaError_t launch_rsolve_f32(const RsolveArgs& a, cudaStream_t s);
 
