@@ -248,24 +248,8 @@ def run_batch(args, emit=True):
     dev = torch.device("cuda:0")
     scalar = args.workload == "scalar_batch"
     specs = gen.scalar_batch_specs() if scalar else gen.batch_specs(args.batch_count, nmax=args.batch_nmax)
-    systems, unknowns = [], 0
-    gcpu = torch.Generator(device=dev).manual_seed(20091234 + 4000)
-    for sp in specs:
-        N, m = sp.n // sp.m, sp.m
-        s = 1.0 / m ** 0.5
-        if m == 1:
-            D = torch.rand((N, 1, 1), generator=gcpu, device=dev, dtype=torch.float64) * 2 + 4
-            B = torch.rand((N, 1, 1), generator=gcpu, device=dev, dtype=torch.float64) * 2 - 1
-            C = torch.rand((N, 1, 1), generator=gcpu, device=dev, dtype=torch.float64) * 2 - 1
-        else:
-            B = torch.randn((N, m, m), generator=gcpu, device=dev, dtype=torch.float64) * s
-            C = torch.randn((N, m, m), generator=gcpu, device=dev, dtype=torch.float64) * s
-            D = torch.randn((N, m, m), generator=gcpu, device=dev, dtype=torch.float64) * s
-            D += 4 * torch.eye(m, device=dev, dtype=torch.float64)
-        F = torch.randn((N * m, 1), generator=gcpu, device=dev, dtype=torch.float64)
-        systems.append({"B": B, "D": D, "C": C, "F": F, "X": torch.empty_like(F),
-                        "prec": "bf16_ir" if sp.lowprec else "fp64"})
-        unknowns += N * m
+    systems = gen.batch_systems_device(specs, dev)
+    unknowns = sum(sd["F"].shape[0] for sd in systems)
     torch.cuda.synchronize()
     from paper_0912_3678_gb300 import tune
     cap = int(args.batch_memcap_gb * 2 ** 30)

@@ -403,6 +403,33 @@ def scalar_batch_specs(count: int = 1024, n: int = 1 << 16, rep: int = 0) -> lis
     return [BatchSpec(n, 1, False, int(SEED_BASE + 1000 * 1 + 100000 * (rep + 1) + k)) for k in range(count)]
 
 
+def batch_systems_device(specs: list, device, seed: int = SEED_BASE + 4000) -> list:
+    """The batch recipe generated on a CUDA device with torch (the sizes of the
+    full batch do not fit a host round trip): per spec, m = 1 the scalar recipe
+    (d ~ U[4,6], dl, du ~ U[-1,1]), m > 1 the block recipe (D = 4I + G/sqrt(m),
+    B, C = G/sqrt(m)); one right-hand side F ~ N(0,1); "prec" from the spec's
+    precision tag.  Returns dicts with B, D, C, F, an empty X and prec."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    out = []
+    for sp in specs:
+        N, m = sp.n // sp.m, sp.m
+        s = 1.0 / m ** 0.5
+        if m == 1:
+            D = torch.rand((N, 1, 1), generator=g, device=device, dtype=torch.float64) * 2 + 4
+            B = torch.rand((N, 1, 1), generator=g, device=device, dtype=torch.float64) * 2 - 1
+            C = torch.rand((N, 1, 1), generator=g, device=device, dtype=torch.float64) * 2 - 1
+        else:
+            B = torch.randn((N, m, m), generator=g, device=device, dtype=torch.float64) * s
+            C = torch.randn((N, m, m), generator=g, device=device, dtype=torch.float64) * s
+            D = torch.randn((N, m, m), generator=g, device=device, dtype=torch.float64) * s
+            D += 4 * torch.eye(m, device=device, dtype=torch.float64)
+        F = torch.randn((N * m, 1), generator=g, device=device, dtype=torch.float64)
+        out.append({"B": B, "D": D, "C": C, "F": F, "X": torch.empty_like(F),
+                    "prec": "bf16_ir" if sp.lowprec else "fp64"})
+    return out
+
+
 def batch_system(spec: BatchSpec, nrhs: int = 1) -> BtriSystem:
     """Materialise one batched system: m = 1 follows the scalar recipe, m > 1
     the block recipe."""

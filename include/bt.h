@@ -195,6 +195,20 @@ bt_status bt_device_rcp(int64_t n, const double* x, double* y, void* stream);
 /* R = F - A X in FP64 with the matrices given to the last bt_factor. */
 bt_status bt_residual(bt_plan plan, const double* F, const double* X, double* R, int nrhs);
 
+/* R = F - A X as the plan's refinement forms it (the refinement residual of
+ * Sec. 2's mixed-precision use, exposed so that it can be checked entry by
+ * entry): FP64 arithmetic for BT_FP64 plans; for refined plans (BT_FP32_IR,
+ * BT_BF16_IR) FP64-accurate arithmetic off the FP64 pipe -- block order 16
+ * with at most 8 right-hand sides: the products on the tensor cores by an
+ * error-free split into 8-bit digit planes (Ozaki, Ogita, Oishi, Rump 2012),
+ * about 2^-49 of max|a_ij| max|x_j| per entry; otherwise double-float
+ * (hi + lo FP32 pairs, TwoProduct and TwoSum: the compensated dot product of
+ * Ogita, Rump and Oishi 2005), about sqrt(3m) 2^-48 of sum_j |a_ij||x_j| --
+ * in both cases rounded to FP32 precision at the end (relative 2^-24 of
+ * |R|; the correction solve is FP32).  Same arguments and errors as
+ * bt_residual. */
+bt_status bt_refine_residual(bt_plan plan, const double* F, const double* X, double* R, int nrhs);
+
 /* Iterative refinement to FP64 accuracy: X = solve(F); repeat
  * { R = F - A X (FP64); stop if the normwise backward error
  *   ||R||_inf / (||A||_inf ||X||_inf + ||F||_inf) <= eta_tol (see
@@ -435,6 +449,9 @@ bt_status abd_factor(abd_plan plan, const double* S, const double* R, const doub
                      const double* B1);
 bt_status abd_solve(abd_plan plan, const double* RHS, double* Y, int nrhs);
 bt_status abd_residual(abd_plan plan, const double* RHS, const double* Y, double* Rout, int nrhs);
+/* The BABD residual as the plan's refinement forms it (bt_refine_residual:
+ * FP64 for BT_FP64 plans, double-float for refined ones). */
+bt_status abd_refine_residual(abd_plan plan, const double* RHS, const double* Y, double* Rout, int nrhs);
 bt_status abd_refine(abd_plan plan, const double* RHS, double* Y, int nrhs, double tol, int maxit,
                      int* iters_out, double* relcorr_out);
 bt_status abd_sync(abd_plan plan);

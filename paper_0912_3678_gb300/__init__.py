@@ -14,8 +14,9 @@ import ctypes
 from . import _lib
 from ._lib import BT_STATUS, PREC, BtBatchDesc, BtError, BtTuning
 
-__all__ = ["BtPlan", "AbdPlan", "BtError", "BT_STATUS", "PREC", "load_library",
-           "bt_plan_create", "bt_factor", "bt_solve", "bt_residual", "bt_refine", "bt_sync", "bt_info",
+__all__ = ["BtPlan", "AbdPlan", "PbtPlan", "BtError", "BT_STATUS", "PREC", "load_library",
+           "bt_plan_create", "bt_factor", "bt_solve", "bt_residual", "bt_refine_residual", "abd_refine_residual",
+           "bt_refine", "bt_sync", "bt_info",
            "bt_plan_levels", "bt_plan_bytes", "bt_plan_trace", "bt_plan_trace_query", "bt_plan_launches",
            "KERNEL_KINDS", "bt_solve_noalloc", "BT_NOALLOC_SCRATCH_BYTES", "bt_plan_create_tuned",
            "bt_batch_create", "bt_batch_run", "bt_batch_finish", "bt_batch_info", "bt_batch_destroy",
@@ -162,6 +163,16 @@ def abd_residual(plan, RHS, Y, Rout, nrhs):
     _lib.check(_lib.load().abd_residual(plan, _ptr(RHS), _ptr(Y), _ptr(Rout), int(nrhs)), "abd_residual")
 
 
+def bt_refine_residual(plan, F, X, R, nrhs):
+    """The residual as the plan's refinement forms it (FP64-accurate, rounded to FP32 precision)."""
+    _lib.check(_lib.load().bt_refine_residual(plan, _ptr(F), _ptr(X), _ptr(R), int(nrhs)), "bt_refine_residual")
+
+
+def abd_refine_residual(plan, RHS, Y, Rout, nrhs):
+    _lib.check(_lib.load().abd_refine_residual(plan, _ptr(RHS), _ptr(Y), _ptr(Rout), int(nrhs)),
+               "abd_refine_residual")
+
+
 def _refine(fn, name, plan, F, X, nrhs, tol, maxit, raise_on_error):
     it = ctypes.c_int(0)
     rc = ctypes.c_double(0.0)
@@ -241,6 +252,57 @@ def ivp_bvm(L, y0, G, T, p, N, Y=None, stream=None):
     _lib.check(_lib.load().ivp_bvm(int(m), int(p), int(N), float(T), _ptr(L), _ptr(y0), _ptr(G), _ptr(Y),
                                    _stream(stream)), "ivp_bvm")
     return Y
+
+
+class PbtPlan:
+    """Block tridiagonal matrix with corner blocks (pbt_*, bt_pbt.h): B[0] couples
+    row 0 to x_{N-1}, C[N-1] couples row N-1 to x_0; FP64."""
+
+    def __init__(self, N, m, nrhs_max=1, p=0, stream=None):
+        self.n, self.m, self.nrhs_max = int(N), int(m), int(nrhs_max)
+        h = ctypes.c_void_p()
+        _lib.check(_lib.load().pbt_plan_create(ctypes.byref(h), int(N), int(m), int(nrhs_max), int(p),
+                                               _stream(stream)), "pbt_plan_create")
+        self.handle = h
+        self._keep = ()
+
+    def factor(self, B, D, C):
+        self._keep = (B, D, C)
+        _lib.check(_lib.load().pbt_factor(self.handle, _ptr(B), _ptr(D), _ptr(C)), "pbt_factor")
+
+    def solve(self, F, X=None):
+        import torch
+        X = torch.empty_like(F) if X is None else X
+        nr = F.shape[1] if F.dim() == 2 else 1
+        _lib.check(_lib.load().pbt_solve(self.handle, _ptr(F), _ptr(X), int(nr)), "pbt_solve")
+        return X
+
+    def residual(self, F, X, R=None):
+        import torch
+        R = torch.empty_like(F) if R is None else R
+        nr = F.shape[1] if F.dim() == 2 else 1
+        _lib.check(_lib.load().pbt_residual(self.handle, _ptr(F), _ptr(X), _ptr(R), int(nr)), "pbt_residual")
+        return R
+
+    def sync(self):
+        _lib.check(_lib.load().pbt_sync(self.handle), "pbt_sync")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            _lib.load().pbt_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def bt_plan_set_pivot_tol(plan, tau: float):
@@ -536,6 +598,12 @@ class BtPlan(_PlanBase):
         bt_residual(self.handle, F, X, R, self._nrhs(F))
         return R
 
+    def refine_residual(self, F, X, R=None):
+        """bt_refine_residual: the residual the refinement uses."""
+        R = self._new_like_rhs(F) if R is None else R
+        bt_refine_residual(self.handle, F, X, R, self._nrhs(F))
+        return R
+
     def refine(self, F, X=None, tol=1e-12, maxit=30, raise_on_error=True):
         X = self._new_like_rhs(F) if X is None else X
         code, it, rc = bt_refine(self.handle, F, X, self._nrhs(F), tol, maxit, raise_on_error)
@@ -678,6 +746,12 @@ class AbdPlan(_PlanBase):
     def residual(self, RHS, Y, Rout=None):
         Rout = self._new_like_rhs(RHS) if Rout is None else Rout
         abd_residual(self.handle, RHS, Y, Rout, self._nrhs(RHS))
+        return Rout
+
+    def refine_residual(self, RHS, Y, Rout=None):
+        """abd_refine_residual: the residual the refinement uses."""
+        Rout = self._new_like_rhs(RHS) if Rout is None else Rout
+        abd_refine_residual(self.handle, RHS, Y, Rout, self._nrhs(RHS))
         return Rout
 
     def refine(self, RHS, Y=None, tol=1e-12, maxit=30, raise_on_error=True):

@@ -28,6 +28,7 @@ SIGNATURES = {
     "bt_factor": (_i32, [_vp, _vp, _vp, _vp]),
     "bt_solve": (_i32, [_vp, _vp, _vp, _i32]),
     "bt_residual": (_i32, [_vp, _vp, _vp, _vp, _i32]),
+    "bt_refine_residual": (_i32, [_vp, _vp, _vp, _vp, _i32]),
     "bt_refine": (_i32, [_vp, _vp, _vp, _i32, _f64, _i32, _pi32, _pf64]),
     "bt_sync": (_i32, [_vp]),
     "bt_info": (_i32, [_vp, _pi32, _pi64, _pi64]),
@@ -44,6 +45,7 @@ SIGNATURES = {
     "abd_factor": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "abd_solve": (_i32, [_vp, _vp, _vp, _i32]),
     "abd_residual": (_i32, [_vp, _vp, _vp, _vp, _i32]),
+    "abd_refine_residual": (_i32, [_vp, _vp, _vp, _vp, _i32]),
     "abd_refine": (_i32, [_vp, _vp, _vp, _i32, _f64, _i32, _pi32, _pf64]),
     "abd_sync": (_i32, [_vp]),
     "abd_plan_destroy": (None, [_vp]),
@@ -89,6 +91,12 @@ SIGNATURES.update({
     "ivp_parareal": (_i32, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _f64, _i32, _i32, _i32, _i32, _f64, _vp, _vp,
                             ctypes.POINTER(ctypes.c_int), _vp]),
     "ivp_bvm": (_i32, [_i32, _i64, _i64, _f64, _vp, _vp, _vp, _vp, _vp]),
+    "pbt_plan_create": (_i32, [_pvp, _i64, _i32, _i32, _i64, _vp]),
+    "pbt_factor": (_i32, [_vp, _vp, _vp, _vp]),
+    "pbt_solve": (_i32, [_vp, _vp, _vp, _i32]),
+    "pbt_residual": (_i32, [_vp, _vp, _vp, _vp, _i32]),
+    "pbt_sync": (_i32, [_vp]),
+    "pbt_plan_destroy": (None, [_vp]),
     "bt_plan_workspace_size": (_i32, [_i32, _i64, _i32, _i32, _i32, ctypes.POINTER(BtTuning), _pi64]),
     "bt_plan_create_in": (_i32, [_pvp, _i32, _i64, _i32, _i32, _i32, ctypes.POINTER(BtTuning), _vp, _i64, _vp]),
 })

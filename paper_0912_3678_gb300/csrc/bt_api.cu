@@ -950,10 +950,17 @@ bt_status run_residual(bt_plan_s* P, const double* F, const double* X, double* R
         if (e != cudaSuccess) return from_cuda(e);
     }
     cudaError_t e = launch(P, K_RESID, 0, 1, [&] {
-        if (P->kind == 0 && df && P->warp && P->L->warp_ok && P->L->warp_ok(P->lv[0].a, P->lv[0].low) &&
+        // warp-kernel plans: double-float from the split copy the factorization
+        // left; other plans of order 16 with up to 8 right-hand sides: the
+        // tensor-core (digit-plane) residual from the FP64 matrix; else
+        // double-float from the FP64 matrix
+        if (P->kind == 0 && df && P->warp && P->lv[0].a.As && P->L->warp_ok && P->L->warp_ok(P->lv[0].a, P->lv[0].low) &&
             ((((uintptr_t)X) | ((uintptr_t)F)) & 15u) == 0)
             return bt::launch_resid_btri_dfs(P->N, P->m, nr, reinterpret_cast<const float2*>(P->lv[0].a.As), X, F,
                                              R, P->stream, maxout);
+        if (P->kind == 0 && df && P->m == 16 && nr <= 8 &&
+            ((((uintptr_t)P->A0) | ((uintptr_t)P->A1) | ((uintptr_t)P->A2) | ((uintptr_t)X) | ((uintptr_t)F)) & 15u) == 0)
+            return bt::launch_resid_btri_oz(P->N, P->m, nr, P->A0, P->A1, P->A2, X, F, R, P->stream, maxout);
         if (P->kind == 0)
             return df ? bt::launch_resid_btri_df(P->N, P->m, nr, P->A0, P->A1, P->A2, X, F, R, P->stream, maxout)
                       : bt::launch_resid_btri(P->N, P->m, nr, P->A0, P->A1, P->A2, X, F, R, P->stream, maxout);
@@ -1298,12 +1305,12 @@ static bt_status padded_call(bt_plan P, const double* F, double* X, int nrhs, Fn
     return e != cudaSuccess ? from_cuda(e) : st;
 }
 
-static bt_status residual_entry(bt_plan P, const double* F, const double* X, double* R, int nrhs) {
-    if (!P->padded) return run_residual(P, F, X, R, nrhs);
+static bt_status residual_entry(bt_plan P, const double* F, const double* X, double* R, int nrhs, bool df = false) {
+    if (!P->padded) return run_residual(P, F, X, R, nrhs, nullptr, df);
     cudaError_t e = bt::launch_pad_rhs(P->lv[0].rows, P->mu, P->m, nrhs, F, P->Fp, P->stream);
     if (e == cudaSuccess) e = bt::launch_pad_rhs(P->lv[0].rows, P->mu, P->m, nrhs, X, P->Xp, P->stream);
     if (e != cudaSuccess) return from_cuda(e);
-    bt_status st = run_residual(P, P->Fp, P->Xp, P->Rp, nrhs);
+    bt_status st = run_residual(P, P->Fp, P->Xp, P->Rp, nrhs, nullptr, df);
     if (st != BT_OK) return st;
     e = bt::launch_unpad_rhs(P->lv[0].rows, P->mu, P->m, nrhs, P->Rp, R, P->stream);
     P->launches += 3;
@@ -1331,6 +1338,16 @@ bt_status abd_residual(abd_plan P, const double* RHS, const double* Y, double* R
     bt_status st = check_solve(P, 1, RHS, Y, nrhs);
     if (st == BT_OK && !Rout) st = BT_ERR_INVALID;
     return st != BT_OK ? st : residual_entry(P, RHS, Y, Rout, nrhs);
+}
+bt_status bt_refine_residual(bt_plan P, const double* F, const double* X, double* R, int nrhs) {
+    bt_status st = check_solve(P, 0, F, X, nrhs);
+    if (st == BT_OK && !R) st = BT_ERR_INVALID;
+    return st != BT_OK ? st : residual_entry(P, F, X, R, nrhs, P->prec != BT_FP64);
+}
+bt_status abd_refine_residual(abd_plan P, const double* RHS, const double* Y, double* Rout, int nrhs) {
+    bt_status st = check_solve(P, 1, RHS, Y, nrhs);
+    if (st == BT_OK && !Rout) st = BT_ERR_INVALID;
+    return st != BT_OK ? st : residual_entry(P, RHS, Y, Rout, nrhs, P->prec != BT_FP64);
 }
 bt_status bt_refine(bt_plan P, const double* F, double* X, int nrhs, double tol, int maxit, int* iters_out,
                     double* relcorr_out) {

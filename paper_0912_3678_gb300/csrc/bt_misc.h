@@ -54,6 +54,13 @@ cudaError_t launch_resid_btri_df(long long N, int m, int nr, const double* B, co
                                  unsigned long long* maxout = nullptr);
 // The same residual for order 16 with the matrix kept as FP32 pairs float2 [3][N][16][16]
 // (B, D, C; written by the warp-per-partition factorization).
+// The same residual with the products on the tensor cores (block tridiagonal,
+// m = 16, nr <= 8; cudaErrorInvalidValue otherwise): Ozaki splitting into
+// 8-bit digit planes, BF16 mma.sync with FP32 accumulation, double-float
+// combination; the result rounded to FP32 precision (bt_resid_df.cu).
+cudaError_t launch_resid_btri_oz(long long N, int m, int nr, const double* B, const double* D, const double* C,
+                                 const double* X, const double* F, double* R, cudaStream_t s,
+                                 unsigned long long* maxout);
 cudaError_t launch_resid_btri_dfs(long long N, int m, int nr, const float2* As, const double* X, const double* F,
                                   double* R, cudaStream_t s, unsigned long long* maxout = nullptr);
 cudaError_t launch_resid_babd_df(long long N, int m, int nr, const double* S, const double* Rm, const double* B0,

@@ -19,6 +19,7 @@
 // Operands with magnitude below 2^-74 keep only their FP32 part (relative
 // error 2^-24 on those terms); the refined paths need entries inside the
 // FP32 range in any case (their local factors are FP32).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -572,12 +573,277 @@ __global__ void __launch_bounds__(kDfThreads) k_resid_btri_dfs(long long N, int 
 
 template <typename K>
 cudaError_t launch_df(K kernel, size_t smem, long long ctas, cudaStream_t s) {
-    if (smem > 48 * 1024) {
+    // the kernels also hold static shared memory (the maxima reduction), so the
+    // dynamic limit is raised whenever the dynamic part comes near 48 KB
+    if (smem > 40 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     (void)ctas;
     return cudaSuccess;
+}
+
+
+// ---------------------------------------------------------------------------
+// The same residual (block tridiagonal, m = 16, up to 8 right-hand sides)
+// with the products on the tensor cores, by the error-free splitting of
+// Ozaki, Ogita, Oishi and Rump (2012): every row i of [B_j D_j C_j] is scaled
+// by 2^(E_i) (E_i the exponent of the row's largest entry) and written as
+// seven signed 8-bit digits, a_ik = sum_p s_ikp 2^(E_i - 7 - 8p) (the value
+// truncated 56 bits below the row maximum); every column n of the window
+// [x_{j-1}; x_j; x_{j+1}] likewise with its own exponent F_n.  A digit is an
+// integer of magnitude below 256, exact in BF16; a product of two digits is
+// below 2^16 and exact in FP32, and a sum of 48 of them (one block row) below
+// 2^21.6.  The products of digit planes p and q are accumulated per weight
+// t = p + q by BF16 mma.sync m16n8k16 tiles with FP32 accumulation: exact
+// for t <= 5 (at most 3 planes pairs per accumulator, below 2^24), and for
+// t = 6, 7 rounded at 2^-54 of (row maximum x column maximum).  Planes with
+// t >= 8 are dropped (below 2^-54 of the same).  The weighted sum
+// sum_t acc_t 2^(56 - 8t) is formed in double-float arithmetic (Knuth's
+// TwoSum), scaled by 2^(E_i + F_n - 70), subtracted from f in double-float
+// and rounded to FP32 (stored as FP64), as the other double-float residuals.
+// Error: about 2^-49 of |A|_max |x|_max per entry, below the refinement's
+// stopping threshold 4(3m+1) 2^-53 (normwise) by a factor 100.
+//
+// One warp per block row; lane (g, t) = (lane / 4, lane % 4) holds the MMA
+// fragments: rows g and g + 8, columns 2t, 2t+1, 2t+8, 2t+9 of each 16 x 16
+// block of A, rows 2t, 2t+1, 2t+8, 2t+9 of column g of each x block.
+constexpr int kOzThreads = 256;
+
+// exponent field (biased) of |v|, 0 for zero and subnormals
+__device__ __forceinline__ int oz_expo(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
+
+// The seven 8-bit digits of |v| below 2^(eb - 1022) (eb: biased exponent of
+// the scale, eb >= the exponent of v), as floats with the sign of v, most
+// significant first.
+__device__ __forceinline__ void oz_digits(double v, int eb, float (&d)[7]) {
+    const unsigned hw = (unsigned)__double2hiint(v), lw = (unsigned)__double2loint(v);
+    const int ef = (int)((hw >> 20) & 0x7ffu);
+    const unsigned sgn = hw & 0x80000000u;
+    unsigned long long I = 0ull;
+    if (ef != 0 && ef != 0x7ff) {
+        const unsigned long long Mv = ((unsigned long long)((hw & 0xfffffu) | 0x100000u) << 32) | lw;
+        const int sh = ef - eb + 3;   // v = M 2^(ef - 1075) = I 2^(eb - 1023 - 55)
+        if (sh >= 0) I = Mv << sh;
+        else if (sh > -64) I = Mv >> (-sh);
+    }
+    const unsigned ih = (unsigned)(I >> 32), il = (unsigned)I;
+#pragma unroll
+    for (int p = 0; p < 7; ++p) {
+        const int bpos = 6 - p;   // byte of I holding digit p
+        const unsigned b = (bpos >= 4) ? ((ih >> (8 * (bpos - 4))) & 0xffu) : ((il >> (8 * bpos)) & 0xffu);
+        const float f = __fsub_rn(__uint_as_float(0x4b000000u | b), 8388608.f);
+        d[p] = __uint_as_float(__float_as_uint(f) | sgn);
+    }
+}
+
+__device__ __forceinline__ unsigned oz_pack(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const unsigned*>(&v);
+}
+
+__device__ __forceinline__ void oz_mma(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Tiles of kOzRows block rows (one per warp): A blocks (rows padded to 18
+// doubles against bank conflicts), the x rows of the window and f, staged by
+// cp.async, two tiles in flight.
+constexpr int kOzRows = kOzThreads / 32;
+constexpr int kOzLd = 18;                       // padded row of a 16 x 16 block
+constexpr int kOzBlk = 16 * kOzLd;              // doubles per staged block
+__host__ __device__ constexpr int oz_stage_doubles(int nr) {
+    return kOzRows * 3 * kOzBlk + (kOzRows + 2) * 16 * nr + kOzRows * 16 * nr;
+}
+
+__device__ __forceinline__ void oz_cp16(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+
+// Stage tile `tile` (block rows j0 .. j0 + kOzRows - 1) into buffer st.
+__device__ __forceinline__ void oz_stage(double* st, long long tile, long long N, int nr, const double* B,
+                                         const double* D, const double* C, const double* X, const double* F) {
+    constexpr int MM = 256;
+    const long long j0 = tile * kOzRows;
+    const int g = (int)((N - j0 < kOzRows) ? (N - j0) : kOzRows);
+    double* sA = st;
+    double* sX = st + kOzRows * 3 * kOzBlk;
+    double* sF = sX + (kOzRows + 2) * 16 * nr;
+    // A: block (w, kt) row r = 16 doubles = 8 chunks of 16 bytes
+    for (int c = threadIdx.x; c < g * 3 * 16 * 8; c += blockDim.x) {
+        const int ch = c & 7, r = (c >> 3) & 15, blk = c >> 7, w = blk / 3, kt = blk % 3;
+        const double* src = (kt == 0 ? B : kt == 1 ? D : C) + (j0 + w) * MM + r * 16 + 2 * ch;
+        oz_cp16(sA + (w * 3 + kt) * kOzBlk + r * kOzLd + 2 * ch, src);
+    }
+    // x rows j0-1 .. j0+g (those inside 0..N-1), f rows j0 .. j0+g-1: 16 nr doubles per block row
+    const int v2 = 8 * nr;   // 16-byte chunks per block row
+    const long long x0 = j0 - 1 < 0 ? 0 : j0 - 1, x1 = (j0 + g + 1 < N) ? j0 + g + 1 : N;
+    for (int c = threadIdx.x; c < (int)(x1 - x0) * v2; c += blockDim.x) {
+        const long long row = x0 + c / v2;
+        oz_cp16(sX + (row - (j0 - 1)) * 16 * nr + 2 * (c % v2), X + row * 16 * nr + 2 * (c % v2));
+    }
+    for (int c = threadIdx.x; c < g * v2; c += blockDim.x)
+        oz_cp16(sF + 2 * c, F + j0 * 16 * nr + 2 * c);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kOzThreads, 1) k_resid_btri_oz16(long long N, int nr, const double* __restrict__ B,
+                                                                   const double* __restrict__ D,
+                                                                   const double* __restrict__ C,
+                                                                   const double* __restrict__ X,
+                                                                   const double* __restrict__ F,
+                                                                   double* __restrict__ R,
+                                                                   unsigned long long* maxout) {
+    constexpr int M = 16;
+    extern __shared__ __align__(16) double oz_sm[];
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, warp = threadIdx.x >> 5;
+    const long long ntiles = (N + kOzRows - 1) / kOzRows;
+    const int SD = oz_stage_doubles(nr);
+    unsigned long long mr = 0ull, mx = 0ull, mf = 0ull;
+    long long tile = blockIdx.x;
+    if (tile < ntiles) oz_stage(oz_sm, tile, N, nr, B, D, C, X, F);
+    for (int it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+        double* st = oz_sm + (it & 1) * SD;
+        const long long nxt = tile + gridDim.x;
+        if (nxt < ntiles) {
+            oz_stage(oz_sm + ((it + 1) & 1) * SD, nxt, N, nr, B, D, C, X, F);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        __syncthreads();
+        const long long j = tile * kOzRows + warp;
+        if (j < N) {
+        const double* sA = st + warp * 3 * kOzBlk;
+        const double* sX = st + kOzRows * 3 * kOzBlk + warp * 16 * nr;   // window rows j-1, j, j+1
+        const double* sF = st + kOzRows * 3 * kOzBlk + (kOzRows + 2) * 16 * nr + warp * 16 * nr;
+        double a[3][8], xv[3][4];
+#pragma unroll
+        for (int kt = 0; kt < 3; ++kt) {
+            const bool present = (kt == 0) ? (j > 0) : (kt == 2) ? (j + 1 < N) : true;
+            const double* blk = sA + kt * kOzBlk;
+            if (present) {
+                const double2 u0 = *reinterpret_cast<const double2*>(blk + g * kOzLd + 2 * t);
+                const double2 u1 = *reinterpret_cast<const double2*>(blk + (g + 8) * kOzLd + 2 * t);
+                const double2 u2 = *reinterpret_cast<const double2*>(blk + g * kOzLd + 2 * t + 8);
+                const double2 u3 = *reinterpret_cast<const double2*>(blk + (g + 8) * kOzLd + 2 * t + 8);
+                a[kt][0] = u0.x; a[kt][1] = u0.y; a[kt][2] = u1.x; a[kt][3] = u1.y;
+                a[kt][4] = u2.x; a[kt][5] = u2.y; a[kt][6] = u3.x; a[kt][7] = u3.y;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) a[kt][e] = 0.0;
+            }
+            const bool col = g < nr;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int k = 2 * t + (e & 1) + 8 * (e >> 1);
+                xv[kt][e] = (present && col) ? sX[(kt * 16 + k) * nr + g] : 0.0;
+            }
+        }
+        // scales: row maxima (rows g, g+8) and the window's column maximum (column g)
+        int ea0 = 0, ea1 = 0, ex = 0;
+#pragma unroll
+        for (int kt = 0; kt < 3; ++kt) {
+            ea0 = max(ea0, max(max(oz_expo(a[kt][0]), oz_expo(a[kt][1])), max(oz_expo(a[kt][4]), oz_expo(a[kt][5]))));
+            ea1 = max(ea1, max(max(oz_expo(a[kt][2]), oz_expo(a[kt][3])), max(oz_expo(a[kt][6]), oz_expo(a[kt][7]))));
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                ex = max(ex, oz_expo(xv[kt][e]));
+                mx = umax_(mx, abs_bits64(xv[kt][e]));
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < 4; o <<= 1) {
+            ea0 = max(ea0, __shfl_xor_sync(0xffffffffu, ea0, o));
+            ea1 = max(ea1, __shfl_xor_sync(0xffffffffu, ea1, o));
+            ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, o));
+        }
+        // digit-plane products, accumulated per weight t = p + q
+        float acc[9][4];
+#pragma unroll
+        for (int u = 0; u < 9; ++u)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[u][e] = 0.f;
+#pragma unroll
+        for (int kt = 0; kt < 3; ++kt) {
+            unsigned af[7][4], bf[7][2];
+            {
+                float d0[7], d1[7];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int eb = (r & 1) ? ea1 : ea0;   // registers 1 and 3 hold row g + 8
+                    oz_digits(a[kt][2 * r], eb, d0);
+                    oz_digits(a[kt][2 * r + 1], eb, d1);
+#pragma unroll
+                    for (int p = 0; p < 7; ++p) af[p][r] = oz_pack(d0[p], d1[p]);
+                }
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    oz_digits(xv[kt][2 * r], ex, d0);
+                    oz_digits(xv[kt][2 * r + 1], ex, d1);
+#pragma unroll
+                    for (int q = 0; q < 7; ++q) bf[q][r] = oz_pack(d0[q], d1[q]);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < 7; ++p)
+#pragma unroll
+                for (int q = 0; q < 7; ++q) {
+                    if (p + q > 7) continue;
+                    const int w = p + q;
+                    // accumulator of weight w (weight 5 split in two: at most 3 plane pairs each)
+                    const int slot = (w < 5) ? w : (w == 5) ? (p < 3 ? 5 : 6) : w + 1;
+                    oz_mma(acc[slot], af[p], bf[q][0], bf[q][1]);
+                }
+        }
+        // r = f - (sum_w acc_w 2^(56 - 8w)) 2^(E_row + F_col - 70), in double-float
+        const float wts[9] = {0x1p56f, 0x1p48f, 0x1p40f, 0x1p32f, 0x1p24f, 0x1p16f, 0x1p16f, 0x1p8f, 1.f};
+        // the other lanes' column exponents: outputs of this lane are columns 2t, 2t+1
+        const int exc0 = __shfl_sync(0xffffffffu, ex, 4 * (2 * t));
+        const int exc1 = __shfl_sync(0xffffffffu, ex, 4 * (2 * t + 1));
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int row = (e < 2) ? g : g + 8;
+            const int colw = 2 * t + (e & 1);
+            if (colw >= nr) continue;
+            float sh = 0.f, sl = 0.f;
+#pragma unroll
+            for (int u = 8; u >= 0; --u) {
+                float err;
+                two_sum(sh, acc[u][e] * wts[u], sh, err);
+                sl = __fadd_rn(sl, err);
+            }
+            const int eb = ((e < 2) ? ea0 : ea1) + ((e & 1) ? exc1 : exc0) - 2046;   // E_row + F_col (unbiased sum)
+            const long long orow = j * M + row;
+            const double fv = sF[row * nr + colw];
+            mf = umax_(mf, abs_bits64(fv));
+            const int k = eb - 70;
+            double rv;
+            if (k > -100 && k < 40) {
+                const float sc = __uint_as_float((unsigned)(k + 127) << 23);
+                const float2 fs = split_f64(fv);
+                float u, ue;
+                two_sum(fs.x, -(sh * sc), u, ue);
+                const float low = __fadd_rn(__fsub_rn(fs.y, sl * sc), ue);
+                rv = f32_to_f64(__fadd_rn(u, low));
+            } else {
+                // far outside the FP32 range of the scaled sum: FP64 arithmetic
+                rv = fv - ldexp(f32_to_f64(sh) + f32_to_f64(sl), k);
+            }
+            if (oz_expo(fv) == 0x7ff || ((e < 2) ? ea0 : ea1) == 0x7ff || ((e & 1) ? exc1 : exc0) == 0x7ff)
+                rv = fv + __longlong_as_double(0x7ff8000000000000ll);   // non-finite operands
+            R[orow * nr + colw] = rv;
+            mr = umax_(mr, abs_bits64(rv));
+        }
+        }
+        __syncthreads();   // the buffer is refilled by the next iteration's staging
+    }
+    if (maxout) block_max3_df(mr, mx, mf, maxout);
 }
 
 }  // namespace
@@ -586,6 +852,24 @@ static size_t resid_dfs_smem(int m, int nr, int G) {
     const int pcp = 1 << df_pair_shift(nr), V = m * nr;
     const size_t nA = (size_t)G * 3 * m * m, nX = (size_t)(G + 2) * V, nF = (size_t)G * V;
     return 2 * nA * sizeof(float2) + 2 * (nX + nF) * sizeof(double) + (size_t)(G + 2) * m * pcp * sizeof(float4);
+}
+
+cudaError_t launch_resid_btri_oz(long long N, int m, int nr, const double* B, const double* D, const double* C,
+                                 const double* X, const double* F, double* R, cudaStream_t s,
+                                 unsigned long long* maxout) {
+    if (N <= 0) return cudaSuccess;
+    if (m != 16 || nr < 1 || nr > 8 || (((uintptr_t)B | (uintptr_t)D | (uintptr_t)C) & 15u)) return cudaErrorInvalidValue;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (((uintptr_t)X | (uintptr_t)F) & 15u) return cudaErrorInvalidValue;
+    const long long ntiles = (N + kOzRows - 1) / kOzRows;
+    long long grid = ntiles < sms ? ntiles : sms;
+    const size_t smem = 2 * sizeof(double) * (size_t)oz_stage_doubles(nr);
+    cudaError_t e = cudaFuncSetAttribute(k_resid_btri_oz16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_resid_btri_oz16<<<(unsigned)grid, kOzThreads, smem, s>>>(N, nr, B, D, C, X, F, R, maxout);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_resid_btri_dfs(long long N, int m, int nr, const float2* As, const double* X, const double* F,
