@@ -54,6 +54,10 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -407,12 +411,33 @@ struct WarpS16 {
     static constexpr int M = 16;
     static constexpr int WARPS = 4;
     static constexpr int SW = 2 * NH + 4;   // exchange row stride (floats)
-    struct Smem {
-        double stage[2][M * WarpF16::SR];    // B_j of two block rows (FP64)
+    static constexpr int S = 4;             // block rows in flight (copy ring depth)
+    static constexpr int NRMAX = 2 * NH;    // right-hand sides the variant takes
+    struct alignas(16) Smem {
+        double sB[S][M * WarpF16::SR];       // forward: B_j (FP64)
+        float sA[S][M * M];                  // forward: D'^{-1}_j; backward: Y_j
+        float sC[S][M * M];                  // forward: W_j; backward: Zc_j
+        double sV[S][M * NRMAX];             // forward: f_j; backward: X_j (update form)
+        float sH[S][M * NRMAX];              // backward: h_j
         float xa[M * SW];                    // exchange row: h_{j-1}, t_j, or x_{j+1}
         float xb[M * SW];                    // exchange row: h_j, or x_L
     };
 };
+
+// Copies of one block row's operands into ring slot b (every lane takes a
+// share; 16-byte copies for the 16 x 16 blocks, 8-byte copies for the
+// right-hand-side rows, whose base need not be 16-byte aligned).
+__device__ __forceinline__ void ring_blk32(float* dst, const float* src, int lane) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) cp_async16(dst + 4 * (q * 32 + lane), src + 4 * (q * 32 + lane));
+}
+__device__ __forceinline__ void ring_vec64(double* dst, const double* src, int n, int lane) {
+    for (int e = lane; e < n; e += 32) cp_async8(dst + e, src + e);
+}
+__device__ __forceinline__ void ring_vec32(float* dst, const float* src, int n, int lane) {
+    // n floats, n a multiple of 4 (16 nr), src 16-byte aligned
+    for (int e = lane; e < n / 4; e += 32) cp_async16(dst + 4 * e, src + 4 * e);
+}
 
 template <int NH>
 __device__ __forceinline__ void load_vec(float (&v)[NH], const double* g, int cbase, int nr) {
@@ -445,7 +470,8 @@ __device__ __forceinline__ void load_row16(float (&v)[16], const float* g) { rea
 template <int NH>
 __device__ __forceinline__ void solve_fwd_w16_body(const LevelArgs& a, const long long i,
                                                    typename WarpS16<NH>::Smem& sm) {
-    constexpr int M = 16, SW = WarpS16<NH>::SW;
+    using WS = WarpS16<NH>;
+    constexpr int M = 16, SW = WS::SW, S = WS::S;
     const int lane = threadIdx.x & 31, r = lane & 15, hc = lane >> 4;
     const int nr = a.nr, E = M * nr, cb = hc * NH;
     const Part pt = part_bounds(a, 0, i);
@@ -458,45 +484,42 @@ __device__ __forceinline__ void solve_fwd_w16_body(const LevelArgs& a, const lon
     float acc[NH];
 #pragma unroll
     for (int q = 0; q < NH; ++q) acc[q] = 0.f;
-    // prefetch of the next row: D'^{-1} row r, W row r, f entries
-    float pDi[16], pW[16], pf[NH];
-    auto fetch = [&](long long j) {
-        load_row16(pDi, gDi + j * MM + r * M);
-        if (pt.hasL) load_row16(pW, gW + j * MM + r * M);
-        load_vec<NH>(pf, a.F + (j * M + r) * nr, cb, nr);
-    };
-    if (pt.s < pt.e) {
-        fetch(pt.s);
-        if (pt.s + 1 < pt.e) stage_blk16(sm.stage[1], a.B + (pt.s + 1 - a.shift) * MM, lane);
-        cp_async_commit();
-    }
-    for (long long j = pt.s; j < pt.e; ++j) {
-        const int buf = (int)((j - pt.s) & 1);
-        float Di[16], Wr[16], t[NH];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            Di[k] = pDi[k];
-            Wr[k] = pW[k];
+    // operands of local row s + t go to ring slot t % S, S - 1 rows ahead of use
+    auto issue = [&](long long t) {
+        const long long j = pt.s + t;
+        if (j < pt.e) {
+            const int b = (int)(t % S);
+            if (j > pt.s) stage_blk16(sm.sB[b], a.B + (j - a.shift) * MM, lane);
+            ring_blk32(sm.sA[b], gDi + j * MM, lane);
+            if (pt.hasL) ring_blk32(sm.sC[b], gW + j * MM, lane);
+            ring_vec64(sm.sV[b], a.F + j * E, E, lane);
         }
+        cp_async_commit();   // one group per row, empty past the end
+    };
+    const long long n = pt.e - pt.s;
 #pragma unroll
-        for (int q = 0; q < NH; ++q) t[q] = pf[q];
-        if (j + 1 < pt.e) fetch(j + 1);
-        // B_j sits in stage[(j - s) & 1]; B_{s+1} was issued before the loop
-        if (j > pt.s && j + 1 < pt.e) stage_blk16(sm.stage[buf ^ 1], a.B + (j + 1 - a.shift) * MM, lane);
-        cp_async_commit();
+    for (int t = 0; t < S - 1; ++t) issue(t);
+    for (long long t = 0; t < n; ++t) {
+        const long long j = pt.s + t;
+        const int b = (int)(t % S);
+        cp_async_wait<S - 2>();
+        __syncwarp();
+        issue(t + S - 1);    // into the slot row t - 1 used
+        float t4[NH];
+#pragma unroll
+        for (int q = 0; q < NH; ++q) t4[q] = (cb + q < nr) ? trunc_f32(sm.sV[b][r * nr + cb + q]) : 0.f;
         if (j > pt.s) {
             // t = f_j - B_j h_{j-1}  (h_{j-1} in xb)
-            cp_async_wait<1>();
-            __syncwarp();
             float Br[16];
-            const double* sb = sm.stage[buf] + r * WarpF16::SR;
+            const double* sbr = sm.sB[b] + r * WarpF16::SR;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) Br[k] = trunc_f32(sb[k]);
-            gemv_acc<NH, true>(t, Br, sm.xb + cb, SW);
+            for (int k = 0; k < 16; ++k) Br[k] = trunc_f32(sbr[k]);
+            gemv_acc<NH, true>(t4, Br, sm.xb + cb, SW);
         }
-        put_vec<NH>(xa, t);
+        put_vec<NH>(xa, t4);
         __syncwarp();
-        float h[NH];
+        float Di[16], h[NH];
+        read_row16(Di, sm.sA[b] + r * M);
 #pragma unroll
         for (int q = 0; q < NH; ++q) h[q] = 0.f;
         gemv_acc<NH, false>(h, Di, sm.xa + cb, SW);
@@ -506,7 +529,12 @@ __device__ __forceinline__ void solve_fwd_w16_body(const LevelArgs& a, const lon
         for (int q = 0; q < NH; ++q)
             if (cb + q < nr) gH[j * E + r * nr + cb + q] = h[q];
         __syncwarp();
-        if (pt.hasL) gemv_acc<NH, false>(acc, Wr, sm.xb + cb, SW);
+        if (pt.hasL) {
+            float Wr[16];
+            read_row16(Wr, sm.sC[b] + r * M);
+            gemv_acc<NH, false>(acc, Wr, sm.xb + cb, SW);
+        }
+        __syncwarp();          // slot b is refilled by the next iteration
     }
     cp_async_wait<0>();
     __syncwarp();
@@ -537,7 +565,8 @@ __device__ __forceinline__ void solve_fwd_w16_body(const LevelArgs& a, const lon
 template <int NH>
 __device__ __forceinline__ void solve_bwd_w16_body(const LevelArgs& a, const long long i,
                                                    typename WarpS16<NH>::Smem& sm) {
-    constexpr int M = 16, SW = WarpS16<NH>::SW;
+    using WS = WarpS16<NH>;
+    constexpr int M = 16, SW = WS::SW, S = WS::S;
     const int lane = threadIdx.x & 31, r = lane & 15, hc = lane >> 4;
     const int nr = a.nr, E = M * nr, cb = hc * NH;
     const Part pt = part_bounds(a, 0, i);
@@ -547,6 +576,22 @@ __device__ __forceinline__ void solve_bwd_w16_body(const LevelArgs& a, const lon
     const float* gH = reinterpret_cast<const float*>(a.Hv);
     float* xa = sm.xa + r * SW + cb;   // x_{j+1}
     float* xb = sm.xb + r * SW + cb;   // x_L
+    auto useY = [&](long long j) { return (j < pt.e - 1) || pt.hasR; };
+    // operands of local row e - 1 - t go to ring slot t % S, S - 1 rows ahead of use
+    auto issue = [&](long long t) {
+        const long long j = pt.e - 1 - t;
+        if (j >= pt.s) {
+            const int b = (int)(t % S);
+            if (useY(j)) ring_blk32(sm.sA[b], gY + j * MM, lane);
+            if (pt.hasL) ring_blk32(sm.sC[b], gZ + j * MM, lane);
+            ring_vec32(sm.sH[b], gH + j * E, E, lane);
+            if (a.accum) ring_vec64(sm.sV[b], a.X + j * E, E, lane);
+        }
+        cp_async_commit();
+    };
+    const long long n = pt.e - pt.s;
+#pragma unroll
+    for (int t = 0; t < S - 1; ++t) issue(t);
     float v[NH];
     float dd = 0.f, xx = 0.f;   // update form: sums of d^2 and of the updated x^2
     if (pt.hasR) {
@@ -578,28 +623,25 @@ __device__ __forceinline__ void solve_bwd_w16_body(const LevelArgs& a, const lon
         put_vec<NH>(xb, v);
     }
     __syncwarp();
-    auto useY = [&](long long j) { return (j < pt.e - 1) || pt.hasR; };
-    float pY[16], pZ[16], ph[NH];
-    auto fetch = [&](long long j) {
-        if (useY(j)) load_row16(pY, gY + j * MM + r * M);
-        if (pt.hasL) load_row16(pZ, gZ + j * MM + r * M);
+    for (long long t = 0; t < n; ++t) {
+        const long long j = pt.e - 1 - t;
+        const int b = (int)(t % S);
+        cp_async_wait<S - 2>();
+        __syncwarp();
+        issue(t + S - 1);    // into the slot row j + 1 used
+        float x[NH];
 #pragma unroll
-        for (int q = 0; q < NH; ++q) ph[q] = (cb + q < nr) ? gH[j * E + r * nr + cb + q] : 0.f;
-    };
-    if (pt.e > pt.s) fetch(pt.e - 1);
-    for (long long j = pt.e - 1; j >= pt.s; --j) {
-        float Yr[16], Zr[16], x[NH];
-        const bool uY = useY(j);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            Yr[k] = pY[k];
-            Zr[k] = pZ[k];
+        for (int q = 0; q < NH; ++q) x[q] = (cb + q < nr) ? sm.sH[b][r * nr + cb + q] : 0.f;
+        if (useY(j)) {
+            float Yr[16];
+            read_row16(Yr, sm.sA[b] + r * M);
+            gemv_acc<NH, true>(x, Yr, sm.xa + cb, SW);
         }
-#pragma unroll
-        for (int q = 0; q < NH; ++q) x[q] = ph[q];
-        if (j - 1 >= pt.s) fetch(j - 1);
-        if (uY) gemv_acc<NH, true>(x, Yr, sm.xa + cb, SW);
-        if (pt.hasL) gemv_acc<NH, false>(x, Zr, sm.xb + cb, SW);
+        if (pt.hasL) {
+            float Zr[16];
+            read_row16(Zr, sm.sC[b] + r * M);
+            gemv_acc<NH, false>(x, Zr, sm.xb + cb, SW);
+        }
         __syncwarp();          // x_{j+1} fully read
         put_vec<NH>(xa, x);
         double* xo = a.X + j * E + r * nr;
@@ -607,7 +649,7 @@ __device__ __forceinline__ void solve_bwd_w16_body(const LevelArgs& a, const lon
 #pragma unroll
             for (int q = 0; q < NH; ++q)
                 if (cb + q < nr) {
-                    const double xn = xo[cb + q] + (double)x[q];
+                    const double xn = sm.sV[b][r * nr + cb + q] + (double)x[q];
                     xo[cb + q] = xn;
                     const float xf = trunc_f32(xn);
                     dd = fmaf(x[q], x[q], dd);
@@ -618,8 +660,10 @@ __device__ __forceinline__ void solve_bwd_w16_body(const LevelArgs& a, const lon
             for (int q = 0; q < NH; ++q)
                 if (cb + q < nr) xo[cb + q] = (double)x[q];
         }
-        __syncwarp();
+        __syncwarp();          // slot b is refilled by the next iteration
     }
+    cp_async_wait<0>();
+    __syncwarp();
     if (a.accum) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
