@@ -65,13 +65,19 @@ __device__ __forceinline__ double widen(float f) {
 }
 
 // Shared-memory staging: every level is processed in chunks of rows of this
-// CTA's share; a chunk's blocks and vectors arrive in one round of coalesced
-// 16-byte loads (L2, past L1) and are then used from shared memory.
+// CTA's share; a chunk's blocks and vectors are copied with cp.async (16-byte
+// copies through L2, past L1, every copy of the chunk in flight at once) and
+// then used from shared memory.
+__device__ __forceinline__ void rs_cp16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void rs_cp_wait() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
 __device__ __forceinline__ void stage_f4(float* dst, const float* src, long long n) {
     // n multiple of 4, both 16-byte aligned
-    const float4* s4 = reinterpret_cast<const float4*>(src);
-    float4* d4 = reinterpret_cast<float4*>(dst);
-    for (int e = threadIdx.x; e < (int)(n / 4); e += blockDim.x) d4[e] = __ldcg(s4 + e);
+    for (int e = threadIdx.x; e < (int)(n / 4); e += blockDim.x) rs_cp16(dst + 4 * e, src + 4 * e);
 }
 __device__ __forceinline__ void zero_f4(float* dst, long long n) {
     float4* d4 = reinterpret_cast<float4*>(dst);
@@ -102,10 +108,53 @@ __device__ __forceinline__ void put_x1(const RsolveArgs& a, int q, long long idx
     if (q == 0) a.X0[idx] = widen(v);
     else a.x[q][idx] = v;
 }
-// dst <- f[q] entries [e0, e0 + n) (n and e0 multiples of 4)
+// dst <- f[q] entries [e0, e0 + n) (n and e0 multiples of 4): cp.async for the
+// FP32 levels; the FP64 first level is loaded kRsUnroll float4 units per thread
+// at a time (all loads issued before the converted values are stored).
+constexpr int kRsUnroll = 4;
 __device__ __forceinline__ void stage_fq(const RsolveArgs& a, int q, float* dst, long long e0, long long n) {
+    if (q > 0) {
+        stage_f4(dst, a.f[q] + e0, n);
+        return;
+    }
     float4* d4 = reinterpret_cast<float4*>(dst);
-    for (int e = threadIdx.x; e < (int)(n / 4); e += blockDim.x) d4[e] = get_f4(a, q, e0 / 4 + e);
+    const int n4 = (int)(n / 4), T = blockDim.x;
+    for (int b = threadIdx.x; b < n4; b += kRsUnroll * T) {
+        float4 v[kRsUnroll];
+#pragma unroll
+        for (int u = 0; u < kRsUnroll; ++u)
+            if (b + u * T < n4) v[u] = get_f4(a, 0, e0 / 4 + b + u * T);
+#pragma unroll
+        for (int u = 0; u < kRsUnroll; ++u)
+            if (b + u * T < n4) d4[b + u * T] = v[u];
+    }
+}
+
+// dst <- the odd rows 2i + 1, i in [c0, c0 + n), of f^q (rows of E entries).
+__device__ __forceinline__ void stage_odd_fq(const RsolveArgs& a, int q, float* dst, long long c0, int n, int E) {
+    const int E4 = E / 4, n4 = n * E4, T = blockDim.x;
+    if (q > 0) {
+        for (int e = threadIdx.x; e < n4; e += T) {
+            const int il = e / E4, w = e - il * E4;
+            rs_cp16(dst + 4 * e, a.f[q] + (2 * (c0 + il) + 1) * E + 4 * w);
+        }
+        return;
+    }
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (int b = threadIdx.x; b < n4; b += kRsUnroll * T) {
+        float4 v[kRsUnroll];
+#pragma unroll
+        for (int u = 0; u < kRsUnroll; ++u) {
+            const int e = b + u * T;
+            if (e < n4) {
+                const int il = e / E4, w = e - il * E4;
+                v[u] = get_f4(a, 0, (2 * (c0 + il) + 1) * E4 + w);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kRsUnroll; ++u)
+            if (b + u * T < n4) d4[b + u * T] = v[u];
+    }
 }
 
 constexpr int kRsSmemFloats = 24 * 1024;   // 96 KB of shared memory per CTA
@@ -137,6 +186,7 @@ __device__ void rs_forward(const RsolveArgs& a, int q, long long lo, long long h
         }
         const long long nf = f1 - f0;
         if (nf < 2 * n + 1) zero_f4(sf + nf * E, (2 * n + 1 - nf) * E);
+        rs_cp_wait();
         __syncthreads();
         if (v4) {
             const int E4 = E / 4, n4 = nr / 4;
@@ -198,17 +248,15 @@ __device__ void rs_backward(const RsolveArgs& a, int q, long long lo, long long 
         for (int e = threadIdx.x; e < (int)nodd * (MM / 4); e += blockDim.x) {
             const int il = e / (MM / 4), w = e % (MM / 4);
             const long long rw = 2 * (c0 + il) + 1;
-            reinterpret_cast<float4*>(sB)[e] = __ldcg(reinterpret_cast<const float4*>(a.B[q] + rw * MM) + w);
-            reinterpret_cast<float4*>(sC)[e] = __ldcg(reinterpret_cast<const float4*>(a.C[q] + rw * MM) + w);
-        }
-        for (int e = threadIdx.x; e < (int)nodd * (E / 4); e += blockDim.x) {
-            const int il = e / (E / 4), w = e - il * (E / 4);
-            reinterpret_cast<float4*>(sf)[e] = get_f4(a, q, (2 * (c0 + il) + 1) * (E / 4) + w);
+            rs_cp16(sB + 4 * e, a.B[q] + rw * MM + 4 * w);
+            rs_cp16(sC + 4 * e, a.C[q] + rw * MM + 4 * w);
         }
         stage_f4(sD, a.Dinv[q] + c0 * MM, nodd * MM);
         const long long xend = (c1 + 1 <= kept) ? c1 + 1 : kept;   // x^{q+1} rows [c0, xend)
         stage_f4(sx, a.x[q + 1] + c0 * E, (xend - c0) * E);
+        stage_odd_fq(a, q, sf, c0, (int)nodd, E);
         if (xend - c0 < n + 1) zero_f4(sx + (xend - c0) * E, (n + 1 - (xend - c0)) * E);
+        rs_cp_wait();
         __syncthreads();
         for (int u = threadIdx.x; u < (int)n * (E / 4); u += blockDim.x) {
             const int il = u / (E / 4);
@@ -311,8 +359,8 @@ __global__ void __launch_bounds__(kRsThreads) k_rsolve_f32(const RsolveArgs a) {
             rs_forward<M>(a, q, 0, (a.K[q] + 1) / 2, sm);   // ends with __syncthreads
         }
         const float* Di = a.Dinv[top];
-        if (top == 0) stage_fq(a, 0, sm, 0, E);
-        else stage_f4(sm, a.f[top], E);
+        stage_fq(a, top, sm, 0, E);
+        rs_cp_wait();
         __syncthreads();
         for (int u = threadIdx.x; u < E; u += blockDim.x) {
             const int r = u / nr, c = u % nr;
