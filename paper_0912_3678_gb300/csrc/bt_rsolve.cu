@@ -9,12 +9,13 @@
 //   backward  x^q_{2i} = x^{q+1}_i,
 //             x^q_{2i+1} = D_{2i+1}^{-1} (f^q_{2i+1} - B_{2i+1} x^{q+1}_i - C_{2i+1} x^{q+1}_{i+1}),
 // with a hardware cluster barrier between levels (no spin loops, no
-// grid-wide dependency); levels with at most kRsCluster rows are finished by
-// one CTA between __syncthreads.  The level vectors live in global memory (L2)
-// and are read past L1 (ld.global.cg); the first level reads the FP64
-// right-hand side and writes the FP64 solution directly, converting as it
-// goes.  The factors come from an FP32 cyclic reduction (or FP32 copies of an
-// FP64 one).
+// grid-wide dependency).  The wide levels keep their vectors in global memory
+// (L2; chunks of rows staged into shared memory with cp.async); the levels of
+// at most kRsSmall rows are finished by CTA 0 from its shared memory, their
+// blocks copied in one batch, between __syncthreads.  The first level reads
+// the FP64 right-hand side and writes the FP64 solution directly, converting
+// as it goes.  The factors come from an FP32 cyclic reduction (or FP32 copies
+// of an FP64 one).
 #include <cuda_runtime.h>
 
 #include "bt_bcr.cuh"
@@ -157,26 +158,103 @@ __device__ __forceinline__ void stage_odd_fq(const RsolveArgs& a, int q, float* 
     }
 }
 
-constexpr int kRsSmemFloats = 24 * 1024;   // 96 KB of shared memory per CTA
-constexpr long long kRsCluster = 64;       // levels with more rows run on the whole cluster
+constexpr int kRsSmemFloats = 56 * 1024;   // 224 KB of shared memory per CTA
+constexpr long long kRsSmall = 32;         // levels with at most this many rows run on CTA 0
+
+// In shared memory an m x m block keeps its rows m + 4 floats apart: a row
+// stays 16-byte aligned and read as float4 pieces, and the rows that the 8
+// lanes of one shared-memory phase read fall in different banks.
+__host__ __device__ constexpr int rs_row_stride(int m) { return m + 4; }
+__host__ __device__ constexpr long long rs_block_floats(int m) { return (long long)m * rs_row_stride(m); }
+
+// nblk consecutive m x m blocks from global memory into padded blocks.
+template <int M>
+__device__ __forceinline__ void stage_blocks(float* dst, const float* src, long long nblk) {
+    constexpr int Q = M / 4, P = rs_row_stride(M);
+    const int n = (int)nblk * M * Q;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int row = e / Q, w = e - row * Q;   // row counts across the blocks
+        rs_cp16(dst + row * P + 4 * w, src + (long long)row * M + 4 * w);
+    }
+}
+// The blocks 2i + 1, i in [c0, c0 + nblk), of a level matrix.
+template <int M>
+__device__ __forceinline__ void stage_odd_blocks(float* dst, const float* src, long long c0, long long nblk) {
+    constexpr int Q = M / 4, P = rs_row_stride(M), MM = M * M;
+    const int n = (int)nblk * M * Q;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) {
+        const int row = e / Q, w = e - row * Q, b = row / M, r = row - b * M;
+        rs_cp16(dst + row * P + 4 * w, src + (2 * (c0 + b) + 1) * MM + r * M + 4 * w);
+    }
+}
+
+// W consecutive floats (16-byte aligned for W == 4).
+template <int W>
+__device__ __forceinline__ void ldw(float (&v)[W], const float* p) {
+    if constexpr (W == 4) {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        v[0] = t.x;
+        v[1] = t.y;
+        v[2] = t.z;
+        v[3] = t.w;
+    } else {
+#pragma unroll
+        for (int w = 0; w < W; ++w) v[w] = p[w];
+    }
+}
+template <int W>
+__device__ __forceinline__ void stw(float* p, const float (&v)[W]) {
+    if constexpr (W == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int w = 0; w < W; ++w) p[w] = v[w];
+    }
+}
+// s[w] +=(-=) sum_k A[k] X[k nr + w]: A one padded block row (float4 pieces),
+// X the W columns of a block vector in shared memory.
+template <int M, int W, bool NEG>
+__device__ __forceinline__ void row_dot(float (&s)[W], const float* A, const float* X, int nr) {
+#pragma unroll
+    for (int kq = 0; kq < M / 4; ++kq) {
+        const float4 a4 = *reinterpret_cast<const float4*>(A + 4 * kq);
+        const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float x[W];
+            ldw<W>(x, X + (4 * kq + j) * nr);
+#pragma unroll
+            for (int w = 0; w < W; ++w) s[w] = fmaf(NEG ? -av[j] : av[j], x[w], s[w]);
+        }
+    }
+}
+// W entries of level q's solution (the FP64 X0 for q == 0).
+template <int W>
+__device__ __forceinline__ void put_xw(const RsolveArgs& a, int q, long long idx, const float (&v)[W]) {
+    if constexpr (W == 4) {
+        put_x4(a, q, idx / 4, make_float4(v[0], v[1], v[2], v[3]));
+    } else {
+#pragma unroll
+        for (int w = 0; w < W; ++w) put_x1(a, q, idx + w, v[w]);
+    }
+}
 
 // Forward step of level q for its kept rows [lo, hi): f^{q+1}_i = f_{2i} +
-// alpha_i f_{2i-1} + gamma_i f_{2i+1}; chunks staged in shared memory.  With
-// nr a multiple of 4 a unit is (row, block-row entry, 4 columns).
-template <int M>
+// alpha_i f_{2i-1} + gamma_i f_{2i+1}; chunks staged in shared memory.  A unit
+// is (row, block-row entry, W columns).
+template <int M, int W>
 __device__ void rs_forward(const RsolveArgs& a, int q, long long lo, long long hi, float* sm) {
-    constexpr int MM = M * M;
-    const int nr = a.nr, E = M * nr;
+    constexpr int MM = M * M, P = rs_row_stride(M), MP = M * P;
+    const int nr = a.nr, E = M * nr, EW = E / W;
     const long long K = a.K[q];
-    const int CH = (kRsSmemFloats - E) / (2 * MM + 2 * E);
-    const bool v4 = (nr & 3) == 0;
+    const int CH = (a.chunk - E) / (2 * MP + 2 * E);
     for (long long c0 = lo; c0 < hi; c0 += CH) {
         const long long c1 = (c0 + CH < hi) ? c0 + CH : hi, n = c1 - c0;
         float* sal = sm;
-        float* sga = sal + n * MM;
-        float* sf = sga + n * MM;   // f rows 2 c0 - 1 .. 2 c1 - 1 (row 2 c0 - 1 at slot 0)
-        stage_f4(sal, a.al[q] + c0 * MM, n * MM);
-        stage_f4(sga, a.ga[q] + c0 * MM, n * MM);
+        float* sga = sal + n * MP;
+        float* sf = sga + n * MP;   // f rows 2 c0 - 1 .. 2 c1 - 1 (row 2 c0 - 1 at slot 0)
+        stage_blocks<M>(sal, a.al[q] + c0 * MM, n);
+        stage_blocks<M>(sga, a.ga[q] + c0 * MM, n);
         const long long f0 = 2 * c0 - 1, f1 = (2 * c1 < K) ? 2 * c1 : K;   // rows [f0, f1)
         if (f0 < 0) {
             zero_f4(sf, E);
@@ -188,70 +266,36 @@ __device__ void rs_forward(const RsolveArgs& a, int q, long long lo, long long h
         if (nf < 2 * n + 1) zero_f4(sf + nf * E, (2 * n + 1 - nf) * E);
         rs_cp_wait();
         __syncthreads();
-        if (v4) {
-            const int E4 = E / 4, n4 = nr / 4;
-            const float4* sf4 = reinterpret_cast<const float4*>(sf);
-            for (int u = threadIdx.x; u < (int)n * E4; u += blockDim.x) {
-                const int il = u / E4, e4 = u - il * E4, r = e4 / n4, c4 = e4 - r * n4;
-                const float* A = sal + il * MM + r * M;
-                const float* G = sga + il * MM + r * M;
-                const float4* vl = sf4 + (2 * il) * E4 + c4;
-                const float4* vr = sf4 + (2 * il + 2) * E4 + c4;
-                float4 s = sf4[(2 * il + 1) * E4 + e4];
-#pragma unroll
-                for (int k = 0; k < M; ++k) {
-                    const float ak = A[k], gk = G[k];
-                    const float4 x0 = vl[k * n4], x1 = vr[k * n4];
-                    s.x = fmaf(ak, x0.x, fmaf(gk, x1.x, s.x));
-                    s.y = fmaf(ak, x0.y, fmaf(gk, x1.y, s.y));
-                    s.z = fmaf(ak, x0.z, fmaf(gk, x1.z, s.z));
-                    s.w = fmaf(ak, x0.w, fmaf(gk, x1.w, s.w));
-                }
-                reinterpret_cast<float4*>(a.f[q + 1])[(c0 + il) * E4 + e4] = s;
-            }
-        } else {
-            for (int u = threadIdx.x; u < (int)n * E; u += blockDim.x) {
-                const int il = u / E, el = u - il * E, r = el / nr, c = el - r * nr;
-                const float* A = sal + il * MM + r * M;
-                const float* G = sga + il * MM + r * M;
-                const float* vl = sf + (2 * il) * E + c;
-                const float* vr = sf + (2 * il + 2) * E + c;
-                float s0 = sf[(2 * il + 1) * E + el], s1 = 0.f;
-#pragma unroll
-                for (int k = 0; k < M; ++k) {
-                    s0 = fmaf(A[k], vl[k * nr], s0);
-                    s1 = fmaf(G[k], vr[k * nr], s1);
-                }
-                a.f[q + 1][(c0 + il) * E + el] = s0 + s1;
-            }
+        for (int u = threadIdx.x; u < (int)n * EW; u += blockDim.x) {
+            const int il = u / EW, e = (u - il * EW) * W, r = e / nr, c = e - r * nr;
+            float s[W];
+            ldw<W>(s, sf + (2 * il + 1) * E + e);
+            row_dot<M, W, false>(s, sal + il * MP + r * P, sf + 2 * il * E + c, nr);
+            row_dot<M, W, false>(s, sga + il * MP + r * P, sf + (2 * il + 2) * E + c, nr);
+            stw<W>(a.f[q + 1] + (c0 + il) * E + e, s);
         }
         __syncthreads();
     }
 }
 
 // Back substitution of level q for the row pairs (2i, 2i+1), i in [lo, hi).
-template <int M>
+template <int M, int W>
 __device__ void rs_backward(const RsolveArgs& a, int q, long long lo, long long hi, float* sm) {
-    constexpr int MM = M * M;
-    const int nr = a.nr, E = M * nr;
+    constexpr int MM = M * M, P = rs_row_stride(M), MP = M * P;
+    const int nr = a.nr, E = M * nr, EW = E / W;
     const long long K = a.K[q], kept = (K + 1) / 2;
-    const int CH = (kRsSmemFloats - E) / (3 * MM + 3 * E);
-    const bool v4 = (nr & 3) == 0;
+    const int CH = (a.chunk - E) / (3 * MP + 3 * E);
     for (long long c0 = lo; c0 < hi; c0 += CH) {
         const long long c1 = (c0 + CH < hi) ? c0 + CH : hi, n = c1 - c0;
         float* sB = sm;               // B of rows 2i+1
-        float* sC = sB + n * MM;      // C of rows 2i+1
-        float* sD = sC + n * MM;      // inverses of rows 2i+1
-        float* sx = sD + n * MM;      // x^{q+1} rows c0 .. c1 (n + 1 rows)
+        float* sC = sB + n * MP;      // C of rows 2i+1
+        float* sD = sC + n * MP;      // inverses of rows 2i+1
+        float* sx = sD + n * MP;      // x^{q+1} rows c0 .. c1 (n + 1 rows)
         float* sf = sx + (n + 1) * E; // f rows 2i+1
         const long long nodd = (2 * c1 <= K) ? n : n - 1;   // row 2 c1 - 1 may not exist
-        for (int e = threadIdx.x; e < (int)nodd * (MM / 4); e += blockDim.x) {
-            const int il = e / (MM / 4), w = e % (MM / 4);
-            const long long rw = 2 * (c0 + il) + 1;
-            rs_cp16(sB + 4 * e, a.B[q] + rw * MM + 4 * w);
-            rs_cp16(sC + 4 * e, a.C[q] + rw * MM + 4 * w);
-        }
-        stage_f4(sD, a.Dinv[q] + c0 * MM, nodd * MM);
+        stage_odd_blocks<M>(sB, a.B[q], c0, nodd);
+        stage_odd_blocks<M>(sC, a.C[q], c0, nodd);
+        stage_blocks<M>(sD, a.Dinv[q] + c0 * MM, nodd);
         const long long xend = (c1 + 1 <= kept) ? c1 + 1 : kept;   // x^{q+1} rows [c0, xend)
         stage_f4(sx, a.x[q + 1] + c0 * E, (xend - c0) * E);
         stage_odd_fq(a, q, sf, c0, (int)nodd, E);
@@ -264,118 +308,180 @@ __device__ void rs_backward(const RsolveArgs& a, int q, long long lo, long long 
             put_x4(a, q, (2 * (c0 + il)) * (E / 4) + w, reinterpret_cast<const float4*>(sx)[il * (E / 4) + w]);
         }
         // pass 1: t = f - B x_l - C x_r in place of f; pass 2: x = D^{-1} t
-        if (v4) {
-            const int n4 = nr / 4, E4 = E / 4;
-            const float4* sx4 = reinterpret_cast<const float4*>(sx);
-            float4* sf4 = reinterpret_cast<float4*>(sf);
-            for (int u = threadIdx.x; u < (int)nodd * E4; u += blockDim.x) {
-                const int il = u / E4, e4 = u - il * E4, r = e4 / n4, c4 = e4 - r * n4;
-                const long long rw = 2 * (c0 + il) + 1;
-                const float rm = (rw + 1 < K) ? 1.f : 0.f;
-                const float* Bo = sB + il * MM + r * M;
-                const float* Co = sC + il * MM + r * M;
-                float4 t = sf4[il * E4 + e4];
-#pragma unroll
-                for (int k = 0; k < M; ++k) {
-                    const float b = Bo[k], cc = Co[k] * rm;
-                    const float4 xl = sx4[il * E4 + k * n4 + c4], xr = sx4[(il + 1) * E4 + k * n4 + c4];
-                    t.x = fmaf(-b, xl.x, fmaf(-cc, xr.x, t.x));
-                    t.y = fmaf(-b, xl.y, fmaf(-cc, xr.y, t.y));
-                    t.z = fmaf(-b, xl.z, fmaf(-cc, xr.z, t.z));
-                    t.w = fmaf(-b, xl.w, fmaf(-cc, xr.w, t.w));
-                }
-                sf4[il * E4 + e4] = t;
-            }
-            __syncthreads();
-            for (int u = threadIdx.x; u < (int)nodd * E4; u += blockDim.x) {
-                const int il = u / E4, e4 = u - il * E4, r = e4 / n4, c4 = e4 - r * n4;
-                const long long rw = 2 * (c0 + il) + 1;
-                const float* Di = sD + il * MM + r * M;
-                float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int k = 0; k < M; ++k) {
-                    const float d = Di[k];
-                    const float4 t = sf4[il * E4 + k * n4 + c4];
-                    x.x = fmaf(d, t.x, x.x);
-                    x.y = fmaf(d, t.y, x.y);
-                    x.z = fmaf(d, t.z, x.z);
-                    x.w = fmaf(d, t.w, x.w);
-                }
-                put_x4(a, q, rw * E4 + e4, x);
-            }
-        } else {
-            for (int u = threadIdx.x; u < (int)nodd * E; u += blockDim.x) {
-                const int il = u / E, el = u - il * E, r = el / nr, c = el - r * nr;
-                const long long rw = 2 * (c0 + il) + 1;
-                const float rm = (rw + 1 < K) ? 1.f : 0.f;
-                const float* Bo = sB + il * MM + r * M;
-                const float* Co = sC + il * MM + r * M;
-                const float* xl = sx + il * E + c;
-                const float* xr = sx + (il + 1) * E + c;
-                float s0 = sf[il * E + el], s1 = 0.f;
-#pragma unroll
-                for (int k = 0; k < M; ++k) {
-                    s0 = fmaf(-Bo[k], xl[k * nr], s0);
-                    s1 = fmaf(-Co[k] * rm, xr[k * nr], s1);
-                }
-                sf[il * E + el] = s0 + s1;
-            }
-            __syncthreads();
-            for (int u = threadIdx.x; u < (int)nodd * E; u += blockDim.x) {
-                const int il = u / E, el = u - il * E, r = el / nr, c = el - r * nr;
-                const long long rw = 2 * (c0 + il) + 1;
-                const float* Di = sD + il * MM + r * M;
-                float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-                for (int k = 0; k < M; k += 2) {
-                    s0 = fmaf(Di[k], sf[il * E + k * nr + c], s0);
-                    s1 = fmaf(Di[k + 1], sf[il * E + (k + 1) * nr + c], s1);
-                }
-                put_x1(a, q, rw * E + el, s0 + s1);
-            }
+        for (int u = threadIdx.x; u < (int)nodd * EW; u += blockDim.x) {
+            const int il = u / EW, e = (u - il * EW) * W, r = e / nr, c = e - r * nr;
+            const long long rw = 2 * (c0 + il) + 1;
+            float t[W];
+            ldw<W>(t, sf + il * E + e);
+            row_dot<M, W, true>(t, sB + il * MP + r * P, sx + il * E + c, nr);
+            if (rw + 1 < K) row_dot<M, W, true>(t, sC + il * MP + r * P, sx + (il + 1) * E + c, nr);
+            stw<W>(sf + il * E + e, t);
         }
         __syncthreads();
+        for (int u = threadIdx.x; u < (int)nodd * EW; u += blockDim.x) {
+            const int il = u / EW, e = (u - il * EW) * W, r = e / nr, c = e - r * nr;
+            const long long rw = 2 * (c0 + il) + 1;
+            float s[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) s[w] = 0.f;
+            row_dot<M, W, false>(s, sD + il * MP + r * P, sf + il * E + c, nr);
+            put_xw<W>(a, q, rw * E + e, s);
+        }
+        __syncthreads();
+    }
+}
+
+// Shared-memory layout of the levels CTA 0 finishes alone, level q (K rows,
+// (K+1)/2 kept, K/2 odd; the top level has only its inverse), blocks padded:
+//   alpha, gamma [(K+1)/2] | D^{-1}, B, C of the odd rows [K/2] |
+//   v [K][m][nr] (f^q, overwritten by x^q)
+// and after the top level one scratch block of the odd rows' t vectors.  Every
+// piece is a multiple of 4 floats (m >= 8), so each stays 16-byte aligned.
+__host__ __device__ inline long long small_level_floats(long long K, int m, int nr, bool top) {
+    const long long MP = rs_block_floats(m), E = (long long)m * nr;
+    if (top) return MP + E;
+    return 2 * ((K + 1) / 2) * MP + 3 * (K / 2) * MP + K * E;
+}
+
+// Levels [big, nlev) on one CTA, vectors and blocks in shared memory; W
+// columns per unit (W = 4 when nr is a multiple of 4).
+template <int M, int W>
+__device__ void rs_small_levels(const RsolveArgs& a, float* S) {
+    constexpr int P = rs_row_stride(M), MP = M * P;
+    const int nr = a.nr, E = M * nr, EW = E / W, T = blockDim.x;
+    const int top = a.nlev - 1, big = a.big;
+    struct Lv {
+        float *al, *ga, *di, *bb, *cc, *v;
+    };
+    auto lv = [&](int q) {
+        const long long K = a.K[q], kept = (K + 1) / 2, odd = K / 2;
+        Lv L;
+        L.al = S + a.soff[q];
+        if (q == top) {
+            L.di = L.al;
+            L.v = L.di + MP;
+            L.ga = L.bb = L.cc = nullptr;
+            return L;
+        }
+        L.ga = L.al + kept * MP;
+        L.di = L.ga + kept * MP;
+        L.bb = L.di + odd * MP;
+        L.cc = L.bb + odd * MP;
+        L.v = L.cc + odd * MP;
+        return L;
+    };
+    float* tmp = S + a.soff[top + 1];
+    // one batch of copies: every level's blocks and f^{big}
+    for (int q = big; q <= top; ++q) {
+        const Lv L = lv(q);
+        if (q == top) {
+            stage_blocks<M>(L.di, a.Dinv[q], 1);
+            continue;
+        }
+        const long long K = a.K[q], kept = (K + 1) / 2, odd = K / 2;
+        stage_blocks<M>(L.al, a.al[q], kept);
+        stage_blocks<M>(L.ga, a.ga[q], kept);
+        stage_blocks<M>(L.di, a.Dinv[q], odd);
+        stage_odd_blocks<M>(L.bb, a.B[q], 0, odd);
+        stage_odd_blocks<M>(L.cc, a.C[q], 0, odd);
+    }
+    stage_fq(a, big, lv(big).v, 0, a.K[big] * E);
+    rs_cp_wait();
+    __syncthreads();
+    // forward: f^{q+1}_i = f_{2i} + alpha_i f_{2i-1} + gamma_i f_{2i+1}
+    for (int q = big; q < top; ++q) {
+        const Lv L = lv(q), N = lv(q + 1);
+        const long long K = a.K[q], kept = (K + 1) / 2;
+        for (int u = threadIdx.x; u < (int)kept * EW; u += T) {
+            const int i = u / EW, e = (u - i * EW) * W, r = e / nr, c = e - r * nr;
+            float s[W];
+            ldw<W>(s, L.v + 2 * i * E + e);
+            if (i > 0) row_dot<M, W, false>(s, L.al + i * MP + r * P, L.v + (2 * i - 1) * E + c, nr);
+            if (2 * i + 1 < K) row_dot<M, W, false>(s, L.ga + i * MP + r * P, L.v + (2 * i + 1) * E + c, nr);
+            stw<W>(N.v + i * E + e, s);
+        }
+        __syncthreads();
+    }
+    // top: x = D^{-1} f
+    {
+        const Lv L = lv(top);
+        for (int u = threadIdx.x; u < EW; u += T) {
+            const int e = u * W, r = e / nr, c = e - r * nr;
+            float s[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) s[w] = 0.f;
+            row_dot<M, W, false>(s, L.di + r * P, L.v + c, nr);
+            stw<W>(tmp + e, s);
+        }
+        __syncthreads();
+        for (int u = threadIdx.x; u < EW; u += T) {
+            float x[W];
+            ldw<W>(x, tmp + u * W);
+            stw<W>(L.v + u * W, x);
+        }
+        __syncthreads();
+    }
+    // backward: x_{2i} = x^{q+1}_i; x_{2i+1} = D^{-1} (f_{2i+1} - B x_{2i} - C x_{2i+2})
+    for (int q = top - 1; q >= big; --q) {
+        const Lv L = lv(q), N = lv(q + 1);
+        const long long K = a.K[q], kept = (K + 1) / 2, odd = K / 2;
+        for (int u = threadIdx.x; u < (int)kept * EW; u += T) {
+            const int i = u / EW, e = (u - i * EW) * W;
+            float x[W];
+            ldw<W>(x, N.v + i * E + e);
+            stw<W>(L.v + 2 * i * E + e, x);
+        }
+        __syncthreads();
+        for (int u = threadIdx.x; u < (int)odd * EW; u += T) {
+            const int i = u / EW, e = (u - i * EW) * W, r = e / nr, c = e - r * nr;
+            float t[W];
+            ldw<W>(t, L.v + (2 * i + 1) * E + e);
+            row_dot<M, W, true>(t, L.bb + i * MP + r * P, L.v + 2 * i * E + c, nr);
+            if (2 * i + 2 < K) row_dot<M, W, true>(t, L.cc + i * MP + r * P, L.v + (2 * i + 2) * E + c, nr);
+            stw<W>(tmp + i * E + e, t);
+        }
+        __syncthreads();
+        for (int u = threadIdx.x; u < (int)odd * EW; u += T) {
+            const int i = u / EW, e = (u - i * EW) * W, r = e / nr, c = e - r * nr;
+            float s[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) s[w] = 0.f;
+            row_dot<M, W, false>(s, L.di + i * MP + r * P, tmp + i * E + c, nr);
+            stw<W>(L.v + (2 * i + 1) * E + e, s);
+        }
+        __syncthreads();
+    }
+    // x^{big} to its level vector (the FP64 solution when big == 0)
+    {
+        const float* v = lv(big).v;
+        const long long n4 = a.K[big] * E / 4;
+        for (long long u = threadIdx.x; u < n4; u += T) put_x4(a, big, u, reinterpret_cast<const float4*>(v)[u]);
     }
 }
 
 template <int M>
 __global__ void __launch_bounds__(kRsThreads) k_rsolve_f32(const RsolveArgs a) {
     extern __shared__ __align__(16) float sm[];
-    const int nr = a.nr;
-    const int E = M * nr;   // multiple of 4 (M >= 8)
     const int rank = (int)cluster_rank();
     const long long nct = (long long)cluster_size();
-    const int top = a.nlev - 1;
+    const int big = a.big;
+    const bool v4 = (a.nr & 3) == 0;
     // levels 0 .. big-1 run on the whole cluster, the rest on CTA 0 alone
-    int big = 0;
-    while (big < top && a.K[big] > kRsCluster) ++big;
     for (int q = 0; q < big; ++q) {
-        const long long kept = (a.K[q] + 1) / 2;
-        rs_forward<M>(a, q, kept * rank / nct, kept * (rank + 1) / nct, sm);
+        const long long kept = (a.K[q] + 1) / 2, lo = kept * rank / nct, hi = kept * (rank + 1) / nct;
+        if (v4) rs_forward<M, 4>(a, q, lo, hi, sm);
+        else rs_forward<M, 1>(a, q, lo, hi, sm);
         cluster_barrier();
     }
     if (rank == 0) {
-        for (int q = big; q < top; ++q) {
-            rs_forward<M>(a, q, 0, (a.K[q] + 1) / 2, sm);   // ends with __syncthreads
-        }
-        const float* Di = a.Dinv[top];
-        stage_fq(a, top, sm, 0, E);
-        rs_cp_wait();
-        __syncthreads();
-        for (int u = threadIdx.x; u < E; u += blockDim.x) {
-            const int r = u / nr, c = u % nr;
-            float s = 0.f;
-#pragma unroll
-            for (int k = 0; k < M; ++k) s = fmaf(Di[r * M + k], sm[k * nr + c], s);
-            put_x1(a, top, u, s);
-        }
-        __syncthreads();
-        for (int q = top - 1; q >= big; --q) rs_backward<M>(a, q, 0, (a.K[q] + 1) / 2, sm);
+        if (v4) rs_small_levels<M, 4>(a, sm + a.chunk);
+        else rs_small_levels<M, 1>(a, sm + a.chunk);
     }
     cluster_barrier();
     for (int q = big - 1; q >= 0; --q) {
-        const long long kept = (a.K[q] + 1) / 2;
-        rs_backward<M>(a, q, kept * rank / nct, kept * (rank + 1) / nct, sm);
+        const long long kept = (a.K[q] + 1) / 2, lo = kept * rank / nct, hi = kept * (rank + 1) / nct;
+        if (v4) rs_backward<M, 4>(a, q, lo, hi, sm);
+        else rs_backward<M, 1>(a, q, lo, hi, sm);
         if (q > 0) cluster_barrier();
     }
 }
@@ -777,8 +883,40 @@ cudaError_t launch_rfactor_f32(const RfactorArgs& a, cudaStream_t s) {
     }
 }
 
-cudaError_t launch_rsolve_f32(const RsolveArgs& a, cudaStream_t s) {
-    if (a.nlev < 1 || a.nlev > kRsMaxLevels || a.nr < 1 || a.nr > 32) return cudaErrorInvalidValue;
+// Split of the levels between the cluster and CTA 0 (the first level of at
+// most kRsSmall rows, or a later one while CTA 0's share does not fit beside
+// a chunk area of at least kRsMinChunk floats) and CTA 0's layout.
+constexpr int kRsMinChunk = 16 * 1024;
+static bool rs_layout(RsolveArgs& a) {
+    const int top = a.nlev - 1, m = a.m, nr = a.nr;
+    const long long MP = rs_block_floats(m), E = (long long)m * nr;
+    long long minc = 3 * MP + 4 * E;
+    if (minc < kRsMinChunk) minc = kRsMinChunk;
+    int big = 0;
+    while (big < top && a.K[big] > kRsSmall) ++big;
+    for (;; ++big) {
+        long long off = 0, tmpn = 0;
+        for (int q = big; q <= top; ++q) {
+            a.soff[q] = (int)off;
+            off += small_level_floats(a.K[q], m, nr, q == top);
+            const long long odd = (q == top) ? 1 : a.K[q] / 2;
+            if (odd > tmpn) tmpn = odd;
+        }
+        a.soff[top + 1] = (int)off;
+        off += tmpn * E;
+        if (off + minc <= kRsSmemFloats) {
+            a.big = big;
+            a.chunk = (int)(kRsSmemFloats - off);
+            return true;
+        }
+        if (big == top) return false;
+    }
+}
+
+cudaError_t launch_rsolve_f32(const RsolveArgs& args, cudaStream_t s) {
+    if (args.nlev < 1 || args.nlev > kRsMaxLevels || args.nr < 1 || args.nr > 32) return cudaErrorInvalidValue;
+    RsolveArgs a = args;
+    if (!rs_layout(a)) return cudaErrorInvalidValue;
     static int ctas[3] = {0, 0, 0};
     switch (a.m) {
         case 8: return launch_rs(k_rsolve_f32<8>, a, s, ctas[0]);
@@ -786,7 +924,6 @@ cudaError_t launch_rsolve_f32(const RsolveArgs& a, cudaStream_t s) {
         case 32: return launch_rs(k_rsolve_f32<32>, a, s, ctas[2]);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace bt

@@ -21,6 +21,12 @@ struct RsolveArgs {
     float* x[kRsMaxLevels];           // [K][m][nr] solution of the level
     const double* F0;                 // level-0 right-hand side (FP64)
     double* X0;                       // level-0 solution (FP64)
+    // Set by launch_rsolve_f32: levels [0, big) run on the whole cluster with
+    // `chunk` floats of shared memory for their chunks; levels [big, nlev) run
+    // on CTA 0 from shared memory, level q's blocks and vector at offset
+    // soff[q] (floats) past the chunk area.
+    int big, chunk;
+    int soff[kRsMaxLevels + 1];
 };
 
 // Conversion of FP64 arrays to FP32 (rounded to nearest): up to kCvtSegs
