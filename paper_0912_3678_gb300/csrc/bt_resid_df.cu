@@ -77,6 +77,44 @@ struct DF {
     __device__ __forceinline__ float value() const { return __fadd_rn(s, l); }
 };
 
+// The same accumulator for two columns at once, on the paired FP32
+// instructions of this GPU (FMUL2, FFMA2, FADD2: two FP32 operations per
+// issued instruction, each component rounded as its scalar form): value =
+// s + l per component, and every operation is that of DF in the same order,
+// so the two columns' results are bit for bit those of two DF accumulators.
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+struct DF2 {
+    float2 s, l;
+    __device__ __forceinline__ void init(float2 s0, float2 l0) {
+        s = s0;
+        l = l0;
+    }
+    // this -= a * x: a = (ahi, alo) one matrix entry, xh / xl the high and low
+    // parts of the two columns' x entries
+    __device__ __forceinline__ void sub(float ahi, float alo, float2 xh, float2 xl) {
+        const float2 ah = make_float2(ahi, ahi);
+        const float2 p = __fmul2_rn(ah, xh);
+        const float2 pe = __ffma2_rn(ah, xh, neg2(p));
+        const float2 np = neg2(p);
+        const float2 s1 = __fadd2_rn(s, np);
+        const float2 bb = __fadd2_rn(s1, neg2(s));
+        const float2 t = __fadd2_rn(__fadd2_rn(s, neg2(__fadd2_rn(s1, neg2(bb)))), __fadd2_rn(np, neg2(bb)));
+        s = s1;
+        l = __fadd2_rn(l, t);
+        l = __ffma2_rn(make_float2(-ahi, -ahi), xl, l);
+        l = __ffma2_rn(make_float2(-alo, -alo), xh, l);
+        l = __fadd2_rn(l, neg2(pe));
+    }
+    __device__ __forceinline__ void merge(const DF2& o) {
+        const float2 s1 = __fadd2_rn(s, o.s);
+        const float2 bb = __fadd2_rn(s1, neg2(s));
+        const float2 t = __fadd2_rn(__fadd2_rn(s, neg2(__fadd2_rn(s1, neg2(bb)))), __fadd2_rn(o.s, neg2(bb)));
+        s = s1;
+        l = __fadd2_rn(__fadd2_rn(l, o.l), t);
+    }
+    __device__ __forceinline__ float2 value() const { return __fadd2_rn(s, l); }
+};
+
 __device__ __forceinline__ unsigned long long abs_bits64(double v) {
     return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
 }
@@ -518,7 +556,7 @@ __global__ void __launch_bounds__(kDfThreads) k_resid_btri_dfs(long long N, int 
                 }
                 if (q >= 1 && q <= g) mx = umax_(mx, m0);
             }
-            sX[idx] = make_float4(a.x, a.y, b.x, b.y);
+            sX[idx] = make_float4(a.x, b.x, a.y, b.y);   // high parts, then low parts
         }
         __syncthreads();
         const double* rf = raw + nX;
@@ -530,14 +568,13 @@ __global__ void __launch_bounds__(kDfThreads) k_resid_btri_dfs(long long N, int 
             const bool two = c0 + 1 < nr;
             const double f0 = rf[(gj * M + r) * nr + c0], f1 = two ? rf[(gj * M + r) * nr + c0 + 1] : 0.0;
             mf = umax_(mf, umax_(abs_bits64(f0), abs_bits64(f1)));
-            DF a[4], b[4];
-            a[0].init(split_f64(f0));
-            b[0].init(split_f64(f1));
-#pragma unroll
-            for (int qq = 1; qq < 4; ++qq) {
-                a[qq].init(make_float2(0.f, 0.f));
-                b[qq].init(make_float2(0.f, 0.f));
+            DF2 a[4];
+            {
+                const float2 s0 = split_f64(f0), s1 = split_f64(f1);
+                a[0].init(make_float2(s0.x, s1.x), make_float2(s0.y, s1.y));
             }
+#pragma unroll
+            for (int qq = 1; qq < 4; ++qq) a[qq].init(make_float2(0.f, 0.f), make_float2(0.f, 0.f));
 #pragma unroll
             for (int blk = 0; blk < 3; ++blk) {
                 const float2* Ar = sA + ((gj * 3 + blk) * M + r) * M;
@@ -546,21 +583,18 @@ __global__ void __launch_bounds__(kDfThreads) k_resid_btri_dfs(long long N, int 
                 for (int k = 0; k < M; ++k) {
                     const float2 ak = Ar[k];
                     const float4 xk = xq[k * pcp];
-                    a[k & 3].sub(ak, make_float2(xk.x, xk.y));
-                    b[k & 3].sub(ak, make_float2(xk.z, xk.w));
+                    a[k & 3].sub(ak.x, ak.y, make_float2(xk.x, xk.y), make_float2(xk.z, xk.w));
                 }
             }
             a[0].merge(a[1]);
             a[2].merge(a[3]);
             a[0].merge(a[2]);
-            b[0].merge(b[1]);
-            b[2].merge(b[3]);
-            b[0].merge(b[2]);
-            const double r0 = f32_to_f64(a[0].value());
+            const float2 v = a[0].value();
+            const double r0 = f32_to_f64(v.x);
             R[row * nr + c0] = r0;
             mr = umax_(mr, abs_bits64(r0));
             if (two) {
-                const double r1 = f32_to_f64(b[0].value());
+                const double r1 = f32_to_f64(v.y);
                 R[row * nr + c0 + 1] = r1;
                 mr = umax_(mr, abs_bits64(r1));
             }
