@@ -230,11 +230,17 @@ __device__ __forceinline__ void factor_warp16_body(const LevelArgs& a, const lon
             for (int k = 0; k < 16; ++k) {
                 float srow[16];
                 read_row16(srow, &sm.ex[h][k * FR]);
-                const float bk = bro[k], wk = w[k];
+                const float2 nb = make_float2(-bro[k], -bro[k]), wk = make_float2(w[k], w[k]);
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    a32[c] = fmaf(-bk, srow[c], a32[c]);
-                    acc[c] = fmaf(wk, srow[c], acc[c]);
+                for (int c = 0; c < 16; c += 2) {
+                    // paired FMAs (FFMA2): each component is the scalar fmaf
+                    const float2 sv = make_float2(srow[c], srow[c + 1]);
+                    const float2 t = __ffma2_rn(nb, sv, make_float2(a32[c], a32[c + 1]));
+                    const float2 u = __ffma2_rn(wk, sv, make_float2(acc[c], acc[c + 1]));
+                    a32[c] = t.x;
+                    a32[c + 1] = t.y;
+                    acc[c] = u.x;
+                    acc[c + 1] = u.y;
                 }
             }
             if (wpend) {
@@ -282,13 +288,16 @@ __device__ __forceinline__ void factor_warp16_body(const LevelArgs& a, const lon
             }
             __syncwarp();
             const float4* s = reinterpret_cast<const float4*>(pb);
+            const float2 nl = make_float2(-l, -l);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const float4 t = s[q];
-                a32[4 * q] = fmaf(-l, t.x, a32[4 * q]);
-                a32[4 * q + 1] = fmaf(-l, t.y, a32[4 * q + 1]);
-                a32[4 * q + 2] = fmaf(-l, t.z, a32[4 * q + 2]);
-                a32[4 * q + 3] = fmaf(-l, t.w, a32[4 * q + 3]);
+                const float2 u0 = __ffma2_rn(nl, make_float2(t.x, t.y), make_float2(a32[4 * q], a32[4 * q + 1]));
+                const float2 u1 = __ffma2_rn(nl, make_float2(t.z, t.w), make_float2(a32[4 * q + 2], a32[4 * q + 3]));
+                a32[4 * q] = u0.x;
+                a32[4 * q + 1] = u0.y;
+                a32[4 * q + 2] = u1.x;
+                a32[4 * q + 3] = u1.y;
             }
             if (mine) {
                 used = true;
