@@ -488,6 +488,9 @@ __device__ __forceinline__ void solve_fwd_w16_body(const LevelArgs& a, const lon
     const float* gDi = reinterpret_cast<const float*>(a.Dinv);
     const float* gW = reinterpret_cast<const float*>(a.W);
     float* gH = reinterpret_cast<float*>(a.Hv);
+    // B_j truncated to FP32: the high parts of the factorization's split copy
+    // when there is one (2 KB per block, as the FP64 block), else converted here
+    const float2* gBs = reinterpret_cast<const float2*>(a.As);
     float* xa = sm.xa + r * SW + cb;
     float* xb = sm.xb + r * SW + cb;
     float acc[NH];
@@ -498,7 +501,9 @@ __device__ __forceinline__ void solve_fwd_w16_body(const LevelArgs& a, const lon
         const long long j = pt.s + t;
         if (j < pt.e) {
             const int b = (int)(t % S);
-            if (j > pt.s) stage_blk16(sm.sB[b], a.B + (j - a.shift) * MM, lane);
+            if (j > pt.s)
+                stage_blk16(sm.sB[b], gBs ? reinterpret_cast<const double*>(gBs + j * MM) : a.B + (j - a.shift) * MM,
+                            lane);
             ring_blk32(sm.sA[b], gDi + j * MM, lane);
             if (pt.hasL) ring_blk32(sm.sC[b], gW + j * MM, lane);
             ring_vec64(sm.sV[b], a.F + j * E, E, lane);
@@ -521,8 +526,14 @@ __device__ __forceinline__ void solve_fwd_w16_body(const LevelArgs& a, const lon
             // t = f_j - B_j h_{j-1}  (h_{j-1} in xb)
             float Br[16];
             const double* sbr = sm.sB[b] + r * WarpF16::SR;
+            if (gBs) {
+                const float2* sp = reinterpret_cast<const float2*>(sbr);
 #pragma unroll
-            for (int k = 0; k < 16; ++k) Br[k] = trunc_f32(sbr[k]);
+                for (int k = 0; k < 16; ++k) Br[k] = sp[k].x;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) Br[k] = trunc_f32(sbr[k]);
+            }
             gemv_acc<NH, true>(t4, Br, sm.xb + cb, SW);
         }
         put_vec<NH>(xa, t4);
@@ -559,9 +570,15 @@ __device__ __forceinline__ void solve_fwd_w16_body(const LevelArgs& a, const lon
         float g[NH], Br[16];
         load_vec<NH>(g, a.F + (e * M + r) * nr, cb, nr);
         if (pt.e > pt.s) {
-            const double* be = a.B + (e - a.shift) * MM + r * M;
+            if (gBs) {
+                const float2* be = gBs + e * MM + r * M;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) Br[k] = trunc_f32(be[k]);
+                for (int k = 0; k < 16; ++k) Br[k] = be[k].x;
+            } else {
+                const double* be = a.B + (e - a.shift) * MM + r * M;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) Br[k] = trunc_f32(be[k]);
+            }
             gemv_acc<NH, true>(g, Br, sm.xb + cb, SW);
         }
         double* fn = a.Fn + i * E + r * nr;
