@@ -77,42 +77,49 @@ struct DF {
     __device__ __forceinline__ float value() const { return __fadd_rn(s, l); }
 };
 
-// The same accumulator for two columns at once, on the paired FP32
-// instructions of this GPU (FMUL2, FFMA2, FADD2: two FP32 operations per
-// issued instruction, each component rounded as its scalar form): value =
-// s + l per component, and every operation is that of DF in the same order,
-// so the two columns' results are bit for bit those of two DF accumulators.
-__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
-struct DF2 {
+// The compensated accumulator on the paired FP32 instructions of this GPU
+// (FMUL2, FFMA2, FADD2: two FP32 operations per issued instruction, each
+// component rounded as its scalar form).  The two components hold the sums
+// over the even and the odd k of one entry, merged at the end; each component
+// takes the steps of DF.sub in the same order.  The matrix entries come
+// negated, (-a_hi, -a_hi+1) and (-a_lo, -a_lo+1) for k, k + 1, so every step
+// adds: a difference x - y is the fused y * (-1) + x (exact product, one
+// rounding) and no operand is negated in flight.
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, make_float2(-1.f, -1.f), x); }
+struct DFk {
     float2 s, l;
-    __device__ __forceinline__ void init(float2 s0, float2 l0) {
-        s = s0;
-        l = l0;
+    __device__ __forceinline__ void init(float s0, float l0) {
+        s = make_float2(s0, 0.f);
+        l = make_float2(l0, 0.f);
     }
-    // this -= a * x: a = (ahi, alo) one matrix entry, xh / xl the high and low
-    // parts of the two columns' x entries
-    __device__ __forceinline__ void sub(float ahi, float alo, float2 xh, float2 xl) {
-        const float2 ah = make_float2(ahi, ahi);
-        const float2 p = __fmul2_rn(ah, xh);
-        const float2 pe = __ffma2_rn(ah, xh, neg2(p));
-        const float2 np = neg2(p);
-        const float2 s1 = __fadd2_rn(s, np);
-        const float2 bb = __fadd2_rn(s1, neg2(s));
-        const float2 t = __fadd2_rn(__fadd2_rn(s, neg2(__fadd2_rn(s1, neg2(bb)))), __fadd2_rn(np, neg2(bb)));
+    __device__ __forceinline__ void zero() { s = l = make_float2(0.f, 0.f); }
+    // this += (-a) x for k and k + 1: na = (-a_hi), nl = (-a_lo), xh / xl the
+    // high and low parts of x_k, x_k+1
+    __device__ __forceinline__ void add(float2 na, float2 nl, float2 xh, float2 xl) {
+        const float2 q = __fmul2_rn(na, xh);                                          // -p
+        const float2 qe = __ffma2_rn(na, xh, sub2(make_float2(0.f, 0.f), q));         // -(a_hi x_hi - p)
+        const float2 s1 = __fadd2_rn(s, q);
+        const float2 bb = sub2(s1, s);
+        const float2 t = __fadd2_rn(sub2(s, sub2(s1, bb)), sub2(q, bb));
         s = s1;
         l = __fadd2_rn(l, t);
-        l = __ffma2_rn(make_float2(-ahi, -ahi), xl, l);
-        l = __ffma2_rn(make_float2(-alo, -alo), xh, l);
-        l = __fadd2_rn(l, neg2(pe));
+        l = __ffma2_rn(na, xl, l);
+        l = __ffma2_rn(nl, xh, l);
+        l = __fadd2_rn(l, qe);
     }
-    __device__ __forceinline__ void merge(const DF2& o) {
+    __device__ __forceinline__ void merge(const DFk& o) {
         const float2 s1 = __fadd2_rn(s, o.s);
-        const float2 bb = __fadd2_rn(s1, neg2(s));
-        const float2 t = __fadd2_rn(__fadd2_rn(s, neg2(__fadd2_rn(s1, neg2(bb)))), __fadd2_rn(o.s, neg2(bb)));
+        const float2 bb = sub2(s1, s);
+        const float2 t = __fadd2_rn(sub2(s, sub2(s1, bb)), sub2(o.s, bb));
         s = s1;
         l = __fadd2_rn(__fadd2_rn(l, o.l), t);
     }
-    __device__ __forceinline__ float2 value() const { return __fadd2_rn(s, l); }
+    // the two components' sums merged, rounded to FP32
+    __device__ __forceinline__ float value() const {
+        float sv, t;
+        two_sum(s.x, s.y, sv, t);
+        return __fadd_rn(sv, __fadd_rn(__fadd_rn(l.x, l.y), t));
+    }
 };
 
 __device__ __forceinline__ unsigned long long abs_bits64(double v) {
@@ -492,10 +499,12 @@ __global__ void __launch_bounds__(kDfThreads) k_resid_btri_df2(long long N, int 
     if (maxout) block_max3_df(mr, mx, mf, maxout);
 }
 
-// Variant of k_resid_btri_df2 for matrices kept as FP32 pairs (hi, lo) by the
-// warp-per-partition factorization (float2 [3][N][M][M]): the pairs are
-// copied straight into a double-buffered shared array, so only x and f are
-// split per call.
+// Variant of k_resid_btri_df2 for the matrix kept by the warp-per-partition
+// factorization as negated FP32 pairs by column pairs, float4 [3][N][M][M/2]
+// of (-hi_k, -hi_k+1, -lo_k, -lo_k+1) for even k: the blocks are copied
+// straight into a double-buffered shared array, so only x and f are split per
+// call (into the same k-pair form).  A thread takes one row entry of two
+// right-hand-side columns, each column in two k-pair accumulators.
 template <int M>
 __global__ void __launch_bounds__(kDfThreads) k_resid_btri_dfs(long long N, int nr, int G, long long ntiles,
                                                                const float2* __restrict__ As,
@@ -503,7 +512,7 @@ __global__ void __launch_bounds__(kDfThreads) k_resid_btri_dfs(long long N, int 
                                                                const double* __restrict__ F, double* __restrict__ R,
                                                                unsigned long long* maxout) {
     extern __shared__ __align__(16) unsigned char smem[];
-    constexpr int MM = M * M;
+    constexpr int MM = M * M, KP = M / 2;
     const int ncp = (nr + 1) / 2, cs = df_pair_shift(nr), pcp = 1 << cs;
     const int V = M * nr;
     const int nA = G * 3 * MM, nX = (G + 2) * V, nF = G * V;
@@ -511,7 +520,7 @@ __global__ void __launch_bounds__(kDfThreads) k_resid_btri_dfs(long long N, int 
     float2* sA1 = sA0 + nA;
     double* raw0 = reinterpret_cast<double*>(sA1 + nA);     // x, f rows, two buffers
     double* raw1 = raw0 + (nX + nF);
-    float4* sX = reinterpret_cast<float4*>(raw1 + (nX + nF));   // [G + 2][M][pcp]
+    float4* sX = reinterpret_cast<float4*>(raw1 + (nX + nF));   // [G + 2][KP][2 pcp] k-pair form
     auto issue = [&](long long t, float2* sA, double* raw) {
         if (t < ntiles) {
             const long long j0 = t * G;
@@ -540,23 +549,28 @@ __global__ void __launch_bounds__(kDfThreads) k_resid_btri_dfs(long long N, int 
         __syncthreads();
         const long long j0 = t * G;
         const int g = (int)((N - j0) < G ? (N - j0) : G);
-        for (int idx = threadIdx.x; idx < ((g + 2) * M) << cs; idx += blockDim.x) {
-            const int cp = idx & (pcp - 1), qk = idx >> cs, q = qk / M, k = qk % M;
+        // x_k, x_k+1 of columns 2 cp, 2 cp + 1 -> two k-pair entries of sX
+        for (int idx = threadIdx.x; idx < ((g + 2) * KP) << cs; idx += blockDim.x) {
+            const int cp = idx & (pcp - 1), qk = idx >> cs, q = qk / KP, kp = qk % KP;
             const long long row = j0 - 1 + q;
-            float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+            float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;   // (column, k) = (0,0), (0,1), (1,0), (1,1)
             if (cp < ncp && row >= 0 && row < N) {
-                const double* src = raw + q * V + k * nr + 2 * cp;
-                const double v0 = src[0];
-                a = split_f64(v0);
-                unsigned long long m0 = abs_bits64(v0);
+                const double* src = raw + q * V + 2 * kp * nr + 2 * cp;
+                const double v00 = src[0], v01 = src[nr];
+                a0 = split_f64(v00);
+                a1 = split_f64(v01);
+                unsigned long long m0 = umax_(abs_bits64(v00), abs_bits64(v01));
                 if (2 * cp + 1 < nr) {
-                    const double v1 = src[1];
-                    b = split_f64(v1);
-                    m0 = umax_(m0, abs_bits64(v1));
+                    const double v10 = src[1], v11 = src[nr + 1];
+                    b0 = split_f64(v10);
+                    b1 = split_f64(v11);
+                    m0 = umax_(m0, umax_(abs_bits64(v10), abs_bits64(v11)));
                 }
                 if (q >= 1 && q <= g) mx = umax_(mx, m0);
             }
-            sX[idx] = make_float4(a.x, b.x, a.y, b.y);   // high parts, then low parts
+            float4* d = sX + (q * KP + kp) * 2 * pcp + 2 * cp;
+            d[0] = make_float4(a0.x, a1.x, a0.y, a1.y);
+            d[1] = make_float4(b0.x, b1.x, b0.y, b1.y);
         }
         __syncthreads();
         const double* rf = raw + nX;
@@ -568,33 +582,34 @@ __global__ void __launch_bounds__(kDfThreads) k_resid_btri_dfs(long long N, int 
             const bool two = c0 + 1 < nr;
             const double f0 = rf[(gj * M + r) * nr + c0], f1 = two ? rf[(gj * M + r) * nr + c0 + 1] : 0.0;
             mf = umax_(mf, umax_(abs_bits64(f0), abs_bits64(f1)));
-            DF2 a[4];
+            DFk a[2], b[2];   // columns c0 (a) and c0 + 1 (b), two accumulators each
             {
                 const float2 s0 = split_f64(f0), s1 = split_f64(f1);
-                a[0].init(make_float2(s0.x, s1.x), make_float2(s0.y, s1.y));
+                a[0].init(s0.x, s0.y);
+                b[0].init(s1.x, s1.y);
+                a[1].zero();
+                b[1].zero();
             }
 #pragma unroll
-            for (int qq = 1; qq < 4; ++qq) a[qq].init(make_float2(0.f, 0.f), make_float2(0.f, 0.f));
-#pragma unroll
             for (int blk = 0; blk < 3; ++blk) {
-                const float2* Ar = sA + ((gj * 3 + blk) * M + r) * M;
-                const float4* xq = sX + (gj + blk) * M * pcp + cp;
+                const float4* Ar = reinterpret_cast<const float4*>(sA + ((gj * 3 + blk) * M + r) * M);
+                const float4* xq = sX + (gj + blk) * KP * 2 * pcp + 2 * cp;
 #pragma unroll
-                for (int k = 0; k < M; ++k) {
-                    const float2 ak = Ar[k];
-                    const float4 xk = xq[k * pcp];
-                    a[k & 3].sub(ak.x, ak.y, make_float2(xk.x, xk.y), make_float2(xk.z, xk.w));
+                for (int kp = 0; kp < KP; ++kp) {
+                    const float4 ak = Ar[kp];
+                    const float4 x0 = xq[kp * 2 * pcp], x1 = xq[kp * 2 * pcp + 1];
+                    const float2 na = make_float2(ak.x, ak.y), nl = make_float2(ak.z, ak.w);
+                    a[kp & 1].add(na, nl, make_float2(x0.x, x0.y), make_float2(x0.z, x0.w));
+                    b[kp & 1].add(na, nl, make_float2(x1.x, x1.y), make_float2(x1.z, x1.w));
                 }
             }
             a[0].merge(a[1]);
-            a[2].merge(a[3]);
-            a[0].merge(a[2]);
-            const float2 v = a[0].value();
-            const double r0 = f32_to_f64(v.x);
+            b[0].merge(b[1]);
+            const double r0 = f32_to_f64(a[0].value());
             R[row * nr + c0] = r0;
             mr = umax_(mr, abs_bits64(r0));
             if (two) {
-                const double r1 = f32_to_f64(v.y);
+                const double r1 = f32_to_f64(b[0].value());
                 R[row * nr + c0 + 1] = r1;
                 mr = umax_(mr, abs_bits64(r1));
             }

@@ -93,9 +93,11 @@ __device__ __forceinline__ void convert_blk16(float* dst, const double* src, boo
             o[2 * q + 1] = sp[2 * q + 1].x;
         }
         if (gs != nullptr) {
+            // the split copy, negated, by column pairs: (-hi_k, -hi_k+1, -lo_k, -lo_k+1), k even
             float4* g4 = reinterpret_cast<float4*>(gs + rr * 16 + c0);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) g4[q] = make_float4(sp[2 * q].x, sp[2 * q].y, sp[2 * q + 1].x, sp[2 * q + 1].y);
+            for (int q = 0; q < 4; ++q)
+                g4[q] = make_float4(-sp[2 * q].x, -sp[2 * q + 1].x, -sp[2 * q].y, -sp[2 * q + 1].y);
         }
     } else {
 #pragma unroll
@@ -488,8 +490,9 @@ __device__ __forceinline__ void solve_fwd_w16_body(const LevelArgs& a, const lon
     const float* gDi = reinterpret_cast<const float*>(a.Dinv);
     const float* gW = reinterpret_cast<const float*>(a.W);
     float* gH = reinterpret_cast<float*>(a.Hv);
-    // B_j truncated to FP32: the high parts of the factorization's split copy
-    // when there is one (2 KB per block, as the FP64 block), else converted here
+    // B_j truncated to FP32: the (negated) high parts of the factorization's
+    // split copy when there is one (2 KB per block, as the FP64 block), else
+    // converted here
     const float2* gBs = reinterpret_cast<const float2*>(a.As);
     float* xa = sm.xa + r * SW + cb;
     float* xb = sm.xb + r * SW + cb;
@@ -527,14 +530,20 @@ __device__ __forceinline__ void solve_fwd_w16_body(const LevelArgs& a, const lon
             float Br[16];
             const double* sbr = sm.sB[b] + r * WarpF16::SR;
             if (gBs) {
-                const float2* sp = reinterpret_cast<const float2*>(sbr);
+                // -B_j row r: entry k at float (k / 2) * 4 + k % 2 of the row
+                const float4* sp = reinterpret_cast<const float4*>(sbr);
 #pragma unroll
-                for (int k = 0; k < 16; ++k) Br[k] = sp[k].x;
+                for (int q = 0; q < 8; ++q) {
+                    const float4 v = sp[q];
+                    Br[2 * q] = v.x;
+                    Br[2 * q + 1] = v.y;
+                }
+                gemv_acc<NH, false>(t4, Br, sm.xb + cb, SW);
             } else {
 #pragma unroll
                 for (int k = 0; k < 16; ++k) Br[k] = trunc_f32(sbr[k]);
+                gemv_acc<NH, true>(t4, Br, sm.xb + cb, SW);
             }
-            gemv_acc<NH, true>(t4, Br, sm.xb + cb, SW);
         }
         put_vec<NH>(xa, t4);
         __syncwarp();
@@ -571,15 +580,20 @@ __device__ __forceinline__ void solve_fwd_w16_body(const LevelArgs& a, const lon
         load_vec<NH>(g, a.F + (e * M + r) * nr, cb, nr);
         if (pt.e > pt.s) {
             if (gBs) {
-                const float2* be = gBs + e * MM + r * M;
+                const float4* be = reinterpret_cast<const float4*>(gBs + e * MM + r * M);
 #pragma unroll
-                for (int k = 0; k < 16; ++k) Br[k] = be[k].x;
+                for (int q = 0; q < 8; ++q) {
+                    const float4 v = be[q];
+                    Br[2 * q] = v.x;
+                    Br[2 * q + 1] = v.y;
+                }
+                gemv_acc<NH, false>(g, Br, sm.xb + cb, SW);
             } else {
                 const double* be = a.B + (e - a.shift) * MM + r * M;
 #pragma unroll
                 for (int k = 0; k < 16; ++k) Br[k] = trunc_f32(be[k]);
+                gemv_acc<NH, true>(g, Br, sm.xb + cb, SW);
             }
-            gemv_acc<NH, true>(g, Br, sm.xb + cb, SW);
         }
         double* fn = a.Fn + i * E + r * nr;
 #pragma unroll
