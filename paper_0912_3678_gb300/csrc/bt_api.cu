@@ -134,6 +134,9 @@ struct bt_plan_s {
     cudaStream_t copy_stream = nullptr;
     cudaStream_t chunk_stream[kChunks] = {};
     cudaEvent_t ev_in = nullptr, ev_rhs = nullptr;
+    // host-array path: the solution is final (the last correction added) / copied out
+    cudaEvent_t ev_xfinal = nullptr, ev_xout = nullptr;
+    bool x_event = false;   // run_refine_async records ev_xfinal before the checking residual
     cudaEvent_t ev_rows[kChunks] = {}, ev_part[kChunks] = {};
     // tracing
     bool trace = false;
@@ -796,7 +799,7 @@ bt_status run_factor(bt_plan_s* P, bool level0_done = false) {
         cudaError_t e = cudaSuccess;
         // warp kernels at level 0 take ||A||_inf while they convert the rows
         const bool wn = (l == 0) && !level0_done && P->warp && L->warp_ok && L->warp_ok(v.a, v.low);
-        P->anorm_fac = false;
+        if (l == 0 && !level0_done) P->anorm_fac = false;
         if (wn) {
             e = cudaMemsetAsync(P->amax, 0, kSlotWords * sizeof(unsigned long long), P->stream);
             v.a.amax = P->amax;
@@ -1087,6 +1090,11 @@ bt_status run_refine_async(bt_plan_s* P, const double* F, double* X, int nr, int
     }
     if (sweeps == 0) {
         cudaError_t e = cudaMemsetAsync(P->norms, 0, 2 * sizeof(double), P->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    if (st == BT_OK && P->x_event) {
+        // X is final: the host-array path copies it out beside the checking residual
+        cudaError_t e = cudaEventRecord(P->ev_xfinal, P->stream);
         if (e != cudaSuccess) return from_cuda(e);
     }
     // final residual of the result: its backward error decides convergence
@@ -1538,6 +1546,8 @@ cudaError_t ensure_host_path(bt_plan_s* P) {
     }
     if (e == cudaSuccess && !P->ev_in) e = cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess && !P->ev_rhs) e = cudaEventCreateWithFlags(&P->ev_rhs, cudaEventDisableTiming);
+    if (e == cudaSuccess && !P->ev_xfinal) e = cudaEventCreateWithFlags(&P->ev_xfinal, cudaEventDisableTiming);
+    if (e == cudaSuccess && !P->ev_xout) e = cudaEventCreateWithFlags(&P->ev_xout, cudaEventDisableTiming);
     return e;
 }
 }  // namespace
@@ -1571,8 +1581,14 @@ bt_status enqueue_host(bt_plan P, const double* B, const double* D, const double
     v.a.C = dC;
     v.a.shift = 0;
     P->anorm_valid = false;
+    // warp kernels take ||A||_inf while they convert the rows, chunk by chunk too
+    const bool wn = P->warp && P->L->warp_ok && P->L->warp_ok(v.a, v.low);
+    if (wn) {
+        e = cudaMemsetAsync(P->amax, 0, kSlotWords * sizeof(unsigned long long), P->stream);
+        v.a.amax = P->amax;
+    }
     // the device copies may still be read by work queued earlier on the plan's stream
-    e = cudaEventRecord(P->ev_in, P->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(P->ev_in, P->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(P->copy_stream, P->ev_in, 0);
     if (e == cudaSuccess) e = cudaMemsetAsync(P->status, 0, 4 * sizeof(long long), P->stream);
     const long long p = v.a.p;
@@ -1642,18 +1658,35 @@ bt_status enqueue_host(bt_plan P, const double* B, const double* D, const double
     if (e == cudaSuccess) e = cudaMemcpyAsync(dF, F, fbytes, cudaMemcpyHostToDevice, P->copy_stream);
     if (e == cudaSuccess) e = cudaEventRecord(P->ev_rhs, P->copy_stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(P->stream, P->ev_rhs, 0);
+    v.a.amax = nullptr;
     if (e != cudaSuccess) return from_cuda(e);
+    if (wn) {
+        P->anorm_valid = true;
+        P->anorm_fac = true;
+    }
     P->overlap = !P->serial;
     bt_status st = run_factor(P, true);
     P->overlap = false;
     P->factored = (st == BT_OK);
+    const bool xev = sweeps >= 0;
+    P->x_event = xev;
     if (st == BT_OK) st = (sweeps < 0) ? run_solve(P, dF, dX, nrhs) : run_refine_async(P, dF, dX, nrhs, sweeps);
+    P->x_event = false;
     if (P->join_pending) {
         cudaError_t ej = join_factor(P);
         if (st == BT_OK && ej != cudaSuccess) st = from_cuda(ej);
     }
     if (st != BT_OK) return st;
-    e = cudaMemcpyAsync(X, dX, fbytes, cudaMemcpyDeviceToHost, P->stream);
+    if (!xev) {
+        e = cudaMemcpyAsync(X, dX, fbytes, cudaMemcpyDeviceToHost, P->stream);
+        return from_cuda(e);
+    }
+    // the copy out runs on the copy stream beside the checking residual; the plan's
+    // stream waits for it
+    e = cudaStreamWaitEvent(P->copy_stream, P->ev_xfinal, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(X, dX, fbytes, cudaMemcpyDeviceToHost, P->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(P->ev_xout, P->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->stream, P->ev_xout, 0);
     return from_cuda(e);
 }
 }  // namespace
@@ -1851,6 +1884,8 @@ void bt_plan_destroy(bt_plan P) {
     }
     if (P->ev_in) cudaEventDestroy(P->ev_in);
     if (P->ev_rhs) cudaEventDestroy(P->ev_rhs);
+    if (P->ev_xfinal) cudaEventDestroy(P->ev_xfinal);
+    if (P->ev_xout) cudaEventDestroy(P->ev_xout);
     if (P->hb) cudaFree(P->hb);
     if (P->ev_fork) cudaEventDestroy(P->ev_fork);
     if (P->ev_join) cudaEventDestroy(P->ev_join);
