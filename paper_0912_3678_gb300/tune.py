@@ -170,7 +170,9 @@ class Tuner:
         trials = []
 
         def run(t):
-            ms = self.time_setting(m, N, prec, nrhs, t, reps, data)
+            # every candidate as the bench runs a step: one replay of the captured
+            # factor + solve (+ 2 refinement corrections) graph, from a cold L2
+            ms = self.time_captured(m, N, prec, nrhs, t, reps, data)
             trials.append((ms, dict(t)))
             return ms
 
