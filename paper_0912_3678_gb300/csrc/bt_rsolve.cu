@@ -630,11 +630,17 @@ __device__ __forceinline__ bool rf_inverse(float (&a)[M * M / 32], float (&b)[M 
                 b[w] *= inv;
             }
         } else {
+            // paired FMAs (FFMA2), each component the scalar fmaf
             const float f = ark * inv;
+            const float2 nf = make_float2(-f, -f);
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                a[w] = fmaf(-f, pa[w], a[w]);
-                b[w] = fmaf(-f, pb[w], b[w]);
+            for (int w = 0; w < W; w += 2) {
+                const float2 ta = __ffma2_rn(nf, make_float2(pa[w], pa[w + 1]), make_float2(a[w], a[w + 1]));
+                const float2 tb = __ffma2_rn(nf, make_float2(pb[w], pb[w + 1]), make_float2(b[w], b[w + 1]));
+                a[w] = ta.x;
+                a[w + 1] = ta.y;
+                b[w] = tb.x;
+                b[w + 1] = tb.y;
             }
         }
         __syncwarp();
@@ -648,18 +654,22 @@ template <int M>
 __device__ __forceinline__ void rf_row_part(float (&out)[M * M / 32], const float (&x)[M], const float* S, int h,
                                             float sgn) {
     constexpr int W = M * M / 32;
-    float acc[W];
+    float2 acc[W / 2];
 #pragma unroll
-    for (int w = 0; w < W; ++w) acc[w] = 0.f;
+    for (int w = 0; w < W / 2; ++w) acc[w] = make_float2(0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < M; ++k) {
         float srow[W];
         rf_lds<W>(srow, S + k * M + W * h);
+        const float2 xk = make_float2(x[k], x[k]);
 #pragma unroll
-        for (int w = 0; w < W; ++w) acc[w] = fmaf(x[k], srow[w], acc[w]);
+        for (int w = 0; w < W / 2; ++w) acc[w] = __ffma2_rn(xk, make_float2(srow[2 * w], srow[2 * w + 1]), acc[w]);
     }
 #pragma unroll
-    for (int w = 0; w < W; ++w) out[w] = sgn * acc[w];
+    for (int w = 0; w < W / 2; ++w) {
+        out[2 * w] = sgn * acc[w].x;
+        out[2 * w + 1] = sgn * acc[w].y;
+    }
 }
 
 template <int M, int NT>
