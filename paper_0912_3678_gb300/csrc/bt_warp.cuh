@@ -524,7 +524,7 @@ __device__ __forceinline__ void solve_fwd_w16_body(const LevelArgs& a, const lon
         issue(t + S - 1);    // into the slot row t - 1 used
         float t4[NH];
 #pragma unroll
-        for (int q = 0; q < NH; ++q) t4[q] = (cb + q < nr) ? trunc_f32(sm.sV[b][r * nr + cb + q]) : 0.f;
+        for (int q = 0; q < NH; ++q) t4[q] = (cb + q < nr) ? __double2float_rz(sm.sV[b][r * nr + cb + q]) : 0.f;
         if (j > pt.s) {
             // t = f_j - B_j h_{j-1}  (h_{j-1} in xb)
             float Br[16];
