@@ -92,6 +92,10 @@ def _workload(name: str, m_opt=None, N_opt=None, nr_opt=None):
 # capture of that launch in the same configuration (workload, path, kernel,
 # level-0 partitions): profiles/factor_cta_fp64_m16_block16.md.  Any other
 # configuration reports null; an entry is dropped when its kernel changes.
+# Estimated forward-error target of the refined paths' stopping test (the metric
+# asks for 1e-10 against FP64; the result is also checked against the oracle).
+FWD_TARGET = 1e-11
+
 MEASURED_TRAFFIC = {
     ("block16", "fp64", "factor", 608): 150.0e6,
     # the split-copy residual's traffic does not depend on the partitioning (any p0)
@@ -718,6 +722,11 @@ def _measure(args, dist, ws, rank, local):
             plan = Plan(N, m, nrhs_max=nr, prec=prec)
 
         sweeps = [0]
+        if prec != "fp64":
+            # the metric's accuracy (1e-10 against FP64) as the refinement's target: stop
+            # on the correction-ratio forward-error estimate 10 times below it, or on the
+            # FP64-level backward error, whichever comes first
+            plan.set_forward_tol(FWD_TARGET)
 
         def step_plain():
             plan.factor(*mats)
@@ -955,7 +964,10 @@ def _measure(args, dist, ws, rank, local):
                    "parallelism": f"replicas x{ws}", "levels": r["levels"],
                    "tuning": tunings.get(head, "built-in"),
                    "launch": "one CUDA graph per step" if r["graph"] else "kernel by kernel",
-                   "refinement_sweeps": r["sweeps"] if head != "fp64" else 0},
+                   "refinement_sweeps": r["sweeps"] if head != "fp64" else 0,
+                   "refinement_stop": (None if head == "fp64" else
+                                       f"estimated forward error <= {FWD_TARGET:g} (correction ratio) or "
+                                       "backward error <= 4(3m+1)u, checked on the captured step")},
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": ws * w["unknowns"] / (r["e2e_ms"] / 1e3), "unit": UNIT, "h2d_bytes_per_step": r["h2d"],

@@ -237,6 +237,20 @@ bt_status bt_refine_result(bt_plan plan, double tol, double* relcorr_out);
  * threshold or the last correction is below tol. */
 bt_status bt_plan_set_backward_tol(bt_plan plan, double eta_tol);
 
+/* Forward-error target of the refinement stopping test, an option of the
+ * mixed-precision refinement (the paper's method has no refinement step;
+ * default: not used).  With fwd_tol > 0, bt_refine also stops, and
+ * bt_refine_result also accepts, when after k >= 1 corrections the estimated
+ * relative forward error of X,
+ *   rho / (1 - rho) * ||D_k||_F / ||X||_F,  rho = ||D_k||_F / ||D_(k-1)||_F,
+ * (D_0 = the first solve, taken as ||X||_F), is <= fwd_tol: the error bound
+ * of a linearly converging refinement with contraction rho, the correction
+ * ratio test of Demmel, Hida, Kahan, Li, Mukherjee and Riedy (2006).  No
+ * estimate (never stops on it) while rho >= 1/2.  An estimate, not a bound:
+ * the backward-error test above stays the certificate.  fwd_tol <= 0 turns
+ * the option off; BT_ERR_INVALID for a NaN. */
+bt_status bt_plan_set_forward_tol(bt_plan plan, double fwd_tol);
+
 /* Breakdown threshold tau of a plan created with bt_tuning.pivot = 1
  * (0 <= tau < 1; default 1e-3): larger values split partitions more often
  * (more separators, smaller multipliers).  Takes effect at the next

@@ -22,7 +22,7 @@ __all__ = ["BtPlan", "AbdPlan", "PbtPlan", "BtError", "BT_STATUS", "PREC", "load
            "bt_batch_create", "bt_batch_run", "bt_batch_finish", "bt_batch_info", "bt_batch_destroy",
            "BtBatch", "CycPlan", "cyc_plan_create", "cyc_factor", "cyc_solve", "cyc_residual", "cyc_refine",
            "BtTuning", "BtBatchDesc", "bt_refine_async", "bt_refine_result",
-           "bt_plan_workspace_size", "bt_plan_anorm", "bt_plan_set_pivot_tol", "ivp_parareal", "ivp_bvm", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay", "bt_factor_solve_host", "bt_plan_capture_host",
+           "bt_plan_workspace_size", "bt_plan_anorm", "bt_plan_set_pivot_tol", "bt_plan_set_backward_tol", "bt_plan_set_forward_tol", "ivp_parareal", "ivp_bvm", "bt_plan_create_in", "bt_plan_capture", "bt_plan_replay", "bt_factor_solve_host", "bt_plan_capture_host",
            "abd_plan_create_tuned",
            "bt_band_to_blocks", "band_to_blocks", "bt_device_rcp", "bt_reduced_export", "bt_plan_destroy", "bt_status_string",
            "abd_plan_create", "abd_factor", "abd_solve", "abd_residual", "abd_refine", "abd_sync",
@@ -307,6 +307,15 @@ class PbtPlan:
 
 def bt_plan_set_pivot_tol(plan, tau: float):
     _lib.check(_lib.load().bt_plan_set_pivot_tol(plan, float(tau)), "bt_plan_set_pivot_tol")
+
+
+def bt_plan_set_backward_tol(plan, eta_tol: float):
+    _lib.check(_lib.load().bt_plan_set_backward_tol(plan, float(eta_tol)), "bt_plan_set_backward_tol")
+
+
+def bt_plan_set_forward_tol(plan, fwd_tol: float):
+    """Estimated forward-error target of the refinement stopping test (<= 0: off)."""
+    _lib.check(_lib.load().bt_plan_set_forward_tol(plan, float(fwd_tol)), "bt_plan_set_forward_tol")
 
 
 def bt_plan_anorm(plan) -> float:
@@ -611,6 +620,10 @@ class BtPlan(_PlanBase):
 
     def anorm(self) -> float:
         return bt_plan_anorm(self.handle)
+
+    def set_forward_tol(self, fwd_tol: float):
+        """Estimated forward-error target of the refinement stopping test (<= 0: off)."""
+        bt_plan_set_forward_tol(self.handle, fwd_tol)
 
     def reduced(self):
         """Top-level reduced matrix (alpha, beta, gamma) of Eq. (redmatr); with

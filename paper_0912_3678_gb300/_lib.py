@@ -80,6 +80,7 @@ SIGNATURES.update({
     "bt_device_rcp": (_i32, [_i64, _vp, _vp, _vp]),
     "bt_refine_result": (_i32, [_vp, _f64, _pf64]),
     "bt_plan_set_backward_tol": (_i32, [_vp, _f64]),
+    "bt_plan_set_forward_tol": (_i32, [_vp, _f64]),
     "bt_plan_anorm": (_i32, [_vp, _vp]),
     "bt_plan_set_pivot_tol": (_i32, [_vp, _f64]),
     "cyc_plan_create": (_i32, [_pvp, _i64, _i32, _i32, _i32, _i64, _vp]),

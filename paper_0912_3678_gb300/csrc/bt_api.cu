@@ -23,7 +23,8 @@ using bt::LevelArgs;
 
 constexpr int kNrhsMax = 32;
 constexpr int kSlotWords = 3 * bt::kMaxSlots;        // words of one maxima slot array
-constexpr int kHostNorms = 2 + 2 * kSlotWords;       // pinned host copy: norms, rmax, amax
+constexpr int kNormWords = 4;                        // ||d||^2, ||x||^2 of the last correction and of the one before
+constexpr int kHostNorms = kNormWords + 2 * kSlotWords;   // pinned host copy: norms, rmax, amax
 
 struct Level {
     LevelArgs a;
@@ -58,7 +59,8 @@ struct bt_plan_s {
     bool pinned = true;
     long long* status = nullptr;
     long long* status_host = nullptr;   // pinned
-    double* norms = nullptr;            // [2] ||d||^2, ||x||^2 of the last correction
+    double* norms = nullptr;            // [4] ||d||^2, ||x||^2 of the last correction, then of the one
+                                        // before it (NaN: none)
     double* norms_host = nullptr;       // pinned: [2] norms, then the rmax and amax slots
     unsigned long long* rmax = nullptr; // [kMaxSlots][3] max |r|, |x|, |f| of the last residual (bit patterns)
     unsigned long long* amax = nullptr; // [kMaxSlots][3] ||A||_inf (bit pattern) in word 0
@@ -66,6 +68,7 @@ struct bt_plan_s {
     bool anorm_fac = false;             // ||A||_inf was taken by the last level-0 factorization
     int async_sweeps = 0;
     double eta_tol = -1.0;              // backward-error stopping threshold (< 0: default)
+    double fwd_tol = -1.0;              // estimated forward-error stopping threshold (<= 0: not used)
     double* partial = nullptr;          // [2*1024]
     double* Rbuf = nullptr;
     double* Dbuf = nullptr;
@@ -178,7 +181,7 @@ void layout(bt_plan_s* P, Arena& ar) {
     const long long mm = (long long)m * m;
     const int nr = P->nrhs_max;
     P->status = (long long*)ar.take(4 * sizeof(long long));
-    P->norms = (double*)ar.take(2 * sizeof(double));
+    P->norms = (double*)ar.take(kNormWords * sizeof(double));
     P->rmax = (unsigned long long*)ar.take(kSlotWords * sizeof(unsigned long long));
     P->amax = (unsigned long long*)ar.take(kSlotWords * sizeof(unsigned long long));
     P->partial = (double*)ar.take(2 * 1024 * sizeof(double));
@@ -994,12 +997,13 @@ double eta_threshold(const bt_plan_s* P) {
 
 // Copy the correction norms (2) and the residual and ||A||_inf slots to the host (async).
 cudaError_t fetch_norms(bt_plan_s* P) {
-    cudaError_t e = cudaMemcpyAsync(P->norms_host, P->norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, P->stream);
+    cudaError_t e = cudaMemcpyAsync(P->norms_host, P->norms, kNormWords * sizeof(double), cudaMemcpyDeviceToHost,
+                                    P->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(P->norms_host + 2, P->rmax, kSlotWords * sizeof(double), cudaMemcpyDeviceToHost,
+        e = cudaMemcpyAsync(P->norms_host + kNormWords, P->rmax, kSlotWords * sizeof(double), cudaMemcpyDeviceToHost,
                             P->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(P->norms_host + 2 + kSlotWords, P->amax, kSlotWords * sizeof(double),
+        e = cudaMemcpyAsync(P->norms_host + kNormWords + kSlotWords, P->amax, kSlotWords * sizeof(double),
                             cudaMemcpyDeviceToHost, P->stream);
     return e;
 }
@@ -1013,8 +1017,8 @@ double slot_max(const double* slots, int w) {
 
 // Normwise backward error ||r||_inf / (||A||_inf ||x||_inf + ||f||_inf) from the host copies.
 double backward_error(const bt_plan_s* P) {
-    const double* rs = P->norms_host + 2;
-    const double* as = P->norms_host + 2 + kSlotWords;
+    const double* rs = P->norms_host + kNormWords;
+    const double* as = P->norms_host + kNormWords + kSlotWords;
     const double rm = slot_max(rs, 0), xm = slot_max(rs, 1), fm = slot_max(rs, 2), am = slot_max(as, 0);
     const double den = am * xm + fm;
     return den > 0.0 ? rm / den : (rm > 0.0 ? INFINITY : 0.0);
@@ -1024,8 +1028,14 @@ double backward_error(const bt_plan_s* P) {
 // and (||d||^2, ||x||^2) in P->norms.  With the warp kernels at level 0 the
 // back substitution applies the update itself and leaves per-partition norm
 // partials; otherwise d goes through Dbuf and the update kernel.
-bt_status run_correction(bt_plan_s* P, double* X, int nr, long long n) {
+bt_status run_correction(bt_plan_s* P, double* X, int nr, long long n, bool first) {
     Level& v0 = P->lv[0];
+    if (!first) {
+        // the norms of the correction before this one, for the forward-error estimate
+        cudaError_t e = cudaMemcpyAsync(P->norms + 2, P->norms, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                        P->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
     const bool w = P->warp && P->nlev >= 1 && P->L->warp_ok && P->L->warp_ok(v0.a, v0.low) && v0.a.nrm;
     if (w) {
         v0.a.accum = 1;
@@ -1043,6 +1053,29 @@ bt_status run_correction(bt_plan_s* P, double* X, int nr, long long n) {
     return from_cuda(e);
 }
 
+// Estimated relative forward error of the current iterate x_k after k >= 1
+// corrections, from the last two corrections under linear convergence:
+// ||x_k - x*|| <= rho / (1 - rho) ||d_k|| with the contraction ratio
+// rho = ||d_k|| / ||d_(k-1)|| (d_0 = x_0, taken as ||x_k||: they differ by
+// ||d_1||), the error estimate of refinement by correction ratios (Demmel,
+// Hida, Kahan, Li, Mukherjee and Riedy 2006).  +inf without a clear
+// contraction (rho >= 1/2) or without norms.
+double forward_estimate(const bt_plan_s* P) {
+    const double dd = P->norms_host[0], xx = P->norms_host[1], dp = P->norms_host[2];
+    if (!(xx > 0.0) || !(dd >= 0.0)) return INFINITY;
+    const double rel = std::sqrt(dd / xx);
+    const double rho = std::isnan(dp) ? rel : ((dp > 0.0) ? std::sqrt(dd / dp) : INFINITY);
+    if (!(rho < 0.5)) return INFINITY;
+    return rho / (1.0 - rho) * rel;
+}
+
+// The norms of the last and the previous correction: zero and none.
+cudaError_t reset_norms(bt_plan_s* P) {
+    cudaError_t e = cudaMemsetAsync(P->norms, 0, 2 * sizeof(double), P->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(P->norms + 2, 0xff, 2 * sizeof(double), P->stream);   // NaN
+    return e;
+}
+
 bt_status run_refine(bt_plan_s* P, const double* F, double* X, int nr, double tol, int maxit, int* iters,
                      double* relcorr) {
     // x = solve(f); then repeat: r = f - A x (FP64); stop when the normwise
@@ -1055,7 +1088,7 @@ bt_status run_refine(bt_plan_s* P, const double* F, double* X, int nr, double to
     if (st != BT_OK) return st;
     const long long n = P->lv[0].rows * P->m * nr;
     const double eta_tol = eta_threshold(P);
-    cudaError_t e = cudaMemsetAsync(P->norms, 0, 2 * sizeof(double), P->stream);
+    cudaError_t e = reset_norms(P);
     if (e != cudaSuccess) return from_cuda(e);
     for (int it = 0;; ++it) {
         st = run_residual(P, F, X, P->Rbuf, nr, P->rmax, P->prec != BT_FP64);
@@ -1072,8 +1105,9 @@ bt_status run_refine(bt_plan_s* P, const double* F, double* X, int nr, double to
         if (!std::isfinite(eta) || (it > 0 && !std::isfinite(rel))) return BT_ERR_NONFINITE;
         if (eta <= eta_tol) return BT_OK;
         if (it > 0 && rel <= tol) return BT_OK;
+        if (it > 0 && P->fwd_tol > 0.0 && forward_estimate(P) <= P->fwd_tol) return BT_OK;
         if (it == maxit) return BT_ERR_NOT_CONVERGED;
-        st = run_correction(P, X, nr, n);
+        st = run_correction(P, X, nr, n, it == 0);
         if (st != BT_OK) return st;
     }
 }
@@ -1083,14 +1117,14 @@ bt_status run_refine_async(bt_plan_s* P, const double* F, double* X, int nr, int
     bt_status st = ensure_anorm(P, false);
     if (st == BT_OK) st = run_solve(P, F, X, nr);
     const long long n = P->lv[0].rows * P->m * nr;
+    if (st == BT_OK) {
+        cudaError_t e = reset_norms(P);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
     for (int it = 0; it < sweeps && st == BT_OK; ++it) {
         st = run_residual(P, F, X, P->Rbuf, nr, nullptr, P->prec != BT_FP64);
-        if (st == BT_OK) st = run_correction(P, X, nr, n);
+        if (st == BT_OK) st = run_correction(P, X, nr, n, it == 0);
         if (st != BT_OK) return st;
-    }
-    if (sweeps == 0) {
-        cudaError_t e = cudaMemsetAsync(P->norms, 0, 2 * sizeof(double), P->stream);
-        if (e != cudaSuccess) return from_cuda(e);
     }
     if (st == BT_OK && P->x_event) {
         // X is final: the host-array path copies it out beside the checking residual
@@ -1396,6 +1430,7 @@ bt_status bt_refine_result(bt_plan P, double tol, double* relcorr_out) {
     if (!std::isfinite(eta)) return BT_ERR_NONFINITE;
     if (eta <= eta_threshold(P)) return BT_OK;
     if (P->async_sweeps > 0 && std::isfinite(rel) && rel <= tol) return BT_OK;
+    if (P->async_sweeps > 0 && P->fwd_tol > 0.0 && forward_estimate(P) <= P->fwd_tol) return BT_OK;
     return BT_ERR_NOT_CONVERGED;
 }
 
@@ -1408,7 +1443,7 @@ bt_status bt_plan_anorm(bt_plan P, double* anorm_out) {
     if (e != cudaSuccess) return from_cuda(e);
     st = read_status(P);
     if (st != BT_OK) return st;
-    *anorm_out = slot_max(P->norms_host + 2 + kSlotWords, 0);
+    *anorm_out = slot_max(P->norms_host + kNormWords + kSlotWords, 0);
     return BT_OK;
 }
 
@@ -1421,6 +1456,12 @@ bt_status bt_plan_set_pivot_tol(bt_plan P, double tau) {
 bt_status bt_plan_set_backward_tol(bt_plan P, double eta_tol) {
     if (!P) return BT_ERR_INVALID;
     P->eta_tol = eta_tol;
+    return BT_OK;
+}
+
+bt_status bt_plan_set_forward_tol(bt_plan P, double fwd_tol) {
+    if (!P || std::isnan(fwd_tol)) return BT_ERR_INVALID;
+    P->fwd_tol = fwd_tol;
     return BT_OK;
 }
 

@@ -356,6 +356,43 @@ def test_refinement_stops_on_backward_error(cuda):
         assert code == 0 and it == 0       # the FP64 solve is already backward stable
 
 
+def test_forward_tol_stops_on_the_correction_ratio(cuda):
+    """bt_plan_set_forward_tol: with the backward-error test switched off
+    (threshold 0) and the correction test out of reach, the refinement stops
+    once rho/(1-rho) ||d_k||/||x|| (rho = ||d_k||/||d_(k-1)||, d_0 = x_0) is below
+    the target; the result's error against the oracle is within 10 times the
+    estimate and below the target.  The async form with the same number of
+    corrections is accepted by bt_refine_result, and is not without the option."""
+    import torch
+
+    import paper_0912_3678_gb300 as bt
+    N, m, nr = 4096, 16, 8
+    s = gen.btri_random(N, m, nr, seed_rep=29)
+    ref = oracle.btri_solve(s.B, s.D, s.C, s.F)
+    B, D, C, F = (to_dev(a, cuda) for a in (s.B, s.D, s.C, s.F))
+    fwd = 1e-11
+    with bt.BtPlan(N, m, nr, prec="fp32_ir") as plan:
+        plan.factor(B, D, C)
+        bt.bt_plan_set_backward_tol(plan.handle, 0.0)
+        plan.set_forward_tol(fwd)
+        X, it, rc, code = plan.refine(F, tol=1e-300)
+        assert code == 0 and it >= 1
+        err = oracle.rel_err(to_host(X), ref)
+        if it == 1:
+            est = rc * rc / (1.0 - rc)       # rho = ||d_1|| / ||x_0||, ||x_0|| ~ ||x||
+            assert est <= fwd and err <= 10 * est + 1e-15
+        assert err <= 10 * fwd
+        X2 = torch.empty_like(F)
+        bt.bt_refine_async(plan.handle, F, X2, nr, it)
+        code2, _ = bt.bt_refine_result(plan.handle, 1e-300)
+        assert code2 == 0
+        assert oracle.rel_err(to_host(X2), ref) <= 10 * fwd
+        plan.set_forward_tol(0.0)
+        bt.bt_refine_async(plan.handle, F, X2, nr, it)
+        code3, _ = bt.bt_refine_result(plan.handle, 1e-300)
+        assert bt.BT_STATUS[code3] == "BT_ERR_NOT_CONVERGED"
+
+
 @pytest.mark.parametrize("m", [1, 5, 16])
 def test_anorm_matches_numpy(cuda, m):
     """||A||_inf used by the stopping test (FP32 sums of truncated entries)
