@@ -575,6 +575,10 @@ class _PlanBase:
         nr = F.shape[1] if len(F.shape) == 2 else 1
         bt_plan_capture_host(self.handle, B, D, C, F, X, nr, sweeps)
 
+    def set_forward_tol(self, fwd_tol: float):
+        """Estimated forward-error target of the refinement stopping test (<= 0: off)."""
+        bt_plan_set_forward_tol(self.handle, fwd_tol)
+
 
 class BtPlan(_PlanBase):
     """Block tridiagonal plan: B_j x_{j-1} + D_j x_j + C_j x_{j+1} = f_j."""
@@ -620,10 +624,6 @@ class BtPlan(_PlanBase):
 
     def anorm(self) -> float:
         return bt_plan_anorm(self.handle)
-
-    def set_forward_tol(self, fwd_tol: float):
-        """Estimated forward-error target of the refinement stopping test (<= 0: off)."""
-        bt_plan_set_forward_tol(self.handle, fwd_tol)
 
     def reduced(self):
         """Top-level reduced matrix (alpha, beta, gamma) of Eq. (redmatr); with
