@@ -224,9 +224,13 @@ bt_status bt_refine(bt_plan plan, const double* F, double* X, int nrhs, double t
 /* Asynchronous refinement for schedulers that must not block: enqueue
  * X = solve(F) and exactly `sweeps` (0..30) corrections { R = F - A X (FP64);
  * D = solve(R); X += D } on the plan's stream, with no host synchronisation.
- * Works for block tridiagonal and BABD plans.  bt_refine_result later
- * synchronises and reports ||D||_F/||X||_F of the last correction: BT_OK if
- * it is <= tol, BT_ERR_NOT_CONVERGED otherwise (or a numerical status). */
+ * Works for block tridiagonal and BABD plans.  The sequence ends with a
+ * residual of the result.  bt_refine_result later synchronises and reports
+ * ||D||_F/||X||_F of the last correction: BT_OK if that residual's backward
+ * error is below the threshold (bt_plan_set_backward_tol), if the last
+ * correction is <= tol, or if the estimated forward error is below the
+ * target set by bt_plan_set_forward_tol; BT_ERR_NOT_CONVERGED otherwise (or
+ * a numerical status). */
 bt_status bt_refine_async(bt_plan plan, const double* F, double* X, int nrhs, int sweeps);
 bt_status bt_refine_result(bt_plan plan, double tol, double* relcorr_out);
 

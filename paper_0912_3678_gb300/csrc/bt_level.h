@@ -54,8 +54,10 @@ struct LevelArgs {
     void* W;
     void* Hv;
     void* Hw;
-    // the level matrix split into FP32 pairs (hi, lo) for the double-float
-    // refinement residual: float2 [3][rows][m][m] (B, D, C); null: not kept
+    // the level matrix split into FP32 (hi, lo) parts for the double-float
+    // refinement residual and the warp forward solve, negated, by column pairs:
+    // float4 (-hi_k, -hi_k+1, -lo_k, -lo_k+1), k even, [3][rows][m][m/2]
+    // (B, D, C; the same bytes as float2 [3][rows][m][m]); null: not kept
     void* As;
     // warp kernels: ||A||_inf maxima slots filled by the factorization (null: not
     // computed there); back substitution in update form X += d with per-partition

@@ -52,8 +52,9 @@ size_t resid_df_smem(int kind, int m, int nr);
 cudaError_t launch_resid_btri_df(long long N, int m, int nr, const double* B, const double* D, const double* C,
                                  const double* X, const double* F, double* R, cudaStream_t s,
                                  unsigned long long* maxout = nullptr);
-// The same residual for order 16 with the matrix kept as FP32 pairs float2 [3][N][16][16]
-// (B, D, C; written by the warp-per-partition factorization).
+// The same residual for order 16 with the matrix kept as the warp-per-partition
+// factorization's split copy (B, D, C as negated FP32 (hi, lo) parts by column
+// pairs, the bytes of float2 [3][N][16][16]).
 // The same residual with the products on the tensor cores (block tridiagonal,
 // m = 16, nr <= 8; cudaErrorInvalidValue otherwise): Ozaki splitting into
 // 8-bit digit planes, BF16 mma.sync with FP32 accumulation, double-float

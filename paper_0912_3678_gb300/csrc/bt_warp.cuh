@@ -22,7 +22,11 @@
 // Pf = sum_j W_j Zc_j, W_{j+1} = -W_j Y_j, Qf = W_e, fused with the next
 // row's Schur product (both read the rows of Y_{j-1} and Zc_{j-1} once).
 // Input block rows (FP64) are staged into shared memory with cp.async,
-// one row ahead, and converted to FP32 by integer operations.
+// one row ahead, and converted to FP32 by integer operations; the block
+// products and the elimination updates run on paired FP32 FMAs (FFMA2).  The
+// factorization also leaves the split copy of the matrix for the refinement
+// residual and the forward solve: negated FP32 (hi, lo) parts by column
+// pairs, (-hi_k, -hi_k+1, -lo_k, -lo_k+1) for even k, 16 bytes.
 #pragma once
 #include "bt_bcr.cuh"
 #include "bt_misc.h"
