@@ -171,8 +171,12 @@ class Tuner:
 
         def run(t):
             # every candidate as the bench runs a step: one replay of the captured
-            # factor + solve (+ 2 refinement corrections) graph, from a cold L2
-            ms = self.time_captured(m, N, prec, nrhs, t, reps, data)
+            # factor + solve (+ 2 refinement corrections) graph, from a cold L2; a
+            # setting whose step cannot be captured is timed call by call
+            try:
+                ms = self.time_captured(m, N, prec, nrhs, t, reps, data)
+            except Exception:
+                ms = self.time_setting(m, N, prec, nrhs, t, reps, data)
             trials.append((ms, dict(t)))
             return ms
 
